@@ -1,0 +1,237 @@
+/*
+ * tsdfs.h -- C ABI of the GB300 (sm_103a) TSDF-Sampling library.
+ *
+ * TSDF-Sampling (arXiv 2311.17878) renders a neural surface field with few
+ * samples per ray: a TSDF volume fused from depth maps (Sec. 3.2, Eq. 3,
+ * Alg. 2) bounds each novel-view ray to an interval [t_n, t_f] around its first
+ * surface (Sec. 3.3, Alg. 1); the number of samples follows the interval
+ * length (Sec. 3.4); the SDF and colour networks run only there and are
+ * volume rendered (Eq. 1, Eq. 2, the rendered normal of Sec. C.1).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named in a struct or argument are DEVICE pointers unless the
+ *    comment says "host".  The caller owns every buffer; the library
+ *    allocates and frees nothing (no cudaMalloc / cudaFree anywhere).
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL = the
+ *    legacy default stream).  Arguments are checked on the host before any
+ *    launch; a check failure returns a negative TSDFS_E_* code, enqueues
+ *    nothing and records a message for tsdfs_last_error().
+ *  - Kernels never trap.  Conditions that only the device can see (a sample
+ *    total above the workspace capacity, a march exceeding its step cap) set
+ *    a bit in a device status word, read back by tsdfs_sync_status().
+ *  - Arrays are row-major; xyz triples are interleaved ([n][3]); grids are
+ *    x-fastest ([nz][ny][nx]).  Ray directions must be unit length (Alg. 1:
+ *    "ray (unit direction vector)").
+ */
+#ifndef TSDFS_H
+#define TSDFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* tsdfs_stream_t; /* identical to cudaStream_t */
+
+/* ---- return codes ------------------------------------------------------- */
+#define TSDFS_OK 0
+#define TSDFS_E_INVALID (-1)     /* bad argument: null pointer, size, parameter  */
+#define TSDFS_E_CUDA (-2)        /* a CUDA runtime call failed                   */
+#define TSDFS_E_WORKSPACE (-3)   /* workspace smaller than the *_workspace_size  */
+#define TSDFS_E_UNSUPPORTED (-4) /* architecture / precision combination         */
+#define TSDFS_E_DEVICE (-5)      /* tsdfs_sync_status: a device-side check fired */
+
+/* device status bits reported by tsdfs_sync_status() */
+#define TSDFS_DEV_SAMPLES_OVERFLOW 1u /* offsets[n_rays] exceeded max_samples   */
+#define TSDFS_DEV_MARCH_CAP 2u        /* a ray hit the voxel-step cap            */
+
+/* ---- TSDF grid (Sec. 3.2; Sec. A.1: V initialised to -1 = unseen, W to 0) -
+ * tsdf holds s / D_T in [-1, 1] (normalised truncated signed distance), as
+ * float (TSDFS_F32) or IEEE half (TSDFS_F16); weight counts fused
+ * observations, saturating at 255.  Voxel (i, j, k) covers
+ * origin + [i, i+1) x [j, j+1) x [k, k+1) * voxel_size; its centre is at
+ * origin + (i + 1/2, j + 1/2, k + 1/2) * voxel_size.                         */
+#define TSDFS_F32 0
+#define TSDFS_F16 1
+typedef struct {
+    int32_t nx, ny, nz;
+    float origin[3];   /* metres, min corner of voxel (0, 0, 0)          */
+    float voxel_size;  /* metres                                           */
+    float trunc;       /* D_T, metres (Eq. 3)                              */
+    int32_t dtype;     /* TSDFS_F32 | TSDFS_F16                            */
+    void* tsdf;        /* device, nz*ny*nx values                          */
+    uint8_t* weight;   /* device, nz*ny*nx                                 */
+} tsdfs_grid;
+
+/* ---- Alg. 1 / Sec. 3.4 parameters ---------------------------------------- */
+typedef struct {
+    float d_s;          /* D_s, surface criterion, metres (Alg. 1)                   */
+    float t_near;       /* start of the original ray range                           */
+    float t_far;        /* original far bound t_f of Alg. 1                           */
+    float step;         /* sample spacing (metres) of the adaptive count, Sec. 3.4   */
+    int32_t nb_radius;  /* neighbourhood radius: 2 -> 5x5x5 (Sec. 4.2)               */
+    int32_t m_confirm;  /* M: consecutive inside voxels before t_f (Sec. 4.2: 15)    */
+    int32_t n_max;      /* cap of the adaptive count                                 */
+    int32_t n_fallback; /* samples over [t0, t_end] when no voxel passes V <= D_s    */
+} tsdfs_bounds_params;
+
+/* per-ray status written by tsdf_ray_bounds */
+#define TSDFS_MISS 0     /* the ray does not overlap the grid box within [t_near, t_far] */
+#define TSDFS_BOUNDED 1  /* [t_n, t_f] from Alg. 1                                       */
+#define TSDFS_FALLBACK 2 /* no surface voxel: [t0, t_end] with n_fallback samples        */
+
+/* ---- networks --------------------------------------------------------------
+ * SDF network: input gamma(x~), x~ = (x - center) / scale, gamma the
+ * positional encoding (x~, sin(2^k x~), cos(2^k x~)), k < L; hidden layers
+ * softplus_beta (linear where beta z > 20); linear output [net_0, feature];
+ * SDF f = scale * net_0; grad f = d net_0 / d x~.  The skip layer takes
+ * concat(h, gamma) / sqrt(2).  Colour network: input (x~, direction encoding,
+ * unit normal grad f / |grad f|, feature), ReLU hidden layers, sigmoid output.
+ *   TSDFS_ARCH_TINY: SDF 3-64-64-64-(1+16), colour 25-64-64-3, no encodings.
+ *   TSDFS_ARCH_ROOM: SDF 39-256-256-256-217, skip, 256-256-256-(1+256), L = 6;
+ *                    colour (3+27+3+256)-256-256-256-256-3, direction L = 4.
+ * Packed fp32 parameters (sdf_w, rgb_w): for each layer in order, W[out][in]
+ * row-major, then b[out].  Opacity (NeuS, the SDF-to-density transform of the
+ * backbone in Eq. 1): alpha = clamp((Phi(f-) - Phi(f+) + eps)/(Phi(f-) + eps),
+ * 0, 1), Phi(x) = sigmoid(inv_s x), f-/+ = f -/+ (delta/2) min(v . grad f, 0).  */
+#define TSDFS_ARCH_TINY 0
+#define TSDFS_ARCH_ROOM 1
+#define TSDFS_PREC_F32 0  /* FP32 SIMT networks                                  */
+#define TSDFS_PREC_BF16 1 /* BF16 tcgen05 networks, FP32 accumulate (packed required) */
+typedef struct {
+    int32_t arch;
+    int32_t precision;
+    const float* sdf_w;  /* device, packed fp32                                         */
+    const float* rgb_w;  /* device, packed fp32                                         */
+    const void* packed;  /* device, tsdfs_packed_size bytes from tsdfs_pack_mlp, or NULL */
+    float center[3];
+    float scale;
+    float inv_s;         /* s of Phi_s (64)                                             */
+    float beta;          /* softplus beta (100)                                         */
+    float alpha_eps;     /* eps of the opacity ratio (1e-5)                             */
+} tsdfs_mlp;
+
+/* ---- errors -------------------------------------------------------------- */
+/* Message of the last failing call on this host thread ("" if none). */
+const char* tsdfs_last_error(void);
+/* Synchronise `stream`, then read and clear the device status word.  Returns
+ * TSDFS_OK, TSDFS_E_DEVICE (bits in *bits_out when non-NULL) or TSDFS_E_CUDA. */
+int tsdfs_sync_status(tsdfs_stream_t stream, uint32_t* bits_out);
+
+/* ---- fusion (Sec. 3.2, Eq. 3, Alg. 2; Sec. A.1 initial values) -------------
+ * tsdfs_grid_init: V = -1 (unseen), W = 0 for every voxel.
+ * tsdf_integrate: per-voxel projective form of Alg. 2.  For each voxel centre
+ *   c and each view in order 0..n_views-1: x_cam = R^T (c - o); skip when
+ *   z <= 0; pixel (floor(fx x/z + cx), floor(fy y/z + cy)), skip when outside
+ *   the image; D = depth at that pixel (range along the unit ray through the
+ *   pixel centre; +inf = no surface); s = clamp(D - v_px . (c - o), -D_T, D_T);
+ *   when s > -D_T: V <- (W V + s/D_T)/(W + 1), W <- min(W + 1, 255).
+ *   depth: device [n_views][H][W] float; K: device [n_views][4] (fx, fy, cx,
+ *   cy); c2w: device [n_views][12], row-major 3x4 [R | o], OpenCV camera axes.
+ *   Runs in fp32 with round-to-nearest and no contraction, in the operation
+ *   order above, so results are reproducible bit for bit.  F16 grids are
+ *   widened, updated in fp32 across all views of the call and rounded once. */
+int tsdfs_grid_init(const tsdfs_grid* grid, tsdfs_stream_t stream);
+int tsdf_integrate(const tsdfs_grid* grid, const float* depth, int32_t n_views, int32_t height, int32_t width,
+                   const float* K, const float* c2w, tsdfs_stream_t stream);
+
+/* ---- far-phase neighbourhood test, precomputed (Alg. 1) ---------------------
+ * bit (k*ny + j)*nx + i of mask_bits (uint32 words, little bit order) is 1 iff
+ * every voxel within Chebyshev radius nb_radius of (i, j, k) has V < 0 (out of
+ * grid = unseen = -1).  mask_bits: device, tsdfs_inside_mask_words() words.
+ * Optional input of tsdf_ray_bounds; results are identical with or without. */
+int64_t tsdfs_inside_mask_words(const tsdfs_grid* grid);
+int tsdfs_inside_mask(const tsdfs_grid* grid, int32_t nb_radius, uint32_t* mask_bits, tsdfs_stream_t stream);
+
+/* ---- ray bounds (Alg. 1) and adaptive count (Sec. 3.4) ----------------------
+ * Per ray: [t0, t_end] = [t_near, t_far] clipped to the grid box (MISS if
+ * empty).  Voxel walk from t0 (crossing parameters recomputed from integer
+ * boundaries, ties x < y < z).  Near phase: first voxel X with
+ * V(centre X) <= d_s / D_T gives t_n = its entry parameter; none: FALLBACK.
+ * Far phase from the same X: m counts consecutive voxels whose neighbourhood
+ * is all negative; when m reaches m_confirm after a step, t_f = the entry of
+ * the next voxel (capped at t_end); else t_f = t_end.  Count n = clamp(ceil(
+ * (t_f - t_n)/step), 1, n_max); FALLBACK: t_n = t0, t_f = t_end, n =
+ * n_fallback; MISS: n = 0, t_n = t_f = 0.  t_zero: first +/- sign change of
+ * the trilinear TSDF at the crossing points from the entry of the voxel before
+ * the near voxel to t_f, secant root; NaN if none or not BOUNDED.
+ * offsets[0..n_rays] = exclusive prefix sum of n (offsets[n_rays] = total).
+ * inside_mask: NULL or the output of tsdfs_inside_mask for p->nb_radius.
+ * t_zero may be NULL.  workspace: device, >= tsdfs_bounds_workspace_size.
+ * Integer results and t_n / t_f equal the fp32-exact reference bit for bit. */
+size_t tsdfs_bounds_workspace_size(int64_t n_rays);
+int tsdf_ray_bounds(const tsdfs_grid* grid, const uint32_t* inside_mask, const float* ray_o, const float* ray_d,
+                    int64_t n_rays, const tsdfs_bounds_params* p, float* t_n, float* t_f, int32_t* n_samples,
+                    int32_t* offsets, float* t_zero, uint8_t* status, void* workspace, size_t ws_bytes,
+                    tsdfs_stream_t stream);
+
+/* ---- render (Sec. 3.4 placement; Eq. 1, Eq. 2; rendered normal Sec. C.1) ----
+ * Ray r has offsets[r+1] - offsets[r] samples at the midpoints
+ * t_i = t_n + (i + 1/2)(t_f - t_n)/n of [t_n, t_f] (FALLBACK rays carry
+ * [t0, t_end] and n_fallback from tsdf_ray_bounds).  Per sample: SDF network
+ * value f, gradient, feature; colour network; NeuS opacity with section width
+ * (t_f - t_n)/n.  Compositing: log T_0 = 0, log T_{i+1} = log T_i +
+ * log1p(-min(alpha_i, 1 - 2^-24)), w_i = exp(log T_i) alpha_i; rgb = sum w c
+ * (black background); wsum = sum w; depth = sum w t / wsum and normal =
+ * sum w n / wsum (both 0 when wsum < 1e-8).  Rays with zero samples give 0.
+ * eik (nullable): per-ray sum over samples of (|grad f| - 1)^2, written only
+ * for BOUNDED rays (0 otherwise).  normal may be NULL.
+ * max_samples bounds offsets[n_rays]; workspace >= tsdfs_render_workspace_size.
+ * precision TSDFS_PREC_BF16 needs mlp->packed from tsdfs_pack_mlp.          */
+size_t tsdfs_render_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays, int64_t max_samples);
+int render_rays(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n, const float* t_f,
+                const int32_t* offsets, const uint8_t* status, int64_t n_rays, int64_t max_samples, float* rgb,
+                float* depth, float* wsum, float* normal, float* eik, void* workspace, size_t ws_bytes,
+                tsdfs_stream_t stream);
+
+/* ---- hierarchical comparator (64 coarse + 32 inverse-CDF fine, Tab. 2 "HS") -
+ * Per ray over [t0, t_end] (t_near/t_far clipped to the grid box of `grid`;
+ * only its geometry fields are read): 64 midpoints, SDF values only; section
+ * weights from the values (NeuS up-sampling opacity: slope min(own,
+ * previous), clipped to [-1e3, 0]); 32 inverse-CDF samples at u = (k+1/2)/32
+ * over pdf ~ w + 1e-5; all 96 sorted samples evaluated fully and composited
+ * with section boundaries halfway between neighbours.  Outputs as render_rays.
+ * workspace >= tsdfs_hier_workspace_size.                                    */
+size_t tsdfs_hier_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays);
+int render_rays_hier96(const tsdfs_mlp* mlp, const tsdfs_grid* grid, const float* ray_o, const float* ray_d,
+                       int64_t n_rays, float t_near, float t_far, float* rgb, float* depth, float* wsum,
+                       float* normal, void* workspace, size_t ws_bytes, tsdfs_stream_t stream);
+
+/* ---- backward of render_rays (training step of the networks) ---------------
+ * Gradients of L = sum(d_rgb . rgb) + sum(d_depth . depth) + d_eik * sum(eik)
+ * with respect to the packed fp32 parameters, ACCUMULATED (+=) into
+ * d_sdf_w / d_rgb_w (same layout as sdf_w / rgb_w; the caller zeroes them).
+ * Activations are recomputed, not stored.  d_depth may be NULL.  FP32 only.
+ * workspace >= tsdfs_backward_workspace_size.                                */
+size_t tsdfs_backward_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays, int64_t max_samples);
+int render_rays_backward(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
+                         const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
+                         int64_t max_samples, const float* d_rgb, const float* d_depth, float d_eik,
+                         float* d_sdf_w, float* d_rgb_w, void* workspace, size_t ws_bytes, tsdfs_stream_t stream);
+
+/* ---- BF16 tensor-core parameter layout --------------------------------------
+ * tsdfs_pack_mlp converts sdf_w / rgb_w to the bf16 K-major tiles the tcgen05
+ * path reads (rounded to nearest even), into `packed` (device,
+ * tsdfs_packed_size bytes).  Repeat after every parameter update.            */
+size_t tsdfs_packed_size(int32_t arch);
+int tsdfs_pack_mlp(const tsdfs_mlp* mlp, void* packed, tsdfs_stream_t stream);
+
+/* ---- kernel timing (instrumentation; no counterpart in the paper) ------------
+ * tsdfs_profile(1) clears the record and starts timing: every kernel launch
+ * of the library is then bracketed by two CUDA events recorded on its launch
+ * stream; tsdfs_profile(0) stops and clears.  tsdfs_profile_read synchronises
+ * the recorded events and returns, for launches whose kernel name starts with
+ * `prefix` ("" = all), the summed device time in ms and the launch count.   */
+int tsdfs_profile(int32_t enable);
+int tsdfs_profile_read(const char* prefix, double* total_ms, int64_t* launches);
+
+/* sizes of the packed fp32 parameter arrays, in floats */
+int64_t tsdfs_sdf_param_count(int32_t arch);
+int64_t tsdfs_rgb_param_count(int32_t arch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSDFS_H */

@@ -134,7 +134,7 @@ static void SFX(dda_init)(SFX(dda_t)* s, const R o[3], const R d[3], const R org
         s->inv[a] = d[a] != (R)0 ? (R)1 / d[a] : (R)INFINITY;
         R p = o[a] + t0 * d[a];
         R g = R_FLOOR((p - org[a]) / vs);
-        int X = g < (R)0 ? 0 : (g > (R)(n[a] - 1) ? n[a] - 1 : (int)g);
+        int X = g >= (R)0 ? (g > (R)(n[a] - 1) ? n[a] - 1 : (int)g) : 0;   /* NaN -> 0 */
         s->X[a] = X;
     }
 }
@@ -161,7 +161,7 @@ static R SFX(trilinear)(const void* V, int f16, const int n[3], const R org[3], 
         R g = (p[a] - org[a]) / vs - (R)0.5;
         R fl = R_FLOOR(g);
         fr[a] = g - fl;
-        if (fl < (R)-1) { fl = (R)-1; fr[a] = (R)1; }
+        if (!(fl >= (R)-1)) { fl = (R)-1; fr[a] = (R)1; }   /* also NaN */
         if (fl > (R)n[a]) { fl = (R)n[a]; fr[a] = (R)0; }
         i0[a] = (int)fl;
     }

@@ -1,0 +1,344 @@
+// C ABI entry points of the render path, error reporting and the device
+// status word.  Argument checks happen here, on the host, before any launch.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace tsdfs {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local char g_msg[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return TSDFS_OK;
+    return fail(TSDFS_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// one status word per device (a __device__ variable has one instance per
+// device context); its device address is looked up once per device
+static __device__ uint32_t g_status_word;
+static std::mutex g_status_mu;
+static uint32_t* g_status_addr[64] = {nullptr};
+
+uint32_t* device_status_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if (!g_status_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
+        g_status_addr[dev] = static_cast<uint32_t*>(p);
+    }
+    return g_status_addr[dev];
+}
+
+// ---------------------------------------------------------------------------
+// kernel timing
+// ---------------------------------------------------------------------------
+struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static ProfRec* g_prof = nullptr;
+static size_t g_prof_n = 0, g_prof_cap = 0;
+
+void prof_begin(const char* name, cudaStream_t st, void** token) {
+    *token = nullptr;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return;
+    if (g_prof_n == g_prof_cap) {
+        size_t cap = g_prof_cap ? 2 * g_prof_cap : 1024;
+        ProfRec* p = static_cast<ProfRec*>(realloc(g_prof, cap * sizeof(ProfRec)));
+        if (!p) return;
+        g_prof = p;
+        g_prof_cap = cap;
+    }
+    ProfRec& r = g_prof[g_prof_n];
+    if (cudaEventCreate(&r.a) != cudaSuccess) return;
+    if (cudaEventCreate(&r.b) != cudaSuccess) {
+        cudaEventDestroy(r.a);
+        return;
+    }
+    r.name = name;
+    cudaEventRecord(r.a, st);
+    *token = reinterpret_cast<void*>(g_prof_n + 1);
+    ++g_prof_n;
+}
+
+void prof_end(void* token, cudaStream_t st) {
+    if (!token) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    size_t i = reinterpret_cast<size_t>(token) - 1;
+    if (i < g_prof_n) cudaEventRecord(g_prof[i].b, st);
+}
+
+static void prof_clear() {
+    for (size_t i = 0; i < g_prof_n; ++i) {
+        cudaEventDestroy(g_prof[i].a);
+        cudaEventDestroy(g_prof[i].b);
+    }
+    g_prof_n = 0;
+}
+
+// ---------------------------------------------------------------------------
+// internal launchers (mlp_simt.cu, composite.cu, bounds.cu)
+// ---------------------------------------------------------------------------
+template <int ARCH>
+int launch_mlp_full_simt(const NetParams& np, const SampleSource& src, SampleRec* rec, int64_t max_samples, cudaStream_t st);
+template <int ARCH>
+int launch_mlp_value_simt(const NetParams& np, const SampleSource& src, float* f_out, cudaStream_t st);
+int launch_composite(const SampleRec* rec, const int32_t* offsets, int per_ray, const uint8_t* status, int64_t n_rays,
+                     const int32_t* total_dev, int64_t capacity, float inv_s, float eps, float* rgb, float* depth,
+                     float* wsum, float* normal, float* eik, cudaStream_t st);
+int launch_hier_setup(const tsdfs_grid* g, const float* ray_o, const float* ray_d, int64_t n_rays, float t_near,
+                      float t_far, float* t0, float* te, uint8_t* status, float* tc, float* dc, cudaStream_t st);
+int launch_hier_fine(const float* fcoarse, const float* tc, const float* t0, const float* te, int64_t n_rays,
+                     float inv_s, float eps, float* t_out, float* d_out, cudaStream_t st);
+int grid_check(const tsdfs_grid* g);
+int mlp_tc_available(int arch);
+int launch_mlp_full_tc(const tsdfs_mlp* mlp, const SampleSource& src, SampleRec* rec, int64_t max_samples,
+                       cudaStream_t st);
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static int mlp_check(const tsdfs_mlp* m) {
+    if (!m) return fail(TSDFS_E_INVALID, "mlp is NULL");
+    if (m->arch != TSDFS_ARCH_TINY && m->arch != TSDFS_ARCH_ROOM) return fail(TSDFS_E_INVALID, "unknown arch %d", m->arch);
+    if (m->precision != TSDFS_PREC_F32 && m->precision != TSDFS_PREC_BF16)
+        return fail(TSDFS_E_INVALID, "unknown precision %d", m->precision);
+    if (!m->sdf_w || !m->rgb_w) return fail(TSDFS_E_INVALID, "sdf_w and rgb_w must be non-NULL");
+    if (!(m->scale > 0.0f) || !(m->beta > 0.0f) || !(m->inv_s > 0.0f) || !(m->alpha_eps >= 0.0f))
+        return fail(TSDFS_E_INVALID, "scale, beta and inv_s must be > 0, alpha_eps >= 0");
+    if (m->precision == TSDFS_PREC_BF16) {
+        if (!m->packed) return fail(TSDFS_E_INVALID, "BF16 precision needs packed weights (tsdfs_pack_mlp)");
+        if (!mlp_tc_available(m->arch)) return fail(TSDFS_E_UNSUPPORTED, "BF16 tensor-core path not available for arch %d", m->arch);
+    }
+    return TSDFS_OK;
+}
+
+static NetParams net_params(const tsdfs_mlp* m) {
+    NetParams np;
+    np.sdf_w = m->sdf_w;
+    np.rgb_w = m->rgb_w;
+    for (int a = 0; a < 3; ++a) np.center[a] = m->center[a];
+    np.scale = m->scale;
+    np.inv_scale = 1.0f / m->scale;
+    np.beta = m->beta;
+    return np;
+}
+
+static int run_full_mlp(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64_t max_samples,
+                        cudaStream_t st) {
+    if (m->precision == TSDFS_PREC_BF16) {
+        ProfScope ps("mlp_tc", st);
+        return launch_mlp_full_tc(m, src, rec, max_samples, st);
+    }
+    ProfScope ps("mlp_simt", st);
+    const NetParams np = net_params(m);
+    return m->arch == TSDFS_ARCH_TINY ? launch_mlp_full_simt<TSDFS_ARCH_TINY>(np, src, rec, max_samples, st)
+                                      : launch_mlp_full_simt<TSDFS_ARCH_ROOM>(np, src, rec, max_samples, st);
+}
+
+}  // namespace tsdfs
+
+using namespace tsdfs;
+
+extern "C" const char* tsdfs_last_error(void) { return g_msg; }
+
+extern "C" int tsdfs_profile(int32_t enable) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_clear();
+    g_prof_on = enable != 0;
+    return TSDFS_OK;
+}
+
+extern "C" int tsdfs_profile_read(const char* prefix, double* total_ms, int64_t* launches) {
+    if (!total_ms || !launches) return fail(TSDFS_E_INVALID, "total_ms and launches must be non-NULL");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    double ms = 0.0;
+    int64_t n = 0;
+    const size_t plen = prefix ? strlen(prefix) : 0;
+    for (size_t i = 0; i < g_prof_n; ++i) {
+        if (plen && strncmp(g_prof[i].name, prefix, plen) != 0) continue;
+        int rc = cuda_check(cudaEventSynchronize(g_prof[i].b), "tsdfs_profile_read synchronize");
+        if (rc) return rc;
+        float e = 0.0f;
+        rc = cuda_check(cudaEventElapsedTime(&e, g_prof[i].a, g_prof[i].b), "tsdfs_profile_read elapsed");
+        if (rc) return rc;
+        ms += e;
+        ++n;
+    }
+    *total_ms = ms;
+    *launches = n;
+    return TSDFS_OK;
+}
+
+extern "C" int tsdfs_sync_status(tsdfs_stream_t stream, uint32_t* bits_out) {
+    int rc = cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "tsdfs_sync_status synchronize");
+    if (rc) return rc;
+    uint32_t bits = 0;
+    rc = cuda_check(cudaMemcpyFromSymbol(&bits, g_status_word, sizeof bits), "tsdfs_sync_status read");
+    if (rc) return rc;
+    const uint32_t zero = 0;
+    rc = cuda_check(cudaMemcpyToSymbol(g_status_word, &zero, sizeof zero), "tsdfs_sync_status clear");
+    if (rc) return rc;
+    if (bits_out) *bits_out = bits;
+    if (bits) return fail(TSDFS_E_DEVICE, "device status bits 0x%x", bits);
+    return TSDFS_OK;
+}
+
+extern "C" int64_t tsdfs_sdf_param_count(int32_t arch) {
+    return arch == TSDFS_ARCH_TINY ? sdf_param_count<TSDFS_ARCH_TINY>()
+                                   : (arch == TSDFS_ARCH_ROOM ? sdf_param_count<TSDFS_ARCH_ROOM>() : -1);
+}
+extern "C" int64_t tsdfs_rgb_param_count(int32_t arch) {
+    return arch == TSDFS_ARCH_TINY ? rgb_param_count<TSDFS_ARCH_TINY>()
+                                   : (arch == TSDFS_ARCH_ROOM ? rgb_param_count<TSDFS_ARCH_ROOM>() : -1);
+}
+
+extern "C" size_t tsdfs_render_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays, int64_t max_samples) {
+    (void)mlp;
+    (void)n_rays;
+    if (max_samples < 0) return 0;
+    return align256((size_t)max_samples * sizeof(SampleRec)) + 256;
+}
+
+extern "C" int render_rays(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
+                           const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
+                           int64_t max_samples, float* rgb, float* depth, float* wsum, float* normal, float* eik,
+                           void* ws, size_t ws_bytes, tsdfs_stream_t stream) {
+    int rc = mlp_check(mlp);
+    if (rc) return rc;
+    if (n_rays < 0 || max_samples < 0) return fail(TSDFS_E_INVALID, "n_rays and max_samples must be >= 0");
+    if (n_rays == 0) return TSDFS_OK;
+    if (!ray_o || !ray_d || !t_n || !t_f || !offsets || !status || !rgb || !depth || !wsum)
+        return fail(TSDFS_E_INVALID, "ray, bound and output pointers must be non-NULL (normal, eik may be NULL)");
+    if (max_samples > (int64_t)INT32_MAX) return fail(TSDFS_E_INVALID, "max_samples must fit int32 offsets");
+    if (!ws || ws_bytes < tsdfs_render_workspace_size(mlp, n_rays, max_samples))
+        return fail(TSDFS_E_WORKSPACE, "render workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    SampleRec* rec = reinterpret_cast<SampleRec*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
+    SampleSource src{};
+    src.mode = kUniform;
+    src.ray_o = ray_o;
+    src.ray_d = ray_d;
+    src.offsets = offsets;
+    src.t_n = t_n;
+    src.t_f = t_f;
+    src.n_rays = n_rays;
+    src.total_dev = offsets + n_rays;
+    src.capacity = max_samples;
+    if (max_samples > 0) {
+        rc = run_full_mlp(mlp, src, rec, max_samples, st);
+        if (rc) return rc;
+    }
+    ProfScope ps("composite", st);
+    return launch_composite(rec, offsets, 0, status, n_rays, offsets + n_rays, max_samples, mlp->inv_s, mlp->alpha_eps,
+                            rgb, depth, wsum, normal, eik, st);
+}
+
+// ---- hierarchical comparator ------------------------------------------------
+struct HierWs {
+    float *t0, *te, *tc, *dc, *fc, *tf, *df;
+    uint8_t* status;
+    SampleRec* rec;
+    size_t bytes;
+};
+
+static HierWs hier_layout(void* base, int64_t n) {
+    HierWs w{};
+    uintptr_t p = (reinterpret_cast<uintptr_t>(base) + 255) & ~uintptr_t(255);
+    auto take = [&](size_t bytes) {
+        uintptr_t q = p;
+        p = (p + bytes + 255) & ~uintptr_t(255);
+        return q;
+    };
+    w.rec = reinterpret_cast<SampleRec*>(take((size_t)n * 96 * sizeof(SampleRec)));
+    w.t0 = reinterpret_cast<float*>(take((size_t)n * 4));
+    w.te = reinterpret_cast<float*>(take((size_t)n * 4));
+    w.tc = reinterpret_cast<float*>(take((size_t)n * 64 * 4));
+    w.dc = reinterpret_cast<float*>(take((size_t)n * 64 * 4));
+    w.fc = reinterpret_cast<float*>(take((size_t)n * 64 * 4));
+    w.tf = reinterpret_cast<float*>(take((size_t)n * 96 * 4));
+    w.df = reinterpret_cast<float*>(take((size_t)n * 96 * 4));
+    w.status = reinterpret_cast<uint8_t*>(take((size_t)n));
+    w.bytes = p - reinterpret_cast<uintptr_t>(base) + 256;
+    return w;
+}
+
+extern "C" size_t tsdfs_hier_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays) {
+    (void)mlp;
+    if (n_rays < 0) return 0;
+    return hier_layout(nullptr, n_rays).bytes + 256;
+}
+
+extern "C" int render_rays_hier96(const tsdfs_mlp* mlp, const tsdfs_grid* grid, const float* ray_o,
+                                  const float* ray_d, int64_t n_rays, float t_near, float t_far, float* rgb,
+                                  float* depth, float* wsum, float* normal, void* ws, size_t ws_bytes,
+                                  tsdfs_stream_t stream) {
+    int rc = mlp_check(mlp);
+    if (rc) return rc;
+    if (!grid) return fail(TSDFS_E_INVALID, "grid is NULL");
+    if (grid->nx <= 0 || grid->ny <= 0 || grid->nz <= 0 || !(grid->voxel_size > 0.0f))
+        return fail(TSDFS_E_INVALID, "grid geometry invalid");
+    if (n_rays < 0) return fail(TSDFS_E_INVALID, "n_rays must be >= 0");
+    if (n_rays == 0) return TSDFS_OK;
+    if (n_rays * 96 > (int64_t)INT32_MAX) return fail(TSDFS_E_INVALID, "too many rays");
+    if (!ray_o || !ray_d || !rgb || !depth || !wsum) return fail(TSDFS_E_INVALID, "ray and output pointers must be non-NULL");
+    if (!(t_near < t_far)) return fail(TSDFS_E_INVALID, "t_near must be < t_far");
+    if (!ws || ws_bytes < tsdfs_hier_workspace_size(mlp, n_rays)) return fail(TSDFS_E_WORKSPACE, "hier workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    HierWs w = hier_layout(ws, n_rays);
+    {
+        ProfScope ps("hier_setup", st);
+        rc = launch_hier_setup(grid, ray_o, ray_d, n_rays, t_near, t_far, w.t0, w.te, w.status, w.tc, w.dc, st);
+    }
+    if (rc) return rc;
+    const NetParams np = net_params(mlp);
+    SampleSource cs{};
+    cs.mode = kExplicit;
+    cs.ray_o = ray_o;
+    cs.ray_d = ray_d;
+    cs.t = w.tc;
+    cs.delta = w.dc;
+    cs.per_ray = 64;
+    cs.total_host = n_rays * 64;
+    cs.capacity = n_rays * 64;
+    {
+        ProfScope ps("mlp_value_simt", st);
+        rc = mlp->arch == TSDFS_ARCH_TINY ? launch_mlp_value_simt<TSDFS_ARCH_TINY>(np, cs, w.fc, st)
+                                          : launch_mlp_value_simt<TSDFS_ARCH_ROOM>(np, cs, w.fc, st);
+    }
+    if (rc) return rc;
+    {
+        ProfScope ps("hier_fine", st);
+        rc = launch_hier_fine(w.fc, w.tc, w.t0, w.te, n_rays, mlp->inv_s, mlp->alpha_eps, w.tf, w.df, st);
+    }
+    if (rc) return rc;
+    SampleSource fs = cs;
+    fs.t = w.tf;
+    fs.delta = w.df;
+    fs.per_ray = 96;
+    fs.total_host = n_rays * 96;
+    fs.capacity = n_rays * 96;
+    rc = run_full_mlp(mlp, fs, w.rec, n_rays * 96, st);
+    if (rc) return rc;
+    ProfScope ps("composite", st);
+    return launch_composite(w.rec, nullptr, 96, w.status, n_rays, nullptr, n_rays * 96, mlp->inv_s, mlp->alpha_eps, rgb,
+                            depth, wsum, normal, nullptr, st);
+}

@@ -1,0 +1,368 @@
+// K3: TSDF sample bounds of Alg. 1 + the adaptive count of Sec. 3.4.
+// K4: exclusive scan of the counts into ragged offsets.
+//
+// One thread per ray; the voxel walk recomputes every crossing parameter from
+// its integer boundary, so the walk is exact to the voxel no matter how long.
+// fp32, round-to-nearest, no contraction (intrinsics + --fmad=false), in the
+// operation order of the oracle's fp32-exact mode, so t_n, t_f, counts and
+// status are identical bit for bit.
+#include "common.cuh"
+
+namespace tsdfs {
+int grid_check(const tsdfs_grid* g);
+
+namespace {
+
+constexpr int kBoundsBlock = 128;
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = kScanBlock * kScanItems;
+
+struct GridDev {
+    const void* V;
+    int f16;
+    int n[3];
+    float org[3];
+    float vs;
+    float trunc;
+};
+
+struct BoundsDev {
+    float d_s, t_near, t_far, step;
+    int nb_radius, m_confirm, n_max, n_fallback;
+};
+
+__device__ __forceinline__ float gval(const GridDev& g, int i, int j, int k) {
+    if (i < 0 || j < 0 || k < 0 || i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return -1.0f;
+    const int64_t idx = ((int64_t)k * g.n[1] + j) * g.n[0] + i;
+    return g.f16 ? __half2float(__ldg(reinterpret_cast<const __half*>(g.V) + idx))
+                 : __ldg(reinterpret_cast<const float*>(g.V) + idx);
+}
+
+struct Dda {
+    int X[3], step[3];
+    float t, inv[3];
+};
+
+__device__ __forceinline__ float dda_cross(const Dda& s, const GridDev& g, const float o[3], int a) {
+    if (s.step[a] == 0) return __int_as_float(0x7f800000);
+    const float b = (float)(s.X[a] + (s.step[a] > 0 ? 1 : 0));
+    return __fmul_rn(__fsub_rn(__fadd_rn(g.org[a], __fmul_rn(b, g.vs)), o[a]), s.inv[a]);
+}
+
+__device__ __forceinline__ bool dda_next(Dda& s, const GridDev& g, const float o[3]) {
+    const float tx = dda_cross(s, g, o, 0), ty = dda_cross(s, g, o, 1), tz = dda_cross(s, g, o, 2);
+    int a = 0;
+    float tm = tx;
+    if (ty < tm) { a = 1; tm = ty; }
+    if (tz < tm) { a = 2; tm = tz; }
+    s.t = tm;
+    s.X[a] += s.step[a];
+    return s.X[a] >= 0 && s.X[a] < g.n[a];
+}
+
+__device__ __forceinline__ float trilinear(const GridDev& g, const float p[3]) {
+    int i0[3];
+    float fr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float gg = __fsub_rn(__fdiv_rn(__fsub_rn(p[a], g.org[a]), g.vs), 0.5f);
+        float fl = floorf(gg);
+        fr[a] = __fsub_rn(gg, fl);
+        if (!(fl >= -1.0f)) { fl = -1.0f; fr[a] = 1.0f; }
+        if (fl > (float)g.n[a]) { fl = (float)g.n[a]; fr[a] = 0.0f; }
+        i0[a] = (int)fl;
+    }
+    float c[2][2][2];
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const int ii = min(max(i0[0] + dx, 0), g.n[0] - 1);
+                const int jj = min(max(i0[1] + dy, 0), g.n[1] - 1);
+                const int kk = min(max(i0[2] + dz, 0), g.n[2] - 1);
+                c[dz][dy][dx] = gval(g, ii, jj, kk);
+            }
+    const float x00 = __fadd_rn(c[0][0][0], __fmul_rn(fr[0], __fsub_rn(c[0][0][1], c[0][0][0])));
+    const float x01 = __fadd_rn(c[0][1][0], __fmul_rn(fr[0], __fsub_rn(c[0][1][1], c[0][1][0])));
+    const float x10 = __fadd_rn(c[1][0][0], __fmul_rn(fr[0], __fsub_rn(c[1][0][1], c[1][0][0])));
+    const float x11 = __fadd_rn(c[1][1][0], __fmul_rn(fr[0], __fsub_rn(c[1][1][1], c[1][1][0])));
+    const float y0 = __fadd_rn(x00, __fmul_rn(fr[1], __fsub_rn(x01, x00)));
+    const float y1 = __fadd_rn(x10, __fmul_rn(fr[1], __fsub_rn(x11, x10)));
+    return __fadd_rn(y0, __fmul_rn(fr[2], __fsub_rn(y1, y0)));
+}
+
+__device__ __forceinline__ bool all_negative(const GridDev& g, const int X[3], int r) {
+    for (int dz = -r; dz <= r; ++dz)
+        for (int dy = -r; dy <= r; ++dy)
+            for (int dx = -r; dx <= r; ++dx)
+                if (!(gval(g, X[0] + dx, X[1] + dy, X[2] + dz) < 0.0f)) return false;
+    return true;
+}
+
+__device__ __forceinline__ bool inside_bit(const uint32_t* __restrict__ mask, const GridDev& g, const int X[3]) {
+    const int64_t idx = ((int64_t)X[2] * g.n[1] + X[1]) * g.n[0] + X[0];
+    return (__ldg(mask + (idx >> 5)) >> (idx & 31)) & 1u;
+}
+
+__device__ __forceinline__ void point_at(const float o[3], const float d[3], float t, float p[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) p[a] = __fadd_rn(o[a], __fmul_rn(t, d[a]));
+}
+
+__global__ void __launch_bounds__(kBoundsBlock) k_ray_bounds(GridDev g, const uint32_t* __restrict__ mask,
+                                                             const float* __restrict__ ray_o,
+                                                             const float* __restrict__ ray_d, int64_t n_rays,
+                                                             BoundsDev p, float* __restrict__ t_n_out,
+                                                             float* __restrict__ t_f_out, int32_t* __restrict__ n_out,
+                                                             float* __restrict__ t_zero_out,
+                                                             uint8_t* __restrict__ status_out, uint32_t* dev_status) {
+    const float kInf = __int_as_float(0x7f800000);
+    const float kNaN = __int_as_float(0x7fffffff);
+    const float ds_norm = __fdiv_rn(p.d_s, g.trunc);
+    const int max_steps = g.n[0] + g.n[1] + g.n[2] + 8;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
+        float o[3], d[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = __ldg(ray_o + 3 * r + a);
+            d[a] = __ldg(ray_d + 3 * r + a);
+        }
+        // ---- clip to the grid box ("RenderingCube") ----
+        float tmin = -kInf, tmax = kInf;
+        bool hit = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float lo = g.org[a], hi = __fadd_rn(g.org[a], __fmul_rn((float)g.n[a], g.vs));
+            if (d[a] == 0.0f) {
+                if (o[a] < lo || o[a] > hi) hit = false;
+                continue;
+            }
+            const float inv = __fdiv_rn(1.0f, d[a]);
+            const float t1 = __fmul_rn(__fsub_rn(lo, o[a]), inv), t2 = __fmul_rn(__fsub_rn(hi, o[a]), inv);
+            const float tl = t1 < t2 ? t1 : t2, th = t1 < t2 ? t2 : t1;
+            if (tl > tmin) tmin = tl;
+            if (th < tmax) tmax = th;
+        }
+        const float t0 = p.t_near > tmin ? p.t_near : tmin;
+        const float t_end = p.t_far < tmax ? p.t_far : tmax;
+        if (!hit || !(t0 < t_end)) {
+            t_n_out[r] = 0.0f; t_f_out[r] = 0.0f; n_out[r] = 0; status_out[r] = TSDFS_MISS;
+            if (t_zero_out) t_zero_out[r] = kNaN;
+            continue;
+        }
+        // ---- voxel walk init ----
+        Dda s;
+        s.t = t0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            s.step[a] = d[a] > 0.0f ? 1 : (d[a] < 0.0f ? -1 : 0);
+            s.inv[a] = d[a] != 0.0f ? __fdiv_rn(1.0f, d[a]) : kInf;
+            const float pa = __fadd_rn(o[a], __fmul_rn(t0, d[a]));
+            const float gg = floorf(__fdiv_rn(__fsub_rn(pa, g.org[a]), g.vs));
+            s.X[a] = gg >= 0.0f ? (gg > (float)(g.n[a] - 1) ? g.n[a] - 1 : (int)gg) : 0;
+        }
+        // ---- near phase: first voxel with V(centre) <= D_s ----
+        bool found = false, in_grid = true;
+        float t_before = t0;
+        int steps = 0;
+        while (in_grid && s.t < t_end) {
+            if (++steps > max_steps) { set_status(dev_status, TSDFS_DEV_MARCH_CAP); in_grid = false; break; }
+            if (gval(g, s.X[0], s.X[1], s.X[2]) <= ds_norm) { found = true; break; }
+            t_before = s.t;
+            in_grid = dda_next(s, g, o);
+        }
+        if (!found) {
+            t_n_out[r] = t0; t_f_out[r] = t_end; n_out[r] = p.n_fallback; status_out[r] = TSDFS_FALLBACK;
+            if (t_zero_out) t_zero_out[r] = kNaN;
+            continue;
+        }
+        const float tn = s.t;
+        float tf = t_end;
+        // ---- zero-crossing search, starting at the entry of the voxel before ----
+        float tz = kNaN, t_prev = t_before, v_prev;
+        {
+            float pp[3];
+            point_at(o, d, t_before, pp);
+            v_prev = trilinear(g, pp);
+            point_at(o, d, tn, pp);
+            const float vn = trilinear(g, pp);
+            if (tn > t_before && v_prev > 0.0f && vn <= 0.0f)
+                tz = __fadd_rn(t_prev, __fmul_rn(__fsub_rn(tn, t_prev), __fdiv_rn(v_prev, __fsub_rn(v_prev, vn))));
+            v_prev = vn;
+            t_prev = tn;
+        }
+        // ---- far phase: consecutive voxels whose neighbourhood is all negative ----
+        int m = 0;
+        while (in_grid && s.t < t_end) {
+            if (++steps > max_steps) { set_status(dev_status, TSDFS_DEV_MARCH_CAP); break; }
+            const bool inside = mask ? inside_bit(mask, g, s.X) : all_negative(g, s.X, p.nb_radius);
+            m = inside ? m + 1 : 0;
+            in_grid = dda_next(s, g, o);
+            const float tc = s.t < t_end ? s.t : t_end;
+            if (tz != tz) {
+                float pp[3];
+                point_at(o, d, tc, pp);
+                const float vc = trilinear(g, pp);
+                if (v_prev > 0.0f && vc <= 0.0f)
+                    tz = __fadd_rn(t_prev, __fmul_rn(__fsub_rn(tc, t_prev), __fdiv_rn(v_prev, __fsub_rn(v_prev, vc))));
+                v_prev = vc;
+                t_prev = tc;
+            }
+            if (m == p.m_confirm) { tf = tc; break; }
+        }
+        // ---- adaptive count (Sec. 3.4) ----
+        const float q = __fdiv_rn(__fsub_rn(tf, tn), p.step);
+        int cnt;
+        if (!(q > 1.0f)) cnt = 1;
+        else if (q >= (float)p.n_max) cnt = p.n_max;
+        else cnt = (int)ceilf(q);
+        if (cnt > p.n_max) cnt = p.n_max;
+        t_n_out[r] = tn; t_f_out[r] = tf; n_out[r] = cnt; status_out[r] = TSDFS_BOUNDED;
+        if (t_zero_out) t_zero_out[r] = tz;
+    }
+}
+
+// ---- K4: three-phase exclusive scan (chunk sums, scan of sums, chunk scan) ----
+__device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        sh[lane] = w;  // inclusive warp prefix
+    }
+    __syncthreads();
+    total = sh[(blockDim.x >> 5) - 1];
+    const int excl = x - v + (warp > 0 ? sh[warp - 1] : 0);
+    __syncthreads();
+    return excl;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_chunk_sums(const int32_t* __restrict__ cnt, int64_t n,
+                                                           int32_t* __restrict__ sums) {
+    __shared__ int sh[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+    int v = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) v += cnt[base + i];
+    int total;
+    block_exclusive_scan(v, sh, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_sums(int32_t* __restrict__ sums, int64_t n_chunks,
+                                                          int32_t* __restrict__ offsets_last, int64_t n_rays) {
+    __shared__ int sh[32];
+    const int per = (int)((n_chunks + kScanBlock - 1) / kScanBlock);
+    const int64_t base = (int64_t)threadIdx.x * per;
+    int v = 0;
+    for (int i = 0; i < per; ++i)
+        if (base + i < n_chunks) v += sums[base + i];
+    int total;
+    int run = block_exclusive_scan(v, sh, total);
+    for (int i = 0; i < per; ++i)
+        if (base + i < n_chunks) {
+            int c = sums[base + i];
+            sums[base + i] = run;
+            run += c;
+        }
+    if (threadIdx.x == 0) offsets_last[n_rays] = total;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_chunk_scan(const int32_t* __restrict__ cnt, int64_t n,
+                                                           const int32_t* __restrict__ sums,
+                                                           int32_t* __restrict__ offsets) {
+    __shared__ int sh[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = base + i < n ? cnt[base + i] : 0;
+        s += v[i];
+    }
+    int total;
+    int run = block_exclusive_scan(s, sh, total) + sums[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) {
+            offsets[base + i] = run;
+            run += v[i];
+        }
+}
+
+}  // namespace
+
+int64_t scan_chunks(int64_t n) { return (n + kScanChunk - 1) / kScanChunk; }
+
+// exclusive scan of n counts into offsets[0..n]; `sums` needs scan_chunks(n) ints
+int exclusive_scan(const int32_t* cnt, int64_t n, int32_t* offsets, int32_t* sums, cudaStream_t st) {
+    const int64_t chunks = scan_chunks(n);
+    if (n == 0) return cuda_check(cudaMemsetAsync(offsets, 0, sizeof(int32_t), st), "scan memset");
+    if (chunks > (int64_t)kScanBlock * 64) return fail(TSDFS_E_INVALID, "too many rays for the scan (%lld)", (long long)n);
+    ProfScope ps("scan", st);
+    k_chunk_sums<<<(unsigned)chunks, kScanBlock, 0, st>>>(cnt, n, sums);
+    k_scan_sums<<<1, kScanBlock, 0, st>>>(sums, chunks, offsets, n);
+    k_chunk_scan<<<(unsigned)chunks, kScanBlock, 0, st>>>(cnt, n, sums, offsets);
+    return cuda_check(cudaGetLastError(), "scan launch");
+}
+
+}  // namespace tsdfs
+
+using namespace tsdfs;
+
+extern "C" size_t tsdfs_bounds_workspace_size(int64_t n_rays) {
+    if (n_rays < 0) return 0;
+    return (size_t)(scan_chunks(n_rays) + 1) * sizeof(int32_t) + 256;
+}
+
+extern "C" int tsdf_ray_bounds(const tsdfs_grid* g, const uint32_t* mask, const float* ray_o, const float* ray_d,
+                               int64_t n_rays, const tsdfs_bounds_params* p, float* t_n, float* t_f,
+                               int32_t* n_samples, int32_t* offsets, float* t_zero, uint8_t* status, void* ws,
+                               size_t ws_bytes, tsdfs_stream_t stream) {
+    int rc = grid_check(g);
+    if (rc) return rc;
+    if (!p) return fail(TSDFS_E_INVALID, "params is NULL");
+    if (n_rays < 0) return fail(TSDFS_E_INVALID, "n_rays must be >= 0");
+    if (n_rays > (int64_t)INT32_MAX) return fail(TSDFS_E_INVALID, "n_rays must fit in int32 offsets");
+    if (!(p->step > 0.0f) || !(p->d_s == p->d_s)) return fail(TSDFS_E_INVALID, "step must be > 0 and d_s finite");
+    if (p->nb_radius < 0 || p->nb_radius > 4) return fail(TSDFS_E_INVALID, "nb_radius must be in [0, 4]");
+    if (p->m_confirm < 1) return fail(TSDFS_E_INVALID, "m_confirm must be >= 1");
+    if (p->n_max < 1 || p->n_fallback < 0 || p->n_max > 4096 || p->n_fallback > 4096)
+        return fail(TSDFS_E_INVALID, "n_max must be in [1, 4096] and n_fallback in [0, 4096]");
+    if ((int64_t)(p->n_max > p->n_fallback ? p->n_max : p->n_fallback) * n_rays > (int64_t)INT32_MAX)
+        return fail(TSDFS_E_INVALID, "sample total could overflow int32 offsets");
+    if (!(p->t_near < p->t_far)) return fail(TSDFS_E_INVALID, "t_near must be < t_far");
+    if (n_rays > 0 && (!ray_o || !ray_d || !t_n || !t_f || !n_samples || !status))
+        return fail(TSDFS_E_INVALID, "ray and output pointers must be non-NULL");
+    if (!offsets) return fail(TSDFS_E_INVALID, "offsets is NULL");
+    if (ws_bytes < tsdfs_bounds_workspace_size(n_rays) || !ws) return fail(TSDFS_E_WORKSPACE, "bounds workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_rays > 0) {
+        GridDev gd{g->tsdf, g->dtype == TSDFS_F16, {g->nx, g->ny, g->nz}, {g->origin[0], g->origin[1], g->origin[2]},
+                   g->voxel_size, g->trunc};
+        BoundsDev bd{p->d_s, p->t_near, p->t_far, p->step, p->nb_radius, p->m_confirm, p->n_max, p->n_fallback};
+        ProfScope ps("ray_bounds", st);
+        k_ray_bounds<<<grid_1d(n_rays, kBoundsBlock, 152 * 64), kBoundsBlock, 0, st>>>(
+            gd, mask, ray_o, ray_d, n_rays, bd, t_n, t_f, n_samples, t_zero, status, device_status_word());
+        rc = cuda_check(cudaGetLastError(), "tsdf_ray_bounds launch");
+        if (rc) return rc;
+    }
+    int32_t* sums = reinterpret_cast<int32_t*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
+    return exclusive_scan(n_samples, n_rays, offsets, sums, st);
+}

@@ -1,0 +1,160 @@
+// Shared device-side definitions of the CUDA path (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "tsdfs.h"
+
+namespace tsdfs {
+
+// ---------------------------------------------------------------------------
+// host-side error reporting (abi.cu)
+// ---------------------------------------------------------------------------
+int fail(int code, const char* fmt, ...);
+int cuda_check(cudaError_t e, const char* what);
+// device status word of the current device (TSDFS_DEV_* bits), see abi.cu
+uint32_t* device_status_word();
+
+// kernel timing (tsdfs_profile): brackets the launches in its scope with events
+void prof_begin(const char* name, cudaStream_t st, void** token);
+void prof_end(void* token, cudaStream_t st);
+struct ProfScope {
+    void* token = nullptr;
+    cudaStream_t st;
+    ProfScope(const char* name, cudaStream_t s) : st(s) { prof_begin(name, s, &token); }
+    ~ProfScope() { prof_end(token, st); }
+};
+
+// ---------------------------------------------------------------------------
+// network architectures (the C ABI's TSDFS_ARCH_* tables)
+// ---------------------------------------------------------------------------
+struct Layer {
+    int in, out;
+};
+
+template <int ARCH> struct Arch;
+
+template <> struct Arch<TSDFS_ARCH_TINY> {
+    static constexpr int kSdfLayers = 4;
+    static constexpr int kRgbLayers = 3;
+    static constexpr int kPeSdf = 0;
+    static constexpr int kPeDir = 0;
+    static constexpr int kSkip = -1;
+    static constexpr int kFeat = 16;
+    static constexpr int kEnc = 3;         // encoded SDF input width
+    static constexpr int kDirEnc = 3;
+    static constexpr int kWidth = 64;       // hidden width
+    __host__ __device__ static constexpr Layer sdf(int l) {
+        return l == 0 ? Layer{3, 64} : (l < 3 ? Layer{64, 64} : Layer{64, 17});
+    }
+    __host__ __device__ static constexpr Layer rgb(int l) {
+        return l == 0 ? Layer{25, 64} : (l == 1 ? Layer{64, 64} : Layer{64, 3});
+    }
+};
+
+template <> struct Arch<TSDFS_ARCH_ROOM> {
+    static constexpr int kSdfLayers = 8;
+    static constexpr int kRgbLayers = 5;
+    static constexpr int kPeSdf = 6;
+    static constexpr int kPeDir = 4;
+    static constexpr int kSkip = 4;
+    static constexpr int kFeat = 256;
+    static constexpr int kEnc = 39;
+    static constexpr int kDirEnc = 27;
+    static constexpr int kWidth = 256;
+    __host__ __device__ static constexpr Layer sdf(int l) {
+        return l == 0 ? Layer{39, 256} : (l == 3 ? Layer{256, 217} : (l == 7 ? Layer{256, 257} : Layer{256, 256}));
+    }
+    __host__ __device__ static constexpr Layer rgb(int l) {
+        return l == 0 ? Layer{289, 256} : (l == 4 ? Layer{256, 3} : Layer{256, 256});
+    }
+};
+
+template <int ARCH> __host__ __device__ constexpr int64_t sdf_param_count() {
+    int64_t n = 0;
+    for (int l = 0; l < Arch<ARCH>::kSdfLayers; ++l) n += (int64_t)Arch<ARCH>::sdf(l).out * (Arch<ARCH>::sdf(l).in + 1);
+    return n;
+}
+template <int ARCH> __host__ __device__ constexpr int64_t rgb_param_count() {
+    int64_t n = 0;
+    for (int l = 0; l < Arch<ARCH>::kRgbLayers; ++l) n += (int64_t)Arch<ARCH>::rgb(l).out * (Arch<ARCH>::rgb(l).in + 1);
+    return n;
+}
+template <int ARCH> __host__ __device__ constexpr int64_t sdf_layer_offset(int l) {
+    int64_t n = 0;
+    for (int i = 0; i < l; ++i) n += (int64_t)Arch<ARCH>::sdf(i).out * (Arch<ARCH>::sdf(i).in + 1);
+    return n;
+}
+template <int ARCH> __host__ __device__ constexpr int64_t rgb_layer_offset(int l) {
+    int64_t n = 0;
+    for (int i = 0; i < l; ++i) n += (int64_t)Arch<ARCH>::rgb(i).out * (Arch<ARCH>::rgb(i).in + 1);
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+// per-sample record between the network kernels and compositing (workspace)
+// ---------------------------------------------------------------------------
+struct __align__(16) SampleRec {
+    float f, dd, t, delta;      // SDF, v . grad f, sample position, section width
+    float r, g, b, gnorm;       // colour, |grad f|
+    float nx, ny, nz, pad;      // unit normal
+};
+static_assert(sizeof(SampleRec) == 48, "record layout");
+
+// how the network kernel finds a sample's ray, t and delta
+enum SampleMode : int {
+    kUniform = 0,   // ragged offsets, midpoints of [t_n, t_f]
+    kExplicit = 1,  // t[g], delta[g] given, ray = g / per_ray
+};
+
+struct NetParams {
+    const float* sdf_w;
+    const float* rgb_w;
+    float center[3];
+    float inv_scale, scale, beta;
+};
+
+struct SampleSource {
+    int mode;
+    const float* ray_o;
+    const float* ray_d;
+    // kUniform
+    const int32_t* offsets;
+    const float* t_n;
+    const float* t_f;
+    int64_t n_rays;
+    // kExplicit
+    const float* t;
+    const float* delta;
+    int per_ray;
+    // total sample count: *total_dev (uniform, = offsets[n_rays]) or total_host
+    const int32_t* total_dev;
+    int64_t total_host;
+    int64_t capacity;  // records available in the workspace
+};
+
+__device__ __forceinline__ int64_t find_ray(const int32_t* __restrict__ offsets, int64_t n_rays, int64_t g) {
+    // largest r with offsets[r] <= g (offsets non-decreasing, offsets[0] = 0)
+    int64_t lo = 0, hi = n_rays;  // invariant offsets[lo] <= g < offsets[hi]
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(offsets + mid) <= g) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void set_status(uint32_t* status, uint32_t bits) {
+    if (status) atomicOr(status, bits);
+}
+
+inline unsigned grid_1d(int64_t n, int block, int max_blocks = 152 * 32) {
+    int64_t b = (n + block - 1) / block;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (unsigned)b;
+}
+
+}  // namespace tsdfs

@@ -517,3 +517,136 @@ def analytic_tsdf(scene, grid: GridSpec):
         s = np.clip(scene.sdf(x) / grid.trunc, -1.0, 1.0)
         out[k] = s.reshape(ny, nx)
     return out
+
+
+def fitted_path(name):
+    import os
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", f"{name}_mlp.npz")
+
+
+def scene_mlp(name) -> MLPSpec:
+    """The network of a scene: the seeded initialisation refined by
+    ``fit_scene_mlp`` (a stand-in for a pre-trained model), if its file exists."""
+    import os
+    spec = tiny_mlp() if name == "tiny" else room_mlp()
+    p = fitted_path(name)
+    if os.path.exists(p):
+        load_mlp(spec, p)
+    return spec
+
+
+# ----------------------------------------------------------------------------
+# torch versions of the heavy fixture geometry (same definitions as above), so
+# full-size depth maps and distance grids can be generated on the device
+# ----------------------------------------------------------------------------
+def _t_boxes_entry(o, d, lo, hi):
+    import torch
+    inv = 1.0 / d
+    t1 = (lo[None] - o[:, None, :]) * inv[:, None, :]
+    t2 = (hi[None] - o[:, None, :]) * inv[:, None, :]
+    t1 = torch.nan_to_num(t1, nan=-float("inf"))
+    t2 = torch.nan_to_num(t2, nan=float("inf"))
+    tmin = torch.amax(torch.minimum(t1, t2), 2)
+    tmax = torch.amin(torch.maximum(t1, t2), 2)
+    hit = (tmax >= tmin) & (tmin > 0)
+    return torch.where(hit, tmin, torch.full_like(tmin, float("inf")))
+
+
+def _t_box_exit(o, d, lo, hi):
+    import torch
+    inv = 1.0 / d
+    t1 = torch.nan_to_num((lo[None] - o) * inv, nan=-float("inf"))
+    t2 = torch.nan_to_num((hi[None] - o) * inv, nan=float("inf"))
+    return torch.amin(torch.maximum(t1, t2), 1)
+
+
+def ray_range_torch(scene, o, d):
+    """Range of unit rays (torch float64 tensors) in a fixture scene."""
+    import torch
+    if isinstance(scene, SphereScene):
+        c = torch.tensor(scene.center, dtype=o.dtype, device=o.device)
+        oc = o - c
+        b = (oc * d).sum(1)
+        cc = (oc * oc).sum(1) - scene.radius ** 2
+        disc = b * b - cc
+        ok = disc >= 0
+        sq = torch.sqrt(torch.clamp(disc, min=0))
+        t0, t1 = -b - sq, -b + sq
+        inf = torch.full_like(b, float("inf"))
+        return torch.where(ok & (t0 > 0), t0, torch.where(ok & (t1 > 0), t1, inf))
+    lo = torch.tensor(scene.box_lo, dtype=o.dtype, device=o.device)
+    hi = torch.tensor(scene.box_hi, dtype=o.dtype, device=o.device)
+    t_wall = _t_box_exit(o, d, torch.tensor(scene.room_lo, dtype=o.dtype, device=o.device),
+                         torch.tensor(scene.room_hi, dtype=o.dtype, device=o.device))
+    if lo.shape[0] == 0:
+        return t_wall
+    t_box = torch.amin(_t_boxes_entry(o, d, lo, hi), 1)
+    return torch.minimum(t_wall, t_box)
+
+
+def render_depth_maps_torch(scene, c2ws, fx, fy, cx, cy, width, height, noise_std=0.0, seed=SEED_NOISE, device="cuda"):
+    """render_depth_maps on a torch device; returns a float32 tensor (V, H, W)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    u, v = torch.meshgrid(torch.arange(width, dtype=torch.float64, device=device) + 0.5,
+                          torch.arange(height, dtype=torch.float64, device=device) + 0.5, indexing="xy")
+    dc = torch.stack([(u - cx) / fx, (v - cy) / fy, torch.ones_like(u)], -1).reshape(-1, 3)
+    out = torch.empty((len(c2ws), height, width), dtype=torch.float32, device=device)
+    for i, c2w in enumerate(c2ws):
+        P = torch.tensor(np.asarray(c2w), dtype=torch.float64, device=device)
+        d = dc @ P[:, :3].T
+        d = d / torch.linalg.norm(d, dim=1, keepdim=True)
+        o = P[:, 3].expand_as(d)
+        t = ray_range_torch(scene, o, d)
+        if noise_std > 0:
+            t = t + torch.tensor(rng.normal(0.0, noise_std, t.shape[0]), dtype=torch.float64, device=device)
+        out[i] = t.reshape(height, width).to(torch.float32)
+    return out
+
+
+def sdf_torch(scene, x):
+    import torch
+    if isinstance(scene, SphereScene):
+        return torch.linalg.norm(x - torch.tensor(scene.center, dtype=x.dtype, device=x.device), dim=1) - scene.radius
+    rlo = torch.tensor(scene.room_lo, dtype=x.dtype, device=x.device)
+    rhi = torch.tensor(scene.room_hi, dtype=x.dtype, device=x.device)
+    d_room = torch.amin(torch.cat([x - rlo, rhi - x], 1), 1)
+    q = torch.clamp(torch.maximum(rlo - x, x - rhi), min=0)
+    out = torch.linalg.norm(q, dim=1)
+    d_room = torch.where(out > 0, -out, d_room)
+    if len(scene.box_lo) == 0:
+        return d_room
+    lo = torch.tensor(scene.box_lo, dtype=x.dtype, device=x.device)
+    hi = torch.tensor(scene.box_hi, dtype=x.dtype, device=x.device)
+    c = 0.5 * (lo + hi)
+    h = 0.5 * (hi - lo)
+    qq = torch.abs(x[:, None, :] - c[None]) - h[None]
+    sb = torch.linalg.norm(torch.clamp(qq, min=0), dim=2) + torch.clamp(torch.amax(qq, 2), max=0)
+    return torch.minimum(d_room, torch.amin(sb, 1))
+
+
+def analytic_tsdf_torch(scene, grid: GridSpec, device="cuda"):
+    """analytic_tsdf on a torch device (float32 tensor (nz, ny, nx))."""
+    import torch
+    o = torch.tensor(grid.origin, dtype=torch.float64, device=device)
+    jj, ii = torch.meshgrid(torch.arange(grid.ny, device=device), torch.arange(grid.nx, device=device), indexing="ij")
+    out = torch.empty((grid.nz, grid.ny, grid.nx), dtype=torch.float32, device=device)
+    for k in range(grid.nz):
+        x = torch.stack([o[0] + (ii + 0.5) * grid.voxel_size, o[1] + (jj + 0.5) * grid.voxel_size,
+                         torch.full(ii.shape, float(o[2] + (k + 0.5) * grid.voxel_size), dtype=torch.float64,
+                                    device=device)], -1).reshape(-1, 3).to(torch.float64)
+        out[k] = torch.clamp(sdf_torch(scene, x) / grid.trunc, -1.0, 1.0).reshape(grid.ny, grid.nx).to(torch.float32)
+    return out
+
+
+def room_workload_torch(device="cuda", n_views=100, width=640, height=480, grid_n=256, noise_std=0.005):
+    """room_workload with the depth maps rendered on a torch device."""
+    wl = room_workload(n_views, width, height, grid_n, noise_std, with_views=False)
+    fx = fy = 500.0 * width / 640.0
+    c2ws = sample_free_poses(wl.scene, np.random.default_rng(SEED_POSES), n_views)
+    depth = render_depth_maps_torch(wl.scene, c2ws, fx, fy, width / 2.0, height / 2.0, width, height, noise_std,
+                                    device=device)
+    V = len(c2ws)
+    wl.views = Views(np.tile(np.array([fx, fy, width / 2.0, height / 2.0], np.float32), (V, 1)),
+                     np.asarray(c2ws, np.float32).reshape(V, 12), depth, width, height)
+    return wl

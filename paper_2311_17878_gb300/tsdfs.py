@@ -1,0 +1,330 @@
+"""Thin Python binding of ``libtsdfs.so`` (the C ABI in ``include/tsdfs.h``).
+
+The functions named like the C entry points marshal torch tensors (device
+memory) and the current torch CUDA stream into the C calls, nothing more:
+every step of the path runs in the library's kernels.  The small helper
+classes at the bottom allocate outputs and workspaces with torch.
+
+There is no fallback: if ``libtsdfs.so`` is missing or fails to load, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtsdfs.so")
+_LIB = None
+_LOCK = threading.Lock()
+
+TSDFS_OK, TSDFS_E_INVALID, TSDFS_E_CUDA, TSDFS_E_WORKSPACE, TSDFS_E_UNSUPPORTED, TSDFS_E_DEVICE = 0, -1, -2, -3, -4, -5
+TSDFS_F32, TSDFS_F16 = 0, 1
+TSDFS_MISS, TSDFS_BOUNDED, TSDFS_FALLBACK = 0, 1, 2
+TSDFS_ARCH_TINY, TSDFS_ARCH_ROOM = 0, 1
+TSDFS_PREC_F32, TSDFS_PREC_BF16 = 0, 1
+TSDFS_DEV_SAMPLES_OVERFLOW, TSDFS_DEV_MARCH_CAP = 1, 2
+
+EXPORTS = ["tsdfs_last_error", "tsdfs_sync_status", "tsdfs_grid_init", "tsdf_integrate", "tsdfs_inside_mask_words",
+           "tsdfs_inside_mask", "tsdfs_bounds_workspace_size", "tsdf_ray_bounds", "tsdfs_render_workspace_size",
+           "render_rays", "tsdfs_hier_workspace_size", "render_rays_hier96", "tsdfs_backward_workspace_size",
+           "render_rays_backward", "tsdfs_packed_size", "tsdfs_pack_mlp", "tsdfs_sdf_param_count",
+           "tsdfs_rgb_param_count"]
+
+
+class TsdfsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tsdfs error {code}: {msg}")
+        self.code = code
+
+
+class tsdfs_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("origin", C.c_float * 3),
+                ("voxel_size", C.c_float), ("trunc", C.c_float), ("dtype", C.c_int32), ("tsdf", C.c_void_p),
+                ("weight", C.c_void_p)]
+
+
+class tsdfs_bounds_params(C.Structure):
+    _fields_ = [("d_s", C.c_float), ("t_near", C.c_float), ("t_far", C.c_float), ("step", C.c_float),
+                ("nb_radius", C.c_int32), ("m_confirm", C.c_int32), ("n_max", C.c_int32), ("n_fallback", C.c_int32)]
+
+
+class tsdfs_mlp(C.Structure):
+    _fields_ = [("arch", C.c_int32), ("precision", C.c_int32), ("sdf_w", C.c_void_p), ("rgb_w", C.c_void_p),
+                ("packed", C.c_void_p), ("center", C.c_float * 3), ("scale", C.c_float), ("inv_s", C.c_float),
+                ("beta", C.c_float), ("alpha_eps", C.c_float)]
+
+
+def lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2311_17878_gb300.build`")
+            L = C.CDLL(LIB_PATH)
+            L.tsdfs_last_error.restype = C.c_char_p
+            for name in ["tsdfs_bounds_workspace_size", "tsdfs_render_workspace_size", "tsdfs_hier_workspace_size",
+                         "tsdfs_backward_workspace_size", "tsdfs_packed_size"]:
+                getattr(L, name).restype = C.c_size_t
+            for name in ["tsdfs_inside_mask_words", "tsdfs_sdf_param_count", "tsdfs_rgb_param_count"]:
+                getattr(L, name).restype = C.c_int64
+            L.tsdfs_bounds_workspace_size.argtypes = [C.c_int64]
+            L.tsdfs_render_workspace_size.argtypes = [C.c_void_p, C.c_int64, C.c_int64]
+            L.tsdfs_hier_workspace_size.argtypes = [C.c_void_p, C.c_int64]
+            L.tsdfs_backward_workspace_size.argtypes = [C.c_void_p, C.c_int64, C.c_int64]
+            L.tsdfs_packed_size.argtypes = [C.c_int32]
+            L.tsdfs_sdf_param_count.argtypes = [C.c_int32]
+            L.tsdfs_rgb_param_count.argtypes = [C.c_int32]
+            _LIB = L
+    return _LIB
+
+
+def _p(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(rc):
+    if rc != TSDFS_OK:
+        raise TsdfsError(rc, lib().tsdfs_last_error().decode())
+
+
+def _cuda(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+# ----------------------------------------------------------------------------
+# same-name wrappers of the C entry points
+# ----------------------------------------------------------------------------
+def tsdfs_last_error() -> str:
+    return lib().tsdfs_last_error().decode()
+
+
+def tsdfs_sync_status():
+    bits = C.c_uint32(0)
+    rc = lib().tsdfs_sync_status(_stream(), C.byref(bits))
+    if rc not in (TSDFS_OK, TSDFS_E_DEVICE):
+        _check(rc)
+    return rc, bits.value
+
+
+def tsdfs_grid_init(grid: "Grid"):
+    _check(lib().tsdfs_grid_init(C.byref(grid.c), _stream()))
+
+
+def tsdf_integrate(grid: "Grid", depth, K, c2w):
+    _cuda(depth, torch.float32, "depth"), _cuda(K, torch.float32, "K"), _cuda(c2w, torch.float32, "c2w")
+    nv, H, W = depth.shape
+    _check(lib().tsdf_integrate(C.byref(grid.c), _p(depth), C.c_int32(nv), C.c_int32(H), C.c_int32(W), _p(K),
+                                _p(c2w), _stream()))
+
+
+def tsdfs_inside_mask_words(grid: "Grid") -> int:
+    return int(lib().tsdfs_inside_mask_words(C.byref(grid.c)))
+
+
+def tsdfs_inside_mask(grid: "Grid", nb_radius: int, mask_bits):
+    _cuda(mask_bits, torch.int32, "mask_bits")
+    _check(lib().tsdfs_inside_mask(C.byref(grid.c), C.c_int32(nb_radius), _p(mask_bits), _stream()))
+
+
+def tsdfs_bounds_workspace_size(n_rays: int) -> int:
+    return int(lib().tsdfs_bounds_workspace_size(C.c_int64(n_rays)))
+
+
+def tsdf_ray_bounds(grid: "Grid", inside_mask, ray_o, ray_d, params: tsdfs_bounds_params, t_n, t_f, n_samples,
+                    offsets, t_zero, status, workspace):
+    n = ray_o.shape[0]
+    _check(lib().tsdf_ray_bounds(C.byref(grid.c), _p(inside_mask), _p(ray_o), _p(ray_d), C.c_int64(n),
+                                 C.byref(params), _p(t_n), _p(t_f), _p(n_samples), _p(offsets), _p(t_zero),
+                                 _p(status), _p(workspace), C.c_size_t(workspace.numel() if workspace is not None else 0),
+                                 _stream()))
+
+
+def tsdfs_render_workspace_size(mlp: "Mlp", n_rays: int, max_samples: int) -> int:
+    return int(lib().tsdfs_render_workspace_size(C.byref(mlp.c), C.c_int64(n_rays), C.c_int64(max_samples)))
+
+
+def render_rays(mlp: "Mlp", ray_o, ray_d, t_n, t_f, offsets, status, max_samples, rgb, depth, wsum, normal, eik,
+                workspace):
+    n = ray_o.shape[0]
+    _check(lib().render_rays(C.byref(mlp.c), _p(ray_o), _p(ray_d), _p(t_n), _p(t_f), _p(offsets), _p(status),
+                             C.c_int64(n), C.c_int64(max_samples), _p(rgb), _p(depth), _p(wsum), _p(normal), _p(eik),
+                             _p(workspace), C.c_size_t(workspace.numel()), _stream()))
+
+
+def tsdfs_hier_workspace_size(mlp: "Mlp", n_rays: int) -> int:
+    return int(lib().tsdfs_hier_workspace_size(C.byref(mlp.c), C.c_int64(n_rays)))
+
+
+def render_rays_hier96(mlp: "Mlp", grid: "Grid", ray_o, ray_d, t_near, t_far, rgb, depth, wsum, normal, workspace):
+    n = ray_o.shape[0]
+    _check(lib().render_rays_hier96(C.byref(mlp.c), C.byref(grid.c), _p(ray_o), _p(ray_d), C.c_int64(n),
+                                    C.c_float(t_near), C.c_float(t_far), _p(rgb), _p(depth), _p(wsum), _p(normal),
+                                    _p(workspace), C.c_size_t(workspace.numel()), _stream()))
+
+
+def tsdfs_backward_workspace_size(mlp: "Mlp", n_rays: int, max_samples: int) -> int:
+    return int(lib().tsdfs_backward_workspace_size(C.byref(mlp.c), C.c_int64(n_rays), C.c_int64(max_samples)))
+
+
+def render_rays_backward(mlp: "Mlp", ray_o, ray_d, t_n, t_f, offsets, status, max_samples, d_rgb, d_depth, d_eik,
+                         d_sdf_w, d_rgb_w, workspace):
+    n = ray_o.shape[0]
+    _check(lib().render_rays_backward(C.byref(mlp.c), _p(ray_o), _p(ray_d), _p(t_n), _p(t_f), _p(offsets),
+                                      _p(status), C.c_int64(n), C.c_int64(max_samples), _p(d_rgb), _p(d_depth),
+                                      C.c_float(d_eik), _p(d_sdf_w), _p(d_rgb_w), _p(workspace),
+                                      C.c_size_t(workspace.numel()), _stream()))
+
+
+def tsdfs_packed_size(arch: int) -> int:
+    return int(lib().tsdfs_packed_size(C.c_int32(arch)))
+
+
+def tsdfs_pack_mlp(mlp: "Mlp", packed):
+    _check(lib().tsdfs_pack_mlp(C.byref(mlp.c), _p(packed), _stream()))
+
+
+def tsdfs_sdf_param_count(arch: int) -> int:
+    return int(lib().tsdfs_sdf_param_count(C.c_int32(arch)))
+
+
+def tsdfs_rgb_param_count(arch: int) -> int:
+    return int(lib().tsdfs_rgb_param_count(C.c_int32(arch)))
+
+
+# ----------------------------------------------------------------------------
+# allocation helpers (torch memory only)
+# ----------------------------------------------------------------------------
+def _bytes(n, device):
+    return torch.empty(max(int(n), 1), dtype=torch.uint8, device=device)
+
+
+class Grid:
+    """A TSDF grid in device memory (V, W) and its ``tsdfs_grid`` descriptor."""
+
+    def __init__(self, spec, device="cuda", V=None, W=None):
+        self.spec = spec
+        shape = (spec.nz, spec.ny, spec.nx)
+        f16 = spec.dtype == "f16"
+        if V is None:
+            V = torch.empty(shape, dtype=torch.float16 if f16 else torch.float32, device=device)
+        if W is None:
+            W = torch.empty(shape, dtype=torch.uint8, device=device)
+        self.V, self.W = V.contiguous(), W.contiguous()
+        self.c = tsdfs_grid(spec.nx, spec.ny, spec.nz, (C.c_float * 3)(*spec.origin), spec.voxel_size, spec.trunc,
+                            TSDFS_F16 if f16 else TSDFS_F32, self.V.data_ptr(), self.W.data_ptr())
+
+    def init(self):
+        tsdfs_grid_init(self)
+        return self
+
+    def integrate(self, depth, K, c2w):
+        tsdf_integrate(self, depth, K, c2w)
+        return self
+
+    def inside_mask(self, nb_radius):
+        bits = torch.empty(tsdfs_inside_mask_words(self), dtype=torch.int32, device=self.V.device)
+        tsdfs_inside_mask(self, nb_radius, bits)
+        return bits
+
+
+def bounds_params(bp) -> tsdfs_bounds_params:
+    return tsdfs_bounds_params(bp.d_s, bp.t_near, bp.t_far, bp.step, bp.nb_radius, bp.m_confirm, bp.n_max,
+                               bp.n_fallback)
+
+
+class Bounds:
+    """Outputs of ``tsdf_ray_bounds`` for a batch of rays (device tensors)."""
+
+    def __init__(self, n, device="cuda"):
+        self.t_n = torch.empty(n, dtype=torch.float32, device=device)
+        self.t_f = torch.empty(n, dtype=torch.float32, device=device)
+        self.n = torch.empty(n, dtype=torch.int32, device=device)
+        self.offsets = torch.empty(n + 1, dtype=torch.int32, device=device)
+        self.t_zero = torch.empty(n, dtype=torch.float32, device=device)
+        self.status = torch.empty(n, dtype=torch.uint8, device=device)
+        self.workspace = _bytes(tsdfs_bounds_workspace_size(n), device)
+
+    def compute(self, grid: Grid, rays_o, rays_d, bp, inside_mask=None):
+        p = bp if isinstance(bp, tsdfs_bounds_params) else bounds_params(bp)
+        tsdf_ray_bounds(grid, inside_mask, rays_o, rays_d, p, self.t_n, self.t_f, self.n, self.offsets, self.t_zero,
+                        self.status, self.workspace)
+        return self
+
+
+class Mlp:
+    """Network parameters on the device and their ``tsdfs_mlp`` descriptor."""
+
+    def __init__(self, spec, precision=TSDFS_PREC_F32, device="cuda"):
+        self.spec = spec
+        self.sdf_w = torch.tensor(spec.packed("sdf"), device=device)
+        self.rgb_w = torch.tensor(spec.packed("rgb"), device=device)
+        self.packed = None
+        self.precision = precision
+        if precision == TSDFS_PREC_BF16:
+            self.packed = torch.zeros(max(tsdfs_packed_size(spec.arch), 1), dtype=torch.uint8, device=device)
+        self.c = tsdfs_mlp(spec.arch, precision, self.sdf_w.data_ptr(), self.rgb_w.data_ptr(),
+                           self.packed.data_ptr() if self.packed is not None else None,
+                           (C.c_float * 3)(*spec.center), spec.scale, spec.inv_s, spec.beta, spec.alpha_eps)
+        if precision == TSDFS_PREC_BF16:
+            tsdfs_pack_mlp(self, self.packed)
+
+    def repack(self):
+        if self.packed is not None:
+            tsdfs_pack_mlp(self, self.packed)
+
+
+class RenderOut:
+    def __init__(self, n, device="cuda"):
+        self.rgb = torch.empty((n, 3), dtype=torch.float32, device=device)
+        self.depth = torch.empty(n, dtype=torch.float32, device=device)
+        self.wsum = torch.empty(n, dtype=torch.float32, device=device)
+        self.normal = torch.empty((n, 3), dtype=torch.float32, device=device)
+        self.eik = torch.empty(n, dtype=torch.float32, device=device)
+
+
+class Renderer:
+    """render_rays with a workspace sized for ``max_samples``."""
+
+    def __init__(self, mlp: Mlp, n_rays, max_samples, device="cuda"):
+        self.mlp = mlp
+        self.max_samples = int(max_samples)
+        self.out = RenderOut(n_rays, device)
+        self.workspace = _bytes(tsdfs_render_workspace_size(mlp, n_rays, self.max_samples), device)
+
+    def render(self, rays_o, rays_d, b: Bounds):
+        o = self.out
+        render_rays(self.mlp, rays_o, rays_d, b.t_n, b.t_f, b.offsets, b.status, self.max_samples, o.rgb, o.depth,
+                    o.wsum, o.normal, o.eik, self.workspace)
+        return o
+
+
+class HierRenderer:
+    def __init__(self, mlp: Mlp, n_rays, device="cuda"):
+        self.mlp = mlp
+        self.out = RenderOut(n_rays, device)
+        self.workspace = _bytes(tsdfs_hier_workspace_size(mlp, n_rays), device)
+
+    def render(self, grid: Grid, rays_o, rays_d, t_near, t_far):
+        o = self.out
+        render_rays_hier96(self.mlp, grid, rays_o, rays_d, t_near, t_far, o.rgb, o.depth, o.wsum, o.normal,
+                           self.workspace)
+        return o

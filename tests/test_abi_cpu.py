@@ -1,0 +1,91 @@
+"""The C-ABI library loads on a machine without a GPU, exports every entry
+point that include/tsdfs.h declares, and rejects bad arguments on the host
+(before any CUDA call)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2311_17878_gb300 import build, synth
+from paper_2311_17878_gb300 import tsdfs as T
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return T.lib()
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "tsdfs.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**([A-Za-z_][A-Za-z0-9_]*)\s*\(", txt, flags=re.M)
+    return sorted(set(n for n in names if n not in ("typedef",)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(T.EXPORTS) <= set(names)
+
+
+def test_param_counts_match_architectures(L):
+    for arch, spec in [(T.TSDFS_ARCH_TINY, synth.tiny_mlp()), (T.TSDFS_ARCH_ROOM, synth.room_mlp())]:
+        assert T.tsdfs_sdf_param_count(arch) == spec.packed("sdf").size
+        assert T.tsdfs_rgb_param_count(arch) == spec.packed("rgb").size
+    assert T.tsdfs_sdf_param_count(7) == -1
+
+
+def test_workspace_sizes_are_monotone(L):
+    assert T.tsdfs_bounds_workspace_size(0) > 0
+    assert T.tsdfs_bounds_workspace_size(10 ** 6) >= T.tsdfs_bounds_workspace_size(10)
+    m = T.tsdfs_mlp()
+    assert L.tsdfs_render_workspace_size(C.byref(m), 10, 1000) >= 1000 * 48
+    assert L.tsdfs_hier_workspace_size(C.byref(m), 100) >= 100 * 96 * 48
+
+
+def _grid_struct(nx=8):
+    return T.tsdfs_grid(nx, nx, nx, (C.c_float * 3)(0, 0, 0), 0.1, 0.3, T.TSDFS_F32, 0x1000, 0x2000)
+
+
+def test_invalid_arguments_fail_on_host(L):
+    g = _grid_struct()
+    p = T.tsdfs_bounds_params(0.1, 0.0, 10.0, 0.1, 2, 15, 32, 96)
+    # NULL grid
+    assert L.tsdf_ray_bounds(None, None, None, None, C.c_int64(0), C.byref(p), None, None, None, None, None, None,
+                             None, C.c_size_t(0), None) == T.TSDFS_E_INVALID
+    assert "grid" in T.tsdfs_last_error()
+    # bad radius
+    p.nb_radius = 9
+    assert L.tsdf_ray_bounds(C.byref(g), None, None, None, C.c_int64(0), C.byref(p), None, None, None,
+                             C.c_void_p(0x3000), None, None, C.c_void_p(0x4000), C.c_size_t(1 << 20),
+                             None) == T.TSDFS_E_INVALID
+    p.nb_radius = 2
+    # workspace too small
+    assert L.tsdf_ray_bounds(C.byref(g), None, C.c_void_p(8), C.c_void_p(8), C.c_int64(100), C.byref(p),
+                             C.c_void_p(8), C.c_void_p(8), C.c_void_p(8), C.c_void_p(8), None, C.c_void_p(8),
+                             C.c_void_p(8), C.c_size_t(1), None) == T.TSDFS_E_WORKSPACE
+    # bad grid geometry
+    g.voxel_size = 0.0
+    assert L.tsdfs_grid_init(C.byref(g), None) == T.TSDFS_E_INVALID
+    g.voxel_size = 0.1
+    g.dtype = 5
+    assert L.tsdf_integrate(C.byref(g), None, 1, 4, 4, None, None, None) == T.TSDFS_E_INVALID
+    # bad mlp
+    m = T.tsdfs_mlp(9, 0, 8, 8, None, (C.c_float * 3)(0, 0, 0), 1.0, 64.0, 100.0, 1e-5)
+    assert L.render_rays(C.byref(m), *([C.c_void_p(8)] * 7), C.c_int64(1), C.c_int64(1), *([C.c_void_p(8)] * 5),
+                         C.c_void_p(8), C.c_size_t(1 << 20), None) == T.TSDFS_E_INVALID
+    m.arch = 0
+    m.precision = T.TSDFS_PREC_BF16
+    assert L.render_rays(C.byref(m), *([C.c_void_p(8)] * 7), C.c_int64(1), C.c_int64(1), *([C.c_void_p(8)] * 5),
+                         C.c_void_p(8), C.c_size_t(1 << 20), None) == T.TSDFS_E_INVALID  # packed is NULL
+    # zero rays is a no-op that succeeds without touching the device
+    m.precision = 0
+    assert L.render_rays(C.byref(m), *([None] * 6), C.c_int64(0), C.c_int64(0), *([None] * 5), None, C.c_size_t(0),
+                         None) == T.TSDFS_OK

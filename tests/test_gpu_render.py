@@ -1,0 +1,155 @@
+"""GPU parity of the render path (sample placement, SDF + colour networks,
+NeuS opacity, compositing) and of the 64 + 32 hierarchical comparator,
+against the FP64 oracle on the same seeded inputs.
+
+Tolerances (FP32 networks): depth 1e-4 relative, colour 2e-3 absolute (the
+stated bars); weight sums and normals are checked too."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cgrid
+from oracle import render as orr
+from paper_2311_17878_gb300 import build, synth
+from paper_2311_17878_gb300 import tsdfs as T
+
+pytestmark = pytest.mark.gpu
+
+DEPTH_REL_F32 = 1e-4
+RGB_ABS = 2e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    T.lib()
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+def oracle_bounds_tiny():
+    wl = synth.tiny_workload()
+    V, _ = cgrid.integrate_projective(wl.grid, wl.views, "f32")
+    b = cgrid.ray_bounds(wl.grid, V, wl.rays_o, wl.rays_d, wl.bounds, "f32")
+    return wl, V, b
+
+
+def gpu_render(spec, o, d, b, precision=T.TSDFS_PREC_F32, max_samples=None):
+    mlp = T.Mlp(spec, precision)
+    n = len(o)
+    offsets = np.concatenate([[0], np.cumsum(b["n"])]).astype(np.int32)
+    total = int(offsets[-1])
+    ms = total if max_samples is None else max_samples
+    r = T.Renderer(mlp, n, max(ms, 1))
+    r.max_samples = ms
+    bb = T.Bounds(n)
+    bb.t_n.copy_(dev(b["t_n"].astype(np.float32)))
+    bb.t_f.copy_(dev(b["t_f"].astype(np.float32)))
+    bb.offsets.copy_(dev(offsets))
+    bb.status.copy_(dev(b["status"]))
+    out = r.render(dev(o), dev(d), bb)
+    torch.cuda.synchronize()
+    return {k: getattr(out, k).cpu().numpy() for k in ("rgb", "depth", "wsum", "normal", "eik")}
+
+
+def compare(got, ref, depth_rel=DEPTH_REL_F32, rgb_abs=RGB_ABS):
+    assert np.max(np.abs(got["rgb"] - ref["rgb"])) < rgb_abs
+    assert np.max(np.abs(got["wsum"] - ref["wsum"])) < rgb_abs
+    ok = ref["wsum"] > 1e-3
+    assert np.all(np.abs(got["depth"][ok] - ref["depth"][ok]) <= depth_rel * np.abs(ref["depth"][ok]) + 1e-6)
+    assert np.max(np.abs(got["normal"][ok] - ref["normal"][ok])) < 1e-2
+
+
+def oracle_render(spec, o, d, b):
+    out = orr.render_bounded(orr.Net(spec), o, d, b["t_n"].astype(np.float64), b["t_f"].astype(np.float64), b["n"])
+    return {k: out[k].detach().numpy() for k in ("rgb", "depth", "wsum", "normal")}, out
+
+
+def test_tiny_render_f32_matches_oracle():
+    wl, V, b = oracle_bounds_tiny()
+    spec = synth.scene_mlp("tiny")
+    got = gpu_render(spec, wl.rays_o, wl.rays_d, b)
+    ref, raw = oracle_render(spec, wl.rays_o, wl.rays_d, b)
+    compare(got, ref)
+    # per-ray eikonal sums of BOUNDED rays
+    counts = b["n"]
+    eik = raw["eik"].detach().numpy()
+    per = np.zeros(len(counts))
+    np.add.at(per, np.repeat(np.arange(len(counts)), counts), eik)
+    per[b["status"] != 1] = 0
+    assert np.allclose(got["eik"], per, rtol=1e-4, atol=1e-5)
+    miss = b["status"] == 0
+    assert np.all(got["rgb"][miss] == 0) and np.all(got["wsum"][miss] == 0)
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == 0
+
+
+def test_tiny_render_geometric_init_matches_oracle():
+    wl, V, b = oracle_bounds_tiny()
+    spec = synth.tiny_mlp()
+    got = gpu_render(spec, wl.rays_o, wl.rays_d, b)
+    ref, _ = oracle_render(spec, wl.rays_o, wl.rays_d, b)
+    compare(got, ref)
+
+
+def test_room_render_f32_matches_oracle():
+    wl = synth.room_workload(with_views=False)
+    V = synth.analytic_tsdf_torch(wl.scene, wl.grid, device="cuda").cpu().numpy()
+    o, d = synth.room_heldout_rays(0)
+    idx = synth.sub_sample(len(o), 384, seed=23)
+    o, d = o[idx], d[idx]
+    b = cgrid.ray_bounds(wl.grid, V, o, d, wl.bounds, "f32")
+    spec = synth.scene_mlp("room")
+    got = gpu_render(spec, o, d, b)
+    ref, _ = oracle_render(spec, o, d, b)
+    compare(got, ref)
+
+
+def test_sample_overflow_sets_status_and_zeroes():
+    wl, V, b = oracle_bounds_tiny()
+    spec = synth.tiny_mlp()
+    total = int(b["n"].sum())
+    got = gpu_render(spec, wl.rays_o, wl.rays_d, b, max_samples=total - 1)
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == T.TSDFS_E_DEVICE and bits & T.TSDFS_DEV_SAMPLES_OVERFLOW
+    assert np.all(got["rgb"] == 0) and np.all(got["wsum"] == 0)
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == 0 and bits == 0
+
+
+def test_ragged_counts_single_and_large():
+    """Rays with 1 sample, the n_max cap, and the 96-sample fallback, mixed."""
+    wl, V, b = oracle_bounds_tiny()
+    rng = np.random.default_rng(5)
+    b = dict(b)
+    n = b["n"].copy()
+    live = b["status"] != 0
+    n[live] = rng.choice([1, 2, 31, 32, 96], live.sum())
+    b["n"] = n.astype(np.int32)
+    spec = synth.scene_mlp("tiny")
+    got = gpu_render(spec, wl.rays_o, wl.rays_d, b)
+    ref, _ = oracle_render(spec, wl.rays_o, wl.rays_d, b)
+    compare(got, ref)
+
+
+def test_tiny_hier96_f32_matches_oracle():
+    wl = synth.tiny_workload()
+    spec = synth.scene_mlp("tiny")
+    bp = wl.bounds
+    t0, te, ok = cgrid.clip_rays(wl.grid, wl.rays_o, wl.rays_d, bp.t_near, bp.t_far, "f32")
+    mlp = T.Mlp(spec)
+    g = T.Grid(wl.grid, V=torch.zeros(wl.grid.shape_zyx, device="cuda"),
+               W=torch.zeros(wl.grid.shape_zyx, dtype=torch.uint8, device="cuda"))
+    h = T.HierRenderer(mlp, 4096)
+    out = h.render(g, dev(wl.rays_o), dev(wl.rays_d), bp.t_near, bp.t_far)
+    torch.cuda.synchronize()
+    got = {k: getattr(out, k).cpu().numpy() for k in ("rgb", "depth", "wsum", "normal")}
+    live = np.nonzero(ok)[0]
+    ro = orr.render_hier(orr.Net(spec), wl.rays_o[live], wl.rays_d[live], t0[live].astype(np.float64),
+                         te[live].astype(np.float64))
+    ref = {k: ro[k].detach().numpy() for k in ("rgb", "depth", "wsum", "normal")}
+    sub = {k: v[live] for k, v in got.items()}
+    compare(sub, ref)
+    assert np.all(got["rgb"][~ok] == 0)
