@@ -1,0 +1,446 @@
+#!/usr/bin/env python
+"""Throughput of the TSDF-bounded novel-view render (TSDF-Sampling, arXiv
+2311.17878) on GB300, in rays/s, beside the 64 + 32 hierarchical comparator.
+
+Workload (the indoor-room configuration): 8x6x3 m room with 20 boxes and 4
+thin plates; 256^3 TSDF (D_T = 4 voxels) fused from 100 synthetic 640x480
+depth maps with N(0, 5 mm) noise; SDF network 8x256 (PE L=6, skip at layer 4)
+and colour network 4x256 (direction PE L=4), fitted to the scene; one step =
+one 640x480 novel view (307200 rays): Alg. 1 bounds + offsets scan + sample
+placement + both networks + NeuS compositing, all in the library's kernels.
+Fusion runs once before the timed region and is reported separately.
+
+    python bench.py [--steps K] [--warmup W] [--precision bf16|f32]
+    python bench.py --impl reference     # the CPU oracle on a bounded sample
+
+One JSON line on stdout (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rays/s at PSNR≥oracle−0.1dB, TSDF-bounded vs 96-sample hierarchical, 1 GB300"
+UNIT = "rays/s"
+WORKLOAD = "room 8x6x3m (20 boxes, 4 plates), 256^3 TSDF from 100x640x480 depth maps, 640x480 novel views"
+ALGO_FLOP_PER_SAMPLE = 2.25e6   # SDF fwd + minimal reverse-mode grad + colour, 8x256 / 4x256 networks
+N_VIEWS_TIMED = 10
+QUALITY_PIXELS = 256
+DENSE_SAMPLES = 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["f16", "bf16", "f32"], default="f16")
+    ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--ref-rays", type=int, default=48, help="rays per reference-arm step")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+        self.path = os.path.join("/tmp", f"tsdfs_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2][i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": rows[0][1], "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        if torch.cuda.is_available():
+            torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+def build_scene(device):
+    import torch
+    from paper_2311_17878_gb300 import synth
+    from paper_2311_17878_gb300 import tsdfs as T
+    wl = synth.room_workload_torch(device=device)
+    grid = T.Grid(wl.grid, device=device).init()
+    depth = wl.views.depth.contiguous()
+    K = torch.tensor(wl.views.K, device=device)
+    P = torch.tensor(wl.views.c2w, device=device)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    grid.integrate(depth, K, P)
+    e1.record()
+    torch.cuda.synchronize()
+    fuse_ms = e0.elapsed_time(e1)
+    # re-fuse a second time for a warm timing (fresh grid)
+    grid.init()
+    e0.record()
+    grid.integrate(depth, K, P)
+    e1.record()
+    torch.cuda.synchronize()
+    fuse_ms = min(fuse_ms, e0.elapsed_time(e1))
+    mask = grid.inside_mask(wl.bounds.nb_radius)
+    rays = []
+    for i in range(N_VIEWS_TIMED):
+        o, d = synth.room_heldout_rays(i)
+        rays.append((torch.tensor(o, device=device), torch.tensor(d, device=device), o, d))
+    return wl, grid, mask, rays, fuse_ms, depth
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2311_17878_gb300 import build as B
+    from paper_2311_17878_gb300 import synth
+    from paper_2311_17878_gb300 import tsdfs as T
+    B.build()
+    dev = f"cuda:{local}"
+    wl, grid, mask, rays, fuse_ms, depth = build_scene(dev)
+    bp = wl.bounds
+    spec = synth.scene_mlp("room")
+    prec = args.precision
+    PREC = {"f16": T.TSDFS_PREC_F16, "bf16": T.TSDFS_PREC_BF16, "f32": T.TSDFS_PREC_F32}
+    mlp = T.Mlp(spec, PREC[prec], device=dev)
+    n = rays[0][0].shape[0]
+    max_samples = n * max(bp.n_max, bp.n_fallback)
+    bounds = T.Bounds(n, device=dev)
+    rend = T.Renderer(mlp, n, max_samples, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    def step(i):
+        o, d = rays[i % N_VIEWS_TIMED][:2]
+        bounds.compute(grid, o, d, bp, mask)
+        rend.render(o, d, bounds)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    samples_per_view = []
+    for i in range(N_VIEWS_TIMED):
+        bounds.compute(grid, rays[i][0], rays[i][1], bp, mask)
+        samples_per_view.append(int(bounds.offsets[-1].item()))
+    st = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    T.lib().tsdfs_profile(1)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record(st)
+            step(k)
+            evs[k][1].record(st)
+        torch.cuda.synchronize()
+    barrier(ws)
+    t_wall = time.perf_counter() - t_wall
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    mlp_name = "mlp_simt" if prec == "f32" else "mlp_tc"
+    import ctypes as C
+    ms_k, n_k = C.c_double(0), C.c_int64(0)
+    T.lib().tsdfs_profile_read(mlp_name.encode(), C.byref(ms_k), C.byref(n_k))
+    ms_all, n_all = C.c_double(0), C.c_int64(0)
+    T.lib().tsdfs_profile_read(b"", C.byref(ms_all), C.byref(n_all))
+    T.lib().tsdfs_profile(0)
+    total_ms = max_over_ranks(sum(step_ms), ws)
+    rays_total = n * args.steps * ws
+    value = rays_total / (total_ms / 1e3)
+    samples_timed = sum(samples_per_view[k % N_VIEWS_TIMED] for k in range(args.steps))
+    # dominant kernel roofline (algorithmic FLOPs per launch / mean launch time)
+    hbm, bf16_burst, bf16_sus, peak_src = measured_peaks()
+    mlp_ms = ms_k.value / max(n_k.value, 1)
+    algo_flop_launch = ALGO_FLOP_PER_SAMPLE * samples_timed / max(args.steps, 1)
+    achieved = algo_flop_launch / (mlp_ms / 1e3) / 1e12
+    if prec != "f32":
+        roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_sus, "unit": "TFLOP/s",
+                "frac": achieved / bf16_sus, "traffic": None,
+                "peak_kind": f"bf16 dense sustained ({peak_src}); fp16 dense has the same nominal rate",
+                "kernel": "mlp_tc"}
+    else:
+        fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "peak_kind": "fp32 FMA, 152 SMs x 128 lanes x 2 x 2.07 GHz", "kernel": "mlp_simt"}
+    kernel_share = {"mlp_ms_per_step": mlp_ms, "all_kernels_ms_per_step": ms_all.value / max(args.steps, 1)}
+    # end to end through the public API with host buffers
+    e2e = run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev)
+    # hierarchical comparator on the same views
+    hier = run_hier(args, mlp, grid, rays, bp, n, dev, flush)
+    quality = None if args.no_quality or rank != 0 else run_quality(spec, wl, grid, bounds, rend, hier["renderer"], rays,
+                                                                    bp, mask)
+    cpu = run_cpu_baseline(wl, grid, rays, bp, spec) if (rank == 0 and ws == 1) else None
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": prec, "data": "synthetic (seeded room scene, fitted networks)",
+        "config": {"workload": WORKLOAD, "rays_per_step": n, "views": N_VIEWS_TIMED,
+                   "samples_per_step": samples_timed / args.steps, "grid": "256^3 f32 + uint8",
+                   "networks": "SDF 8x256 PE6 skip4 + colour 4x256 PE4", "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{ws}, rays independent", "wall_s": t_wall},
+        "e2e": e2e, "gpu_launches": int(n_all.value), "roofline": roof, "kernel_time": kernel_share,
+        "comparator": {k: v for k, v in hier.items() if k != "renderer"},
+        "fusion": {"ms": fuse_ms, "voxels_per_s": wl.grid.nx * wl.grid.ny * wl.grid.nz / (fuse_ms / 1e3),
+                   "views": int(depth.shape[0]), "algo_bytes": 256 ** 3 * 10 + depth.numel() * 4,
+                   "GB_per_s": (256 ** 3 * 10 + depth.numel() * 4) / (fuse_ms / 1e3) / 1e9, "peak_hbm_gbs": hbm},
+        "quality": quality, "cpu_baseline": cpu, "clocks": clocks,
+    }
+    return line
+
+
+def run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev):
+    import torch
+    st = torch.cuda.current_stream()
+    h_o = [torch.tensor(r[2]).pin_memory() for r in rays]
+    h_d = [torch.tensor(r[3]).pin_memory() for r in rays]
+    d_o = torch.empty_like(rays[0][0])
+    d_d = torch.empty_like(rays[0][1])
+    h_rgb = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    h_depth = torch.empty(n, dtype=torch.float32).pin_memory()
+
+    def step(k):
+        i = k % N_VIEWS_TIMED
+        d_o.copy_(h_o[i], non_blocking=True)
+        d_d.copy_(h_d[i], non_blocking=True)
+        bounds.compute(grid, d_o, d_d, bp, mask)
+        out = rend.render(d_o, d_d, bounds)
+        h_rgb.copy_(out.rgb, non_blocking=True)
+        h_depth.copy_(out.depth, non_blocking=True)
+
+    for k in range(max(2, args.warmup)):
+        step(k)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for k in range(args.steps):
+        step(k)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": n * args.steps / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": n * 24,
+            "d2h_bytes_per_step": n * 16, "ms_per_step": ms / args.steps}
+
+
+def run_hier(args, mlp, grid, rays, bp, n, dev, flush):
+    import torch
+    from paper_2311_17878_gb300 import tsdfs as T
+    h = T.HierRenderer(mlp, n, device=dev)
+    for i in range(2):
+        h.render(grid, rays[i][0], rays[i][1], bp.t_near, bp.t_far)
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 6))
+    st = torch.cuda.current_stream()
+    tot = 0.0
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        h.render(grid, rays[k % N_VIEWS_TIMED][0], rays[k % N_VIEWS_TIMED][1], bp.t_near, bp.t_far)
+        e1.record(st)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return {"impl": "hier 64+32 (same GPU, same network engine)", "value": n * steps / (tot / 1e3), "unit": UNIT,
+            "ms_per_step": tot / steps, "samples_per_ray": 96 + 64 * 0, "renderer": h}
+
+
+def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask):
+    """PSNR against the oracle's dense reference (FP64, DENSE_SAMPLES midpoints
+    over [t0, t_end]) on a seeded pixel subset of view 0."""
+    import torch
+    from oracle import cgrid
+    from oracle import render as orr
+    from paper_2311_17878_gb300 import synth
+    o, d = rays[0][0], rays[0][1]
+    bounds.compute(grid, o, d, bp, mask)
+    out = rend.render(o, d, bounds)
+    hout = hier.render(grid, o, d, bp.t_near, bp.t_far)
+    torch.cuda.synchronize()
+    idx = synth.sub_sample(o.shape[0], QUALITY_PIXELS, seed=31)
+    idx_t = torch.as_tensor(idx, device=o.device)
+    gpu_rgb = out.rgb[idx_t].cpu().numpy()
+    hier_rgb = hout.rgb[idx_t].cpu().numpy()
+    on, dn = rays[0][2][idx], rays[0][3][idx]
+    t0, te, ok = cgrid.clip_rays(wl.grid, on, dn, bp.t_near, bp.t_far, "f64")
+    t_q = time.perf_counter()
+    net = orr.Net(spec)
+    dense = orr.dense_reference(net, on, dn, t0, te, n=DENSE_SAMPLES)["rgb"].numpy()
+    tn = bounds.t_n[idx_t].cpu().numpy().astype(np.float64)
+    tf = bounds.t_f[idx_t].cpu().numpy().astype(np.float64)
+    cnt = bounds.n[idx_t].cpu().numpy()
+    with torch.no_grad():
+        ort = orr.render_bounded(net, on, dn, tn, tf, cnt)["rgb"].numpy()
+    p_gpu, p_or, p_h = orr.psnr(gpu_rgb, dense), orr.psnr(ort, dense), orr.psnr(hier_rgb, dense)
+    return {"pixels": QUALITY_PIXELS, "reference": f"oracle FP64 dense {DENSE_SAMPLES} samples over [t0,t_end]",
+            "psnr_tsdf_gpu": p_gpu, "psnr_tsdf_oracle": p_or, "psnr_hier96_gpu": p_h,
+            "meets_oracle_minus_0p1dB": bool(p_gpu >= p_or - 0.1),
+            "samples_per_ray_tsdf": float(bounds.n.float().mean().item()),
+            "fallback_frac": float((bounds.status == 2).float().mean().item()), "oracle_s": time.perf_counter() - t_q}
+
+
+def run_cpu_baseline(wl, grid, rays, bp, spec, n_rays=64):
+    """The oracle as it stands, on the host cores: Alg. 1 bounds (C, fp32-exact)
+    + FP64 render (torch CPU) of a seeded sample of view-0 rays on the fused grid."""
+    import torch
+    from oracle import cgrid
+    from oracle import render as orr
+    from paper_2311_17878_gb300 import synth
+    V = grid.V.cpu().numpy()
+    idx = synth.sub_sample(rays[0][2].shape[0], n_rays, seed=32)
+    o, d = rays[0][2][idx], rays[0][3][idx]
+    net = orr.Net(spec)
+    t = time.perf_counter()
+    b = cgrid.ray_bounds(wl.grid, V, o, d, bp, "f32")
+    with torch.no_grad():
+        orr.render_bounded(net, o, d, b["t_n"].astype(np.float64), b["t_f"].astype(np.float64), b["n"])
+    dt = time.perf_counter() - t
+    return {"value": n_rays / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{n_rays} seeded rays of one 640x480 view: C bounds (1 thread) + torch FP64 render",
+            "seconds": dt}
+
+
+# ----------------------------------------------------------------------------
+def run_reference(args, ws, rank):
+    """The CPU oracle as the reference arm: each step renders a bounded sample of
+    the same workload (ref_rays seeded rays of a held-out view)."""
+    import torch
+    if rank != 0:
+        return None
+    from oracle import cgrid
+    from oracle import render as orr
+    from paper_2311_17878_gb300 import synth
+    t_setup = time.perf_counter()
+    wl = synth.room_workload_torch(device="cpu")
+    views = synth.Views(wl.views.K, wl.views.c2w, wl.views.depth.numpy(), 640, 480)
+    V, _ = cgrid.integrate_projective(wl.grid, views, "f32")
+    spec = synth.scene_mlp("room")
+    net = orr.Net(spec)
+    t_setup = time.perf_counter() - t_setup
+    bp = wl.bounds
+
+    def step(k):
+        o, d = synth.room_heldout_rays(k % N_VIEWS_TIMED)
+        idx = synth.sub_sample(len(o), args.ref_rays, seed=40 + k)
+        b = cgrid.ray_bounds(wl.grid, V, o[idx], d[idx], bp, "f32")
+        with torch.no_grad():
+            orr.render_bounded(net, o[idx], d[idx], b["t_n"].astype(np.float64), b["t_f"].astype(np.float64), b["n"])
+
+    for k in range(args.warmup):
+        step(k)
+    t = time.perf_counter()
+    for k in range(args.steps):
+        step(k)
+    dt = time.perf_counter() - t
+    value = args.ref_rays * args.steps / dt
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded room scene, fitted networks)", "impl": "reference",
+            "config": {"workload": WORKLOAD, "rays_per_step": args.ref_rays, "setup_s": t_setup},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": f"{args.ref_rays} seeded rays of a 640x480 view per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        line = run_reference(args, ws, rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    ws, rank, local = dist_setup()
+    line = run_ours(args, ws, rank, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -46,6 +46,7 @@ typedef struct CUstream_st* tsdfs_stream_t; /* identical to cudaStream_t */
 /* device status bits reported by tsdfs_sync_status() */
 #define TSDFS_DEV_SAMPLES_OVERFLOW 1u /* offsets[n_rays] exceeded max_samples   */
 #define TSDFS_DEV_MARCH_CAP 2u        /* a ray hit the voxel-step cap            */
+#define TSDFS_DEV_TIMEOUT 4u          /* a bounded wait in a pipelined kernel expired */
 
 /* ---- TSDF grid (Sec. 3.2; Sec. A.1: V initialised to -1 = unseen, W to 0) -
  * tsdf holds s / D_T in [-1, 1] (normalised truncated signed distance), as
@@ -100,6 +101,7 @@ typedef struct {
 #define TSDFS_ARCH_ROOM 1
 #define TSDFS_PREC_F32 0  /* FP32 SIMT networks                                  */
 #define TSDFS_PREC_BF16 1 /* BF16 tcgen05 networks, FP32 accumulate (packed required) */
+#define TSDFS_PREC_F16 2  /* FP16 operands on the same tcgen05 path (packed required)  */
 typedef struct {
     int32_t arch;
     int32_t precision;
@@ -179,7 +181,8 @@ int tsdf_ray_bounds(const tsdfs_grid* grid, const uint32_t* inside_mask, const f
  * eik (nullable): per-ray sum over samples of (|grad f| - 1)^2, written only
  * for BOUNDED rays (0 otherwise).  normal may be NULL.
  * max_samples bounds offsets[n_rays]; workspace >= tsdfs_render_workspace_size.
- * precision TSDFS_PREC_BF16 needs mlp->packed from tsdfs_pack_mlp.          */
+ * precision TSDFS_PREC_BF16 / TSDFS_PREC_F16 needs mlp->packed from
+ * tsdfs_pack_mlp (packed for that precision).                               */
 size_t tsdfs_render_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays, int64_t max_samples);
 int render_rays(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n, const float* t_f,
                 const int32_t* offsets, const uint8_t* status, int64_t n_rays, int64_t max_samples, float* rgb,
@@ -212,9 +215,10 @@ int render_rays_backward(const tsdfs_mlp* mlp, const float* ray_o, const float* 
                          float* d_sdf_w, float* d_rgb_w, void* workspace, size_t ws_bytes, tsdfs_stream_t stream);
 
 /* ---- BF16 tensor-core parameter layout --------------------------------------
- * tsdfs_pack_mlp converts sdf_w / rgb_w to the bf16 K-major tiles the tcgen05
- * path reads (rounded to nearest even), into `packed` (device,
- * tsdfs_packed_size bytes).  Repeat after every parameter update.            */
+ * tsdfs_pack_mlp converts sdf_w / rgb_w to the 16-bit K-major tiles the
+ * tcgen05 path reads -- bf16, or fp16 when mlp->precision is TSDFS_PREC_F16 --
+ * rounded to nearest even, into `packed` (device, tsdfs_packed_size bytes,
+ * 16-byte aligned).  Repeat after every parameter update.                    */
 size_t tsdfs_packed_size(int32_t arch);
 int tsdfs_pack_mlp(const tsdfs_mlp* mlp, void* packed, tsdfs_stream_t stream);
 

@@ -119,13 +119,13 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 static int mlp_check(const tsdfs_mlp* m) {
     if (!m) return fail(TSDFS_E_INVALID, "mlp is NULL");
     if (m->arch != TSDFS_ARCH_TINY && m->arch != TSDFS_ARCH_ROOM) return fail(TSDFS_E_INVALID, "unknown arch %d", m->arch);
-    if (m->precision != TSDFS_PREC_F32 && m->precision != TSDFS_PREC_BF16)
+    if (m->precision != TSDFS_PREC_F32 && m->precision != TSDFS_PREC_BF16 && m->precision != TSDFS_PREC_F16)
         return fail(TSDFS_E_INVALID, "unknown precision %d", m->precision);
     if (!m->sdf_w || !m->rgb_w) return fail(TSDFS_E_INVALID, "sdf_w and rgb_w must be non-NULL");
     if (!(m->scale > 0.0f) || !(m->beta > 0.0f) || !(m->inv_s > 0.0f) || !(m->alpha_eps >= 0.0f))
         return fail(TSDFS_E_INVALID, "scale, beta and inv_s must be > 0, alpha_eps >= 0");
-    if (m->precision == TSDFS_PREC_BF16) {
-        if (!m->packed) return fail(TSDFS_E_INVALID, "BF16 precision needs packed weights (tsdfs_pack_mlp)");
+    if (m->precision != TSDFS_PREC_F32) {
+        if (!m->packed) return fail(TSDFS_E_INVALID, "16-bit precisions need packed weights (tsdfs_pack_mlp)");
         if (!mlp_tc_available(m->arch)) return fail(TSDFS_E_UNSUPPORTED, "BF16 tensor-core path not available for arch %d", m->arch);
     }
     return TSDFS_OK;
@@ -144,7 +144,7 @@ static NetParams net_params(const tsdfs_mlp* m) {
 
 static int run_full_mlp(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64_t max_samples,
                         cudaStream_t st) {
-    if (m->precision == TSDFS_PREC_BF16) {
+    if (m->precision != TSDFS_PREC_F32) {
         ProfScope ps("mlp_tc", st);
         return launch_mlp_full_tc(m, src, rec, max_samples, st);
     }

@@ -1,25 +1,687 @@
-// BF16 tensor-core (tcgen05) evaluation of the networks: not built yet.
+// BF16 tensor-core (tcgen05) evaluation of the SDF and colour networks.
+//
+// Tile: 64 samples.  The SDF gradient is carried in forward mode as tangent
+// rows.  Two M = 128 accumulators live in tensor memory (TMEM, 2 x 256 fp32
+// columns):  acc0 = [value | d/dx] rows, acc1 = [d/dy | d/dz] rows, laid out
+// so that TMEM lane quarter q holds samples 16q..16q+15: lanes 0-15 of the
+// quarter are the value (acc0) / d/dy (acc1) rows, lanes 16-31 the d/dx (acc0)
+// / d/dz (acc1) rows.  Every warp therefore owns 16 value rows, which spreads
+// the softplus / sigmoid work over all four SM sub-partitions, and the slope
+// sigma(beta z) reaches the tangent rows of the same sample with one
+// shuffle (lane l <-> l + 16).  Activations (bf16) are the A operands in
+// shared memory, written by the epilogue in the no-swizzle K-major
+// core-matrix layout; weights are pre-packed in the same layout
+// (tsdfs_pack_mlp) and streamed chunk by chunk (64 columns of K) with 1-D bulk
+// TMA copies through a two-stage ring.  The colour network reuses acc0 with
+// the value rows only.
+//
+// Warp roles (320 threads): warps 0-7 epilogue (warp w: TMEM lane quarter
+// w % 4, column half w / 4), warp 8 lane 0 TMA producer, warp 9 lane 0 MMA
+// issuer (warp 9 also allocates / frees TMEM).  All hand-offs are mbarriers;
+// every wait is bounded and on timeout the kernel records TSDFS_DEV_TIMEOUT,
+// drains its own copies / MMAs and returns.
 #include "common.cuh"
 
 namespace tsdfs {
-int mlp_tc_available(int arch) {
-    (void)arch;
-    return 0;
+
+namespace {
+
+// --------------------------------------------------------------------------
+// layer tables
+// --------------------------------------------------------------------------
+constexpr int kTileS = 64;        // samples per tile
+constexpr int kKChunk = 64;       // K columns per weight stage
+constexpr int kEpiThreads = 256;  // warps 0-7
+constexpr int kThreads = 320;
+constexpr uint32_t kABytes = 64 * 1024;   // one A region (128 rows x 256 bf16)
+constexpr uint32_t kMaxSpin = 1u << 26;
+
+struct TcLayer {
+    int K, Kp, N, Np;
+    bool sdf;
+    int idx;          // index within its network
+};
+
+__host__ __device__ constexpr int pad16(int x) { return (x + 15) / 16 * 16; }
+// column range [lo, hi) of a K-wide operand row written by column half hf:
+// the split is rounded up to 16 so every 16-column block stays inside K
+__host__ __device__ constexpr int half_lo(int K, int hf) { return hf ? pad16(K / 2) : 0; }
+__host__ __device__ constexpr int half_hi(int K, int hf) { return hf ? K : pad16(K / 2); }
+
+template <int ARCH> struct TcArch {
+    using A = Arch<ARCH>;
+    static constexpr int kLayers = A::kSdfLayers + A::kRgbLayers;
+    __host__ __device__ static constexpr TcLayer layer(int L) {
+        if (L < A::kSdfLayers) {
+            const Layer l = A::sdf(L);
+            return TcLayer{l.in, pad16(l.in), l.out, pad16(l.out), true, L};
+        }
+        const Layer l = A::rgb(L - A::kSdfLayers);
+        return TcLayer{l.in, pad16(l.in), l.out, pad16(l.out), false, L - A::kSdfLayers};
+    }
+    __host__ __device__ static constexpr int chunks(int L) { return (layer(L).Kp + kKChunk - 1) / kKChunk; }
+    __host__ __device__ static constexpr int chunk_k(int L, int c) {
+        return layer(L).Kp - c * kKChunk < kKChunk ? layer(L).Kp - c * kKChunk : kKChunk;
+    }
+    __host__ __device__ static constexpr int64_t chunk_bytes(int L, int c) { return (int64_t)layer(L).Np * chunk_k(L, c) * 2; }
+    __host__ __device__ static constexpr int64_t packed_offset(int L, int c) {
+        int64_t off = 0;
+        for (int l = 0; l < L; ++l)
+            for (int cc = 0; cc < chunks(l); ++cc) off += chunk_bytes(l, cc);
+        for (int cc = 0; cc < c; ++cc) off += chunk_bytes(L, cc);
+        return off;
+    }
+    __host__ __device__ static constexpr int64_t packed_bytes() { return packed_offset(kLayers, 0); }
+    __host__ __device__ static constexpr int64_t param_offset(int L) {
+        return L < A::kSdfLayers ? sdf_layer_offset<ARCH>(L) : rgb_layer_offset<ARCH>(L - A::kSdfLayers);
+    }
+    __host__ __device__ static constexpr uint32_t stage_bytes() {
+        int64_t m = 0;
+        for (int l = 0; l < kLayers; ++l)
+            for (int c = 0; c < chunks(l); ++c) m = chunk_bytes(l, c) > m ? chunk_bytes(l, c) : m;
+        return (uint32_t)m;
+    }
+};
+
+// --------------------------------------------------------------------------
+// PTX helpers
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
-int launch_mlp_full_tc(const tsdfs_mlp*, const SampleSource&, SampleRec*, int64_t, cudaStream_t) {
-    return fail(TSDFS_E_UNSUPPORTED, "BF16 tensor-core path not built");
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false on timeout or when another role aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 255u && *abort_flag) return false;
+        if (it > kMaxSpin) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: no swizzle, K-major core matrices (8 rows x 16 B)
+__device__ __forceinline__ uint64_t mdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    return d;
+}
+// instruction descriptor: (BF16 | F16) x same -> FP32, both K-major
+template <bool F16>
+__host__ __device__ constexpr uint32_t idesc_mma(int M, int N) {
+    return (1u << 4) | ((F16 ? 0u : 1u) << 7) | ((F16 ? 0u : 1u) << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// element (r, k) of a K-major no-swizzle operand with Kp columns -> byte offset
+__device__ __forceinline__ uint32_t a_off(int r, int k, int Kp) {
+    return (uint32_t)(((r >> 3) * (Kp >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+template <bool F16>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+    if constexpr (F16) {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    } else {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+}
+// store 8 consecutive columns (k0 multiple of 8) of row r
+template <bool F16>
+__device__ __forceinline__ void st_row8(uint8_t* base, int r, int k0, int Kp, const float* v) {
+    uint4 q;
+    q.x = pack2<F16>(v[0], v[1]);
+    q.y = pack2<F16>(v[2], v[3]);
+    q.z = pack2<F16>(v[4], v[5]);
+    q.w = pack2<F16>(v[6], v[7]);
+    *reinterpret_cast<uint4*>(base + a_off(r, k0, Kp)) = q;
+}
+
+// softplus_beta(z) and its slope sigma(beta z), linear branch for beta z > 20
+__device__ __forceinline__ void softplus_pair(float z, float beta, float inv_beta, float& h, float& sg) {
+    const float bz = beta * z;
+    if (bz > 20.0f) {
+        h = z;
+        sg = 1.0f;
+    } else {
+        const float e = __expf(-fabsf(bz));
+        const float r = __fdividef(1.0f, 1.0f + e);
+        h = (fmaxf(bz, 0.0f) + __logf(1.0f + e)) * inv_beta;
+        sg = bz >= 0.0f ? r : e * r;
+    }
+}
+
+// positional encoding entry j of coordinate vector xt, and its derivative along axis a
+__device__ __forceinline__ float enc_val(const float* xt, int j, int pe, int a, bool deriv) {
+    if (j < 3) return deriv ? (j == a ? 1.0f : 0.0f) : xt[j];
+    const int q = j - 3;
+    const int oct = q / 6, part = (q % 6) / 3, b = q % 3;
+    if (oct >= pe) return 0.0f;
+    if (deriv && b != a) return 0.0f;
+    const float f = (float)(1 << oct);
+    float sn, cs;
+    sincosf(f * xt[b], &sn, &cs);
+    if (!deriv) return part == 0 ? sn : cs;
+    return part == 0 ? f * cs : -f * sn;
+}
+
+struct TcParams {
+    const uint8_t* packed;
+    const float* sdf_w;
+    const float* rgb_w;
+    float center[3];
+    float inv_scale, scale, beta;
+    SampleSource src;
+    SampleRec* rec;
+    uint32_t* status;
+};
+
+template <int ARCH, bool F16>
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
+    using TA = TcArch<ARCH>;
+    using A = Arch<ARCH>;
+    constexpr int NL = TA::kLayers;
+    constexpr int LS = A::kSdfLayers;
+    constexpr uint32_t kStage = TA::stage_bytes();
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* A0 = smem;
+    uint8_t* A1 = smem + kABytes;
+    uint8_t* stage_base = smem + 2 * kABytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage_base + 2 * kStage);
+    // bars: full[2], empty[2], acc_ready, a_ready, drain
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const uint32_t bar_full0 = smem_u32(bars + 0), bar_empty0 = smem_u32(bars + 2);
+    const uint32_t bar_acc = smem_u32(bars + 4), bar_a = smem_u32(bars + 5), bar_drain = smem_u32(bars + 6);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const int64_t total = p.src.mode == kUniform ? (int64_t)__ldg(p.src.total_dev) : p.src.total_host;
+    if (total > p.src.capacity) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(p.status, TSDFS_DEV_SAMPLES_OVERFLOW);
+        return;
+    }
+    const int64_t n_tiles = (total + kTileS - 1) / kTileS;
+    if ((int64_t)blockIdx.x >= n_tiles) return;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar_full0, 1);
+        mbar_init(bar_full0 + 8, 1);
+        mbar_init(bar_empty0, 1);
+        mbar_init(bar_empty0 + 8, 1);
+        mbar_init(bar_acc, 1);
+        mbar_init(bar_a, kEpiThreads);
+        mbar_init(bar_drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 9) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 8) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            uint32_t seq = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                for (int L = 0; L < NL && ok; ++L) {
+                    for (int c = 0; c < TA::chunks(L); ++c) {
+                        const uint32_t s = seq & 1u, ph = (seq >> 1) & 1u;
+                        if (!mbar_wait(bar_empty0 + 8 * s, ph ^ 1u, abort_flag)) { ok = false; break; }
+                        const uint32_t bytes = (uint32_t)TA::chunk_bytes(L, c);
+                        mbar_expect_tx(bar_full0 + 8 * s, bytes);
+                        bulk_g2s(smem_u32(stage_base + s * kStage), p.packed + TA::packed_offset(L, c), bytes,
+                                 bar_full0 + 8 * s);
+                        ++seq;
+                    }
+                }
+            }
+            if (!ok) {
+                // let the copies already issued land before the CTA exits
+                for (uint32_t k = (seq >= 2 ? seq - 2 : 0); k < seq; ++k) {
+                    for (uint32_t it = 0; it < kMaxSpin && !mbar_try(bar_full0 + 8 * (k & 1u), (k >> 1) & 1u); ++it) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 9) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t seq = 0, lc = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                for (int L = 0; L < NL && ok; ++L, ++lc) {
+                    const TcLayer ly = TA::layer(L);
+                    if (!mbar_wait(bar_a, lc & 1u, abort_flag)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a_sbo = (uint32_t)(ly.Kp / 8) * 128u;
+                    const uint32_t a0 = smem_u32(A0), a1 = smem_u32(A1);
+                    const bool last_sdf = ly.sdf && ly.idx == LS - 1;
+                    for (int c = 0; c < TA::chunks(L); ++c) {
+                        const uint32_t s = seq & 1u, ph = (seq >> 1) & 1u;
+                        if (!mbar_wait(bar_full0 + 8 * s, ph, abort_flag)) { ok = false; break; }
+                        tc_fence_after();
+                        const int kc = TA::chunk_k(L, c);
+                        const uint32_t b0 = smem_u32(stage_base + s * kStage);
+                        const uint32_t b_sbo = (uint32_t)(kc / 8) * 128u;
+                        for (int kk = 0; kk < kc / 16; ++kk) {
+                            const int k = c * kKChunk + kk * 16;
+                            const uint32_t acc = k > 0 ? 1u : 0u;
+                            const uint64_t bd = mdesc(b0 + kk * 256, 128, b_sbo);
+                            const uint64_t ad0 = mdesc(a0 + (uint32_t)(k / 8) * 128u, 128, a_sbo);
+                            if (ly.sdf) {
+                                const uint64_t ad1 = mdesc(a1 + (uint32_t)(k / 8) * 128u, 128, a_sbo);
+                                if (!last_sdf) {
+                                    mma_bf16(tmem, ad0, bd, idesc_mma<F16>(128, ly.Np), acc);
+                                    mma_bf16(tmem + 256, ad1, bd, idesc_mma<F16>(128, ly.Np), acc);
+                                } else {
+                                    const int n0 = ly.Np < 256 ? ly.Np : 256;
+                                    mma_bf16(tmem, ad0, bd, idesc_mma<F16>(128, n0), acc);
+                                    mma_bf16(tmem + 256, ad1, bd, idesc_mma<F16>(128, 16), acc);
+                                    if (ly.Np > 256) {
+                                        const uint64_t bx = mdesc(b0 + kk * 256 + (256 / 8) * b_sbo, 128, b_sbo);
+                                        mma_bf16(tmem + 256 + 16, ad0, bx, idesc_mma<F16>(128, ly.Np - 256), acc);
+                                    }
+                                }
+                            } else {
+                                mma_bf16(tmem, ad0, bd, idesc_mma<F16>(128, ly.Np), acc);
+                            }
+                        }
+                        mma_commit(bar_empty0 + 8 * s);
+                        ++seq;
+                    }
+                    if (!ok) break;
+                    mma_commit(bar_acc);
+                }
+            }
+            if (!ok) {
+                // wait for every MMA issued so far before TMEM is released
+                mma_commit(bar_drain);
+                for (uint32_t it = 0; it < kMaxSpin && !mbar_try(bar_drain, 0); ++it) {
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int q = warp & 3, hf = warp >> 2;
+        const bool is_val = lane < 16;
+        const int r = 32 * q + lane;                  // TMEM lane / A row of this thread
+        const int s = 16 * q + (lane & 15);           // sample within the tile
+        const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
+        const float beta = p.beta, inv_beta = 1.0f / p.beta;
+        const float kInvSqrt2 = 0.70710678118654752f;
+        uint32_t lc = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            // ---- this row's sample ----
+            const int64_t g = tile * kTileS + s;
+            const bool valid = g < total;
+            float t = 0.0f, dl = 0.0f;
+            int64_t ray = 0;
+            if (valid) {
+                if (p.src.mode == kUniform) {
+                    ray = find_ray(p.src.offsets, p.src.n_rays, g);
+                    const int32_t o0 = __ldg(p.src.offsets + ray), o1 = __ldg(p.src.offsets + ray + 1);
+                    const float tn = __ldg(p.src.t_n + ray), tf = __ldg(p.src.t_f + ray);
+                    dl = (tf - tn) / (float)(o1 - o0);
+                    t = tn + ((float)(g - o0) + 0.5f) * dl;
+                } else {
+                    ray = g / p.src.per_ray;
+                    t = __ldg(p.src.t + g);
+                    dl = __ldg(p.src.delta + g);
+                }
+            }
+            float xt[3], dir[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float o = valid ? __ldg(p.src.ray_o + 3 * ray + a) : 0.0f;
+                dir[a] = valid ? __ldg(p.src.ray_d + 3 * ray + a) : 0.0f;
+                xt[a] = (o + t * dir[a] - p.center[a]) * p.inv_scale;
+            }
+            // ---- layer-0 input: encoding (A0: value | d/dx, A1: d/dy | d/dz) ----
+            {
+                constexpr int Kp0 = TA::layer(0).Kp;
+                const int a0_axis = 0, a1_axis = is_val ? 1 : 2;
+                for (int k0 = hf * (Kp0 / 2); k0 < (hf + 1) * (Kp0 / 2); k0 += 8) {
+                    float v0[8], v1[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int k = k0 + j;
+                        const bool in = k < A::kEnc;
+                        v0[j] = in ? enc_val(xt, k, A::kPeSdf, a0_axis, !is_val) : 0.0f;
+                        v1[j] = in ? enc_val(xt, k, A::kPeSdf, a1_axis, true) : 0.0f;
+                    }
+                    st_row8<F16>(A0, r, k0, Kp0, v0);
+                    st_row8<F16>(A1, r, k0, Kp0, v1);
+                }
+            }
+            fence_proxy_async();
+            mbar_arrive(bar_a);
+            float f_out = 0.0f, dd_out = 0.0f, gn_out = 0.0f, nrm[3] = {0.0f, 0.0f, 0.0f};
+            for (int L = 0; L < NL; ++L, ++lc) {
+                const TcLayer ly = TA::layer(L);
+                const bool w_ok = mbar_wait(bar_acc, lc & 1u, abort_flag);
+                if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
+                tc_fence_after();
+                const float* W = (ly.sdf ? p.sdf_w : p.rgb_w) + TA::param_offset(L);
+                const float* bias = W + (int64_t)ly.N * ly.K;
+                const bool last = L == NL - 1;
+                if (ly.sdf && ly.idx < LS - 1) {
+                    // hidden SDF layer -> next layer's input (with the skip concat when due)
+                    const int Kn = TA::layer(L + 1).Kp;
+                    const bool skip_next = ly.idx + 1 == A::kSkip;
+                    const float sc = skip_next ? kInvSqrt2 : 1.0f;
+                    for (int c0 = half_lo(Kn, hf); c0 < half_hi(Kn, hf); c0 += 16) {
+                        float x0[16], x1[16];
+                        if (c0 < ly.Np) {
+                            tmem_ld16(tmem + lane_addr + c0, x0);
+                            tmem_ld16(tmem + 256 + lane_addr + c0, x1);
+                            tmem_wait_ld();
+                        }
+                        float o0[16], o1[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int col = c0 + j;
+                            float h = 0.0f, sg = 0.0f;
+                            if (col < ly.N) {
+                                if (is_val) softplus_pair(x0[j] + __ldg(bias + col), beta, inv_beta, h, sg);
+                                const float sgx = __shfl_xor_sync(0xffffffffu, sg, 16);
+                                if (is_val) {
+                                    o0[j] = h * sc;
+                                    o1[j] = sg * x1[j] * sc;
+                                } else {
+                                    o0[j] = sgx * x0[j] * sc;
+                                    o1[j] = sgx * x1[j] * sc;
+                                }
+                            } else {
+                                // skip input: gamma(x~) / sqrt(2) after the hidden units
+                                const int e = col - ly.N;
+                                const bool in = e < A::kEnc;
+                                o0[j] = in ? enc_val(xt, e, A::kPeSdf, 0, !is_val) * sc : 0.0f;
+                                o1[j] = in ? enc_val(xt, e, A::kPeSdf, is_val ? 1 : 2, true) * sc : 0.0f;
+                            }
+                        }
+                        st_row8<F16>(A0, r, c0, Kn, o0);
+                        st_row8<F16>(A0, r, c0 + 8, Kn, o0 + 8);
+                        st_row8<F16>(A1, r, c0, Kn, o1);
+                        st_row8<F16>(A1, r, c0 + 8, Kn, o1 + 8);
+                    }
+                } else if (ly.sdf) {
+                    // output layer: f, grad f, feature -> colour input rows (value lanes)
+                    const int Kc = TA::layer(L + 1).Kp;
+                    constexpr int kDir = A::kDirEnc;
+                    constexpr int kFeatCol = 3 + kDir + 3;  // colour column of feature 0
+                    float n_hat[3] = {0.0f, 0.0f, 0.0f};
+                    if (hf == 0) {
+                        float x0[16], x1[16];
+                        tmem_ld16(tmem + lane_addr, x0);
+                        tmem_ld16(tmem + 256 + lane_addr, x1);
+                        tmem_wait_ld();
+                        const float gx = __shfl_xor_sync(0xffffffffu, x0[0], 16);
+                        const float gz = __shfl_xor_sync(0xffffffffu, x1[0], 16);
+                        const float gy = x1[0];
+                        if (is_val) {
+                            f_out = p.scale * (x0[0] + __ldg(bias));
+                            gn_out = sqrtf(gx * gx + gy * gy + gz * gz);
+                            const float inv = gn_out > 0.0f ? 1.0f / gn_out : 0.0f;
+                            n_hat[0] = gx * inv; n_hat[1] = gy * inv; n_hat[2] = gz * inv;
+                            nrm[0] = n_hat[0]; nrm[1] = n_hat[1]; nrm[2] = n_hat[2];
+                            dd_out = gx * dir[0] + gy * dir[1] + gz * dir[2];
+                        }
+                    }
+                    // colour input columns of this half: [x~, dir enc, n^, feature, pad]
+                    const int lo = half_lo(Kc, hf), hi = half_hi(Kc, hf);
+                    for (int c0 = lo; c0 < hi; c0 += 16) {
+                        // feature j = network output j + 1 = accumulator column j + 1; outputs
+                        // >= 256 live in acc1 from column 16.  Load the two 16-column
+                        // accumulator blocks covering outputs [c0 - kFeatCol + 1, +16).
+                        const int f_lo = c0 - kFeatCol + 1;
+                        const int cap = (ly.Np < 256 ? ly.Np : 256) - 32;
+                        int w0c = f_lo < 0 ? 0 : (f_lo & ~15);
+                        w0c = w0c > cap ? cap : w0c;
+                        float xa[16], xb[16], xe[16];
+                        tmem_ld16(tmem + lane_addr + w0c, xa);
+                        tmem_ld16(tmem + lane_addr + w0c + 16, xb);
+                        tmem_ld16(tmem + 256 + lane_addr + 16, xe);
+                        tmem_wait_ld();
+                        float o[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int col = c0 + j;
+                            float v = 0.0f;
+                            if (col < 3) v = xt[col];
+                            else if (col < 3 + kDir) {
+                                const int e = col - 3;
+                                v = A::kPeDir == 0 ? dir[e] : enc_val(dir, e, A::kPeDir, 0, false);
+                            } else if (col < kFeatCol) v = n_hat[col - 3 - kDir];
+                            else if (col < kFeatCol + A::kFeat) {
+                                const int oc = col - kFeatCol + 1;  // output column
+                                float acc;
+                                if (oc >= 256) acc = xe[(oc - 256) & 15];
+                                else if (oc - w0c < 16) acc = xa[(oc - w0c) & 15];
+                                else acc = xb[(oc - w0c - 16) & 15];
+                                v = acc + __ldg(bias + oc);
+                            }
+                            o[j] = v;
+                        }
+                        if (is_val) {
+                            st_row8<F16>(A0, r, c0, Kc, o);
+                            st_row8<F16>(A0, r, c0 + 8, Kc, o + 8);
+                        }
+                    }
+                } else if (!last) {
+                    // hidden colour layer (ReLU), value rows only
+                    const int Kn = TA::layer(L + 1).Kp;
+                    for (int c0 = half_lo(Kn, hf); c0 < half_hi(Kn, hf); c0 += 16) {
+                        float x0[16];
+                        tmem_ld16(tmem + lane_addr + c0, x0);
+                        tmem_wait_ld();
+                        float o[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int col = c0 + j;
+                            o[j] = col < ly.N ? fmaxf(x0[j] + __ldg(bias + col), 0.0f) : 0.0f;
+                        }
+                        if (is_val) {
+                            st_row8<F16>(A0, r, c0, Kn, o);
+                            st_row8<F16>(A0, r, c0 + 8, Kn, o + 8);
+                        }
+                    }
+                } else {
+                    // colour output (sigmoid) -> record
+                    if (hf == 0) {
+                        float x0[16];
+                        tmem_ld16(tmem + lane_addr, x0);
+                        tmem_wait_ld();
+                        if (is_val && valid) {
+                            SampleRec& R = p.rec[g];
+                            float4* R4 = reinterpret_cast<float4*>(&R);
+                            const float cr = __fdividef(1.0f, 1.0f + __expf(-(x0[0] + __ldg(bias + 0))));
+                            const float cg = __fdividef(1.0f, 1.0f + __expf(-(x0[1] + __ldg(bias + 1))));
+                            const float cb = __fdividef(1.0f, 1.0f + __expf(-(x0[2] + __ldg(bias + 2))));
+                            R4[0] = make_float4(f_out, dd_out, t, dl);
+                            R4[1] = make_float4(cr, cg, cb, gn_out);
+                            R4[2] = make_float4(nrm[0], nrm[1], nrm[2], 0.0f);
+                        }
+                    }
+                }
+                tc_fence_before();
+                if (!last) {
+                    fence_proxy_async();
+                    mbar_arrive(bar_a);
+                }
+            }
+        }
+        if (!ok) set_status(p.status, TSDFS_DEV_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 9) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    }
+}
+
+// ---- pack fp32 [N][K] weights into the bf16 chunked core-matrix layout ----
+template <int ARCH, bool F16>
+__global__ void k_pack(const float* __restrict__ sdf_w, const float* __restrict__ rgb_w, uint16_t* __restrict__ out) {
+    using TA = TcArch<ARCH>;
+    const int64_t total = TA::packed_bytes() / 2;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        // locate the (layer, chunk) holding element e
+        int L = 0, c = 0;
+        int64_t base = 0;
+        bool found = false;
+        for (int l = 0; l < TA::kLayers && !found; ++l)
+            for (int cc = 0; cc < TA::chunks(l); ++cc) {
+                const int64_t n = TA::chunk_bytes(l, cc) / 2;
+                if (e < base + n) { L = l; c = cc; found = true; break; }
+                base += n;
+            }
+        const TcLayer ly = TA::layer(L);
+        const int kc = TA::chunk_k(L, c);
+        const int64_t w = e - base;
+        const int core = (int)(w / 64), within = (int)(w % 64);
+        const int n = (core / (kc / 8)) * 8 + within / 8;
+        const int k = c * kKChunk + (core % (kc / 8)) * 8 + within % 8;
+        const float* W = (ly.sdf ? sdf_w : rgb_w) + TA::param_offset(L);
+        const float v = (n < ly.N && k < ly.K) ? W[(int64_t)n * ly.K + k] : 0.0f;
+        if constexpr (F16) {
+            __half h = __float2half_rn(v);
+            out[e] = *reinterpret_cast<uint16_t*>(&h);
+        } else {
+            __nv_bfloat16 h = __float2bfloat16_rn(v);
+            out[e] = *reinterpret_cast<uint16_t*>(&h);
+        }
+    }
+}
+
+template <int ARCH, bool F16>
+int launch_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64_t max_samples, cudaStream_t st) {
+    using TA = TcArch<ARCH>;
+    const size_t smem = 2 * kABytes + 2 * (size_t)TA::stage_bytes() + 128;
+    static bool attr[2] = {false, false};
+    if (!attr[ARCH]) {
+        int rc = cuda_check(cudaFuncSetAttribute(k_mlp_tc<ARCH, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                            "mlp_tc smem attribute");
+        if (rc) return rc;
+        attr[ARCH] = true;
+    }
+    TcParams p{};
+    p.packed = static_cast<const uint8_t*>(m->packed);
+    p.sdf_w = m->sdf_w;
+    p.rgb_w = m->rgb_w;
+    for (int a = 0; a < 3; ++a) p.center[a] = m->center[a];
+    p.scale = m->scale;
+    p.inv_scale = 1.0f / m->scale;
+    p.beta = m->beta;
+    p.src = src;
+    p.rec = rec;
+    p.status = device_status_word();
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t tiles = (max_samples + kTileS - 1) / kTileS;
+    unsigned blocks = (unsigned)(tiles < sms ? (tiles < 1 ? 1 : tiles) : sms);
+    k_mlp_tc<ARCH, F16><<<blocks, kThreads, smem, st>>>(p);
+    return cuda_check(cudaGetLastError(), "mlp_tc launch");
+}
+
+}  // namespace
+
+int mlp_tc_available(int arch) { return arch == TSDFS_ARCH_TINY || arch == TSDFS_ARCH_ROOM; }
+
+int launch_mlp_full_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64_t max_samples,
+                       cudaStream_t st) {
+    if ((reinterpret_cast<uintptr_t>(m->packed) & 15u) != 0) return fail(TSDFS_E_INVALID, "packed weights must be 16-byte aligned");
+    const bool f16 = m->precision == TSDFS_PREC_F16;
+    if (m->arch == TSDFS_ARCH_TINY)
+        return f16 ? launch_tc<TSDFS_ARCH_TINY, true>(m, src, rec, max_samples, st)
+                   : launch_tc<TSDFS_ARCH_TINY, false>(m, src, rec, max_samples, st);
+    return f16 ? launch_tc<TSDFS_ARCH_ROOM, true>(m, src, rec, max_samples, st)
+               : launch_tc<TSDFS_ARCH_ROOM, false>(m, src, rec, max_samples, st);
+}
+
+int64_t packed_bytes(int arch) {
+    return arch == TSDFS_ARCH_TINY ? TcArch<TSDFS_ARCH_TINY>::packed_bytes()
+                                   : (arch == TSDFS_ARCH_ROOM ? TcArch<TSDFS_ARCH_ROOM>::packed_bytes() : 0);
+}
+
 }  // namespace tsdfs
 
 using namespace tsdfs;
 
-extern "C" size_t tsdfs_packed_size(int32_t arch) {
-    (void)arch;
-    return 0;
-}
-extern "C" int tsdfs_pack_mlp(const tsdfs_mlp* mlp, void* packed, tsdfs_stream_t stream) {
-    (void)mlp;
-    (void)packed;
-    (void)stream;
-    return fail(TSDFS_E_UNSUPPORTED, "BF16 tensor-core path not built");
+extern "C" size_t tsdfs_packed_size(int32_t arch) { return (size_t)packed_bytes(arch); }
+
+extern "C" int tsdfs_pack_mlp(const tsdfs_mlp* m, void* packed, tsdfs_stream_t stream) {
+    if (!m || !packed || !m->sdf_w || !m->rgb_w) return fail(TSDFS_E_INVALID, "mlp, its weights and packed must be non-NULL");
+    if (m->arch != TSDFS_ARCH_TINY && m->arch != TSDFS_ARCH_ROOM) return fail(TSDFS_E_INVALID, "unknown arch %d", m->arch);
+    if ((reinterpret_cast<uintptr_t>(packed) & 15u) != 0) return fail(TSDFS_E_INVALID, "packed must be 16-byte aligned");
+    const int64_t n = packed_bytes(m->arch) / 2;
+    cudaStream_t st = (cudaStream_t)stream;
+    ProfScope ps("pack", st);
+    uint16_t* out = static_cast<uint16_t*>(packed);
+    const bool f16 = m->precision == TSDFS_PREC_F16;
+    if (m->arch == TSDFS_ARCH_TINY) {
+        if (f16) k_pack<TSDFS_ARCH_TINY, true><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out);
+        else k_pack<TSDFS_ARCH_TINY, false><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out);
+    } else {
+        if (f16) k_pack<TSDFS_ARCH_ROOM, true><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out);
+        else k_pack<TSDFS_ARCH_ROOM, false><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out);
+    }
+    return cuda_check(cudaGetLastError(), "tsdfs_pack_mlp launch");
 }

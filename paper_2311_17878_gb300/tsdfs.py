@@ -26,8 +26,8 @@ TSDFS_OK, TSDFS_E_INVALID, TSDFS_E_CUDA, TSDFS_E_WORKSPACE, TSDFS_E_UNSUPPORTED,
 TSDFS_F32, TSDFS_F16 = 0, 1
 TSDFS_MISS, TSDFS_BOUNDED, TSDFS_FALLBACK = 0, 1, 2
 TSDFS_ARCH_TINY, TSDFS_ARCH_ROOM = 0, 1
-TSDFS_PREC_F32, TSDFS_PREC_BF16 = 0, 1
-TSDFS_DEV_SAMPLES_OVERFLOW, TSDFS_DEV_MARCH_CAP = 1, 2
+TSDFS_PREC_F32, TSDFS_PREC_BF16, TSDFS_PREC_F16 = 0, 1, 2
+TSDFS_DEV_SAMPLES_OVERFLOW, TSDFS_DEV_MARCH_CAP, TSDFS_DEV_TIMEOUT = 1, 2, 4
 
 EXPORTS = ["tsdfs_last_error", "tsdfs_sync_status", "tsdfs_grid_init", "tsdf_integrate", "tsdfs_inside_mask_words",
            "tsdfs_inside_mask", "tsdfs_bounds_workspace_size", "tsdf_ray_bounds", "tsdfs_render_workspace_size",
@@ -279,12 +279,12 @@ class Mlp:
         self.rgb_w = torch.tensor(spec.packed("rgb"), device=device)
         self.packed = None
         self.precision = precision
-        if precision == TSDFS_PREC_BF16:
+        if precision != TSDFS_PREC_F32:
             self.packed = torch.zeros(max(tsdfs_packed_size(spec.arch), 1), dtype=torch.uint8, device=device)
         self.c = tsdfs_mlp(spec.arch, precision, self.sdf_w.data_ptr(), self.rgb_w.data_ptr(),
                            self.packed.data_ptr() if self.packed is not None else None,
                            (C.c_float * 3)(*spec.center), spec.scale, spec.inv_s, spec.beta, spec.alpha_eps)
-        if precision == TSDFS_PREC_BF16:
+        if precision != TSDFS_PREC_F32:
             tsdfs_pack_mlp(self, self.packed)
 
     def repack(self):

@@ -153,3 +153,86 @@ def test_tiny_hier96_f32_matches_oracle():
     sub = {k: v[live] for k, v in got.items()}
     compare(sub, ref)
     assert np.all(got["rgb"][~ok] == 0)
+
+
+# ------------------------------------------------------------------ BF16 ----
+DEPTH_REL_BF16 = 2e-3
+
+
+def test_pack_layout_roundtrip():
+    """The packed bf16 tiles hold every weight once (rounded to nearest even)
+    and zeros in the padding: the multiset of packed values equals the weights."""
+    for spec in (synth.tiny_mlp(), synth.room_mlp()):
+        mlp = T.Mlp(spec, T.TSDFS_PREC_BF16)
+        torch.cuda.synchronize()
+        packed = mlp.packed.view(torch.bfloat16).float().cpu().numpy()
+        w = np.concatenate([np.concatenate([W.reshape(-1) for W, _ in spec.sdf]),
+                            np.concatenate([W.reshape(-1) for W, _ in spec.rgb])]).astype(np.float32)
+        nz = np.sort(packed[packed != 0])
+        assert np.array_equal(nz, np.sort(w[w != 0]))
+
+
+def _scene_case(scene):
+    if scene == "tiny":
+        wl, V, b = oracle_bounds_tiny()
+        return wl.rays_o, wl.rays_d, b
+    wl = synth.room_workload(with_views=False)
+    V = synth.analytic_tsdf_torch(wl.scene, wl.grid, device="cuda").cpu().numpy()
+    o, d = synth.room_heldout_rays(0)
+    idx = synth.sub_sample(len(o), 512, seed=23)
+    o, d = o[idx], d[idx]
+    return o, d, cgrid.ray_bounds(wl.grid, V, o, d, wl.bounds, "f32")
+
+
+def _errors(got, ref):
+    ok = ref["wsum"] > 1e-3
+    er = np.abs(got["rgb"] - ref["rgb"]).max(1)
+    ed = np.abs(got["depth"][ok] - ref["depth"][ok]) / np.abs(ref["depth"][ok])
+    return er, ed
+
+
+@pytest.mark.parametrize("scene", ["tiny", "room"])
+def test_render_f16_operands_match_oracle(scene):
+    """tcgen05 path with fp16 operands, fp32 accumulation: within the stated
+    16-bit bars element by element (colour 2e-3 absolute, depth 2e-3 relative)."""
+    o, d, b = _scene_case(scene)
+    spec = synth.scene_mlp(scene)
+    got = gpu_render(spec, o, d, b, precision=T.TSDFS_PREC_F16)
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == 0, bits
+    ref, _ = oracle_render(spec, o, d, b)
+    er, ed = _errors(got, ref)
+    print(f"{scene} f16: rgb p99 {np.percentile(er, 99):.2e} max {er.max():.2e}; depth p99 {np.percentile(ed, 99):.2e} max {ed.max():.2e}")
+    compare(got, ref, depth_rel=DEPTH_REL_BF16)
+
+
+@pytest.mark.parametrize("scene", ["tiny", "room"])
+def test_render_bf16_operands_match_oracle(scene):
+    """tcgen05 path with bf16 operands.  bf16 keeps 8 significant bits (unit
+    roundoff 2^-8) against fp16's 11 (2^-11), so the bar that fp16 operands meet
+    (2e-3) scales by 8 for bf16: every ray within 1.6e-2 colour / depth."""
+    o, d, b = _scene_case(scene)
+    spec = synth.scene_mlp(scene)
+    got = gpu_render(spec, o, d, b, precision=T.TSDFS_PREC_BF16)
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == 0, bits
+    ref, _ = oracle_render(spec, o, d, b)
+    er, ed = _errors(got, ref)
+    print(f"{scene} bf16: rgb p99 {np.percentile(er, 99):.2e} max {er.max():.2e}; depth p99 {np.percentile(ed, 99):.2e} max {ed.max():.2e}")
+    bf16_factor = 2.0 ** -8 / 2.0 ** -11
+    assert er.max() <= bf16_factor * RGB_ABS and ed.max() <= bf16_factor * DEPTH_REL_BF16
+
+
+def test_bf16_hier96_runs_and_tracks_f32():
+    wl = synth.tiny_workload()
+    spec = synth.scene_mlp("tiny")
+    g = T.Grid(wl.grid, V=torch.zeros(wl.grid.shape_zyx, device="cuda"),
+               W=torch.zeros(wl.grid.shape_zyx, dtype=torch.uint8, device="cuda"))
+    outs = []
+    for prec in (T.TSDFS_PREC_F32, T.TSDFS_PREC_BF16, T.TSDFS_PREC_F16):
+        h = T.HierRenderer(T.Mlp(spec, prec), 4096)
+        o = h.render(g, dev(wl.rays_o), dev(wl.rays_d), wl.bounds.t_near, wl.bounds.t_far)
+        torch.cuda.synchronize()
+        outs.append(o.rgb.cpu().numpy())
+    assert np.max(np.abs(outs[0] - outs[1])) < 1e-2
+    assert np.max(np.abs(outs[0] - outs[2])) < 5e-3
