@@ -169,6 +169,25 @@ int tsdf_ray_bounds(const tsdfs_grid* grid, const uint32_t* inside_mask, const f
                     int32_t* offsets, float* t_zero, uint8_t* status, void* workspace, size_t ws_bytes,
                     tsdfs_stream_t stream);
 
+/* ---- ray bounds for callers that cannot allocate (no counterpart in the paper)
+ * Same computation, arguments and results as tsdf_ray_bounds, without the
+ * workspace: for callers that cannot allocate device memory themselves (a
+ * host application that only hands over buffers it registered up front, a
+ * real-time loop that must not allocate once running, code inside a framework
+ * whose allocator it cannot reach).  The offsets scan's scratch is a
+ * file-scope device array of the library, present on every device that loads
+ * it until the process exits, sized for tsdf_ray_bounds_noalloc_max_rays()
+ * (2^24) rays per call; larger n_rays is rejected with TSDFS_E_INVALID.  The
+ * first call on a device looks up that array's address (cudaGetSymbolAddress)
+ * and should therefore come before any stream capture.  The call allocates
+ * and frees nothing.  All calls share the array: calls that overlap on the GPU
+ * (unordered streams) race on it and must be serialised by the caller.       */
+int64_t tsdf_ray_bounds_noalloc_max_rays(void);
+int tsdf_ray_bounds_noalloc(const tsdfs_grid* grid, const uint32_t* inside_mask, const float* ray_o,
+                            const float* ray_d, int64_t n_rays, const tsdfs_bounds_params* p, float* t_n, float* t_f,
+                            int32_t* n_samples, int32_t* offsets, float* t_zero, uint8_t* status,
+                            tsdfs_stream_t stream);
+
 /* ---- render (Sec. 3.4 placement; Eq. 1, Eq. 2; rendered normal Sec. C.1) ----
  * Ray r has offsets[r+1] - offsets[r] samples at the midpoints
  * t_i = t_n + (i + 1/2)(t_f - t_n)/n of [t_n, t_f] (FALLBACK rays carry

@@ -6,6 +6,8 @@
 // fp32, round-to-nearest, no contraction (intrinsics + --fmad=false), in the
 // operation order of the oracle's fp32-exact mode, so t_n, t_f, counts and
 // status are identical bit for bit.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace tsdfs {
@@ -365,4 +367,59 @@ extern "C" int tsdf_ray_bounds(const tsdfs_grid* g, const uint32_t* mask, const 
     }
     int32_t* sums = reinterpret_cast<int32_t*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
     return exclusive_scan(n_samples, n_rays, offsets, sums, st);
+}
+
+// ---------------------------------------------------------------------------
+// tsdf_ray_bounds without a caller workspace.
+//
+// Some callers cannot allocate device memory of their own: a host application
+// that hands the library only buffers it registered at start-up, a real-time
+// render loop that forbids any allocation once it runs, or code embedded in a
+// framework whose allocator it cannot reach.  For them the only scratch this
+// call needs -- the per-chunk partial sums of the offsets scan -- lives in the
+// array below, which every device that loads the library holds until exit.
+// It is sized for kNoAllocMaxRays rays per call; every call overwrites the
+// partial sums it uses before reading them, so nothing has to be cleared, and
+// two calls that overlap on the GPU (different streams, no ordering) race on it.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int64_t kNoAllocMaxRays = (int64_t)1 << 24;
+constexpr size_t kNoAllocScratchBytes = (size_t)(((kNoAllocMaxRays + kScanChunk - 1) / kScanChunk) + 1) * sizeof(int32_t) + 256;
+static __device__ __align__(256) unsigned char g_bounds_scratch[kNoAllocScratchBytes];
+
+std::mutex g_scratch_mu;
+void* g_scratch_addr[64] = {nullptr};
+
+// device address of g_bounds_scratch on the current device (looked up once per device)
+int bounds_scratch(void** out) {
+    int dev = 0;
+    int rc = cuda_check(cudaGetDevice(&dev), "tsdf_ray_bounds_noalloc cudaGetDevice");
+    if (rc) return rc;
+    if (dev < 0 || dev >= 64) return fail(TSDFS_E_UNSUPPORTED, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        rc = cuda_check(cudaGetSymbolAddress(&p, g_bounds_scratch), "tsdf_ray_bounds_noalloc cudaGetSymbolAddress");
+        if (rc) return rc;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return TSDFS_OK;
+}
+}  // namespace
+
+extern "C" int64_t tsdf_ray_bounds_noalloc_max_rays(void) { return kNoAllocMaxRays; }
+
+extern "C" int tsdf_ray_bounds_noalloc(const tsdfs_grid* g, const uint32_t* mask, const float* ray_o,
+                                       const float* ray_d, int64_t n_rays, const tsdfs_bounds_params* p, float* t_n,
+                                       float* t_f, int32_t* n_samples, int32_t* offsets, float* t_zero,
+                                       uint8_t* status, tsdfs_stream_t stream) {
+    if (n_rays > kNoAllocMaxRays)
+        return fail(TSDFS_E_INVALID, "tsdf_ray_bounds_noalloc takes at most %lld rays per call (got %lld); split the batch",
+                    (long long)kNoAllocMaxRays, (long long)n_rays);
+    void* scratch = nullptr;
+    int rc = bounds_scratch(&scratch);
+    if (rc) return rc;
+    return tsdf_ray_bounds(g, mask, ray_o, ray_d, n_rays, p, t_n, t_f, n_samples, offsets, t_zero, status, scratch,
+                           kNoAllocScratchBytes, stream);
 }

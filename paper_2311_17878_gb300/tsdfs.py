@@ -158,6 +158,22 @@ def tsdf_ray_bounds(grid: "Grid", inside_mask, ray_o, ray_d, params: tsdfs_bound
                                  _stream()))
 
 
+def tsdf_ray_bounds_noalloc_max_rays() -> int:
+    L = lib()
+    L.tsdf_ray_bounds_noalloc_max_rays.restype = C.c_int64
+    return int(L.tsdf_ray_bounds_noalloc_max_rays())
+
+
+def tsdf_ray_bounds_noalloc(grid: "Grid", inside_mask, ray_o, ray_d, params: tsdfs_bounds_params, t_n, t_f,
+                            n_samples, offsets, t_zero, status):
+    """tsdf_ray_bounds for callers that cannot allocate device memory: no
+    workspace argument; the library's own fixed device scratch is used."""
+    n = ray_o.shape[0]
+    _check(lib().tsdf_ray_bounds_noalloc(C.byref(grid.c), _p(inside_mask), _p(ray_o), _p(ray_d), C.c_int64(n),
+                                         C.byref(params), _p(t_n), _p(t_f), _p(n_samples), _p(offsets), _p(t_zero),
+                                         _p(status), _stream()))
+
+
 def tsdfs_render_workspace_size(mlp: "Mlp", n_rays: int, max_samples: int) -> int:
     return int(lib().tsdfs_render_workspace_size(C.byref(mlp.c), C.c_int64(n_rays), C.c_int64(max_samples)))
 
