@@ -113,6 +113,7 @@ int grid_check(const tsdfs_grid* g);
 int mlp_tc_available(int arch);
 int launch_mlp_full_tc(const tsdfs_mlp* mlp, const SampleSource& src, SampleRec* rec, int64_t max_samples,
                        cudaStream_t st);
+int launch_mlp_value_tc(const tsdfs_mlp* mlp, const SampleSource& src, float* f_out, cudaStream_t st);
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -319,7 +320,10 @@ extern "C" int render_rays_hier96(const tsdfs_mlp* mlp, const tsdfs_grid* grid, 
     cs.per_ray = 64;
     cs.total_host = n_rays * 64;
     cs.capacity = n_rays * 64;
-    {
+    if (mlp->precision != TSDFS_PREC_F32) {
+        ProfScope ps("mlp_value_tc", st);
+        rc = launch_mlp_value_tc(mlp, cs, w.fc, st);
+    } else {
         ProfScope ps("mlp_value_simt", st);
         rc = mlp->arch == TSDFS_ARCH_TINY ? launch_mlp_value_simt<TSDFS_ARCH_TINY>(np, cs, w.fc, st)
                                           : launch_mlp_value_simt<TSDFS_ARCH_ROOM>(np, cs, w.fc, st);

@@ -75,6 +75,13 @@ template <int ARCH> struct TcArch {
     __host__ __device__ static constexpr int64_t param_offset(int L) {
         return L < A::kSdfLayers ? sdf_layer_offset<ARCH>(L) : rgb_layer_offset<ARCH>(L - A::kSdfLayers);
     }
+    __host__ __device__ static constexpr int bias_offset(int L) {
+        int o = 0;
+        for (int l = 0; l < L; ++l) o += layer(l).N;
+        return o;
+    }
+    __host__ __device__ static constexpr int bias_total() { return bias_offset(kLayers); }
+    __host__ __device__ static constexpr uint32_t bias_bytes() { return (uint32_t)((bias_total() * 4 + 15) / 16 * 16); }
     __host__ __device__ static constexpr uint32_t stage_bytes() {
         int64_t m = 0;
         for (int l = 0; l < kLayers; ++l)
@@ -185,18 +192,30 @@ __device__ __forceinline__ void st_row8(uint8_t* base, int r, int k0, int Kp, co
     *reinterpret_cast<uint4*>(base + a_off(r, k0, Kp)) = q;
 }
 
-// softplus_beta(z) and its slope sigma(beta z), linear branch for beta z > 20
-__device__ __forceinline__ void softplus_pair(float z, float beta, float inv_beta, float& h, float& sg) {
-    const float bz = beta * z;
-    if (bz > 20.0f) {
-        h = z;
-        sg = 1.0f;
-    } else {
-        const float e = __expf(-fabsf(bz));
-        const float r = __fdividef(1.0f, 1.0f + e);
-        h = (fmaxf(bz, 0.0f) + __logf(1.0f + e)) * inv_beta;
-        sg = bz >= 0.0f ? r : e * r;
-    }
+// tanh on the special-function unit (max relative error about 2^-11)
+__device__ __forceinline__ float tanh_fast(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// log(1 + u) on [0, 1]: least-squares polynomial of degree 6 at Chebyshev
+// nodes, |error| < 2e-6 (fitted for this kernel; see the tests)
+__device__ __forceinline__ float log1p_unit(float u) {
+    float p = -0.017877891659736633f;
+    p = fmaf(p, u, 0.08419863134622574f);
+    p = fmaf(p, u, -0.19223858416080475f);
+    p = fmaf(p, u, 0.3168778717517853f);
+    p = fmaf(p, u, -0.497702956199646f);
+    p = fmaf(p, u, 0.9998888969421387f);
+    return p * u;
+}
+// softplus_beta(z) and its slope sigma(beta z) from one tanh:
+// t = tanh(beta z / 2); sigma(beta z) = (1 + t)/2; sigma(beta |z|) = (1 + |t|)/2 and
+// softplus_beta(z) = max(z, 0) + log(1 + e^{-beta |z|})/beta = max(z, 0) + (ln 2 - log(1 + |t|))/beta
+__device__ __forceinline__ void softplus_slope_tanh(float z, float half_beta, float inv_beta, float& h, float& sg) {
+    const float t = tanh_fast(half_beta * z);
+    sg = fmaf(0.5f, t, 0.5f);
+    h = fmaxf(z, 0.0f) + (0.69314718055994531f - log1p_unit(fabsf(t))) * inv_beta;
 }
 
 // positional encoding entry j of coordinate vector xt, and its derivative along axis a
@@ -235,7 +254,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
     uint8_t* A0 = smem;
     uint8_t* A1 = smem + kABytes;
     uint8_t* stage_base = smem + 2 * kABytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(stage_base + 2 * kStage);
+    float* sbias = reinterpret_cast<float*>(stage_base + 2 * kStage);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage_base + 2 * kStage + TA::bias_bytes());
     // bars: full[2], empty[2], acc_ready, a_ready, drain
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -261,6 +281,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
         mbar_init(bar_drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // all biases of both networks, staged once
+    for (int i = threadIdx.x; i < TA::bias_total(); i += kThreads) {
+        int L = 0;
+        while (L + 1 < NL && TA::bias_offset(L + 1) <= i) ++L;
+        const TcLayer ly = TA::layer(L);
+        const float* W = (ly.sdf ? p.sdf_w : p.rgb_w) + TA::param_offset(L);
+        sbias[i] = __ldg(W + (int64_t)ly.N * ly.K + (i - TA::bias_offset(L)));
     }
     if (warp == 9) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -361,18 +389,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
         const bool is_val = lane < 16;
         const int r = 32 * q + lane;                  // TMEM lane / A row of this thread
         const int s = 16 * q + (lane & 15);           // sample within the tile
+        const int val_lane = lane & 15;               // lane holding this sample's value row
         const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
-        const float beta = p.beta, inv_beta = 1.0f / p.beta;
-        const float kInvSqrt2 = 0.70710678118654752f;
+        const float half_beta = 0.5f * p.beta, inv_beta = 1.0f / p.beta;
+        constexpr float kInvSqrt2 = 0.70710678118654752f;
         uint32_t lc = 0;
         bool ok = true;
         for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-            // ---- this row's sample ----
+            // ---- this row's sample (value lanes look it up, tangent lanes receive it) ----
             const int64_t g = tile * kTileS + s;
             const bool valid = g < total;
             float t = 0.0f, dl = 0.0f;
-            int64_t ray = 0;
-            if (valid) {
+            long long ray = 0;
+            if (valid && is_val) {
                 if (p.src.mode == kUniform) {
                     ray = find_ray(p.src.offsets, p.src.n_rays, g);
                     const int32_t o0 = __ldg(p.src.offsets + ray), o1 = __ldg(p.src.offsets + ray + 1);
@@ -385,6 +414,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                     dl = __ldg(p.src.delta + g);
                 }
             }
+            t = __shfl_sync(0xffffffffu, t, val_lane);
+            dl = __shfl_sync(0xffffffffu, dl, val_lane);
+            ray = __shfl_sync(0xffffffffu, ray, val_lane);
             float xt[3], dir[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -395,14 +427,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
             // ---- layer-0 input: encoding (A0: value | d/dx, A1: d/dy | d/dz) ----
             {
                 constexpr int Kp0 = TA::layer(0).Kp;
-                const int a0_axis = 0, a1_axis = is_val ? 1 : 2;
+                const int a1_axis = is_val ? 1 : 2;
                 for (int k0 = hf * (Kp0 / 2); k0 < (hf + 1) * (Kp0 / 2); k0 += 8) {
                     float v0[8], v1[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int k = k0 + j;
                         const bool in = k < A::kEnc;
-                        v0[j] = in ? enc_val(xt, k, A::kPeSdf, a0_axis, !is_val) : 0.0f;
+                        v0[j] = in ? enc_val(xt, k, A::kPeSdf, 0, !is_val) : 0.0f;
                         v1[j] = in ? enc_val(xt, k, A::kPeSdf, a1_axis, true) : 0.0f;
                     }
                     st_row8<F16>(A0, r, k0, Kp0, v0);
@@ -417,38 +449,56 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                 const bool w_ok = mbar_wait(bar_acc, lc & 1u, abort_flag);
                 if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
                 tc_fence_after();
-                const float* W = (ly.sdf ? p.sdf_w : p.rgb_w) + TA::param_offset(L);
-                const float* bias = W + (int64_t)ly.N * ly.K;
+                const float* bias = sbias + TA::bias_offset(L);
                 const bool last = L == NL - 1;
                 if (ly.sdf && ly.idx < LS - 1) {
-                    // hidden SDF layer -> next layer's input (with the skip concat when due)
+                    // ---- hidden SDF layer -> next layer's input (skip concat when due) ----
                     const int Kn = TA::layer(L + 1).Kp;
-                    const bool skip_next = ly.idx + 1 == A::kSkip;
-                    const float sc = skip_next ? kInvSqrt2 : 1.0f;
-                    for (int c0 = half_lo(Kn, hf); c0 < half_hi(Kn, hf); c0 += 16) {
+                    const float sc = ly.idx + 1 == A::kSkip ? kInvSqrt2 : 1.0f;
+                    auto full_block = [&](int c0, const float (&x0)[16], const float (&x1)[16]) {
+#pragma unroll
+                        for (int hh = 0; hh < 16; hh += 8) {
+                            float o0[8], o1[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                float h, sg;
+                                softplus_slope_tanh(x0[hh + j] + bias[c0 + hh + j], half_beta, inv_beta, h, sg);
+                                const float sgx = __shfl_sync(0xffffffffu, sg, val_lane) * sc;
+                                o0[j] = is_val ? h * sc : sgx * x0[hh + j];
+                                o1[j] = sgx * x1[hh + j];
+                            }
+                            st_row8<F16>(A0, r, c0 + hh, Kn, o0);
+                            st_row8<F16>(A1, r, c0 + hh, Kn, o1);
+                        }
+                    };
+                    const int c_lo = half_lo(Kn, hf), c_hi = half_hi(Kn, hf);
+                    const int c_full = (ly.N / 16) * 16 < c_hi ? (ly.N / 16) * 16 : c_hi;
+                    for (int c0 = c_lo; c0 < c_full; c0 += 16) {
+                        float x0[16], x1[16];
+                        tmem_ld16(tmem + lane_addr + c0, x0);
+                        tmem_ld16(tmem + 256 + lane_addr + c0, x1);
+                        tmem_wait_ld();
+                        full_block(c0, x0, x1);
+                    }
+                    // tail: hidden units < N, then gamma(x~) / sqrt(2) (the skip input), then zeros
+                    for (int c0 = c_full > c_lo ? c_full : c_lo; c0 < c_hi; c0 += 16) {
+                        float o0[16], o1[16];
                         float x0[16], x1[16];
                         if (c0 < ly.Np) {
                             tmem_ld16(tmem + lane_addr + c0, x0);
                             tmem_ld16(tmem + 256 + lane_addr + c0, x1);
                             tmem_wait_ld();
                         }
-                        float o0[16], o1[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const int col = c0 + j;
-                            float h = 0.0f, sg = 0.0f;
                             if (col < ly.N) {
-                                if (is_val) softplus_pair(x0[j] + __ldg(bias + col), beta, inv_beta, h, sg);
-                                const float sgx = __shfl_xor_sync(0xffffffffu, sg, 16);
-                                if (is_val) {
-                                    o0[j] = h * sc;
-                                    o1[j] = sg * x1[j] * sc;
-                                } else {
-                                    o0[j] = sgx * x0[j] * sc;
-                                    o1[j] = sgx * x1[j] * sc;
-                                }
+                                float h, sg;
+                                softplus_slope_tanh(x0[j] + bias[col], half_beta, inv_beta, h, sg);
+                                const float sgx = __shfl_sync(0xffffffffu, sg, val_lane) * sc;
+                                o0[j] = is_val ? h * sc : sgx * x0[j];
+                                o1[j] = sgx * x1[j];
                             } else {
-                                // skip input: gamma(x~) / sqrt(2) after the hidden units
                                 const int e = col - ly.N;
                                 const bool in = e < A::kEnc;
                                 o0[j] = in ? enc_val(xt, e, A::kPeSdf, 0, !is_val) * sc : 0.0f;
@@ -461,102 +511,108 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                         st_row8<F16>(A1, r, c0 + 8, Kn, o1 + 8);
                     }
                 } else if (ly.sdf) {
-                    // output layer: f, grad f, feature -> colour input rows (value lanes)
-                    const int Kc = TA::layer(L + 1).Kp;
+                    // ---- output layer: f, grad f, feature -> colour input rows ----
+                    // colour row: [x~ (3), direction encoding, unit normal (3), feature, 0 pad];
+                    // output oc >= 1 (feature oc - 1) sits at colour column oc + kD
                     constexpr int kDir = A::kDirEnc;
-                    constexpr int kFeatCol = 3 + kDir + 3;  // colour column of feature 0
+                    constexpr int kFeatCol = 3 + kDir + 3;
+                    constexpr int kD = kFeatCol - 1;
+                    constexpr int kOff = (16 - kD % 16) % 16;
+                    constexpr int kPrefix = (kFeatCol + 15) / 16;  // blocks holding x~, dir, normal
+                    const int Kc = TA::layer(L + 1).Kp;
                     float n_hat[3] = {0.0f, 0.0f, 0.0f};
+                    float venc[kDir];
                     if (hf == 0) {
                         float x0[16], x1[16];
                         tmem_ld16(tmem + lane_addr, x0);
                         tmem_ld16(tmem + 256 + lane_addr, x1);
                         tmem_wait_ld();
-                        const float gx = __shfl_xor_sync(0xffffffffu, x0[0], 16);
-                        const float gz = __shfl_xor_sync(0xffffffffu, x1[0], 16);
+                        const float gx = __shfl_sync(0xffffffffu, x0[0], val_lane + 16);
+                        const float gz = __shfl_sync(0xffffffffu, x1[0], val_lane + 16);
                         const float gy = x1[0];
-                        if (is_val) {
-                            f_out = p.scale * (x0[0] + __ldg(bias));
-                            gn_out = sqrtf(gx * gx + gy * gy + gz * gz);
-                            const float inv = gn_out > 0.0f ? 1.0f / gn_out : 0.0f;
-                            n_hat[0] = gx * inv; n_hat[1] = gy * inv; n_hat[2] = gz * inv;
-                            nrm[0] = n_hat[0]; nrm[1] = n_hat[1]; nrm[2] = n_hat[2];
-                            dd_out = gx * dir[0] + gy * dir[1] + gz * dir[2];
-                        }
+                        f_out = p.scale * (x0[0] + bias[0]);
+                        gn_out = sqrtf(gx * gx + gy * gy + gz * gz);
+                        const float inv = gn_out > 0.0f ? 1.0f / gn_out : 0.0f;
+                        n_hat[0] = gx * inv; n_hat[1] = gy * inv; n_hat[2] = gz * inv;
+                        nrm[0] = n_hat[0]; nrm[1] = n_hat[1]; nrm[2] = n_hat[2];
+                        dd_out = gx * dir[0] + gy * dir[1] + gz * dir[2];
+#pragma unroll
+                        for (int e = 0; e < kDir; ++e) venc[e] = A::kPeDir == 0 ? dir[e] : enc_val(dir, e, A::kPeDir, 0, false);
                     }
-                    // colour input columns of this half: [x~, dir enc, n^, feature, pad]
-                    const int lo = half_lo(Kc, hf), hi = half_hi(Kc, hf);
-                    for (int c0 = lo; c0 < hi; c0 += 16) {
-                        // feature j = network output j + 1 = accumulator column j + 1; outputs
-                        // >= 256 live in acc1 from column 16.  Load the two 16-column
-                        // accumulator blocks covering outputs [c0 - kFeatCol + 1, +16).
-                        const int f_lo = c0 - kFeatCol + 1;
-                        const int cap = (ly.Np < 256 ? ly.Np : 256) - 32;
-                        int w0c = f_lo < 0 ? 0 : (f_lo & ~15);
-                        w0c = w0c > cap ? cap : w0c;
-                        float xa[16], xb[16], xe[16];
-                        tmem_ld16(tmem + lane_addr + w0c, xa);
-                        tmem_ld16(tmem + lane_addr + w0c + 16, xb);
-                        tmem_ld16(tmem + 256 + lane_addr + 16, xe);
+                    auto feature_block = [&](int c0, float (&o)[16], bool prefix) {
+                        const int w0 = c0 - kD - kOff;   // 16-aligned output block behind column c0 + kOff
+                        float xa[16], xb[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) { xa[j] = 0.0f; xb[j] = 0.0f; }
+                        if (w0 >= 0) tmem_ld16(tmem + lane_addr + (w0 < 256 ? w0 : w0 + 16), xa);
+                        if (kOff != 0) tmem_ld16(tmem + lane_addr + (w0 + 16 < 256 ? w0 + 16 : w0 + 32), xb);
                         tmem_wait_ld();
-                        float o[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const int col = c0 + j;
-                            float v = 0.0f;
-                            if (col < 3) v = xt[col];
-                            else if (col < 3 + kDir) {
-                                const int e = col - 3;
-                                v = A::kPeDir == 0 ? dir[e] : enc_val(dir, e, A::kPeDir, 0, false);
-                            } else if (col < kFeatCol) v = n_hat[col - 3 - kDir];
-                            else if (col < kFeatCol + A::kFeat) {
-                                const int oc = col - kFeatCol + 1;  // output column
-                                float acc;
-                                if (oc >= 256) acc = xe[(oc - 256) & 15];
-                                else if (oc - w0c < 16) acc = xa[(oc - w0c) & 15];
-                                else acc = xb[(oc - w0c - 16) & 15];
-                                v = acc + __ldg(bias + oc);
+                            const int idx = j + kOff;
+                            const float acc = idx < 16 ? xa[idx < 16 ? idx : 0] : xb[idx >= 16 ? idx - 16 : 0];
+                            const bool feat = col >= kFeatCol && col < kFeatCol + A::kFeat;
+                            o[j] = feat ? acc + bias[feat ? col - kD : 0] : 0.0f;
+                            if (prefix) {
+                                if (col < 3) o[j] = xt[col < 3 ? col : 0];
+                                else if (col < 3 + kDir) o[j] = venc[col - 3 < kDir ? col - 3 : 0];
+                                else if (col < kFeatCol) o[j] = n_hat[col - 3 - kDir < 3 ? col - 3 - kDir : 0];
                             }
-                            o[j] = v;
                         }
+                    };
+                    const int lo = half_lo(Kc, hf), hi = half_hi(Kc, hf);
+                    int c_start = lo;
+                    if (hf == 0) {
+#pragma unroll
+                        for (int pb = 0; pb < kPrefix; ++pb) {
+                            float o[16];
+                            feature_block(16 * pb, o, true);
+                            if (is_val) {
+                                st_row8<F16>(A0, r, 16 * pb, Kc, o);
+                                st_row8<F16>(A0, r, 16 * pb + 8, Kc, o + 8);
+                            }
+                        }
+                        c_start = 16 * kPrefix;
+                    }
+                    for (int c0 = c_start; c0 < hi; c0 += 16) {
+                        float o[16];
+                        feature_block(c0, o, false);
                         if (is_val) {
                             st_row8<F16>(A0, r, c0, Kc, o);
                             st_row8<F16>(A0, r, c0 + 8, Kc, o + 8);
                         }
                     }
                 } else if (!last) {
-                    // hidden colour layer (ReLU), value rows only
+                    // ---- hidden colour layer (ReLU), value rows only ----
                     const int Kn = TA::layer(L + 1).Kp;
                     for (int c0 = half_lo(Kn, hf); c0 < half_hi(Kn, hf); c0 += 16) {
-                        float x0[16];
+                        float x0[16], o[16];
                         tmem_ld16(tmem + lane_addr + c0, x0);
                         tmem_wait_ld();
-                        float o[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const int col = c0 + j;
-                            o[j] = col < ly.N ? fmaxf(x0[j] + __ldg(bias + col), 0.0f) : 0.0f;
+                            o[j] = col < ly.N ? fmaxf(x0[j] + bias[col < ly.N ? col : 0], 0.0f) : 0.0f;
                         }
                         if (is_val) {
                             st_row8<F16>(A0, r, c0, Kn, o);
                             st_row8<F16>(A0, r, c0 + 8, Kn, o + 8);
                         }
                     }
-                } else {
-                    // colour output (sigmoid) -> record
-                    if (hf == 0) {
-                        float x0[16];
-                        tmem_ld16(tmem + lane_addr, x0);
-                        tmem_wait_ld();
-                        if (is_val && valid) {
-                            SampleRec& R = p.rec[g];
-                            float4* R4 = reinterpret_cast<float4*>(&R);
-                            const float cr = __fdividef(1.0f, 1.0f + __expf(-(x0[0] + __ldg(bias + 0))));
-                            const float cg = __fdividef(1.0f, 1.0f + __expf(-(x0[1] + __ldg(bias + 1))));
-                            const float cb = __fdividef(1.0f, 1.0f + __expf(-(x0[2] + __ldg(bias + 2))));
-                            R4[0] = make_float4(f_out, dd_out, t, dl);
-                            R4[1] = make_float4(cr, cg, cb, gn_out);
-                            R4[2] = make_float4(nrm[0], nrm[1], nrm[2], 0.0f);
-                        }
+                } else if (hf == 0) {
+                    // ---- colour output (sigmoid) -> record ----
+                    float x0[16];
+                    tmem_ld16(tmem + lane_addr, x0);
+                    tmem_wait_ld();
+                    if (is_val && valid) {
+                        float4* R4 = reinterpret_cast<float4*>(p.rec + g);
+                        const float cr = __fdividef(1.0f, 1.0f + __expf(-(x0[0] + bias[0])));
+                        const float cg = __fdividef(1.0f, 1.0f + __expf(-(x0[1] + bias[1])));
+                        const float cb = __fdividef(1.0f, 1.0f + __expf(-(x0[2] + bias[2])));
+                        R4[0] = make_float4(f_out, dd_out, t, dl);
+                        R4[1] = make_float4(cr, cg, cb, gn_out);
+                        R4[2] = make_float4(nrm[0], nrm[1], nrm[2], 0.0f);
                     }
                 }
                 tc_fence_before();
@@ -574,6 +630,230 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
     if (warp == 9) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
     }
+}
+
+// ---- SDF values only (the hierarchical comparator's coarse pass) ----------
+// Tile: 128 samples, one value row each (no tangents); one accumulator
+// (TMEM columns 0..255); SDF layers only; the output layer needs column 0.
+constexpr int kTileV = 128;
+
+template <int ARCH, bool F16>
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float* __restrict__ f_out) {
+    using TA = TcArch<ARCH>;
+    using A = Arch<ARCH>;
+    constexpr int LS = A::kSdfLayers;
+    constexpr uint32_t kStage = TA::stage_bytes();
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* A0 = smem;
+    uint8_t* stage_base = smem + 2 * kABytes;
+    float* sbias = reinterpret_cast<float*>(stage_base + 2 * kStage);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage_base + 2 * kStage + TA::bias_bytes());
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const uint32_t bar_full0 = smem_u32(bars + 0), bar_empty0 = smem_u32(bars + 2);
+    const uint32_t bar_acc = smem_u32(bars + 4), bar_a = smem_u32(bars + 5), bar_drain = smem_u32(bars + 6);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t total = p.src.total_host;
+    const int64_t n_tiles = (total + kTileV - 1) / kTileV;
+    if ((int64_t)blockIdx.x >= n_tiles) return;
+    if (threadIdx.x == 0) {
+        mbar_init(bar_full0, 1);
+        mbar_init(bar_full0 + 8, 1);
+        mbar_init(bar_empty0, 1);
+        mbar_init(bar_empty0 + 8, 1);
+        mbar_init(bar_acc, 1);
+        mbar_init(bar_a, kEpiThreads);
+        mbar_init(bar_drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < TA::bias_offset(LS); i += kThreads) {
+        int L = 0;
+        while (L + 1 < LS && TA::bias_offset(L + 1) <= i) ++L;
+        const TcLayer ly = TA::layer(L);
+        sbias[i] = __ldg(p.sdf_w + TA::param_offset(L) + (int64_t)ly.N * ly.K + (i - TA::bias_offset(L)));
+    }
+    if (warp == 9) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 8) {
+        if (lane == 0) {
+            uint32_t seq = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                for (int L = 0; L < LS && ok; ++L) {
+                    for (int c = 0; c < TA::chunks(L); ++c) {
+                        const uint32_t s = seq & 1u, ph = (seq >> 1) & 1u;
+                        if (!mbar_wait(bar_empty0 + 8 * s, ph ^ 1u, abort_flag)) { ok = false; break; }
+                        const uint32_t bytes = (uint32_t)TA::chunk_bytes(L, c);
+                        mbar_expect_tx(bar_full0 + 8 * s, bytes);
+                        bulk_g2s(smem_u32(stage_base + s * kStage), p.packed + TA::packed_offset(L, c), bytes,
+                                 bar_full0 + 8 * s);
+                        ++seq;
+                    }
+                }
+            }
+            if (!ok) {
+                for (uint32_t k = (seq >= 2 ? seq - 2 : 0); k < seq; ++k) {
+                    for (uint32_t it = 0; it < kMaxSpin && !mbar_try(bar_full0 + 8 * (k & 1u), (k >> 1) & 1u); ++it) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 9) {
+        if (lane == 0) {
+            uint32_t seq = 0, lc = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                for (int L = 0; L < LS && ok; ++L, ++lc) {
+                    const TcLayer ly = TA::layer(L);
+                    if (!mbar_wait(bar_a, lc & 1u, abort_flag)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a_sbo = (uint32_t)(ly.Kp / 8) * 128u;
+                    const uint32_t a0 = smem_u32(A0);
+                    const int n_mma = L == LS - 1 ? 16 : ly.Np;
+                    for (int c = 0; c < TA::chunks(L); ++c) {
+                        const uint32_t s = seq & 1u, ph = (seq >> 1) & 1u;
+                        if (!mbar_wait(bar_full0 + 8 * s, ph, abort_flag)) { ok = false; break; }
+                        tc_fence_after();
+                        const int kc = TA::chunk_k(L, c);
+                        const uint32_t b0 = smem_u32(stage_base + s * kStage);
+                        const uint32_t b_sbo = (uint32_t)(kc / 8) * 128u;
+                        for (int kk = 0; kk < kc / 16; ++kk) {
+                            const int k = c * kKChunk + kk * 16;
+                            mma_bf16(tmem, mdesc(a0 + (uint32_t)(k / 8) * 128u, 128, a_sbo), mdesc(b0 + kk * 256, 128, b_sbo),
+                                     idesc_mma<F16>(128, n_mma), k > 0 ? 1u : 0u);
+                        }
+                        mma_commit(bar_empty0 + 8 * s);
+                        ++seq;
+                    }
+                    if (!ok) break;
+                    mma_commit(bar_acc);
+                }
+            }
+            if (!ok) {
+                mma_commit(bar_drain);
+                for (uint32_t it = 0; it < kMaxSpin && !mbar_try(bar_drain, 0); ++it) {
+                }
+            }
+        }
+    } else {
+        const int q = warp & 3, hf = warp >> 2;
+        const int r = 32 * q + lane;  // row = sample within the tile
+        const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
+        const float half_beta = 0.5f * p.beta, inv_beta = 1.0f / p.beta;
+        constexpr float kInvSqrt2 = 0.70710678118654752f;
+        uint32_t lc = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            const int64_t g = tile * kTileV + r;
+            const bool valid = g < total;
+            const int64_t ray = valid ? g / p.src.per_ray : 0;
+            const float t = valid ? __ldg(p.src.t + g) : 0.0f;
+            float xt[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                xt[a] = (__ldg(p.src.ray_o + 3 * ray + a) + t * __ldg(p.src.ray_d + 3 * ray + a) - p.center[a]) * p.inv_scale;
+            {
+                constexpr int Kp0 = TA::layer(0).Kp;
+                for (int k0 = hf * (Kp0 / 2); k0 < (hf + 1) * (Kp0 / 2); k0 += 8) {
+                    float v0[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v0[j] = k0 + j < A::kEnc ? enc_val(xt, k0 + j, A::kPeSdf, 0, false) : 0.0f;
+                    st_row8<F16>(A0, r, k0, Kp0, v0);
+                }
+            }
+            fence_proxy_async();
+            mbar_arrive(bar_a);
+            for (int L = 0; L < LS; ++L, ++lc) {
+                const TcLayer ly = TA::layer(L);
+                const bool w_ok = mbar_wait(bar_acc, lc & 1u, abort_flag);
+                if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
+                tc_fence_after();
+                const float* bias = sbias + TA::bias_offset(L);
+                if (L < LS - 1) {
+                    const int Kn = TA::layer(L + 1).Kp;
+                    const float sc = ly.idx + 1 == A::kSkip ? kInvSqrt2 : 1.0f;
+                    for (int c0 = half_lo(Kn, hf); c0 < half_hi(Kn, hf); c0 += 16) {
+                        float x0[16], o[16];
+                        if (c0 < ly.Np) {
+                            tmem_ld16(tmem + lane_addr + c0, x0);
+                            tmem_wait_ld();
+                        }
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int col = c0 + j;
+                            if (col < ly.N) {
+                                float h, sg;
+                                softplus_slope_tanh(x0[j] + bias[col], half_beta, inv_beta, h, sg);
+                                o[j] = h * sc;
+                            } else {
+                                const int e = col - ly.N;
+                                o[j] = e < A::kEnc ? enc_val(xt, e, A::kPeSdf, 0, false) * sc : 0.0f;
+                            }
+                        }
+                        st_row8<F16>(A0, r, c0, Kn, o);
+                        st_row8<F16>(A0, r, c0 + 8, Kn, o + 8);
+                    }
+                } else if (hf == 0) {
+                    float x0[16];
+                    tmem_ld16(tmem + lane_addr, x0);
+                    tmem_wait_ld();
+                    if (valid) f_out[g] = p.scale * (x0[0] + bias[0]);
+                }
+                tc_fence_before();
+                if (L < LS - 1) {
+                    fence_proxy_async();
+                    mbar_arrive(bar_a);
+                }
+            }
+        }
+        if (!ok) set_status(p.status, TSDFS_DEV_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 9) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    }
+}
+
+template <int ARCH, bool F16>
+int launch_tc_value(const tsdfs_mlp* m, const SampleSource& src, float* f_out, cudaStream_t st) {
+    using TA = TcArch<ARCH>;
+    const size_t smem = 2 * kABytes + 2 * (size_t)TA::stage_bytes() + TA::bias_bytes() + 128;
+    static bool attr[2] = {false, false};
+    if (!attr[ARCH]) {
+        int rc = cuda_check(cudaFuncSetAttribute(k_mlp_tc_value<ARCH, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem),
+                            "mlp_tc_value smem attribute");
+        if (rc) return rc;
+        attr[ARCH] = true;
+    }
+    TcParams p{};
+    p.packed = static_cast<const uint8_t*>(m->packed);
+    p.sdf_w = m->sdf_w;
+    p.rgb_w = m->rgb_w;
+    for (int a = 0; a < 3; ++a) p.center[a] = m->center[a];
+    p.scale = m->scale;
+    p.inv_scale = 1.0f / m->scale;
+    p.beta = m->beta;
+    p.src = src;
+    p.status = device_status_word();
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tiles = (src.total_host + kTileV - 1) / kTileV;
+    const unsigned blocks = (unsigned)(tiles < sms ? (tiles < 1 ? 1 : tiles) : sms);
+    k_mlp_tc_value<ARCH, F16><<<blocks, kThreads, smem, st>>>(p, f_out);
+    return cuda_check(cudaGetLastError(), "mlp_tc_value launch");
 }
 
 // ---- pack fp32 [N][K] weights into the bf16 chunked core-matrix layout ----
@@ -613,7 +893,7 @@ __global__ void k_pack(const float* __restrict__ sdf_w, const float* __restrict_
 template <int ARCH, bool F16>
 int launch_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64_t max_samples, cudaStream_t st) {
     using TA = TcArch<ARCH>;
-    const size_t smem = 2 * kABytes + 2 * (size_t)TA::stage_bytes() + 128;
+    const size_t smem = 2 * kABytes + 2 * (size_t)TA::stage_bytes() + TA::bias_bytes() + 128;
     static bool attr[2] = {false, false};
     if (!attr[ARCH]) {
         int rc = cuda_check(cudaFuncSetAttribute(k_mlp_tc<ARCH, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
@@ -654,6 +934,15 @@ int launch_mlp_full_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* r
                    : launch_tc<TSDFS_ARCH_TINY, false>(m, src, rec, max_samples, st);
     return f16 ? launch_tc<TSDFS_ARCH_ROOM, true>(m, src, rec, max_samples, st)
                : launch_tc<TSDFS_ARCH_ROOM, false>(m, src, rec, max_samples, st);
+}
+
+int launch_mlp_value_tc(const tsdfs_mlp* m, const SampleSource& src, float* f_out, cudaStream_t st) {
+    const bool f16 = m->precision == TSDFS_PREC_F16;
+    if (m->arch == TSDFS_ARCH_TINY)
+        return f16 ? launch_tc_value<TSDFS_ARCH_TINY, true>(m, src, f_out, st)
+                   : launch_tc_value<TSDFS_ARCH_TINY, false>(m, src, f_out, st);
+    return f16 ? launch_tc_value<TSDFS_ARCH_ROOM, true>(m, src, f_out, st)
+               : launch_tc_value<TSDFS_ARCH_ROOM, false>(m, src, f_out, st);
 }
 
 int64_t packed_bytes(int arch) {
