@@ -222,15 +222,22 @@ int render_rays_hier96(const tsdfs_mlp* mlp, const tsdfs_grid* grid, const float
                        float* normal, void* workspace, size_t ws_bytes, tsdfs_stream_t stream);
 
 /* ---- backward of render_rays (training step of the networks) ---------------
- * Gradients of L = sum(d_rgb . rgb) + sum(d_depth . depth) + d_eik * sum(eik)
- * with respect to the packed fp32 parameters, ACCUMULATED (+=) into
- * d_sdf_w / d_rgb_w (same layout as sdf_w / rgb_w; the caller zeroes them).
- * Activations are recomputed, not stored.  d_depth may be NULL.  FP32 only.
+ * Gradients of L = sum_r d_rgb_r . rgb_r + d_depth_r depth_r + d_eik_r eik_r
+ * (the outputs of render_rays for the same inputs; eik_r is the per-ray sum
+ * of (|grad f| - 1)^2 over the samples of BOUNDED rays) with respect to the
+ * packed fp32 parameters, ACCUMULATED (+=) into d_sdf_w / d_rgb_w (layout of
+ * sdf_w / rgb_w; the caller zeroes them).  This includes the second-order
+ * terms through grad f (opacity, colour-network normal, eikonal).  d_rgb:
+ * [n_rays][3]; d_depth, d_eik: [n_rays] or NULL (zero).  Activations are
+ * recomputed per tile of samples, never stored per batch: the workspace is
+ * the per-sample records plus a fixed per-SM scratch (activations of one tile
+ * and a private gradient copy per block), independent of the batch beyond
+ * max_samples.  FP32 networks only (mlp->precision is ignored).
  * workspace >= tsdfs_backward_workspace_size.                                */
 size_t tsdfs_backward_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays, int64_t max_samples);
 int render_rays_backward(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
                          const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
-                         int64_t max_samples, const float* d_rgb, const float* d_depth, float d_eik,
+                         int64_t max_samples, const float* d_rgb, const float* d_depth, const float* d_eik,
                          float* d_sdf_w, float* d_rgb_w, void* workspace, size_t ws_bytes, tsdfs_stream_t stream);
 
 /* ---- BF16 tensor-core parameter layout --------------------------------------

@@ -206,7 +206,7 @@ def render_rays_backward(mlp: "Mlp", ray_o, ray_d, t_n, t_f, offsets, status, ma
     n = ray_o.shape[0]
     _check(lib().render_rays_backward(C.byref(mlp.c), _p(ray_o), _p(ray_d), _p(t_n), _p(t_f), _p(offsets),
                                       _p(status), C.c_int64(n), C.c_int64(max_samples), _p(d_rgb), _p(d_depth),
-                                      C.c_float(d_eik), _p(d_sdf_w), _p(d_rgb_w), _p(workspace),
+                                      _p(d_eik), _p(d_sdf_w), _p(d_rgb_w), _p(workspace),
                                       C.c_size_t(workspace.numel()), _stream()))
 
 
@@ -344,3 +344,36 @@ class HierRenderer:
         render_rays_hier96(self.mlp, grid, rays_o, rays_d, t_near, t_far, o.rgb, o.depth, o.wsum, o.normal,
                            self.workspace)
         return o
+
+
+class RenderFunction(torch.autograd.Function):
+    """render_rays as a differentiable torch op over the packed fp32 parameters.
+
+    forward(sdf_w, rgb_w, mlp, rays_o, rays_d, bounds, max_samples) -> (rgb, depth, eik);
+    backward calls render_rays_backward (FP32 networks, activations recomputed).
+    """
+
+    @staticmethod
+    def forward(ctx, sdf_w, rgb_w, mlp, rays_o, rays_d, b, max_samples):
+        n = rays_o.shape[0]
+        out = RenderOut(n, device=rays_o.device)
+        ws = _bytes(tsdfs_render_workspace_size(mlp, n, max_samples), rays_o.device)
+        render_rays(mlp, rays_o, rays_d, b.t_n, b.t_f, b.offsets, b.status, max_samples, out.rgb, out.depth,
+                    out.wsum, out.normal, out.eik, ws)
+        ctx.mlp, ctx.b, ctx.max_samples = mlp, b, max_samples
+        ctx.save_for_backward(rays_o, rays_d)
+        return out.rgb, out.depth, out.eik
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_eik):
+        rays_o, rays_d = ctx.saved_tensors
+        mlp, b, ms = ctx.mlp, ctx.b, ctx.max_samples
+        n = rays_o.shape[0]
+        d_sdf = torch.zeros_like(mlp.sdf_w)
+        d_rgb = torch.zeros_like(mlp.rgb_w)
+        ws = _bytes(tsdfs_backward_workspace_size(mlp, n, ms), rays_o.device)
+        gr = (g_rgb if g_rgb is not None else torch.zeros((n, 3), device=rays_o.device)).contiguous().float()
+        gd = None if g_depth is None else g_depth.contiguous().float()
+        ge = None if g_eik is None else g_eik.contiguous().float()
+        render_rays_backward(mlp, rays_o, rays_d, b.t_n, b.t_f, b.offsets, b.status, ms, gr, gd, ge, d_sdf, d_rgb, ws)
+        return d_sdf, d_rgb, None, None, None, None, None

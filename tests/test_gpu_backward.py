@@ -1,0 +1,107 @@
+"""GPU parity of render_rays_backward (parameter gradients through compositing,
+the NeuS opacity, both networks and the second-order terms through grad f)
+against the oracle's FP64 reverse-mode gradient of the same functional, whose
+own correctness is pinned by central differences in the CPU tests."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cgrid
+from oracle import render as orr
+from paper_2311_17878_gb300 import build, synth
+from paper_2311_17878_gb300 import tsdfs as T
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    T.lib()
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+def case(scene, n_rays, seed):
+    if scene == "tiny":
+        wl = synth.tiny_workload()
+        V, _ = cgrid.integrate_projective(wl.grid, wl.views, "f32")
+        o, d = wl.rays_o, wl.rays_d
+        b = cgrid.ray_bounds(wl.grid, V, o, d, wl.bounds, "f32")
+        live = np.nonzero(b["status"] != 0)[0]
+        idx = np.random.default_rng(seed).choice(live, n_rays, replace=False)
+    else:
+        wl = synth.room_workload(with_views=False)
+        V = synth.analytic_tsdf_torch(wl.scene, wl.grid, device="cuda").cpu().numpy()
+        o, d = synth.room_heldout_rays(0)
+        idx = synth.sub_sample(len(o), n_rays, seed=seed)
+        b = cgrid.ray_bounds(wl.grid, V, o[idx], d[idx], wl.bounds, "f32")
+        return o[idx], d[idx], b
+    b = {k: v[idx] for k, v in b.items()}
+    return o[idx], d[idx], b
+
+
+def oracle_grads(spec, o, d, b, d_rgb, d_depth, d_eik):
+    net = orr.Net(spec, requires_grad=True)
+    out = orr.render_bounded(net, o, d, b["t_n"].astype(np.float64), b["t_f"].astype(np.float64), b["n"])
+    counts = torch.as_tensor(b["n"].astype(np.int64))
+    eik_ray = torch.zeros(len(counts), dtype=torch.float64).index_add(
+        0, torch.repeat_interleave(torch.arange(len(counts)), counts), out["eik"])
+    eik_ray = eik_ray * torch.as_tensor(b["status"] == 1)
+    L = (out["rgb"] * torch.as_tensor(d_rgb, dtype=torch.float64)).sum() \
+        + (out["depth"] * torch.as_tensor(d_depth, dtype=torch.float64)).sum() \
+        + (eik_ray * torch.as_tensor(d_eik, dtype=torch.float64)).sum()
+    gs = torch.autograd.grad(L, net.params())
+    sdf = np.concatenate([np.concatenate([gs[2 * i].numpy().reshape(-1), gs[2 * i + 1].numpy()]) for i in range(len(spec.sdf))])
+    k = 2 * len(spec.sdf)
+    rgb = np.concatenate([np.concatenate([gs[k + 2 * i].numpy().reshape(-1), gs[k + 2 * i + 1].numpy()]) for i in range(len(spec.rgb))])
+    return sdf, rgb
+
+
+@pytest.mark.parametrize("scene,n_rays", [("tiny", 96), ("room", 48)])
+def test_backward_matches_oracle_gradient(scene, n_rays):
+    o, d, b = case(scene, n_rays, seed=41)
+    spec = synth.scene_mlp(scene)
+    rng = np.random.default_rng(7)
+    d_rgb = rng.normal(0, 1, (n_rays, 3)).astype(np.float32)
+    d_depth = rng.normal(0, 1, n_rays).astype(np.float32)
+    d_eik = np.full(n_rays, 0.1, np.float32)
+    mlp = T.Mlp(spec)
+    offsets = np.concatenate([[0], np.cumsum(b["n"])]).astype(np.int32)
+    total = int(offsets[-1])
+    d_sdf = torch.zeros_like(mlp.sdf_w)
+    d_rw = torch.zeros_like(mlp.rgb_w)
+    ws = torch.empty(T.tsdfs_backward_workspace_size(mlp, n_rays, total), dtype=torch.uint8, device="cuda")
+    T.render_rays_backward(mlp, dev(o), dev(d), dev(b["t_n"].astype(np.float32)), dev(b["t_f"].astype(np.float32)),
+                           dev(offsets), dev(b["status"]), total, dev(d_rgb), dev(d_depth), dev(d_eik), d_sdf, d_rw, ws)
+    torch.cuda.synchronize()
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == 0, bits
+    ref_sdf, ref_rgb = oracle_grads(spec, o, d, b, d_rgb, d_depth, d_eik)
+    for got, ref, name in [(d_sdf.cpu().numpy(), ref_sdf, "sdf"), (d_rw.cpu().numpy(), ref_rgb, "rgb")]:
+        scale = np.abs(ref).max()
+        err = np.abs(got - ref).max() / scale
+        print(f"{scene} d{name}: max |err| / max |grad| = {err:.2e} (max |grad| {scale:.3e})")
+        assert err < 2e-3, name
+
+
+def test_autograd_function_accumulates_and_matches_direct_call():
+    o, d, b = case("tiny", 64, seed=5)
+    spec = synth.scene_mlp("tiny")
+    mlp = T.Mlp(spec)
+    offsets = np.concatenate([[0], np.cumsum(b["n"])]).astype(np.int32)
+    bb = T.Bounds(len(o))
+    bb.t_n.copy_(dev(b["t_n"].astype(np.float32)))
+    bb.t_f.copy_(dev(b["t_f"].astype(np.float32)))
+    bb.offsets.copy_(dev(offsets))
+    bb.status.copy_(dev(b["status"]))
+    sdf_w = mlp.sdf_w.clone().requires_grad_(True)
+    rgb_w = mlp.rgb_w.clone().requires_grad_(True)
+    rgb, depth, eik = T.RenderFunction.apply(sdf_w, rgb_w, mlp, dev(o), dev(d), bb, int(offsets[-1]))
+    target = torch.rand_like(rgb)
+    loss = (rgb - target).abs().mean() + 0.1 * eik.sum() / max(int(b["n"][b["status"] == 1].sum()), 1)
+    loss.backward()
+    assert torch.isfinite(sdf_w.grad).all() and torch.isfinite(rgb_w.grad).all()
+    assert sdf_w.grad.abs().sum() > 0 and rgb_w.grad.abs().sum() > 0
