@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--precision", choices=["f16", "bf16", "f32"], default="f16")
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--ref-rays", type=int, default=48, help="rays per reference-arm step")
+    ap.add_argument("--ds-vox", type=float, default=1.0, help="D_s of Alg. 1 in voxels (Sec. 4.2 uses 1)")
     return ap.parse_args()
 
 
@@ -141,35 +142,63 @@ def measured_peaks():
 
 
 # ----------------------------------------------------------------------------
-def build_scene(device):
+NET_DEPTH_W, NET_DEPTH_H = 320, 240   # resolution of the network-rendered training views
+
+
+def build_scene(device, mlp):
+    """Fuse the room's TSDF twice: from the 100 analytic 640x480 depth maps (the
+    configuration's fusion workload, timed) and from the network's own rendered
+    depth of the same training poses (Sec. 3.2: the TSDF is built from the
+    trained model's depth, Eq. 2), rendered with the same-GPU 64+32 sampler.
+    The second grid is the one the timed render path marches."""
     import torch
     from paper_2311_17878_gb300 import synth
     from paper_2311_17878_gb300 import tsdfs as T
     wl = synth.room_workload_torch(device=device)
-    grid = T.Grid(wl.grid, device=device).init()
+    grid_an = T.Grid(wl.grid, device=device).init()
     depth = wl.views.depth.contiguous()
     K = torch.tensor(wl.views.K, device=device)
     P = torch.tensor(wl.views.c2w, device=device)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    grid.integrate(depth, K, P)
-    e1.record()
-    torch.cuda.synchronize()
-    fuse_ms = e0.elapsed_time(e1)
-    # re-fuse a second time for a warm timing (fresh grid)
-    grid.init()
-    e0.record()
-    grid.integrate(depth, K, P)
-    e1.record()
-    torch.cuda.synchronize()
-    fuse_ms = min(fuse_ms, e0.elapsed_time(e1))
+    fuse_ms = []
+    for _ in range(3):
+        grid_an.init()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        grid_an.integrate(depth, K, P)
+        e1.record()
+        torch.cuda.synchronize()
+        fuse_ms.append(e0.elapsed_time(e1))
+    # the network's depth of the training views
+    t_net = time.perf_counter()
+    c2ws = wl.views.c2w.reshape(-1, 3, 4).astype(np.float64)
+    f = 500.0 * NET_DEPTH_W / 640.0
+    hier = T.HierRenderer(mlp, NET_DEPTH_W * NET_DEPTH_H, device=device)
+    ndepth = torch.empty((len(c2ws), NET_DEPTH_H, NET_DEPTH_W), dtype=torch.float32, device=device)
+    bp = wl.bounds
+    for i, c2w in enumerate(c2ws):
+        o, d = synth.pinhole_rays(c2w, f, f, NET_DEPTH_W / 2.0, NET_DEPTH_H / 2.0, NET_DEPTH_W, NET_DEPTH_H)
+        out = hier.render(grid_an, torch.tensor(o, dtype=torch.float32, device=device),
+                          torch.tensor(d, dtype=torch.float32, device=device), bp.t_near, bp.t_far)
+        ndepth[i] = torch.where(out.wsum > 0.5, out.depth, torch.full_like(out.depth, float("inf"))).reshape(
+            NET_DEPTH_H, NET_DEPTH_W)
+    Kn = torch.tensor(np.tile(np.array([f, f, NET_DEPTH_W / 2.0, NET_DEPTH_H / 2.0], np.float32), (len(c2ws), 1)),
+                      device=device)
+    grid = T.Grid(wl.grid, device=device).init()
+    grid.integrate(ndepth, Kn, P)
     mask = grid.inside_mask(wl.bounds.nb_radius)
+    torch.cuda.synchronize()
+    t_net = time.perf_counter() - t_net
     rays = []
     for i in range(N_VIEWS_TIMED):
         o, d = synth.room_heldout_rays(i)
         rays.append((torch.tensor(o, device=device), torch.tensor(d, device=device), o, d))
-    return wl, grid, mask, rays, fuse_ms, depth
+    fusion = {"workload": "100 analytic 640x480 depth maps into 256^3", "ms": min(fuse_ms),
+              "voxels_per_s": wl.grid.nx * wl.grid.ny * wl.grid.nz / (min(fuse_ms) / 1e3),
+              "voxel_views_per_s": wl.grid.nx * wl.grid.ny * wl.grid.nz * depth.shape[0] / (min(fuse_ms) / 1e3),
+              "grid_for_render": f"fused from the network's depth of the 100 training poses at {NET_DEPTH_W}x{NET_DEPTH_H} "
+                                 f"(64+32 sampler, same GPU), setup {t_net:.1f} s"}
+    return wl, grid, grid_an, mask, rays, fusion, depth
 
 
 def run_ours(args, ws, rank, local):
@@ -179,12 +208,13 @@ def run_ours(args, ws, rank, local):
     from paper_2311_17878_gb300 import tsdfs as T
     B.build()
     dev = f"cuda:{local}"
-    wl, grid, mask, rays, fuse_ms, depth = build_scene(dev)
-    bp = wl.bounds
     spec = synth.scene_mlp("room")
     prec = args.precision
     PREC = {"f16": T.TSDFS_PREC_F16, "bf16": T.TSDFS_PREC_BF16, "f32": T.TSDFS_PREC_F32}
     mlp = T.Mlp(spec, PREC[prec], device=dev)
+    mlp_depth = mlp if prec != "f32" else T.Mlp(spec, T.TSDFS_PREC_F16, device=dev)
+    wl, grid, grid_an, mask, rays, fusion, depth = build_scene(dev, mlp_depth)
+    bp = synth.BoundsParams(**{**wl.bounds.__dict__, "d_s": args.ds_vox * wl.grid.voxel_size})
     n = rays[0][0].shape[0]
     max_samples = n * max(bp.n_max, bp.n_fallback)
     bounds = T.Bounds(n, device=dev)
@@ -199,10 +229,11 @@ def run_ours(args, ws, rank, local):
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
-    samples_per_view = []
+    samples_per_view, fallback_per_view = [], []
     for i in range(N_VIEWS_TIMED):
         bounds.compute(grid, rays[i][0], rays[i][1], bp, mask)
         samples_per_view.append(int(bounds.offsets[-1].item()))
+        fallback_per_view.append(round(float((bounds.status == 2).float().mean().item()), 4))
     st = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     T.lib().tsdfs_profile(1)
@@ -253,6 +284,7 @@ def run_ours(args, ws, rank, local):
     quality = None if args.no_quality or rank != 0 else run_quality(spec, wl, grid, bounds, rend, hier["renderer"], rays,
                                                                     bp, mask)
     cpu = run_cpu_baseline(wl, grid, rays, bp, spec) if (rank == 0 and ws == 1) else None
+    train = run_train(spec, wl, grid, mask, dev) if rank == 0 else None
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -260,16 +292,56 @@ def run_ours(args, ws, rank, local):
         "dtype": prec, "data": "synthetic (seeded room scene, fitted networks)",
         "config": {"workload": WORKLOAD, "rays_per_step": n, "views": N_VIEWS_TIMED,
                    "samples_per_step": samples_timed / args.steps, "grid": "256^3 f32 + uint8",
+                   "d_s_vox": args.ds_vox, "fallback_frac_per_view": fallback_per_view,
                    "networks": "SDF 8x256 PE6 skip4 + colour 4x256 PE4", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}, rays independent", "wall_s": t_wall},
         "e2e": e2e, "gpu_launches": int(n_all.value), "roofline": roof, "kernel_time": kernel_share,
         "comparator": {k: v for k, v in hier.items() if k != "renderer"},
-        "fusion": {"ms": fuse_ms, "voxels_per_s": wl.grid.nx * wl.grid.ny * wl.grid.nz / (fuse_ms / 1e3),
-                   "views": int(depth.shape[0]), "algo_bytes": 256 ** 3 * 10 + depth.numel() * 4,
-                   "GB_per_s": (256 ** 3 * 10 + depth.numel() * 4) / (fuse_ms / 1e3) / 1e9, "peak_hbm_gbs": hbm},
+        "fusion": fusion, "train_step": train,
         "quality": quality, "cpu_baseline": cpu, "clocks": clocks,
     }
     return line
+
+
+def run_train(spec, wl, grid, mask, dev, n_rays=8192, iters=5):
+    """One training step of the networks (FP32): 8192 random rays of the training
+    views, bounds, render through the autograd op, L1 colour + 0.1 eikonal on the
+    bounded samples, backward (render_rays_backward)."""
+    import torch
+    from paper_2311_17878_gb300 import synth
+    from paper_2311_17878_gb300 import tsdfs as T
+    mlp = T.Mlp(spec, T.TSDFS_PREC_F32, device=dev)
+    o, d, vi, px, py = synth.random_rays_from_views(wl.views, n_rays)
+    o, d = torch.tensor(o, device=dev), torch.tensor(d, device=dev)
+    target = torch.rand((n_rays, 3), device=dev, generator=torch.Generator(device=dev).manual_seed(0))
+    b = T.Bounds(n_rays, device=dev)
+    ms_cap = n_rays * max(wl.bounds.n_max, wl.bounds.n_fallback)
+    sdf_w = mlp.sdf_w.clone().requires_grad_(True)
+    rgb_w = mlp.rgb_w.clone().requires_grad_(True)
+
+    def step():
+        b.compute(grid, o, d, wl.bounds, mask)
+        n_b = torch.clamp((b.n * (b.status == 1)).sum(), min=1)
+        rgb, depth, eik = T.RenderFunction.apply(sdf_w, rgb_w, mlp, o, d, b, ms_cap)
+        loss = (rgb - target).abs().mean() + 0.1 * eik.sum() / n_b
+        sdf_w.grad = None
+        rgb_w.grad = None
+        loss.backward()
+        return loss
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        loss = step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    return {"rays": n_rays, "ms_per_step": ms, "rays_per_s": n_rays / (ms / 1e3),
+            "samples": int(b.offsets[-1].item()), "loss": float(loss.item()),
+            "what": "bounds + render (fp32) + L1 + 0.1 eikonal + backward through both networks"}
 
 
 def run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev):
@@ -354,11 +426,40 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask):
     with torch.no_grad():
         ort = orr.render_bounded(net, on, dn, tn, tf, cnt)["rgb"].numpy()
     p_gpu, p_or, p_h = orr.psnr(gpu_rgb, dense), orr.psnr(ort, dense), orr.psnr(hier_rgb, dense)
+    # D_s sweep (surface criterion of Alg. 1) on the same pixels: GPU bounds + render
+    from paper_2311_17878_gb300 import tsdfs as T
+    vs = wl.grid.voxel_size
+    sweep = []
+    b2 = T.Bounds(o.shape[0], device=o.device)
+    for ds, st_vox in ((1.0, 2.0), (2.0, 2.0), (3.0, 2.0), (2.0, 1.0), (3.0, 1.0), (2.0, 0.5), (3.0, 0.5), (3.0, 0.25)):
+        bp2 = synth.BoundsParams(**{**bp.__dict__, "d_s": ds * vs, "step": st_vox * vs,
+                                    "n_max": int(bp.n_max * max(1.0, bp.step / (st_vox * vs)))})
+        b2.compute(grid, o, d, bp2, mask)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b2.compute(grid, o, d, bp2, mask)
+        o2 = rend.render(o, d, b2)
+        e1.record()
+        torch.cuda.synchronize()
+        sweep.append({"d_s_vox": ds, "step_vox": st_vox, "psnr": orr.psnr(o2.rgb[idx_t].cpu().numpy(), dense),
+                      "samples_per_ray": float(b2.n.float().mean().item()),
+                      "fallback_frac": float((b2.status == 2).float().mean().item()),
+                      "ms_view0": e0.elapsed_time(e1)})
+    dd = orr.dense_reference(net, on, dn, t0, te, n=DENSE_SAMPLES)
+    err = np.abs(gpu_rgb - dd["rgb"].numpy()).max(1)
+    worst = []
+    for i in np.argsort(-err)[:8]:
+        worst.append({"err": float(err[i]), "wsum": float(out.wsum[idx_t][i].item()),
+                      "depth": float(out.depth[idx_t][i].item()), "depth_dense": float(dd["depth"][i]),
+                      "t_n": float(tn[i]), "t_f": float(tf[i]), "n": int(cnt[i]),
+                      "status": int(bounds.status[idx_t][i].item())})
     return {"pixels": QUALITY_PIXELS, "reference": f"oracle FP64 dense {DENSE_SAMPLES} samples over [t0,t_end]",
-            "psnr_tsdf_gpu": p_gpu, "psnr_tsdf_oracle": p_or, "psnr_hier96_gpu": p_h,
-            "meets_oracle_minus_0p1dB": bool(p_gpu >= p_or - 0.1),
+            "worst": worst, "d_s_vox": bp.d_s / vs, "psnr_tsdf_gpu": p_gpu, "psnr_tsdf_oracle": p_or, "psnr_hier96_gpu": p_h,
+            "meets_oracle_minus_0p1dB": bool(p_gpu >= p_or - 0.1), "tsdf_ge_hier96": bool(p_gpu >= p_h),
             "samples_per_ray_tsdf": float(bounds.n.float().mean().item()),
-            "fallback_frac": float((bounds.status == 2).float().mean().item()), "oracle_s": time.perf_counter() - t_q}
+            "fallback_frac": float((bounds.status == 2).float().mean().item()), "d_s_sweep": sweep,
+            "oracle_s": time.perf_counter() - t_q}
 
 
 def run_cpu_baseline(wl, grid, rays, bp, spec, n_rays=64):
