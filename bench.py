@@ -47,7 +47,13 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["f16", "bf16", "f32"], default="f16")
     ap.add_argument("--no-quality", action="store_true")
-    ap.add_argument("--ref-rays", type=int, default=48, help="rays per reference-arm step")
+    ap.add_argument("--sweep", action="store_true", help="add the D_s / spacing quality sweep")
+    ap.add_argument("--grid-source", choices=["network", "analytic"], default="network",
+                    help="depth maps the marched grid is fused from (analytic: the exact scene, no network pre-pass)")
+    ap.add_argument("--rays", type=int, default=0, help="seeded subset of each view's rays (0: all 307200)")
+    ap.add_argument("--only-main", action="store_true", help="time the render path only (no e2e / comparator / "
+                                                                  "quality / cpu / training legs): the small profiling case")
+    ap.add_argument("--ref-rays", type=int, default=2048, help="rays per reference-arm step")
     ap.add_argument("--ds-vox", type=float, default=1.0, help="D_s of Alg. 1 in voxels (Sec. 4.2 uses 1)")
     return ap.parse_args()
 
@@ -145,7 +151,7 @@ def measured_peaks():
 NET_DEPTH_W, NET_DEPTH_H = 320, 240   # resolution of the network-rendered training views
 
 
-def build_scene(device, mlp):
+def build_scene(device, mlp, source="network", n_rays=0):
     """Fuse the room's TSDF twice: from the 100 analytic 640x480 depth maps (the
     configuration's fusion workload, timed) and from the network's own rendered
     depth of the same training poses (Sec. 3.2: the TSDF is built from the
@@ -169,6 +175,20 @@ def build_scene(device, mlp):
         e1.record()
         torch.cuda.synchronize()
         fuse_ms.append(e0.elapsed_time(e1))
+    rays = []
+    for i in range(N_VIEWS_TIMED):
+        o, d = synth.room_heldout_rays(i)
+        if n_rays:
+            idx = np.sort(synth.sub_sample(len(o), n_rays, seed=50 + i))
+            o, d = np.ascontiguousarray(o[idx]), np.ascontiguousarray(d[idx])
+        rays.append((torch.tensor(o, device=device), torch.tensor(d, device=device), o, d))
+    fusion = {"workload": "100 analytic 640x480 depth maps into 256^3", "ms": min(fuse_ms),
+              "voxels_per_s": wl.grid.nx * wl.grid.ny * wl.grid.nz / (min(fuse_ms) / 1e3),
+              "voxel_views_per_s": wl.grid.nx * wl.grid.ny * wl.grid.nz * depth.shape[0] / (min(fuse_ms) / 1e3)}
+    if source == "analytic":
+        mask = grid_an.inside_mask(wl.bounds.nb_radius)
+        fusion["grid_for_render"] = "fused from the 100 analytic depth maps"
+        return wl, grid_an, grid_an, mask, rays, fusion, depth
     # the network's depth of the training views
     t_net = time.perf_counter()
     c2ws = wl.views.c2w.reshape(-1, 3, 4).astype(np.float64)
@@ -189,15 +209,8 @@ def build_scene(device, mlp):
     mask = grid.inside_mask(wl.bounds.nb_radius)
     torch.cuda.synchronize()
     t_net = time.perf_counter() - t_net
-    rays = []
-    for i in range(N_VIEWS_TIMED):
-        o, d = synth.room_heldout_rays(i)
-        rays.append((torch.tensor(o, device=device), torch.tensor(d, device=device), o, d))
-    fusion = {"workload": "100 analytic 640x480 depth maps into 256^3", "ms": min(fuse_ms),
-              "voxels_per_s": wl.grid.nx * wl.grid.ny * wl.grid.nz / (min(fuse_ms) / 1e3),
-              "voxel_views_per_s": wl.grid.nx * wl.grid.ny * wl.grid.nz * depth.shape[0] / (min(fuse_ms) / 1e3),
-              "grid_for_render": f"fused from the network's depth of the 100 training poses at {NET_DEPTH_W}x{NET_DEPTH_H} "
-                                 f"(64+32 sampler, same GPU), setup {t_net:.1f} s"}
+    fusion["grid_for_render"] = (f"fused from the network's depth of the 100 training poses at {NET_DEPTH_W}x"
+                                 f"{NET_DEPTH_H} (64+32 sampler, same GPU), setup {t_net:.1f} s")
     return wl, grid, grid_an, mask, rays, fusion, depth
 
 
@@ -213,7 +226,7 @@ def run_ours(args, ws, rank, local):
     PREC = {"f16": T.TSDFS_PREC_F16, "bf16": T.TSDFS_PREC_BF16, "f32": T.TSDFS_PREC_F32}
     mlp = T.Mlp(spec, PREC[prec], device=dev)
     mlp_depth = mlp if prec != "f32" else T.Mlp(spec, T.TSDFS_PREC_F16, device=dev)
-    wl, grid, grid_an, mask, rays, fusion, depth = build_scene(dev, mlp_depth)
+    wl, grid, grid_an, mask, rays, fusion, depth = build_scene(dev, mlp_depth, args.grid_source, args.rays)
     bp = synth.BoundsParams(**{**wl.bounds.__dict__, "d_s": args.ds_vox * wl.grid.voxel_size})
     n = rays[0][0].shape[0]
     max_samples = n * max(bp.n_max, bp.n_fallback)
@@ -277,14 +290,15 @@ def run_ours(args, ws, rank, local):
                 "frac": achieved / fp32_peak, "traffic": None,
                 "peak_kind": "fp32 FMA, 152 SMs x 128 lanes x 2 x 2.07 GHz", "kernel": "mlp_simt"}
     kernel_share = {"mlp_ms_per_step": mlp_ms, "all_kernels_ms_per_step": ms_all.value / max(args.steps, 1)}
+    main_only = args.only_main
     # end to end through the public API with host buffers
-    e2e = run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev)
+    e2e = None if main_only else run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev)
     # hierarchical comparator on the same views
-    hier = run_hier(args, mlp, grid, rays, bp, n, dev, flush)
-    quality = None if args.no_quality or rank != 0 else run_quality(spec, wl, grid, bounds, rend, hier["renderer"], rays,
-                                                                    bp, mask)
-    cpu = run_cpu_baseline(wl, grid, rays, bp, spec) if (rank == 0 and ws == 1) else None
-    train = run_train(spec, wl, grid, mask, dev) if rank == 0 else None
+    hier = {} if main_only else run_hier(args, mlp, grid, rays, bp, n, dev, flush)
+    quality = None if (args.no_quality or main_only or rank != 0) else run_quality(
+        spec, wl, grid, bounds, rend, hier["renderer"], rays, bp, mask, args.sweep)
+    cpu = run_cpu_baseline(wl, grid, rays, bp, spec) if (rank == 0 and ws == 1 and not main_only) else None
+    train = run_train(spec, wl, grid, mask, dev) if (rank == 0 and not main_only) else None
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -293,6 +307,7 @@ def run_ours(args, ws, rank, local):
         "config": {"workload": WORKLOAD, "rays_per_step": n, "views": N_VIEWS_TIMED,
                    "samples_per_step": samples_timed / args.steps, "grid": "256^3 f32 + uint8",
                    "d_s_vox": args.ds_vox, "fallback_frac_per_view": fallback_per_view,
+                   "grid_source": args.grid_source, "ray_subset": args.rays or None,
                    "networks": "SDF 8x256 PE6 skip4 + colour 4x256 PE4", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}, rays independent", "wall_s": t_wall},
         "e2e": e2e, "gpu_launches": int(n_all.value), "roofline": roof, "kernel_time": kernel_share,
@@ -399,7 +414,7 @@ def run_hier(args, mlp, grid, rays, bp, n, dev, flush):
             "ms_per_step": tot / steps, "samples_per_ray": 96 + 64 * 0, "renderer": h}
 
 
-def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask):
+def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=False):
     """PSNR against the oracle's dense reference (FP64, DENSE_SAMPLES midpoints
     over [t0, t_end]) on a seeded pixel subset of view 0."""
     import torch
@@ -419,7 +434,8 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask):
     t0, te, ok = cgrid.clip_rays(wl.grid, on, dn, bp.t_near, bp.t_far, "f64")
     t_q = time.perf_counter()
     net = orr.Net(spec)
-    dense = orr.dense_reference(net, on, dn, t0, te, n=DENSE_SAMPLES)["rgb"].numpy()
+    dd = orr.dense_reference(net, on, dn, t0, te, n=DENSE_SAMPLES)
+    dense = dd["rgb"].numpy()
     tn = bounds.t_n[idx_t].cpu().numpy().astype(np.float64)
     tf = bounds.t_f[idx_t].cpu().numpy().astype(np.float64)
     cnt = bounds.n[idx_t].cpu().numpy()
@@ -431,7 +447,8 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask):
     vs = wl.grid.voxel_size
     sweep = []
     b2 = T.Bounds(o.shape[0], device=o.device)
-    for ds, st_vox in ((1.0, 2.0), (2.0, 2.0), (3.0, 2.0), (2.0, 1.0), (3.0, 1.0), (2.0, 0.5), (3.0, 0.5), (3.0, 0.25)):
+    grid_sweep = ((1.0, 2.0), (2.0, 2.0), (3.0, 2.0), (2.0, 1.0), (3.0, 1.0), (2.0, 0.5), (3.0, 0.5), (3.0, 0.25))
+    for ds, st_vox in (grid_sweep if sweep_on else ()):
         bp2 = synth.BoundsParams(**{**bp.__dict__, "d_s": ds * vs, "step": st_vox * vs,
                                     "n_max": int(bp.n_max * max(1.0, bp.step / (st_vox * vs)))})
         b2.compute(grid, o, d, bp2, mask)
@@ -446,8 +463,7 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask):
                       "samples_per_ray": float(b2.n.float().mean().item()),
                       "fallback_frac": float((b2.status == 2).float().mean().item()),
                       "ms_view0": e0.elapsed_time(e1)})
-    dd = orr.dense_reference(net, on, dn, t0, te, n=DENSE_SAMPLES)
-    err = np.abs(gpu_rgb - dd["rgb"].numpy()).max(1)
+    err = np.abs(gpu_rgb - dense).max(1)
     worst = []
     for i in np.argsort(-err)[:8]:
         worst.append({"err": float(err[i]), "wsum": float(out.wsum[idx_t][i].item()),
@@ -462,25 +478,30 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask):
             "oracle_s": time.perf_counter() - t_q}
 
 
-def run_cpu_baseline(wl, grid, rays, bp, spec, n_rays=64):
+def run_cpu_baseline(wl, grid, rays, bp, spec, seconds=10.0, chunk=2048):
     """The oracle as it stands, on the host cores: Alg. 1 bounds (C, fp32-exact)
-    + FP64 render (torch CPU) of a seeded sample of view-0 rays on the fused grid."""
+    + FP64 render (torch CPU) of seeded chunks of view-0 rays on the fused grid,
+    repeated until about `seconds` of CPU work."""
     import torch
     from oracle import cgrid
     from oracle import render as orr
     from paper_2311_17878_gb300 import synth
     V = grid.V.cpu().numpy()
-    idx = synth.sub_sample(rays[0][2].shape[0], n_rays, seed=32)
-    o, d = rays[0][2][idx], rays[0][3][idx]
+    n_view = rays[0][2].shape[0]
+    order = synth.sub_sample(n_view, n_view, seed=32)
     net = orr.Net(spec)
-    t = time.perf_counter()
-    b = cgrid.ray_bounds(wl.grid, V, o, d, bp, "f32")
-    with torch.no_grad():
-        orr.render_bounded(net, o, d, b["t_n"].astype(np.float64), b["t_f"].astype(np.float64), b["n"])
+    done, t = 0, time.perf_counter()
+    while done < n_view and time.perf_counter() - t < seconds:
+        idx = order[done:done + chunk]
+        o, d = rays[0][2][idx], rays[0][3][idx]
+        b = cgrid.ray_bounds(wl.grid, V, o, d, bp, "f32")
+        with torch.no_grad():
+            orr.render_bounded(net, o, d, b["t_n"].astype(np.float64), b["t_f"].astype(np.float64), b["n"])
+        done += len(idx)
     dt = time.perf_counter() - t
-    return {"value": n_rays / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"{n_rays} seeded rays of one 640x480 view: C bounds (1 thread) + torch FP64 render",
-            "seconds": dt}
+    return {"value": done / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{done} seeded rays of one 640x480 view in chunks of {chunk}: C bounds (1 thread) "
+                      f"+ torch FP64 render", "seconds": dt}
 
 
 # ----------------------------------------------------------------------------

@@ -75,9 +75,10 @@ template <int ARCH> struct TcArch {
     __host__ __device__ static constexpr int64_t param_offset(int L) {
         return L < A::kSdfLayers ? sdf_layer_offset<ARCH>(L) : rgb_layer_offset<ARCH>(L - A::kSdfLayers);
     }
+    // each layer's biases start on a 16-float boundary (zero padded to Np)
     __host__ __device__ static constexpr int bias_offset(int L) {
         int o = 0;
-        for (int l = 0; l < L; ++l) o += layer(l).N;
+        for (int l = 0; l < L; ++l) o += layer(l).Np;
         return o;
     }
     __host__ __device__ static constexpr int bias_total() { return bias_offset(kLayers); }
@@ -166,6 +167,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// 16 TMEM lanes x 16 columns (two 16x256b repetitions): thread t receives lane
+// base + t/4 in registers 0, 1 (columns 2(t%4), 2(t%4)+1) and 4, 5 (the same
+// columns + 8), and lane base + 8 + t/4 in registers 2, 3 and 6, 7
+__device__ __forceinline__ void tmem_ld16x256_x2(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+// four 8x8 16-bit matrices to shared memory: thread i supplies the address of row
+// i % 8 of matrix i / 8; register j holds row t/4, columns 2(t%4), 2(t%4)+1 of matrix j
+__device__ __forceinline__ void stmatrix4(uint32_t addr, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(r0), "r"(r1), "r"(r2),
+                 "r"(r3)
+                 : "memory");
+}
 
 // element (r, k) of a K-major no-swizzle operand with Kp columns -> byte offset
 __device__ __forceinline__ uint32_t a_off(int r, int k, int Kp) {
@@ -198,15 +217,15 @@ __device__ __forceinline__ float tanh_fast(float x) {
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-// log(1 + u) on [0, 1]: least-squares polynomial of degree 6 at Chebyshev
-// nodes, |error| < 2e-6 (fitted for this kernel; see the tests)
+// log(1 + u) on [0, 1]: degree-4 polynomial with p(0) = 0 and p(1) = ln 2 exactly,
+// minimax-fitted (Lawson iteration) at Chebyshev nodes, |error| < 8e-5; divided by
+// beta = 100 in the softplus this is below the FP16 rounding of the activations
+// (fitted for this kernel; see the tests)
 __device__ __forceinline__ float log1p_unit(float u) {
-    float p = -0.017877891659736633f;
-    p = fmaf(p, u, 0.08419863134622574f);
-    p = fmaf(p, u, -0.19223858416080475f);
-    p = fmaf(p, u, 0.3168778717517853f);
-    p = fmaf(p, u, -0.497702956199646f);
-    p = fmaf(p, u, 0.9998888969421387f);
+    float p = -0.05692862346768379f;
+    p = fmaf(p, u, 0.22263112664222717f);
+    p = fmaf(p, u, -0.4698040187358856f);
+    p = fmaf(p, u, 0.9972487092018127f);
     return p * u;
 }
 // softplus_beta(z) and its slope sigma(beta z) from one tanh:
@@ -288,7 +307,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
         while (L + 1 < NL && TA::bias_offset(L + 1) <= i) ++L;
         const TcLayer ly = TA::layer(L);
         const float* W = (ly.sdf ? p.sdf_w : p.rgb_w) + TA::param_offset(L);
-        sbias[i] = __ldg(W + (int64_t)ly.N * ly.K + (i - TA::bias_offset(L)));
+        const int j = i - TA::bias_offset(L);
+        sbias[i] = j < ly.N ? __ldg(W + (int64_t)ly.N * ly.K + j) : 0.0f;
     }
     if (warp == 9) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -391,6 +411,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
         const int s = 16 * q + (lane & 15);           // sample within the tile
         const int val_lane = lane & 15;               // lane holding this sample's value row
         const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
+        // hidden layers read 16-lane fragments: value rows (acc0) / d/dy rows (acc1) at
+        // lanes 32q..32q+15, d/dx (acc0) / d/dz (acc1) at 32q+16..32q+31, so one thread
+        // holds all four rows of its samples and applies the slope without a shuffle
+        const int fs = lane >> 2, fc = 2 * (lane & 3);
+        const uint32_t t_v = tmem + lane_addr, t_x = tmem + (((uint32_t)(32 * q + 16)) << 16);
+        const uint32_t t_y = t_v + 256, t_z = t_x + 256;
         const float half_beta = 0.5f * p.beta, inv_beta = 1.0f / p.beta;
         constexpr float kInvSqrt2 = 0.70710678118654752f;
         uint32_t lc = 0;
@@ -424,6 +450,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                 dir[a] = valid ? __ldg(p.src.ray_d + 3 * ray + a) : 0.0f;
                 xt[a] = (o + t * dir[a] - p.center[a]) * p.inv_scale;
             }
+            // the two samples of this thread in the 16x256b fragments: 16q + fs, 16q + fs + 8
+            float xa[3], xb[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                xa[a] = __shfl_sync(0xffffffffu, xt[a], fs);
+                xb[a] = __shfl_sync(0xffffffffu, xt[a], fs + 8);
+            }
             // ---- layer-0 input: encoding (A0: value | d/dx, A1: d/dy | d/dz) ----
             {
                 constexpr int Kp0 = TA::layer(0).Kp;
@@ -453,62 +486,87 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                 const bool last = L == NL - 1;
                 if (ly.sdf && ly.idx < LS - 1) {
                     // ---- hidden SDF layer -> next layer's input (skip concat when due) ----
+                    // thread: samples fs, fs + 8 of quarter q; columns c0 + 8g + fc + {0, 1};
+                    // stmatrix rows: lane i addresses A row 32q + i (value rows, then d/dx
+                    // rows in A0; d/dy, then d/dz in A1), matching the fragment order
                     const int Kn = TA::layer(L + 1).Kp;
                     const float sc = ly.idx + 1 == A::kSkip ? kInvSqrt2 : 1.0f;
-                    auto full_block = [&](int c0, const float (&x0)[16], const float (&x1)[16]) {
-#pragma unroll
-                        for (int hh = 0; hh < 16; hh += 8) {
-                            float o0[8], o1[8];
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                float h, sg;
-                                softplus_slope_tanh(x0[hh + j] + bias[c0 + hh + j], half_beta, inv_beta, h, sg);
-                                const float sgx = __shfl_sync(0xffffffffu, sg, val_lane) * sc;
-                                o0[j] = is_val ? h * sc : sgx * x0[hh + j];
-                                o1[j] = sgx * x1[hh + j];
-                            }
-                            st_row8<F16>(A0, r, c0 + hh, Kn, o0);
-                            st_row8<F16>(A1, r, c0 + hh, Kn, o1);
-                        }
-                    };
+                    const uint32_t row0 = smem_u32(A0) + a_off(32 * q + lane, 0, Kn);
+                    const uint32_t row1 = smem_u32(A1) + a_off(32 * q + lane, 0, Kn);
                     const int c_lo = half_lo(Kn, hf), c_hi = half_hi(Kn, hf);
                     const int c_full = (ly.N / 16) * 16 < c_hi ? (ly.N / 16) * 16 : c_hi;
                     for (int c0 = c_lo; c0 < c_full; c0 += 16) {
-                        float x0[16], x1[16];
-                        tmem_ld16(tmem + lane_addr + c0, x0);
-                        tmem_ld16(tmem + 256 + lane_addr + c0, x1);
+                        float v[8], x[8], y[8], z[8];
+                        tmem_ld16x256_x2(t_v + c0, v);
+                        tmem_ld16x256_x2(t_x + c0, x);
+                        tmem_ld16x256_x2(t_y + c0, y);
+                        tmem_ld16x256_x2(t_z + c0, z);
                         tmem_wait_ld();
-                        full_block(c0, x0, x1);
+#pragma unroll
+                        for (int g8 = 0; g8 < 2; ++g8) {
+                            const float2 b = *reinterpret_cast<const float2*>(bias + c0 + 8 * g8 + fc);
+                            float hv[4], xv[4], yv[4], zv[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int k = 4 * g8 + e;
+                                float h, sg;
+                                softplus_slope_tanh(v[k] + ((e & 1) ? b.y : b.x), half_beta, inv_beta, h, sg);
+                                sg *= sc;
+                                hv[e] = h * sc;
+                                xv[e] = sg * x[k];
+                                yv[e] = sg * y[k];
+                                zv[e] = sg * z[k];
+                            }
+                            const uint32_t co = (uint32_t)((c0 + 8 * g8) >> 3) * 128u;
+                            stmatrix4(row0 + co, pack2<F16>(hv[0], hv[1]), pack2<F16>(hv[2], hv[3]),
+                                      pack2<F16>(xv[0], xv[1]), pack2<F16>(xv[2], xv[3]));
+                            stmatrix4(row1 + co, pack2<F16>(yv[0], yv[1]), pack2<F16>(yv[2], yv[3]),
+                                      pack2<F16>(zv[0], zv[1]), pack2<F16>(zv[2], zv[3]));
+                        }
                     }
                     // tail: hidden units < N, then gamma(x~) / sqrt(2) (the skip input), then zeros
                     for (int c0 = c_full > c_lo ? c_full : c_lo; c0 < c_hi; c0 += 16) {
-                        float o0[16], o1[16];
-                        float x0[16], x1[16];
+                        float v[8], x[8], y[8], z[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) { v[j] = 0.0f; x[j] = 0.0f; y[j] = 0.0f; z[j] = 0.0f; }
                         if (c0 < ly.Np) {
-                            tmem_ld16(tmem + lane_addr + c0, x0);
-                            tmem_ld16(tmem + 256 + lane_addr + c0, x1);
+                            tmem_ld16x256_x2(t_v + c0, v);
+                            tmem_ld16x256_x2(t_x + c0, x);
+                            tmem_ld16x256_x2(t_y + c0, y);
+                            tmem_ld16x256_x2(t_z + c0, z);
                             tmem_wait_ld();
                         }
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int col = c0 + j;
-                            if (col < ly.N) {
-                                float h, sg;
-                                softplus_slope_tanh(x0[j] + bias[col], half_beta, inv_beta, h, sg);
-                                const float sgx = __shfl_sync(0xffffffffu, sg, val_lane) * sc;
-                                o0[j] = is_val ? h * sc : sgx * x0[j];
-                                o1[j] = sgx * x1[j];
-                            } else {
-                                const int e = col - ly.N;
-                                const bool in = e < A::kEnc;
-                                o0[j] = in ? enc_val(xt, e, A::kPeSdf, 0, !is_val) * sc : 0.0f;
-                                o1[j] = in ? enc_val(xt, e, A::kPeSdf, is_val ? 1 : 2, true) * sc : 0.0f;
+                        for (int g8 = 0; g8 < 2; ++g8) {
+                            float hv[4], xv[4], yv[4], zv[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int k = 4 * g8 + e;
+                                const int col = c0 + 8 * g8 + fc + (e & 1);
+                                if (col < ly.N) {
+                                    float h, sg;
+                                    softplus_slope_tanh(v[k] + bias[col], half_beta, inv_beta, h, sg);
+                                    sg *= sc;
+                                    hv[e] = h * sc;
+                                    xv[e] = sg * x[k];
+                                    yv[e] = sg * y[k];
+                                    zv[e] = sg * z[k];
+                                } else {
+                                    const int en = col - ly.N;
+                                    const bool in = en < A::kEnc;
+                                    const float* xs = (e & 2) ? xb : xa;
+                                    hv[e] = in ? enc_val(xs, en, A::kPeSdf, 0, false) * sc : 0.0f;
+                                    xv[e] = in ? enc_val(xs, en, A::kPeSdf, 0, true) * sc : 0.0f;
+                                    yv[e] = in ? enc_val(xs, en, A::kPeSdf, 1, true) * sc : 0.0f;
+                                    zv[e] = in ? enc_val(xs, en, A::kPeSdf, 2, true) * sc : 0.0f;
+                                }
                             }
+                            const uint32_t co = (uint32_t)((c0 + 8 * g8) >> 3) * 128u;
+                            stmatrix4(row0 + co, pack2<F16>(hv[0], hv[1]), pack2<F16>(hv[2], hv[3]),
+                                      pack2<F16>(xv[0], xv[1]), pack2<F16>(xv[2], xv[3]));
+                            stmatrix4(row1 + co, pack2<F16>(yv[0], yv[1]), pack2<F16>(yv[2], yv[3]),
+                                      pack2<F16>(zv[0], zv[1]), pack2<F16>(zv[2], zv[3]));
                         }
-                        st_row8<F16>(A0, r, c0, Kn, o0);
-                        st_row8<F16>(A0, r, c0 + 8, Kn, o0 + 8);
-                        st_row8<F16>(A1, r, c0, Kn, o1);
-                        st_row8<F16>(A1, r, c0 + 8, Kn, o1 + 8);
                     }
                 } else if (ly.sdf) {
                     // ---- output layer: f, grad f, feature -> colour input rows ----
@@ -671,7 +729,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
         int L = 0;
         while (L + 1 < LS && TA::bias_offset(L + 1) <= i) ++L;
         const TcLayer ly = TA::layer(L);
-        sbias[i] = __ldg(p.sdf_w + TA::param_offset(L) + (int64_t)ly.N * ly.K + (i - TA::bias_offset(L)));
+        const int j = i - TA::bias_offset(L);
+        sbias[i] = j < ly.N ? __ldg(p.sdf_w + TA::param_offset(L) + (int64_t)ly.N * ly.K + j) : 0.0f;
     }
     if (warp == 9) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
