@@ -6,20 +6,21 @@
 // so that TMEM lane quarter q holds samples 16q..16q+15: lanes 0-15 of the
 // quarter are the value (acc0) / d/dy (acc1) rows, lanes 16-31 the d/dx (acc0)
 // / d/dz (acc1) rows.  Every warp therefore owns 16 value rows, which spreads
-// the softplus / sigmoid work over all four SM sub-partitions, and the slope
-// sigma(beta z) reaches the tangent rows of the same sample with one
-// shuffle (lane l <-> l + 16).  Activations (bf16) are the A operands in
-// shared memory, written by the epilogue in the no-swizzle K-major
-// core-matrix layout; weights are pre-packed in the same layout
-// (tsdfs_pack_mlp) and streamed chunk by chunk (64 columns of K) with 1-D bulk
-// TMA copies through a two-stage ring.  The colour network reuses acc0 with
-// the value rows only.
+// the softplus / sigmoid work over all four SM sub-partitions; hidden layers
+// read 16-lane fragments so that one thread holds all four rows of a sample.
+// Activations (fp16 / bf16) are the A operands in shared memory, written by
+// the epilogue in the no-swizzle K-major core-matrix layout; weights are
+// pre-packed in the same layout (tsdfs_pack_mlp) and streamed chunk by chunk
+// (kKChunk columns of K) with 1-D bulk TMA copies through a kStages-deep ring.
+// The colour network reuses acc0 with the value rows only.
 //
-// Warp roles (320 threads): warps 0-7 epilogue (warp w: TMEM lane quarter
-// w % 4, column half w / 4), warp 8 lane 0 TMA producer, warp 9 lane 0 MMA
-// issuer (warp 9 also allocates / frees TMEM).  All hand-offs are mbarriers;
-// every wait is bounded and on timeout the kernel records TSDFS_DEV_TIMEOUT,
-// drains its own copies / MMAs and returns.
+// Warp roles: warps 0-7 epilogue (warp w: TMEM lane quarter w % 4, column
+// half w / 4), warp 8 lane 0 MMA issuer (warp 8 also allocates / frees TMEM),
+// warps 9 .. 8 + kStages lane 0 TMA producers, one per ring stage: bulk copies
+// issued by one thread towards different mbarriers do not overlap (measured),
+// so each stage has a thread of its own.  All hand-offs are mbarriers; every
+// wait is bounded and on timeout the kernel records TSDFS_DEV_TIMEOUT, drains
+// its own copies / MMAs and returns.
 #include "common.cuh"
 
 namespace tsdfs {
@@ -30,9 +31,12 @@ namespace {
 // layer tables
 // --------------------------------------------------------------------------
 constexpr int kTileS = 64;        // samples per tile
-constexpr int kKChunk = 64;       // K columns per weight stage
+constexpr int kKChunk = 64;       // K columns per weight chunk
+constexpr int kStages = 2;        // weight chunks in flight (ring depth), one producer warp each
+constexpr uint32_t kBarBytes = 256;  // mbarriers, TMEM slot and abort flag
 constexpr int kEpiThreads = 256;  // warps 0-7
-constexpr int kThreads = 320;
+constexpr int kMmaWarp = 8;
+constexpr int kThreads = 32 * (kMmaWarp + 1 + kStages);
 constexpr uint32_t kABytes = 64 * 1024;   // one A region (128 rows x 256 bf16)
 constexpr uint32_t kMaxSpin = 1u << 26;
 
@@ -273,13 +277,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
     uint8_t* A0 = smem;
     uint8_t* A1 = smem + kABytes;
     uint8_t* stage_base = smem + 2 * kABytes;
-    float* sbias = reinterpret_cast<float*>(stage_base + 2 * kStage);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(stage_base + 2 * kStage + TA::bias_bytes());
+    float* sbias = reinterpret_cast<float*>(stage_base + kStages * kStage);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage_base + kStages * kStage + TA::bias_bytes());
     // bars: full[2], empty[2], acc_ready, a_ready, drain
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 3);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    const uint32_t bar_full0 = smem_u32(bars + 0), bar_empty0 = smem_u32(bars + 2);
-    const uint32_t bar_acc = smem_u32(bars + 4), bar_a = smem_u32(bars + 5), bar_drain = smem_u32(bars + 6);
+    const uint32_t bar_full0 = smem_u32(bars + 0), bar_empty0 = smem_u32(bars + kStages);
+    const uint32_t bar_acc = smem_u32(bars + 2 * kStages), bar_a = smem_u32(bars + 2 * kStages + 1);
+    const uint32_t bar_drain = smem_u32(bars + 2 * kStages + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const int64_t total = p.src.mode == kUniform ? (int64_t)__ldg(p.src.total_dev) : p.src.total_host;
@@ -291,10 +296,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
     if ((int64_t)blockIdx.x >= n_tiles) return;
 
     if (threadIdx.x == 0) {
-        mbar_init(bar_full0, 1);
-        mbar_init(bar_full0 + 8, 1);
-        mbar_init(bar_empty0, 1);
-        mbar_init(bar_empty0 + 8, 1);
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(bar_full0 + 8 * i, 1);
+            mbar_init(bar_empty0 + 8 * i, 1);
+        }
         mbar_init(bar_acc, 1);
         mbar_init(bar_a, kEpiThreads);
         mbar_init(bar_drain, 1);
@@ -310,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
         const int j = i - TA::bias_offset(L);
         sbias[i] = j < ly.N ? __ldg(W + (int64_t)ly.N * ly.K + j) : 0.0f;
     }
-    if (warp == 9) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -320,33 +325,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 8) {
-        // ------------------------------------------------------------ producer
+    if (warp > kMmaWarp) {
+        // ------------------------------------------- producers (one per stage)
         if (lane == 0) {
-            uint32_t seq = 0;
+            const uint32_t own = (uint32_t)(warp - kMmaWarp - 1);
+            uint32_t seq = 0, issued = 0;
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
                 for (int L = 0; L < NL && ok; ++L) {
-                    for (int c = 0; c < TA::chunks(L); ++c) {
-                        const uint32_t s = seq & 1u, ph = (seq >> 1) & 1u;
-                        if (!mbar_wait(bar_empty0 + 8 * s, ph ^ 1u, abort_flag)) { ok = false; break; }
+                    for (int c = 0; c < TA::chunks(L); ++c, ++seq) {
+                        if (seq % kStages != own) continue;
+                        const uint32_t ph = (seq / kStages) & 1u;
+                        if (!mbar_wait(bar_empty0 + 8 * own, ph ^ 1u, abort_flag)) { ok = false; break; }
                         const uint32_t bytes = (uint32_t)TA::chunk_bytes(L, c);
-                        mbar_expect_tx(bar_full0 + 8 * s, bytes);
-                        bulk_g2s(smem_u32(stage_base + s * kStage), p.packed + TA::packed_offset(L, c), bytes,
-                                 bar_full0 + 8 * s);
-                        ++seq;
+                        mbar_expect_tx(bar_full0 + 8 * own, bytes);
+                        bulk_g2s(smem_u32(stage_base + own * kStage), p.packed + TA::packed_offset(L, c), bytes,
+                                 bar_full0 + 8 * own);
+                        ++issued;
                     }
                 }
             }
-            if (!ok) {
-                // let the copies already issued land before the CTA exits
-                for (uint32_t k = (seq >= 2 ? seq - 2 : 0); k < seq; ++k) {
-                    for (uint32_t it = 0; it < kMaxSpin && !mbar_try(bar_full0 + 8 * (k & 1u), (k >> 1) & 1u); ++it) {
-                    }
+            if (!ok && issued > 0) {
+                // let the copy in flight into this stage land before the CTA exits
+                for (uint32_t it = 0; it < kMaxSpin && !mbar_try(bar_full0 + 8 * own, (issued - 1) & 1u); ++it) {
                 }
             }
         }
-    } else if (warp == 9) {
+    } else if (warp == kMmaWarp) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
             uint32_t seq = 0, lc = 0;
@@ -360,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                     const uint32_t a0 = smem_u32(A0), a1 = smem_u32(A1);
                     const bool last_sdf = ly.sdf && ly.idx == LS - 1;
                     for (int c = 0; c < TA::chunks(L); ++c) {
-                        const uint32_t s = seq & 1u, ph = (seq >> 1) & 1u;
+                        const uint32_t s = seq % kStages, ph = (seq / kStages) & 1u;
                         if (!mbar_wait(bar_full0 + 8 * s, ph, abort_flag)) { ok = false; break; }
                         tc_fence_after();
                         const int kc = TA::chunk_k(L, c);
@@ -685,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 9) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
     }
 }
@@ -704,21 +709,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* A0 = smem;
     uint8_t* stage_base = smem + 2 * kABytes;
-    float* sbias = reinterpret_cast<float*>(stage_base + 2 * kStage);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(stage_base + 2 * kStage + TA::bias_bytes());
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+    float* sbias = reinterpret_cast<float*>(stage_base + kStages * kStage);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage_base + kStages * kStage + TA::bias_bytes());
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 3);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    const uint32_t bar_full0 = smem_u32(bars + 0), bar_empty0 = smem_u32(bars + 2);
-    const uint32_t bar_acc = smem_u32(bars + 4), bar_a = smem_u32(bars + 5), bar_drain = smem_u32(bars + 6);
+    const uint32_t bar_full0 = smem_u32(bars + 0), bar_empty0 = smem_u32(bars + kStages);
+    const uint32_t bar_acc = smem_u32(bars + 2 * kStages), bar_a = smem_u32(bars + 2 * kStages + 1);
+    const uint32_t bar_drain = smem_u32(bars + 2 * kStages + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t total = p.src.total_host;
     const int64_t n_tiles = (total + kTileV - 1) / kTileV;
     if ((int64_t)blockIdx.x >= n_tiles) return;
     if (threadIdx.x == 0) {
-        mbar_init(bar_full0, 1);
-        mbar_init(bar_full0 + 8, 1);
-        mbar_init(bar_empty0, 1);
-        mbar_init(bar_empty0 + 8, 1);
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(bar_full0 + 8 * i, 1);
+            mbar_init(bar_empty0 + 8 * i, 1);
+        }
         mbar_init(bar_acc, 1);
         mbar_init(bar_a, kEpiThreads);
         mbar_init(bar_drain, 1);
@@ -732,7 +738,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
         const int j = i - TA::bias_offset(L);
         sbias[i] = j < ly.N ? __ldg(p.sdf_w + TA::param_offset(L) + (int64_t)ly.N * ly.K + j) : 0.0f;
     }
-    if (warp == 9) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(256));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -742,31 +748,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 8) {
+    if (warp > kMmaWarp) {
         if (lane == 0) {
-            uint32_t seq = 0;
+            const uint32_t own = (uint32_t)(warp - kMmaWarp - 1);
+            uint32_t seq = 0, issued = 0;
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
                 for (int L = 0; L < LS && ok; ++L) {
-                    for (int c = 0; c < TA::chunks(L); ++c) {
-                        const uint32_t s = seq & 1u, ph = (seq >> 1) & 1u;
-                        if (!mbar_wait(bar_empty0 + 8 * s, ph ^ 1u, abort_flag)) { ok = false; break; }
+                    for (int c = 0; c < TA::chunks(L); ++c, ++seq) {
+                        if (seq % kStages != own) continue;
+                        const uint32_t ph = (seq / kStages) & 1u;
+                        if (!mbar_wait(bar_empty0 + 8 * own, ph ^ 1u, abort_flag)) { ok = false; break; }
                         const uint32_t bytes = (uint32_t)TA::chunk_bytes(L, c);
-                        mbar_expect_tx(bar_full0 + 8 * s, bytes);
-                        bulk_g2s(smem_u32(stage_base + s * kStage), p.packed + TA::packed_offset(L, c), bytes,
-                                 bar_full0 + 8 * s);
-                        ++seq;
+                        mbar_expect_tx(bar_full0 + 8 * own, bytes);
+                        bulk_g2s(smem_u32(stage_base + own * kStage), p.packed + TA::packed_offset(L, c), bytes,
+                                 bar_full0 + 8 * own);
+                        ++issued;
                     }
                 }
             }
-            if (!ok) {
-                for (uint32_t k = (seq >= 2 ? seq - 2 : 0); k < seq; ++k) {
-                    for (uint32_t it = 0; it < kMaxSpin && !mbar_try(bar_full0 + 8 * (k & 1u), (k >> 1) & 1u); ++it) {
-                    }
+            if (!ok && issued > 0) {
+                for (uint32_t it = 0; it < kMaxSpin && !mbar_try(bar_full0 + 8 * own, (issued - 1) & 1u); ++it) {
                 }
             }
         }
-    } else if (warp == 9) {
+    } else if (warp == kMmaWarp) {
         if (lane == 0) {
             uint32_t seq = 0, lc = 0;
             bool ok = true;
@@ -779,7 +785,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
                     const uint32_t a0 = smem_u32(A0);
                     const int n_mma = L == LS - 1 ? 16 : ly.Np;
                     for (int c = 0; c < TA::chunks(L); ++c) {
-                        const uint32_t s = seq & 1u, ph = (seq >> 1) & 1u;
+                        const uint32_t s = seq % kStages, ph = (seq / kStages) & 1u;
                         if (!mbar_wait(bar_full0 + 8 * s, ph, abort_flag)) { ok = false; break; }
                         tc_fence_after();
                         const int kc = TA::chunk_k(L, c);
@@ -879,7 +885,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 9) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
     }
 }
@@ -887,7 +893,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
 template <int ARCH, bool F16>
 int launch_tc_value(const tsdfs_mlp* m, const SampleSource& src, float* f_out, cudaStream_t st) {
     using TA = TcArch<ARCH>;
-    const size_t smem = 2 * kABytes + 2 * (size_t)TA::stage_bytes() + TA::bias_bytes() + 128;
+    const size_t smem = 2 * kABytes + kStages * (size_t)TA::stage_bytes() + TA::bias_bytes() + kBarBytes;
     static bool attr[2] = {false, false};
     if (!attr[ARCH]) {
         int rc = cuda_check(cudaFuncSetAttribute(k_mlp_tc_value<ARCH, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -952,7 +958,7 @@ __global__ void k_pack(const float* __restrict__ sdf_w, const float* __restrict_
 template <int ARCH, bool F16>
 int launch_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64_t max_samples, cudaStream_t st) {
     using TA = TcArch<ARCH>;
-    const size_t smem = 2 * kABytes + 2 * (size_t)TA::stage_bytes() + TA::bias_bytes() + 128;
+    const size_t smem = 2 * kABytes + kStages * (size_t)TA::stage_bytes() + TA::bias_bytes() + kBarBytes;
     static bool attr[2] = {false, false};
     if (!attr[ARCH]) {
         int rc = cuda_check(cudaFuncSetAttribute(k_mlp_tc<ARCH, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
