@@ -212,12 +212,25 @@ extern "C" int64_t tsdfs_rgb_param_count(int32_t arch) {
                                    : (arch == TSDFS_ARCH_ROOM ? rgb_param_count<TSDFS_ARCH_ROOM>() : -1);
 }
 
+// render workspace: the per-sample records, then the ray index of every sample
 extern "C" size_t tsdfs_render_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays, int64_t max_samples) {
     (void)mlp;
     (void)n_rays;
     if (max_samples < 0) return 0;
-    return align256((size_t)max_samples * sizeof(SampleRec)) + 256;
+    return align256((size_t)max_samples * sizeof(SampleRec)) + align256((size_t)max_samples * sizeof(int32_t)) + 256;
 }
+
+namespace tsdfs {
+// ray index of every sample: thread r writes r into offsets[r] .. offsets[r+1] - 1
+// (nothing at or beyond capacity: the network kernel flags that overflow itself)
+__global__ void k_sample_ray(const int32_t* __restrict__ offsets, int64_t n_rays, int64_t capacity,
+                             int32_t* __restrict__ sample_ray) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o0 = offsets[r], o1 = offsets[r + 1] < capacity ? offsets[r + 1] : capacity;
+        for (int64_t i = o0; i < o1; ++i) sample_ray[i] = (int32_t)r;
+    }
+}
+}  // namespace tsdfs
 
 extern "C" int render_rays(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
                            const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
@@ -234,6 +247,8 @@ extern "C" int render_rays(const tsdfs_mlp* mlp, const float* ray_o, const float
         return fail(TSDFS_E_WORKSPACE, "render workspace too small");
     cudaStream_t st = (cudaStream_t)stream;
     SampleRec* rec = reinterpret_cast<SampleRec*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
+    int32_t* sample_ray = reinterpret_cast<int32_t*>(reinterpret_cast<uintptr_t>(rec) +
+                                                     align256((size_t)max_samples * sizeof(SampleRec)));
     SampleSource src{};
     src.mode = kUniform;
     src.ray_o = ray_o;
@@ -245,6 +260,13 @@ extern "C" int render_rays(const tsdfs_mlp* mlp, const float* ray_o, const float
     src.total_dev = offsets + n_rays;
     src.capacity = max_samples;
     if (max_samples > 0) {
+        if (mlp->precision != TSDFS_PREC_F32) {
+            ProfScope ps("sample_ray", st);
+            k_sample_ray<<<grid_1d(n_rays, 256), 256, 0, st>>>(offsets, n_rays, max_samples, sample_ray);
+            rc = cuda_check(cudaGetLastError(), "sample_ray launch");
+            if (rc) return rc;
+            src.sample_ray = sample_ray;
+        }
         rc = run_full_mlp(mlp, src, rec, max_samples, st);
         if (rc) return rc;
     }

@@ -126,6 +126,7 @@ struct SampleSource {
     const float* t_n;
     const float* t_f;
     int64_t n_rays;
+    const int32_t* sample_ray;  // optional: ray of every sample (else a binary search of offsets)
     // kExplicit
     const float* t;
     const float* delta;

@@ -87,6 +87,13 @@ template <int ARCH> struct TcArch {
     }
     __host__ __device__ static constexpr int bias_total() { return bias_offset(kLayers); }
     __host__ __device__ static constexpr uint32_t bias_bytes() { return (uint32_t)((bias_total() * 4 + 15) / 16 * 16); }
+    // per-tile sample table of the full kernel (coordinates, direction, t, delta, encodings)
+    __host__ __device__ static constexpr uint32_t table_bytes() {
+        return (uint32_t)(kTileS * (8 + 6 * (A::kPeSdf + A::kPeDir)) * 4);
+    }
+    __host__ __device__ static constexpr size_t full_smem_bytes() {
+        return 2 * (size_t)kABytes + kStages * (size_t)stage_bytes() + bias_bytes() + kBarBytes + table_bytes();
+    }
     __host__ __device__ static constexpr uint32_t stage_bytes() {
         int64_t m = 0;
         for (int l = 0; l < kLayers; ++l)
@@ -255,6 +262,21 @@ __device__ __forceinline__ float enc_val(const float* xt, int j, int pe, int a, 
     return part == 0 ? f * cs : -f * sn;
 }
 
+// the same entry from the per-tile tables: sx = the 3 coordinates, spe = sin / cos of
+// 2^oct x_b at ((oct * 3 + b) * 2 + {0: sin, 1: cos}); comp 0 = value, comp a + 1 =
+// derivative along axis a
+__device__ __forceinline__ float enc_tab(const float* sx, const float* spe, int pe, int j, int comp) {
+    if (j < 3) return comp == 0 ? sx[j] : (j == comp - 1 ? 1.0f : 0.0f);
+    const int qq = j - 3;
+    const int oct = qq / 6, part = (qq % 6) / 3, b = qq % 3;
+    if (oct >= pe) return 0.0f;
+    const float sn = spe[(oct * 3 + b) * 2], cs = spe[(oct * 3 + b) * 2 + 1];
+    if (comp == 0) return part == 0 ? sn : cs;
+    if (b != comp - 1) return 0.0f;
+    const float f = (float)(1 << oct);
+    return part == 0 ? f * cs : -f * sn;
+}
+
 struct TcParams {
     const uint8_t* packed;
     const float* sdf_w;
@@ -280,11 +302,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
     float* sbias = reinterpret_cast<float*>(stage_base + kStages * kStage);
     uint64_t* bars = reinterpret_cast<uint64_t*>(stage_base + kStages * kStage + TA::bias_bytes());
     // bars: full[2], empty[2], acc_ready, a_ready, drain
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 3);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const uint32_t bar_full0 = smem_u32(bars + 0), bar_empty0 = smem_u32(bars + kStages);
     const uint32_t bar_acc = smem_u32(bars + 2 * kStages), bar_a = smem_u32(bars + 2 * kStages + 1);
-    const uint32_t bar_drain = smem_u32(bars + 2 * kStages + 2);
+    const uint32_t bar_drain = smem_u32(bars + 2 * kStages + 2), bar_tab = smem_u32(bars + 2 * kStages + 3);
+    // per-tile sample table: [x~ (3), direction (3), t, delta] per sample, then sin / cos of the
+    // positional encodings of x~ (kPeSdf octaves) and of the direction (kPeDir octaves)
+    float* s_x = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + kBarBytes);
+    float* s_pe = s_x + kTileS * 8;
+    float* s_pd = s_pe + kTileS * A::kPeSdf * 6;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const int64_t total = p.src.mode == kUniform ? (int64_t)__ldg(p.src.total_dev) : p.src.total_host;
@@ -303,6 +330,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
         mbar_init(bar_acc, 1);
         mbar_init(bar_a, kEpiThreads);
         mbar_init(bar_drain, 1);
+        mbar_init(bar_tab, kEpiThreads);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -424,59 +452,91 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
         const uint32_t t_y = t_v + 256, t_z = t_x + 256;
         const float half_beta = 0.5f * p.beta, inv_beta = 1.0f / p.beta;
         constexpr float kInvSqrt2 = 0.70710678118654752f;
-        uint32_t lc = 0;
+        uint32_t lc = 0, tab_ph = 0;
         bool ok = true;
         for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-            // ---- this row's sample (value lanes look it up, tangent lanes receive it) ----
-            const int64_t g = tile * kTileS + s;
-            const bool valid = g < total;
-            float t = 0.0f, dl = 0.0f;
-            long long ray = 0;
-            if (valid && is_val) {
-                if (p.src.mode == kUniform) {
-                    ray = find_ray(p.src.offsets, p.src.n_rays, g);
-                    const int32_t o0 = __ldg(p.src.offsets + ray), o1 = __ldg(p.src.offsets + ray + 1);
-                    const float tn = __ldg(p.src.t_n + ray), tf = __ldg(p.src.t_f + ray);
-                    dl = (tf - tn) / (float)(o1 - o0);
-                    t = tn + ((float)(g - o0) + 0.5f) * dl;
-                } else {
-                    ray = g / p.src.per_ray;
-                    t = __ldg(p.src.t + g);
-                    dl = __ldg(p.src.delta + g);
+            // ---- per-tile sample table: epilogue thread et < 64 looks up sample et ----
+            const int et = threadIdx.x;
+            if (et < kTileS) {
+                const int64_t g = tile * kTileS + et;
+                float t = 0.0f, dl = 0.0f, xs[3] = {0.0f, 0.0f, 0.0f}, ds[3] = {0.0f, 0.0f, 0.0f};
+                if (g < total) {
+                    int64_t ray;
+                    if (p.src.mode == kUniform) {
+                        ray = p.src.sample_ray ? (int64_t)__ldg(p.src.sample_ray + g) : find_ray(p.src.offsets, p.src.n_rays, g);
+                        const int32_t o0 = __ldg(p.src.offsets + ray), o1 = __ldg(p.src.offsets + ray + 1);
+                        const float tn = __ldg(p.src.t_n + ray), tf = __ldg(p.src.t_f + ray);
+                        dl = (tf - tn) / (float)(o1 - o0);
+                        t = tn + ((float)(g - o0) + 0.5f) * dl;
+                    } else {
+                        ray = g / p.src.per_ray;
+                        t = __ldg(p.src.t + g);
+                        dl = __ldg(p.src.delta + g);
+                    }
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        ds[a] = __ldg(p.src.ray_d + 3 * ray + a);
+                        xs[a] = (__ldg(p.src.ray_o + 3 * ray + a) + t * ds[a] - p.center[a]) * p.inv_scale;
+                    }
+                }
+                float* sx = s_x + et * 8;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    sx[a] = xs[a];
+                    sx[3 + a] = ds[a];
+                }
+                sx[6] = t;
+                sx[7] = dl;
+            }
+            mbar_arrive(bar_tab);
+            if (!__all_sync(0xffffffffu, mbar_wait(bar_tab, tab_ph & 1u, abort_flag))) { ok = false; break; }
+            ++tab_ph;
+            // ---- sin / cos of the encodings: thread et < 192 -> (sample et / 3, axis et % 3) ----
+            if (et < 3 * kTileS) {
+                const int sm = et / 3, a = et % 3;
+                const float xv = s_x[sm * 8 + a], dv = s_x[sm * 8 + 3 + a];
+#pragma unroll
+                for (int oct = 0; oct < A::kPeSdf; ++oct) {
+                    float sn, cs;
+                    sincosf((float)(1 << oct) * xv, &sn, &cs);
+                    s_pe[((sm * A::kPeSdf + oct) * 3 + a) * 2] = sn;
+                    s_pe[((sm * A::kPeSdf + oct) * 3 + a) * 2 + 1] = cs;
+                }
+#pragma unroll
+                for (int oct = 0; oct < A::kPeDir; ++oct) {
+                    float sn, cs;
+                    sincosf((float)(1 << oct) * dv, &sn, &cs);
+                    s_pd[((sm * A::kPeDir + oct) * 3 + a) * 2] = sn;
+                    s_pd[((sm * A::kPeDir + oct) * 3 + a) * 2 + 1] = cs;
                 }
             }
-            t = __shfl_sync(0xffffffffu, t, val_lane);
-            dl = __shfl_sync(0xffffffffu, dl, val_lane);
-            ray = __shfl_sync(0xffffffffu, ray, val_lane);
-            float xt[3], dir[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float o = valid ? __ldg(p.src.ray_o + 3 * ray + a) : 0.0f;
-                dir[a] = valid ? __ldg(p.src.ray_d + 3 * ray + a) : 0.0f;
-                xt[a] = (o + t * dir[a] - p.center[a]) * p.inv_scale;
-            }
-            // the two samples of this thread in the 16x256b fragments: 16q + fs, 16q + fs + 8
-            float xa[3], xb[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                xa[a] = __shfl_sync(0xffffffffu, xt[a], fs);
-                xb[a] = __shfl_sync(0xffffffffu, xt[a], fs + 8);
-            }
-            // ---- layer-0 input: encoding (A0: value | d/dx, A1: d/dy | d/dz) ----
+            mbar_arrive(bar_tab);
+            if (!__all_sync(0xffffffffu, mbar_wait(bar_tab, tab_ph & 1u, abort_flag))) { ok = false; break; }
+            ++tab_ph;
+            // ---- layer-0 input: encoding rows, stored as 16x256b-ordered stmatrix fragments ----
             {
                 constexpr int Kp0 = TA::layer(0).Kp;
-                const int a1_axis = is_val ? 1 : 2;
-                for (int k0 = hf * (Kp0 / 2); k0 < (hf + 1) * (Kp0 / 2); k0 += 8) {
-                    float v0[8], v1[8];
+                const int sa = 16 * q + fs, sb = sa + 8;
+                const float* xa = s_x + sa * 8;
+                const float* xb = s_x + sb * 8;
+                const float* pa = s_pe + sa * A::kPeSdf * 6;
+                const float* pb = s_pe + sb * A::kPeSdf * 6;
+                const uint32_t row0 = smem_u32(A0) + a_off(32 * q + lane, 0, Kp0);
+                const uint32_t row1 = smem_u32(A1) + a_off(32 * q + lane, 0, Kp0);
+                for (int c8 = hf * (Kp0 / 2); c8 < (hf + 1) * (Kp0 / 2); c8 += 8) {
+                    float v[4][4];   // [component][(sample a, col 0), (a, 1), (b, 0), (b, 1)]
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int k = k0 + j;
-                        const bool in = k < A::kEnc;
-                        v0[j] = in ? enc_val(xt, k, A::kPeSdf, 0, !is_val) : 0.0f;
-                        v1[j] = in ? enc_val(xt, k, A::kPeSdf, a1_axis, true) : 0.0f;
-                    }
-                    st_row8<F16>(A0, r, k0, Kp0, v0);
-                    st_row8<F16>(A1, r, k0, Kp0, v1);
+                    for (int cp = 0; cp < 4; ++cp)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int j = c8 + fc + (e & 1);
+                            v[cp][e] = j < A::kEnc ? enc_tab((e & 2) ? xb : xa, (e & 2) ? pb : pa, A::kPeSdf, j, cp) : 0.0f;
+                        }
+                    const uint32_t co = (uint32_t)(c8 >> 3) * 128u;
+                    stmatrix4(row0 + co, pack2<F16>(v[0][0], v[0][1]), pack2<F16>(v[0][2], v[0][3]),
+                              pack2<F16>(v[1][0], v[1][1]), pack2<F16>(v[1][2], v[1][3]));
+                    stmatrix4(row1 + co, pack2<F16>(v[2][0], v[2][1]), pack2<F16>(v[2][2], v[2][3]),
+                              pack2<F16>(v[3][0], v[3][1]), pack2<F16>(v[3][2], v[3][3]));
                 }
             }
             fence_proxy_async();
@@ -530,6 +590,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                         }
                     }
                     // tail: hidden units < N, then gamma(x~) / sqrt(2) (the skip input), then zeros
+                    const float* sxa = s_x + (16 * q + fs) * 8;
+                    const float* sxb = sxa + 8 * 8;
+                    const float* spa = s_pe + (16 * q + fs) * A::kPeSdf * 6;
+                    const float* spb = spa + 8 * A::kPeSdf * 6;
                     for (int c0 = c_full > c_lo ? c_full : c_lo; c0 < c_hi; c0 += 16) {
                         float v[8], x[8], y[8], z[8];
 #pragma unroll
@@ -545,25 +609,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                         for (int g8 = 0; g8 < 2; ++g8) {
                             float hv[4], xv[4], yv[4], zv[4];
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int k = 4 * g8 + e;
-                                const int col = c0 + 8 * g8 + fc + (e & 1);
+                            for (int cc = 0; cc < 2; ++cc) {
+                                const int col = c0 + 8 * g8 + fc + cc;
                                 if (col < ly.N) {
-                                    float h, sg;
-                                    softplus_slope_tanh(v[k] + bias[col], half_beta, inv_beta, h, sg);
-                                    sg *= sc;
-                                    hv[e] = h * sc;
-                                    xv[e] = sg * x[k];
-                                    yv[e] = sg * y[k];
-                                    zv[e] = sg * z[k];
+#pragma unroll
+                                    for (int e = cc; e < 4; e += 2) {
+                                        const int k = 4 * g8 + e;
+                                        float h, sg;
+                                        softplus_slope_tanh(v[k] + bias[col], half_beta, inv_beta, h, sg);
+                                        sg *= sc;
+                                        hv[e] = h * sc;
+                                        xv[e] = sg * x[k];
+                                        yv[e] = sg * y[k];
+                                        zv[e] = sg * z[k];
+                                    }
                                 } else {
+                                    // encoding entry en of both samples: decoded once per column
                                     const int en = col - ly.N;
-                                    const bool in = en < A::kEnc;
-                                    const float* xs = (e & 2) ? xb : xa;
-                                    hv[e] = in ? enc_val(xs, en, A::kPeSdf, 0, false) * sc : 0.0f;
-                                    xv[e] = in ? enc_val(xs, en, A::kPeSdf, 0, true) * sc : 0.0f;
-                                    yv[e] = in ? enc_val(xs, en, A::kPeSdf, 1, true) * sc : 0.0f;
-                                    zv[e] = in ? enc_val(xs, en, A::kPeSdf, 2, true) * sc : 0.0f;
+                                    const int qq = en - 3, oct = qq / 6, part = (qq % 6) / 3, b = en < 3 ? en : qq % 3;
+                                    const bool coord = en < 3, in = en < A::kEnc && (coord || oct < A::kPeSdf);
+                                    const float f = coord ? 1.0f : (float)(1 << (oct > 0 ? oct : 0)) * sc;
+                                    const int ti = ((coord ? 0 : oct) * 3 + b) * 2;
+#pragma unroll
+                                    for (int e = cc; e < 4; e += 2) {
+                                        const float* sx = (e & 2) ? sxb : sxa;
+                                        const float* sp = (e & 2) ? spb : spa;
+                                        float val = 0.0f, der = 0.0f;
+                                        if (in) {
+                                            if (coord) {
+                                                val = sx[b] * sc;
+                                                der = sc;
+                                            } else {
+                                                const float sn = sp[ti], cs = sp[ti + 1];
+                                                val = (part == 0 ? sn : cs) * sc;
+                                                der = part == 0 ? f * cs : -f * sn;
+                                            }
+                                        }
+                                        hv[e] = val;
+                                        xv[e] = b == 0 ? der : 0.0f;
+                                        yv[e] = b == 1 ? der : 0.0f;
+                                        zv[e] = b == 2 ? der : 0.0f;
+                                    }
                                 }
                             }
                             const uint32_t co = (uint32_t)((c0 + 8 * g8) >> 3) * 128u;
@@ -598,9 +684,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                         const float inv = gn_out > 0.0f ? 1.0f / gn_out : 0.0f;
                         n_hat[0] = gx * inv; n_hat[1] = gy * inv; n_hat[2] = gz * inv;
                         nrm[0] = n_hat[0]; nrm[1] = n_hat[1]; nrm[2] = n_hat[2];
-                        dd_out = gx * dir[0] + gy * dir[1] + gz * dir[2];
+                        const float* ds = s_x + s * 8 + 3;
+                        dd_out = gx * ds[0] + gy * ds[1] + gz * ds[2];
 #pragma unroll
-                        for (int e = 0; e < kDir; ++e) venc[e] = A::kPeDir == 0 ? dir[e] : enc_val(dir, e, A::kPeDir, 0, false);
+                        for (int e = 0; e < kDir; ++e) venc[e] = enc_tab(ds, s_pd + s * A::kPeDir * 6, A::kPeDir, e, 0);
                     }
                     auto feature_block = [&](int c0, float (&o)[16], bool prefix) {
                         const int w0 = c0 - kD - kOff;   // 16-aligned output block behind column c0 + kOff
@@ -618,7 +705,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                             const bool feat = col >= kFeatCol && col < kFeatCol + A::kFeat;
                             o[j] = feat ? acc + bias[feat ? col - kD : 0] : 0.0f;
                             if (prefix) {
-                                if (col < 3) o[j] = xt[col < 3 ? col : 0];
+                                if (col < 3) o[j] = s_x[s * 8 + (col < 3 ? col : 0)];
                                 else if (col < 3 + kDir) o[j] = venc[col - 3 < kDir ? col - 3 : 0];
                                 else if (col < kFeatCol) o[j] = n_hat[col - 3 - kDir < 3 ? col - 3 - kDir : 0];
                             }
@@ -668,7 +755,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                     float x0[16];
                     tmem_ld16(tmem + lane_addr, x0);
                     tmem_wait_ld();
-                    if (is_val && valid) {
+                    const int64_t g = tile * kTileS + s;
+                    if (is_val && g < total) {
+                        const float t = s_x[s * 8 + 6], dl = s_x[s * 8 + 7];
                         float4* R4 = reinterpret_cast<float4*>(p.rec + g);
                         const float cr = __fdividef(1.0f, 1.0f + __expf(-(x0[0] + bias[0])));
                         const float cg = __fdividef(1.0f, 1.0f + __expf(-(x0[1] + bias[1])));
@@ -958,7 +1047,8 @@ __global__ void k_pack(const float* __restrict__ sdf_w, const float* __restrict_
 template <int ARCH, bool F16>
 int launch_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64_t max_samples, cudaStream_t st) {
     using TA = TcArch<ARCH>;
-    const size_t smem = 2 * kABytes + kStages * (size_t)TA::stage_bytes() + TA::bias_bytes() + kBarBytes;
+    constexpr size_t smem = TA::full_smem_bytes();
+    static_assert(smem <= 232448, "k_mlp_tc shared memory exceeds 227 KB");
     static bool attr[2] = {false, false};
     if (!attr[ARCH]) {
         int rc = cuda_check(cudaFuncSetAttribute(k_mlp_tc<ARCH, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
