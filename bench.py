@@ -34,6 +34,7 @@ METRIC = "rays/s at PSNR≥oracle−0.1dB, TSDF-bounded vs 96-sample hierarchica
 UNIT = "rays/s"
 WORKLOAD = "room 8x6x3m (20 boxes, 4 plates), 256^3 TSDF from 100x640x480 depth maps, 640x480 novel views"
 ALGO_FLOP_PER_SAMPLE = 2.25e6   # SDF fwd + minimal reverse-mode grad + colour, 8x256 / 4x256 networks
+EXEC_FLOP_PER_SAMPLE = 4.75e6   # what the tensor-core kernel issues: value + 3 tangent rows, padded colour rows
 N_VIEWS_TIMED = 10
 QUALITY_PIXELS = 256
 DENSE_SAMPLES = 1024
@@ -280,10 +281,10 @@ def run_ours(args, ws, rank, local):
     algo_flop_launch = ALGO_FLOP_PER_SAMPLE * samples_timed / max(args.steps, 1)
     achieved = algo_flop_launch / (mlp_ms / 1e3) / 1e12
     if prec != "f32":
-        roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_sus, "unit": "TFLOP/s",
-                "frac": achieved / bf16_sus, "traffic": None,
-                "peak_kind": f"bf16 dense sustained ({peak_src}); fp16 dense has the same nominal rate",
-                "kernel": "mlp_tc"}
+        roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_burst, "unit": "TFLOP/s",
+                "frac": achieved / bf16_burst, "traffic": None,
+                "peak_kind": f"bf16 dense burst ({peak_src}); fp16 dense has the same nominal rate",
+                "kernel": "mlp_tc", "executed_tflops": achieved * EXEC_FLOP_PER_SAMPLE / ALGO_FLOP_PER_SAMPLE}
     else:
         fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
