@@ -32,10 +32,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "rays/s at PSNR≥oracle−0.1dB, TSDF-bounded vs 96-sample hierarchical, 1 GB300"
 UNIT = "rays/s"
-WORKLOAD = "room 8x6x3m (20 boxes, 4 plates), 256^3 TSDF from 100x640x480 depth maps, 640x480 novel views"
+WORKLOADS = {
+    "view": "room 8x6x3m (20 boxes, 4 plates), 256^3 TSDF from 100x640x480 depth maps, 640x480 novel views",
+    "panorama": "room 8x6x3m (20 boxes, 4 plates), 256^3 TSDF from 100x640x480 depth maps, 1024x512 equirect "
+                "panoramas from 4 in-room centres (ragged 1-64 samples, fallback 96)",
+}
+WORKLOAD = WORKLOADS["view"]
 ALGO_FLOP_PER_SAMPLE = 2.25e6   # SDF fwd + minimal reverse-mode grad + colour, 8x256 / 4x256 networks
 EXEC_FLOP_PER_SAMPLE = 4.75e6   # what the tensor-core kernel issues: value + 3 tangent rows, padded colour rows
-N_VIEWS_TIMED = 10
+N_VIEWS_TIMED = 10   # views cycled by the timed steps (4 for the panorama workload)
 QUALITY_PIXELS = 256
 DENSE_SAMPLES = 1024
 
@@ -52,6 +57,13 @@ def parse():
     ap.add_argument("--grid-source", choices=["network", "analytic"], default="network",
                     help="depth maps the marched grid is fused from (analytic: the exact scene, no network pre-pass)")
     ap.add_argument("--rays", type=int, default=0, help="seeded subset of each view's rays (0: all 307200)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="view",
+                    help="view: 640x480 held-out views; panorama: 1024x512 equirect panoramas")
+    ap.add_argument("--graph", action="store_true", help="replay each view's bounds + render as a captured CUDA graph")
+    ap.add_argument("--train-pitch", type=float, default=None,
+                    help="largest pitch (degrees) of the random training poses (default: the synthetic recipe's)")
+    ap.add_argument("--quality-only", action="store_true", help="main timing + quality (no e2e / comparator / cpu / "
+                                                                   "training legs)")
     ap.add_argument("--only-main", action="store_true", help="time the render path only (no e2e / comparator / "
                                                                   "quality / cpu / training legs): the small profiling case")
     ap.add_argument("--ref-rays", type=int, default=2048, help="rays per reference-arm step")
@@ -152,7 +164,7 @@ def measured_peaks():
 NET_DEPTH_W, NET_DEPTH_H = 320, 240   # resolution of the network-rendered training views
 
 
-def build_scene(device, mlp, source="network", n_rays=0):
+def build_scene(device, mlp, source="network", n_rays=0, workload="view"):
     """Fuse the room's TSDF twice: from the 100 analytic 640x480 depth maps (the
     configuration's fusion workload, timed) and from the network's own rendered
     depth of the same training poses (Sec. 3.2: the TSDF is built from the
@@ -177,8 +189,9 @@ def build_scene(device, mlp, source="network", n_rays=0):
         torch.cuda.synchronize()
         fuse_ms.append(e0.elapsed_time(e1))
     rays = []
+    centres = synth.room_panorama_centres(N_VIEWS_TIMED) if workload == "panorama" else None
     for i in range(N_VIEWS_TIMED):
-        o, d = synth.room_heldout_rays(i)
+        o, d = synth.room_heldout_rays(i) if centres is None else synth.room_panorama_rays(center=tuple(centres[i]))
         if n_rays:
             idx = np.sort(synth.sub_sample(len(o), n_rays, seed=50 + i))
             o, d = np.ascontiguousarray(o[idx]), np.ascontiguousarray(d[idx])
@@ -221,13 +234,16 @@ def run_ours(args, ws, rank, local):
     from paper_2311_17878_gb300 import synth
     from paper_2311_17878_gb300 import tsdfs as T
     B.build()
+    if args.train_pitch is not None:
+        synth.TRAIN_PITCH_DEG = args.train_pitch
     dev = f"cuda:{local}"
     spec = synth.scene_mlp("room")
     prec = args.precision
     PREC = {"f16": T.TSDFS_PREC_F16, "bf16": T.TSDFS_PREC_BF16, "f32": T.TSDFS_PREC_F32}
     mlp = T.Mlp(spec, PREC[prec], device=dev)
     mlp_depth = mlp if prec != "f32" else T.Mlp(spec, T.TSDFS_PREC_F16, device=dev)
-    wl, grid, grid_an, mask, rays, fusion, depth = build_scene(dev, mlp_depth, args.grid_source, args.rays)
+    wl, grid, grid_an, mask, rays, fusion, depth = build_scene(dev, mlp_depth, args.grid_source, args.rays,
+                                                               args.workload)
     bp = synth.BoundsParams(**{**wl.bounds.__dict__, "d_s": args.ds_vox * wl.grid.voxel_size})
     n = rays[0][0].shape[0]
     max_samples = n * max(bp.n_max, bp.n_fallback)
@@ -243,6 +259,27 @@ def run_ours(args, ws, rank, local):
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
+    graphs = []
+    if args.graph:
+        # each view's bounds + render as one CUDA graph (no host synchronisation inside)
+        for i in range(N_VIEWS_TIMED):
+            step(i)
+        torch.cuda.synchronize()
+        for i in range(N_VIEWS_TIMED):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                step(i)
+            graphs.append(g)
+        for i in range(N_VIEWS_TIMED):
+            graphs[i].replay()
+        torch.cuda.synchronize()
+
+    def timed_step(k):
+        if graphs:
+            graphs[k % N_VIEWS_TIMED].replay()
+        else:
+            step(k)
+
     samples_per_view, fallback_per_view = [], []
     for i in range(N_VIEWS_TIMED):
         bounds.compute(grid, rays[i][0], rays[i][1], bp, mask)
@@ -258,11 +295,19 @@ def run_ours(args, ws, rank, local):
         for k in range(args.steps):
             flush.fill_(float(k))
             evs[k][0].record(st)
-            step(k)
+            timed_step(k)
             evs[k][1].record(st)
         torch.cuda.synchronize()
     barrier(ws)
     t_wall = time.perf_counter() - t_wall
+    if graphs:
+        # graph replays carry no per-kernel events: time the kernels on an eager pass over the same views
+        T.lib().tsdfs_profile(0)
+        T.lib().tsdfs_profile(1)
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            step(k)
+        torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     mlp_name = "mlp_simt" if prec == "f32" else "mlp_tc"
     import ctypes as C
@@ -292,14 +337,15 @@ def run_ours(args, ws, rank, local):
                 "peak_kind": "fp32 FMA, 152 SMs x 128 lanes x 2 x 2.07 GHz", "kernel": "mlp_simt"}
     kernel_share = {"mlp_ms_per_step": mlp_ms, "all_kernels_ms_per_step": ms_all.value / max(args.steps, 1)}
     main_only = args.only_main
+    lean = main_only or args.quality_only
     # end to end through the public API with host buffers
-    e2e = None if main_only else run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev)
+    e2e = None if lean else run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev)
     # hierarchical comparator on the same views
-    hier = {} if main_only else run_hier(args, mlp, grid, rays, bp, n, dev, flush)
+    hier = {} if lean else run_hier(args, mlp, grid, rays, bp, n, dev, flush)
     quality = None if (args.no_quality or main_only or rank != 0) else run_quality(
-        spec, wl, grid, bounds, rend, hier["renderer"], rays, bp, mask, args.sweep)
-    cpu = run_cpu_baseline(wl, grid, rays, bp, spec) if (rank == 0 and ws == 1 and not main_only) else None
-    train = run_train(spec, wl, grid, mask, dev) if (rank == 0 and not main_only) else None
+        spec, wl, grid, bounds, rend, hier.get("renderer"), rays, bp, mask, args.sweep)
+    cpu = run_cpu_baseline(wl, grid, rays, bp, spec) if (rank == 0 and ws == 1 and not lean) else None
+    train = run_train(spec, wl, grid, mask, dev) if (rank == 0 and not lean) else None
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -309,6 +355,7 @@ def run_ours(args, ws, rank, local):
                    "samples_per_step": samples_timed / args.steps, "grid": "256^3 f32 + uint8",
                    "d_s_vox": args.ds_vox, "fallback_frac_per_view": fallback_per_view,
                    "grid_source": args.grid_source, "ray_subset": args.rays or None,
+                   "cuda_graph": bool(graphs), "train_pitch_deg": synth.TRAIN_PITCH_DEG,
                    "networks": "SDF 8x256 PE6 skip4 + colour 4x256 PE4", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}, rays independent", "wall_s": t_wall},
         "e2e": e2e, "gpu_launches": int(n_all.value), "roofline": roof, "kernel_time": kernel_share,
@@ -425,12 +472,12 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=Fal
     o, d = rays[0][0], rays[0][1]
     bounds.compute(grid, o, d, bp, mask)
     out = rend.render(o, d, bounds)
-    hout = hier.render(grid, o, d, bp.t_near, bp.t_far)
+    hout = hier.render(grid, o, d, bp.t_near, bp.t_far) if hier is not None else None
     torch.cuda.synchronize()
     idx = synth.sub_sample(o.shape[0], QUALITY_PIXELS, seed=31)
     idx_t = torch.as_tensor(idx, device=o.device)
     gpu_rgb = out.rgb[idx_t].cpu().numpy()
-    hier_rgb = hout.rgb[idx_t].cpu().numpy()
+    hier_rgb = hout.rgb[idx_t].cpu().numpy() if hout is not None else None
     on, dn = rays[0][2][idx], rays[0][3][idx]
     t0, te, ok = cgrid.clip_rays(wl.grid, on, dn, bp.t_near, bp.t_far, "f64")
     t_q = time.perf_counter()
@@ -442,7 +489,8 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=Fal
     cnt = bounds.n[idx_t].cpu().numpy()
     with torch.no_grad():
         ort = orr.render_bounded(net, on, dn, tn, tf, cnt)["rgb"].numpy()
-    p_gpu, p_or, p_h = orr.psnr(gpu_rgb, dense), orr.psnr(ort, dense), orr.psnr(hier_rgb, dense)
+    p_gpu, p_or = orr.psnr(gpu_rgb, dense), orr.psnr(ort, dense)
+    p_h = orr.psnr(hier_rgb, dense) if hier_rgb is not None else None
     # D_s sweep (surface criterion of Alg. 1) on the same pixels: GPU bounds + render
     from paper_2311_17878_gb300 import tsdfs as T
     vs = wl.grid.voxel_size
@@ -473,7 +521,7 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=Fal
                       "status": int(bounds.status[idx_t][i].item())})
     return {"pixels": QUALITY_PIXELS, "reference": f"oracle FP64 dense {DENSE_SAMPLES} samples over [t0,t_end]",
             "worst": worst, "d_s_vox": bp.d_s / vs, "psnr_tsdf_gpu": p_gpu, "psnr_tsdf_oracle": p_or, "psnr_hier96_gpu": p_h,
-            "meets_oracle_minus_0p1dB": bool(p_gpu >= p_or - 0.1), "tsdf_ge_hier96": bool(p_gpu >= p_h),
+            "meets_oracle_minus_0p1dB": bool(p_gpu >= p_or - 0.1), "tsdf_ge_hier96": bool(p_gpu >= p_h) if p_h is not None else None,
             "samples_per_ray_tsdf": float(bounds.n.float().mean().item()),
             "fallback_frac": float((bounds.status == 2).float().mean().item()), "d_s_sweep": sweep,
             "oracle_s": time.perf_counter() - t_q}
@@ -501,7 +549,7 @@ def run_cpu_baseline(wl, grid, rays, bp, spec, seconds=10.0, chunk=2048):
         done += len(idx)
     dt = time.perf_counter() - t
     return {"value": done / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"{done} seeded rays of one 640x480 view in chunks of {chunk}: C bounds (1 thread) "
+            "sample": f"{done} seeded rays of image 0 of the workload in chunks of {chunk}: C bounds (1 thread) "
                       f"+ torch FP64 render", "seconds": dt}
 
 
@@ -525,7 +573,10 @@ def run_reference(args, ws, rank):
     bp = wl.bounds
 
     def step(k):
-        o, d = synth.room_heldout_rays(k % N_VIEWS_TIMED)
+        if args.workload == "panorama":
+            o, d = synth.room_panorama_rays(center=tuple(synth.room_panorama_centres(N_VIEWS_TIMED)[k % N_VIEWS_TIMED]))
+        else:
+            o, d = synth.room_heldout_rays(k % N_VIEWS_TIMED)
         idx = synth.sub_sample(len(o), args.ref_rays, seed=40 + k)
         b = cgrid.ray_bounds(wl.grid, V, o[idx], d[idx], bp, "f32")
         with torch.no_grad():
@@ -543,12 +594,15 @@ def run_reference(args, ws, rank):
             "dtype": "f64", "data": "synthetic (seeded room scene, fitted networks)", "impl": "reference",
             "config": {"workload": WORKLOAD, "rays_per_step": args.ref_rays, "setup_s": t_setup},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-                             "sample": f"{args.ref_rays} seeded rays of a 640x480 view per step"},
+                             "sample": f"{args.ref_rays} seeded rays of one image of the workload per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
+    global WORKLOAD, N_VIEWS_TIMED
     args = parse()
+    WORKLOAD = WORKLOADS[args.workload]
+    N_VIEWS_TIMED = 4 if args.workload == "panorama" else 10
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         ws = int(os.environ.get("WORLD_SIZE", "1"))

@@ -220,6 +220,11 @@ def make_box_room(seed, room_lo, room_hi, n_boxes, n_plates, plate_thick=0.02, p
     return BoxRoomScene(room_lo, room_hi, lo, hi, albedo, n_plates)
 
 
+# largest pitch of the room's random training poses (held-out views use 15 as well);
+# a wider range trades horizontal coverage for floor / ceiling coverage
+TRAIN_PITCH_DEG = 15.0
+
+
 def sample_free_poses(scene, rng, n, margin=0.3, height=(1.0, 2.0), pitch_deg=15.0, clearance=0.3):
     """Random in-room camera poses, rejected when closer than ``clearance`` to solid space."""
     poses = []
@@ -455,7 +460,7 @@ def room_workload(n_views=100, width=640, height=480, grid_n=256, noise_std=0.00
     vs = grid.voxel_size
     fx = fy = 500.0 * width / 640.0
     cx, cy = width / 2.0, height / 2.0
-    c2ws = sample_free_poses(scene, np.random.default_rng(SEED_POSES), n_views)
+    c2ws = sample_free_poses(scene, np.random.default_rng(SEED_POSES), n_views, pitch_deg=TRAIN_PITCH_DEG)
     depth = render_depth_maps(scene, c2ws, fx, fy, cx, cy, width, height, noise_std) if with_views else None
     bounds = BoundsParams(d_s=vs, t_near=0.05, t_far=12.0, step=2 * vs, n_max=64)
     views = _views(c2ws, fx, fy, cx, cy, width, height, depth) if with_views else None
@@ -473,6 +478,12 @@ def room_heldout_rays(i=0, width=640, height=480):
 def room_panorama_rays(width=1024, height=512, center=(0.3, -0.2, 1.5)):
     o, d = equirect_rays(center, width, height)
     return o.astype(np.float32), d.astype(np.float32)
+
+
+def room_panorama_centres(n=4):
+    """Seeded in-room panorama centres, clear of solids (the ragged-batching case)."""
+    poses = sample_free_poses(room_scene(), np.random.default_rng(SEED_HELDOUT + 100), n)
+    return poses.reshape(n, 3, 4)[:, :, 3].copy()
 
 
 def random_rays_from_views(views: Views, n, seed=SEED_TRAIN_RAYS):
@@ -643,7 +654,7 @@ def room_workload_torch(device="cuda", n_views=100, width=640, height=480, grid_
     """room_workload with the depth maps rendered on a torch device."""
     wl = room_workload(n_views, width, height, grid_n, noise_std, with_views=False)
     fx = fy = 500.0 * width / 640.0
-    c2ws = sample_free_poses(wl.scene, np.random.default_rng(SEED_POSES), n_views)
+    c2ws = sample_free_poses(wl.scene, np.random.default_rng(SEED_POSES), n_views, pitch_deg=TRAIN_PITCH_DEG)
     depth = render_depth_maps_torch(wl.scene, c2ws, fx, fy, width / 2.0, height / 2.0, width, height, noise_std,
                                     device=device)
     V = len(c2ws)
