@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--graph", action="store_true", help="replay each view's bounds + render as a captured CUDA graph")
     ap.add_argument("--train-pitch", type=float, default=None,
                     help="largest pitch (degrees) of the random training poses (default: the synthetic recipe's)")
+    ap.add_argument("--recovery-tau", type=float, default=None,
+                    help="recovery pass of Sec. 4.5: re-render rays whose weight sum stays below tau (off by default)")
     ap.add_argument("--quality-only", action="store_true", help="main timing + quality (no e2e / comparator / cpu / "
                                                                    "training legs)")
     ap.add_argument("--only-main", action="store_true", help="time the render path only (no e2e / comparator / "
@@ -249,12 +251,15 @@ def run_ours(args, ws, rank, local):
     max_samples = n * max(bp.n_max, bp.n_fallback)
     bounds = T.Bounds(n, device=dev)
     rend = T.Renderer(mlp, n, max_samples, device=dev)
+    rec = T.Recovery(mlp, n, bp.n_fallback, device=dev) if args.recovery_tau is not None else None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
     def step(i):
         o, d = rays[i % N_VIEWS_TIMED][:2]
         bounds.compute(grid, o, d, bp, mask)
-        rend.render(o, d, bounds)
+        out = rend.render(o, d, bounds)
+        if rec is not None:
+            rec.apply(grid, o, d, bp, args.recovery_tau, out, bounds)
 
     for i in range(args.warmup):
         step(i)
@@ -283,7 +288,12 @@ def run_ours(args, ws, rank, local):
     samples_per_view, fallback_per_view = [], []
     for i in range(N_VIEWS_TIMED):
         bounds.compute(grid, rays[i][0], rays[i][1], bp, mask)
-        samples_per_view.append(int(bounds.offsets[-1].item()))
+        extra = 0
+        if rec is not None:
+            out_i = rend.render(rays[i][0], rays[i][1], bounds)
+            rec.apply(grid, rays[i][0], rays[i][1], bp, args.recovery_tau, out_i, bounds)
+            extra = int(rec.bounds.offsets[-1].item())
+        samples_per_view.append(int(bounds.offsets[-1].item()) + extra)
         fallback_per_view.append(round(float((bounds.status == 2).float().mean().item()), 4))
     st = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -322,9 +332,10 @@ def run_ours(args, ws, rank, local):
     samples_timed = sum(samples_per_view[k % N_VIEWS_TIMED] for k in range(args.steps))
     # dominant kernel roofline (algorithmic FLOPs per launch / mean launch time)
     hbm, bf16_burst, bf16_sus, peak_src = measured_peaks()
-    mlp_ms = ms_k.value / max(n_k.value, 1)
-    algo_flop_launch = ALGO_FLOP_PER_SAMPLE * samples_timed / max(args.steps, 1)
-    achieved = algo_flop_launch / (mlp_ms / 1e3) / 1e12
+    # algorithmic FLOPs of the timed steps over the kernel's time in the same steps (with the
+    # recovery pass a step launches the kernel twice, so per-launch means would mislead)
+    mlp_ms = ms_k.value / max(args.steps, 1)
+    achieved = ALGO_FLOP_PER_SAMPLE * samples_timed / (ms_k.value / 1e3) / 1e12 if ms_k.value > 0 else 0.0
     if prec != "f32":
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_burst, "unit": "TFLOP/s",
                 "frac": achieved / bf16_burst, "traffic": None,
@@ -335,7 +346,8 @@ def run_ours(args, ws, rank, local):
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": None,
                 "peak_kind": "fp32 FMA, 152 SMs x 128 lanes x 2 x 2.07 GHz", "kernel": "mlp_simt"}
-    kernel_share = {"mlp_ms_per_step": mlp_ms, "all_kernels_ms_per_step": ms_all.value / max(args.steps, 1)}
+    kernel_share = {"mlp_ms_per_step": mlp_ms, "mlp_launches_per_step": n_k.value / max(args.steps, 1),
+                    "all_kernels_ms_per_step": ms_all.value / max(args.steps, 1)}
     main_only = args.only_main
     lean = main_only or args.quality_only
     # end to end through the public API with host buffers
@@ -343,7 +355,7 @@ def run_ours(args, ws, rank, local):
     # hierarchical comparator on the same views
     hier = {} if lean else run_hier(args, mlp, grid, rays, bp, n, dev, flush)
     quality = None if (args.no_quality or main_only or rank != 0) else run_quality(
-        spec, wl, grid, bounds, rend, hier.get("renderer"), rays, bp, mask, args.sweep)
+        spec, wl, grid, bounds, rend, hier.get("renderer"), rays, bp, mask, args.sweep, rec, args.recovery_tau)
     cpu = run_cpu_baseline(wl, grid, rays, bp, spec) if (rank == 0 and ws == 1 and not lean) else None
     train = run_train(spec, wl, grid, mask, dev) if (rank == 0 and not lean) else None
     clocks = clk.summary()
@@ -356,6 +368,7 @@ def run_ours(args, ws, rank, local):
                    "d_s_vox": args.ds_vox, "fallback_frac_per_view": fallback_per_view,
                    "grid_source": args.grid_source, "ray_subset": args.rays or None,
                    "cuda_graph": bool(graphs), "train_pitch_deg": synth.TRAIN_PITCH_DEG,
+                   "recovery_tau": args.recovery_tau,
                    "networks": "SDF 8x256 PE6 skip4 + colour 4x256 PE4", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}, rays independent", "wall_s": t_wall},
         "e2e": e2e, "gpu_launches": int(n_all.value), "roofline": roof, "kernel_time": kernel_share,
@@ -462,9 +475,11 @@ def run_hier(args, mlp, grid, rays, bp, n, dev, flush):
             "ms_per_step": tot / steps, "samples_per_ray": 96 + 64 * 0, "renderer": h}
 
 
-def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=False):
+def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=False, rec=None, tau=None):
     """PSNR against the oracle's dense reference (FP64, DENSE_SAMPLES midpoints
-    over [t0, t_end]) on a seeded pixel subset of view 0."""
+    over [t0, t_end]) on a seeded pixel subset of view 0.  The oracle's own TSDF
+    render takes its bounds from its fp32 Alg. 1 on the same grid (and, with a
+    recovery threshold, its own recovery pass of Sec. 4.5)."""
     import torch
     from oracle import cgrid
     from oracle import render as orr
@@ -472,6 +487,9 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=Fal
     o, d = rays[0][0], rays[0][1]
     bounds.compute(grid, o, d, bp, mask)
     out = rend.render(o, d, bounds)
+    if rec is not None:
+        first_wsum = out.wsum.clone()
+        rec.apply(grid, o, d, bp, tau, out, bounds)
     hout = hier.render(grid, o, d, bp.t_near, bp.t_far) if hier is not None else None
     torch.cuda.synchronize()
     idx = synth.sub_sample(o.shape[0], QUALITY_PIXELS, seed=31)
@@ -484,11 +502,16 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=Fal
     net = orr.Net(spec)
     dd = orr.dense_reference(net, on, dn, t0, te, n=DENSE_SAMPLES)
     dense = dd["rgb"].numpy()
-    tn = bounds.t_n[idx_t].cpu().numpy().astype(np.float64)
-    tf = bounds.t_f[idx_t].cpu().numpy().astype(np.float64)
-    cnt = bounds.n[idx_t].cpu().numpy()
-    with torch.no_grad():
-        ort = orr.render_bounded(net, on, dn, tn, tf, cnt)["rgb"].numpy()
+    ob = cgrid.ray_bounds(wl.grid, grid.V.cpu().numpy(), on, dn, bp, "f32")
+    tn, tf, cnt = ob["t_n"].astype(np.float64), ob["t_f"].astype(np.float64), ob["n"]
+    if rec is not None:
+        t0f, tef, _ = cgrid.clip_rays(wl.grid, on, dn, bp.t_near, bp.t_far, "f32")
+        ro, again = orr.render_recovered(net, on, dn, tn, tf, cnt, ob["status"], t0f.astype(np.float64),
+                                         tef.astype(np.float64), tau, bp.n_fallback)
+        ort = ro["rgb"].numpy()
+    else:
+        with torch.no_grad():
+            ort = orr.render_bounded(net, on, dn, tn, tf, cnt)["rgb"].numpy()
     p_gpu, p_or = orr.psnr(gpu_rgb, dense), orr.psnr(ort, dense)
     p_h = orr.psnr(hier_rgb, dense) if hier_rgb is not None else None
     # D_s sweep (surface criterion of Alg. 1) on the same pixels: GPU bounds + render
@@ -524,6 +547,9 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=Fal
             "meets_oracle_minus_0p1dB": bool(p_gpu >= p_or - 0.1), "tsdf_ge_hier96": bool(p_gpu >= p_h) if p_h is not None else None,
             "samples_per_ray_tsdf": float(bounds.n.float().mean().item()),
             "fallback_frac": float((bounds.status == 2).float().mean().item()), "d_s_sweep": sweep,
+            "recovery": None if rec is None else {
+                "tau": tau, "recovered_frac": float((rec.bounds.status == 2).float().mean().item()),
+                "recovered_frac_oracle_pixels": float(np.mean(again))},
             "oracle_s": time.perf_counter() - t_q}
 
 

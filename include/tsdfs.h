@@ -208,6 +208,29 @@ int render_rays(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, co
                 float* depth, float* wsum, float* normal, float* eik, void* workspace, size_t ws_bytes,
                 tsdfs_stream_t stream);
 
+/* ---- recovery of rays the bounds missed (Sec. 4.5, threshold tau of Tab. 5) ----
+ * A second pass for rays whose accumulated weight stays low: every BOUNDED ray
+ * r with wsum[r] < tau (wsum from a first render_rays) gets status2 =
+ * TSDFS_FALLBACK, [t_n2, t_f2] = [t0, t_end] (its grid-box clip of
+ * [t_near, t_far], fp32 as in tsdf_ray_bounds) and n2 = p->n_fallback; every
+ * other ray (MISS, FALLBACK, or wsum >= tau) gets n2 = 0, status2 = TSDFS_MISS,
+ * t_n2 = t_f2 = 0.  offsets2 is the exclusive scan of n2 (n_rays + 1 entries).
+ * Render the second pass with render_rays(t_n2, t_f2, offsets2, status2) into
+ * separate outputs, then tsdf_recovery_merge.  All arrays are device memory,
+ * caller-owned, ray-major as in tsdf_ray_bounds; p->d_s, step, n_max,
+ * nb_radius and m_confirm are not used.  ws >= tsdfs_bounds_workspace_size.
+ * Asynchronous on stream; argument errors return negative codes.            */
+int tsdf_recovery_bounds(const tsdfs_grid* grid, const float* ray_o, const float* ray_d, int64_t n_rays,
+                         const tsdfs_bounds_params* p, float tau, const float* wsum, const uint8_t* status,
+                         float* t_n2, float* t_f2, int32_t* n2, int32_t* offsets2, uint8_t* status2, void* ws,
+                         size_t ws_bytes, tsdfs_stream_t stream);
+/* Copy the second render's rgb[3], depth, wsum (and normal[3] when both normal
+ * pointers are non-NULL; both or neither) over the first render's outputs for
+ * the rays with status2 == TSDFS_FALLBACK.  Device pointers, in place.       */
+int tsdf_recovery_merge(int64_t n_rays, const uint8_t* status2, const float* rgb2, const float* depth2,
+                        const float* wsum2, const float* normal2, float* rgb, float* depth, float* wsum,
+                        float* normal, tsdfs_stream_t stream);
+
 /* ---- hierarchical comparator (64 coarse + 32 inverse-CDF fine, Tab. 2 "HS") -
  * Per ray over [t0, t_end] (t_near/t_far clipped to the grid box of `grid`;
  * only its geometry fields are read): 64 midpoints, SDF values only; section

@@ -250,6 +250,29 @@ def render_bounded(net, rays_o, rays_d, t_n, t_f, counts):
     return render_samples(net, o, d, t, dl, mask)
 
 
+STATUS_BOUNDED = 1   # ray status written by the bounds pass: 0 MISS, 1 BOUNDED, 2 FALLBACK
+
+
+def render_recovered(net, rays_o, rays_d, t_n, t_f, counts, status, t0, t_end, tau, n_fallback=96):
+    """Sec. 4.5 (threshold tau of Tab. 5): render the TSDF-bounded samples; every
+    BOUNDED ray whose accumulated weight stays below tau is rendered again with
+    n_fallback midpoints over its whole [t0, t_end], and that render replaces the
+    first.  Returns (merged outputs, boolean mask of the re-rendered rays)."""
+    with torch.no_grad():
+        first = render_bounded(net, rays_o, rays_d, t_n, t_f, counts)
+    status = np.asarray(status)
+    again = (status == STATUS_BOUNDED) & (first["wsum"].numpy() < tau)
+    out = {k: first[k].clone() for k in ("rgb", "depth", "wsum", "normal")}
+    if again.any():
+        with torch.no_grad():
+            second = render_uniform(net, np.asarray(rays_o)[again], np.asarray(rays_d)[again],
+                                    np.asarray(t0)[again], np.asarray(t_end)[again], n_fallback)
+        idx = torch.as_tensor(np.nonzero(again)[0])
+        for k in out:
+            out[k][idx] = second[k]
+    return out, again
+
+
 def render_uniform(net, rays_o, rays_d, t0, t_end, n):
     """n midpoint samples over [t0, t_end] (the fallback and the dense reference)."""
     return render_bounded(net, rays_o, rays_d, t0, t_end, np.full(len(np.asarray(t0)), n, np.int64))

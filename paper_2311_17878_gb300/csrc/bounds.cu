@@ -114,6 +114,30 @@ __device__ __forceinline__ void point_at(const float o[3], const float d[3], flo
     for (int a = 0; a < 3; ++a) p[a] = __fadd_rn(o[a], __fmul_rn(t, d[a]));
 }
 
+// clip a ray to the grid box ("RenderingCube") within [t_near, t_far]: [t0, t_end]
+__device__ __forceinline__ bool clip_box(const GridDev& g, const float o[3], const float d[3], float t_near, float t_far,
+                                         float& t0, float& t_end) {
+    const float kInf = __int_as_float(0x7f800000);
+    float tmin = -kInf, tmax = kInf;
+    bool hit = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float lo = g.org[a], hi = __fadd_rn(g.org[a], __fmul_rn((float)g.n[a], g.vs));
+        if (d[a] == 0.0f) {
+            if (o[a] < lo || o[a] > hi) hit = false;
+            continue;
+        }
+        const float inv = __fdiv_rn(1.0f, d[a]);
+        const float t1 = __fmul_rn(__fsub_rn(lo, o[a]), inv), t2 = __fmul_rn(__fsub_rn(hi, o[a]), inv);
+        const float tl = t1 < t2 ? t1 : t2, th = t1 < t2 ? t2 : t1;
+        if (tl > tmin) tmin = tl;
+        if (th < tmax) tmax = th;
+    }
+    t0 = t_near > tmin ? t_near : tmin;
+    t_end = t_far < tmax ? t_far : tmax;
+    return hit && t0 < t_end;
+}
+
 __global__ void __launch_bounds__(kBoundsBlock) k_ray_bounds(GridDev g, const uint32_t* __restrict__ mask,
                                                              const float* __restrict__ ray_o,
                                                              const float* __restrict__ ray_d, int64_t n_rays,
@@ -133,24 +157,8 @@ __global__ void __launch_bounds__(kBoundsBlock) k_ray_bounds(GridDev g, const ui
             d[a] = __ldg(ray_d + 3 * r + a);
         }
         // ---- clip to the grid box ("RenderingCube") ----
-        float tmin = -kInf, tmax = kInf;
-        bool hit = true;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float lo = g.org[a], hi = __fadd_rn(g.org[a], __fmul_rn((float)g.n[a], g.vs));
-            if (d[a] == 0.0f) {
-                if (o[a] < lo || o[a] > hi) hit = false;
-                continue;
-            }
-            const float inv = __fdiv_rn(1.0f, d[a]);
-            const float t1 = __fmul_rn(__fsub_rn(lo, o[a]), inv), t2 = __fmul_rn(__fsub_rn(hi, o[a]), inv);
-            const float tl = t1 < t2 ? t1 : t2, th = t1 < t2 ? t2 : t1;
-            if (tl > tmin) tmin = tl;
-            if (th < tmax) tmax = th;
-        }
-        const float t0 = p.t_near > tmin ? p.t_near : tmin;
-        const float t_end = p.t_far < tmax ? p.t_far : tmax;
-        if (!hit || !(t0 < t_end)) {
+        float t0, t_end;
+        if (!clip_box(g, o, d, p.t_near, p.t_far, t0, t_end)) {
             t_n_out[r] = 0.0f; t_f_out[r] = 0.0f; n_out[r] = 0; status_out[r] = TSDFS_MISS;
             if (t_zero_out) t_zero_out[r] = kNaN;
             continue;
@@ -224,6 +232,30 @@ __global__ void __launch_bounds__(kBoundsBlock) k_ray_bounds(GridDev g, const ui
         if (cnt > p.n_max) cnt = p.n_max;
         t_n_out[r] = tn; t_f_out[r] = tf; n_out[r] = cnt; status_out[r] = TSDFS_BOUNDED;
         if (t_zero_out) t_zero_out[r] = tz;
+    }
+}
+
+// ---- recovery (Sec. 4.5): BOUNDED rays whose weight sum stayed below tau are
+// rendered again over the whole [t0, t_end] with n_fallback samples ----
+__global__ void __launch_bounds__(kBoundsBlock) k_recovery_bounds(GridDev g, const float* __restrict__ ray_o,
+                                                                  const float* __restrict__ ray_d, int64_t n_rays,
+                                                                  BoundsDev p, float tau,
+                                                                  const float* __restrict__ wsum,
+                                                                  const uint8_t* __restrict__ status,
+                                                                  float* __restrict__ t_n2, float* __restrict__ t_f2,
+                                                                  int32_t* __restrict__ n2, uint8_t* __restrict__ status2) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
+        float o[3], d[3], t0 = 0.0f, t_end = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = __ldg(ray_o + 3 * r + a);
+            d[a] = __ldg(ray_d + 3 * r + a);
+        }
+        const bool again = status[r] == TSDFS_BOUNDED && wsum[r] < tau && clip_box(g, o, d, p.t_near, p.t_far, t0, t_end);
+        t_n2[r] = again ? t0 : 0.0f;
+        t_f2[r] = again ? t_end : 0.0f;
+        n2[r] = again ? p.n_fallback : 0;
+        status2[r] = again ? (uint8_t)TSDFS_FALLBACK : (uint8_t)TSDFS_MISS;
     }
 }
 
@@ -367,6 +399,38 @@ extern "C" int tsdf_ray_bounds(const tsdfs_grid* g, const uint32_t* mask, const 
     }
     int32_t* sums = reinterpret_cast<int32_t*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
     return exclusive_scan(n_samples, n_rays, offsets, sums, st);
+}
+
+extern "C" int tsdf_recovery_bounds(const tsdfs_grid* g, const float* ray_o, const float* ray_d, int64_t n_rays,
+                                    const tsdfs_bounds_params* p, float tau, const float* wsum, const uint8_t* status,
+                                    float* t_n2, float* t_f2, int32_t* n2, int32_t* offsets2, uint8_t* status2,
+                                    void* ws, size_t ws_bytes, tsdfs_stream_t stream) {
+    int rc = grid_check(g);
+    if (rc) return rc;
+    if (!p) return fail(TSDFS_E_INVALID, "params is NULL");
+    if (n_rays < 0 || n_rays > (int64_t)INT32_MAX) return fail(TSDFS_E_INVALID, "n_rays must be in [0, 2^31)");
+    if (!(p->t_near < p->t_far)) return fail(TSDFS_E_INVALID, "t_near must be < t_far");
+    if (p->n_fallback < 0 || p->n_fallback > 4096) return fail(TSDFS_E_INVALID, "n_fallback must be in [0, 4096]");
+    if ((int64_t)p->n_fallback * n_rays > (int64_t)INT32_MAX)
+        return fail(TSDFS_E_INVALID, "sample total could overflow int32 offsets");
+    if (!(tau == tau)) return fail(TSDFS_E_INVALID, "tau must not be NaN");
+    if (n_rays > 0 && (!ray_o || !ray_d || !wsum || !status || !t_n2 || !t_f2 || !n2 || !status2))
+        return fail(TSDFS_E_INVALID, "ray, input and output pointers must be non-NULL");
+    if (!offsets2) return fail(TSDFS_E_INVALID, "offsets2 is NULL");
+    if (ws_bytes < tsdfs_bounds_workspace_size(n_rays) || !ws) return fail(TSDFS_E_WORKSPACE, "recovery workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_rays > 0) {
+        GridDev gd{g->tsdf, g->dtype == TSDFS_F16, {g->nx, g->ny, g->nz}, {g->origin[0], g->origin[1], g->origin[2]},
+                   g->voxel_size, g->trunc};
+        BoundsDev bd{p->d_s, p->t_near, p->t_far, p->step, p->nb_radius, p->m_confirm, p->n_max, p->n_fallback};
+        ProfScope ps("recovery_bounds", st);
+        k_recovery_bounds<<<grid_1d(n_rays, kBoundsBlock, 152 * 64), kBoundsBlock, 0, st>>>(
+            gd, ray_o, ray_d, n_rays, bd, tau, wsum, status, t_n2, t_f2, n2, status2);
+        rc = cuda_check(cudaGetLastError(), "tsdf_recovery_bounds launch");
+        if (rc) return rc;
+    }
+    int32_t* sums = reinterpret_cast<int32_t*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
+    return exclusive_scan(n2, n_rays, offsets2, sums, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -183,6 +183,24 @@ __global__ void k_hier_fine(const float* __restrict__ fcoarse, const float* __re
     }
 }
 
+// recovery merge: rays re-rendered by the recovery pass take the second render's outputs
+__global__ void k_recovery_merge(int64_t n_rays, const uint8_t* __restrict__ status2, const float* __restrict__ rgb2,
+                                 const float* __restrict__ depth2, const float* __restrict__ wsum2,
+                                 const float* __restrict__ normal2, float* __restrict__ rgb, float* __restrict__ depth,
+                                 float* __restrict__ wsum, float* __restrict__ normal) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
+        if (status2[r] != TSDFS_FALLBACK) continue;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rgb[3 * r + c] = rgb2[3 * r + c];
+        depth[r] = depth2[r];
+        wsum[r] = wsum2[r];
+        if (normal && normal2) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) normal[3 * r + c] = normal2[3 * r + c];
+        }
+    }
+}
+
 }  // namespace
 
 int launch_composite(const SampleRec* rec, const int32_t* offsets, int per_ray, const uint8_t* status, int64_t n_rays,
@@ -208,3 +226,20 @@ int launch_hier_fine(const float* fcoarse, const float* tc, const float* t0, con
 }
 
 }  // namespace tsdfs
+
+using namespace tsdfs;
+
+extern "C" int tsdf_recovery_merge(int64_t n_rays, const uint8_t* status2, const float* rgb2, const float* depth2,
+                                   const float* wsum2, const float* normal2, float* rgb, float* depth, float* wsum,
+                                   float* normal, tsdfs_stream_t stream) {
+    if (n_rays < 0) return fail(TSDFS_E_INVALID, "n_rays must be >= 0");
+    if (n_rays == 0) return TSDFS_OK;
+    if (!status2 || !rgb2 || !depth2 || !wsum2 || !rgb || !depth || !wsum)
+        return fail(TSDFS_E_INVALID, "status, colour, depth and weight pointers must be non-NULL");
+    if ((normal == nullptr) != (normal2 == nullptr)) return fail(TSDFS_E_INVALID, "normal and normal2: both or neither");
+    cudaStream_t st = (cudaStream_t)stream;
+    ProfScope ps("recovery_merge", st);
+    k_recovery_merge<<<grid_1d(n_rays, 256), 256, 0, st>>>(n_rays, status2, rgb2, depth2, wsum2, normal2, rgb, depth,
+                                                          wsum, normal);
+    return cuda_check(cudaGetLastError(), "tsdf_recovery_merge launch");
+}

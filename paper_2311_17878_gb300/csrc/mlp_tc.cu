@@ -21,6 +21,8 @@
 // so each stage has a thread of its own.  All hand-offs are mbarriers; every
 // wait is bounded and on timeout the kernel records TSDFS_DEV_TIMEOUT, drains
 // its own copies / MMAs and returns.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace tsdfs {
@@ -188,6 +190,25 @@ __device__ __forceinline__ void tmem_ld16x256_x2(uint32_t taddr, float (&v)[8]) 
                  : "r"(taddr));
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+// one 16x256b repetition: 16 lanes x 8 columns, registers 0, 1 = lane base + t/4 and
+// 2, 3 = lane base + 8 + t/4, at columns 2(t%4), 2(t%4)+1
+__device__ __forceinline__ void tmem_ld16x256_x1(uint32_t taddr, float* v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
+}
+// wait for this thread's TMEM loads; the registers they fill are operands, so no use of
+// them can be scheduled before the wait
+__device__ __forceinline__ void tmem_wait_ld16(float (&d)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3]), "+f"(d[4]), "+f"(d[5]), "+f"(d[6]), "+f"(d[7]),
+                   "+f"(d[8]), "+f"(d[9]), "+f"(d[10]), "+f"(d[11]), "+f"(d[12]), "+f"(d[13]), "+f"(d[14]), "+f"(d[15])
+                 :
+                 : "memory");
 }
 // four 8x8 16-bit matrices to shared memory: thread i supplies the address of row
 // i % 8 of matrix i / 8; register j holds row t/4, columns 2(t%4), 2(t%4)+1 of matrix j
@@ -560,35 +581,55 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                     const uint32_t row1 = smem_u32(A1) + a_off(32 * q + lane, 0, Kn);
                     const int c_lo = half_lo(Kn, hf), c_hi = half_hi(Kn, hf);
                     const int c_full = (ly.N / 16) * 16 < c_hi ? (ly.N / 16) * 16 : c_hi;
-                    for (int c0 = c_lo; c0 < c_full; c0 += 16) {
-                        float v[8], x[8], y[8], z[8];
-                        tmem_ld16x256_x2(t_v + c0, v);
-                        tmem_ld16x256_x2(t_x + c0, x);
-                        tmem_ld16x256_x2(t_y + c0, y);
-                        tmem_ld16x256_x2(t_z + c0, z);
-                        tmem_wait_ld();
+                    // 8-column groups, software-pipelined: the TMEM loads of group c + 8 are in
+                    // flight while group c is computed.  buf = [value(4) | d/dx(4) | d/dy(4) | d/dz(4)],
+                    // each 4 = (sample a, col 0), (a, col 1), (b, col 0), (b, col 1)
+                    auto ld8 = [&](int c, float (&d)[16]) {
+                        tmem_ld16x256_x1(t_v + c, d);
+                        tmem_ld16x256_x1(t_x + c, d + 4);
+                        tmem_ld16x256_x1(t_y + c, d + 8);
+                        tmem_ld16x256_x1(t_z + c, d + 12);
+                    };
+                    auto group = [&](int c, const float (&d)[16], auto skip_tag) {
+                        constexpr bool kSkipIn = decltype(skip_tag)::value;
+                        const float2 b = *reinterpret_cast<const float2*>(bias + c + fc);
+                        float hv[4], xv[4], yv[4], zv[4];
 #pragma unroll
-                        for (int g8 = 0; g8 < 2; ++g8) {
-                            const float2 b = *reinterpret_cast<const float2*>(bias + c0 + 8 * g8 + fc);
-                            float hv[4], xv[4], yv[4], zv[4];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int k = 4 * g8 + e;
-                                float h, sg;
-                                softplus_slope_tanh(v[k] + ((e & 1) ? b.y : b.x), half_beta, inv_beta, h, sg);
-                                sg *= sc;
-                                hv[e] = h * sc;
-                                xv[e] = sg * x[k];
-                                yv[e] = sg * y[k];
-                                zv[e] = sg * z[k];
+                        for (int e = 0; e < 4; ++e) {
+                            float h, sg;
+                            softplus_slope_tanh(d[e] + ((e & 1) ? b.y : b.x), half_beta, inv_beta, h, sg);
+                            if constexpr (kSkipIn) {
+                                sg *= kInvSqrt2;
+                                h *= kInvSqrt2;
                             }
-                            const uint32_t co = (uint32_t)((c0 + 8 * g8) >> 3) * 128u;
-                            stmatrix4(row0 + co, pack2<F16>(hv[0], hv[1]), pack2<F16>(hv[2], hv[3]),
-                                      pack2<F16>(xv[0], xv[1]), pack2<F16>(xv[2], xv[3]));
-                            stmatrix4(row1 + co, pack2<F16>(yv[0], yv[1]), pack2<F16>(yv[2], yv[3]),
-                                      pack2<F16>(zv[0], zv[1]), pack2<F16>(zv[2], zv[3]));
+                            hv[e] = h;
+                            xv[e] = sg * d[4 + e];
+                            yv[e] = sg * d[8 + e];
+                            zv[e] = sg * d[12 + e];
                         }
-                    }
+                        const uint32_t co = (uint32_t)(c >> 3) * 128u;
+                        stmatrix4(row0 + co, pack2<F16>(hv[0], hv[1]), pack2<F16>(hv[2], hv[3]),
+                                  pack2<F16>(xv[0], xv[1]), pack2<F16>(xv[2], xv[3]));
+                        stmatrix4(row1 + co, pack2<F16>(yv[0], yv[1]), pack2<F16>(yv[2], yv[3]),
+                                  pack2<F16>(zv[0], zv[1]), pack2<F16>(zv[2], zv[3]));
+                    };
+                    auto body = [&](auto skip_tag) {
+                        if (c_full <= c_lo) return;
+                        float bufA[16], bufB[16];
+                        ld8(c_lo, bufA);
+                        tmem_wait_ld16(bufA);
+                        for (int c0 = c_lo; c0 < c_full; c0 += 16) {
+                            ld8(c0 + 8, bufB);
+                            group(c0, bufA, skip_tag);
+                            tmem_wait_ld16(bufB);
+                            const bool more = c0 + 16 < c_full;
+                            if (more) ld8(c0 + 16, bufA);
+                            group(c0 + 8, bufB, skip_tag);
+                            if (more) tmem_wait_ld16(bufA);
+                        }
+                    };
+                    if (sc != 1.0f) body(std::integral_constant<bool, true>{});
+                    else body(std::integral_constant<bool, false>{});
                     // tail: hidden units < N, then gamma(x~) / sqrt(2) (the skip input), then zeros
                     const float* sxa = s_x + (16 * q + fs) * 8;
                     const float* sxb = sxa + 8 * 8;

@@ -174,6 +174,21 @@ def tsdf_ray_bounds_noalloc(grid: "Grid", inside_mask, ray_o, ray_d, params: tsd
                                          _p(status), _stream()))
 
 
+def tsdf_recovery_bounds(grid: "Grid", ray_o, ray_d, params: tsdfs_bounds_params, tau, wsum, status, t_n2, t_f2, n2,
+                         offsets2, status2, workspace):
+    n = ray_o.shape[0]
+    _check(lib().tsdf_recovery_bounds(C.byref(grid.c), _p(ray_o), _p(ray_d), C.c_int64(n), C.byref(params),
+                                      C.c_float(tau), _p(wsum), _p(status), _p(t_n2), _p(t_f2), _p(n2), _p(offsets2),
+                                      _p(status2), _p(workspace),
+                                      C.c_size_t(workspace.numel() if workspace is not None else 0), _stream()))
+
+
+def tsdf_recovery_merge(status2, rgb2, depth2, wsum2, normal2, rgb, depth, wsum, normal):
+    n = status2.shape[0]
+    _check(lib().tsdf_recovery_merge(C.c_int64(n), _p(status2), _p(rgb2), _p(depth2), _p(wsum2), _p(normal2), _p(rgb),
+                                     _p(depth), _p(wsum), _p(normal), _stream()))
+
+
 def tsdfs_render_workspace_size(mlp: "Mlp", n_rays: int, max_samples: int) -> int:
     return int(lib().tsdfs_render_workspace_size(C.byref(mlp.c), C.c_int64(n_rays), C.c_int64(max_samples)))
 
@@ -331,6 +346,25 @@ class Renderer:
         render_rays(self.mlp, rays_o, rays_d, b.t_n, b.t_f, b.offsets, b.status, self.max_samples, o.rgb, o.depth,
                     o.wsum, o.normal, o.eik, self.workspace)
         return o
+
+
+class Recovery:
+    """The recovery pass of Sec. 4.5 for a batch of rays: rays whose weight sum
+    after ``Renderer.render`` stays below ``tau`` are rendered again over the
+    whole [t0, t_end] with ``n_fallback`` samples, and merged into ``out``."""
+
+    def __init__(self, mlp: Mlp, n, n_fallback=96, device="cuda"):
+        self.bounds = Bounds(n, device)
+        self.render2 = Renderer(mlp, n, max(n * n_fallback, 1), device)
+
+    def apply(self, grid: Grid, rays_o, rays_d, bp, tau, out: RenderOut, first: Bounds):
+        p = bp if isinstance(bp, tsdfs_bounds_params) else bounds_params(bp)
+        b = self.bounds
+        tsdf_recovery_bounds(grid, rays_o, rays_d, p, tau, out.wsum, first.status, b.t_n, b.t_f, b.n, b.offsets,
+                             b.status, b.workspace)
+        o2 = self.render2.render(rays_o, rays_d, b)
+        tsdf_recovery_merge(b.status, o2.rgb, o2.depth, o2.wsum, o2.normal, out.rgb, out.depth, out.wsum, out.normal)
+        return out
 
 
 class HierRenderer:

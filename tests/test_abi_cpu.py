@@ -89,3 +89,22 @@ def test_invalid_arguments_fail_on_host(L):
     m.precision = 0
     assert L.render_rays(C.byref(m), *([None] * 6), C.c_int64(0), C.c_int64(0), *([None] * 5), None, C.c_size_t(0),
                          None) == T.TSDFS_OK
+
+
+def test_recovery_arguments_fail_on_host(L):
+    g = _grid_struct()
+    p = T.tsdfs_bounds_params(0.1, 0.0, 10.0, 0.1, 2, 15, 32, 96)
+    v = C.c_void_p(8)
+    args = lambda tau, ws: (C.byref(g), v, v, C.c_int64(100), C.byref(p), C.c_float(tau), v, v, v, v, v, v, v, v,
+                            C.c_size_t(ws), None)
+    assert L.tsdf_recovery_bounds(None, v, v, C.c_int64(1), C.byref(p), C.c_float(0.9), *([v] * 8),
+                                  C.c_size_t(1 << 20), None) == T.TSDFS_E_INVALID
+    assert L.tsdf_recovery_bounds(*args(float("nan"), 1 << 20)) == T.TSDFS_E_INVALID
+    assert "tau" in T.tsdfs_last_error()
+    assert L.tsdf_recovery_bounds(*args(0.95, 1)) == T.TSDFS_E_WORKSPACE
+    p.n_fallback = 5000
+    assert L.tsdf_recovery_bounds(*args(0.95, 1 << 20)) == T.TSDFS_E_INVALID
+    # merge: normal and normal2 both or neither; zero rays succeed without the device
+    assert L.tsdf_recovery_merge(C.c_int64(4), v, v, v, v, None, v, v, v, v, None) == T.TSDFS_E_INVALID
+    assert L.tsdf_recovery_merge(C.c_int64(-1), v, v, v, v, v, v, v, v, v, None) == T.TSDFS_E_INVALID
+    assert L.tsdf_recovery_merge(C.c_int64(0), None, None, None, None, None, None, None, None, None, None) == T.TSDFS_OK
