@@ -210,6 +210,10 @@ __device__ __forceinline__ void tmem_wait_ld16(float (&d)[16]) {
                  :
                  : "memory");
 }
+// two 8x8 16-bit matrices: threads 0-15 give the row addresses (row i % 8 of matrix i / 8)
+__device__ __forceinline__ void stmatrix2(uint32_t addr, uint32_t r0, uint32_t r1) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x2.shared.b16 [%0], {%1,%2};" ::"r"(addr), "r"(r0), "r"(r1) : "memory");
+}
 // four 8x8 16-bit matrices to shared memory: thread i supplies the address of row
 // i % 8 of matrix i / 8; register j holds row t/4, columns 2(t%4), 2(t%4)+1 of matrix j
 __device__ __forceinline__ void stmatrix4(uint32_t addr, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
@@ -775,20 +779,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                         }
                     }
                 } else if (!last) {
-                    // ---- hidden colour layer (ReLU), value rows only ----
+                    // ---- hidden colour layer (ReLU), value rows only: a 16x256b fragment at
+                    // lane 32q holds value rows only (samples 16q + fs and 16q + 8 + fs) ----
                     const int Kn = TA::layer(L + 1).Kp;
+                    const uint32_t row0 = smem_u32(A0) + a_off(32 * q + (lane & 15), 0, Kn);
                     for (int c0 = half_lo(Kn, hf); c0 < half_hi(Kn, hf); c0 += 16) {
-                        float x0[16], o[16];
-                        tmem_ld16(tmem + lane_addr + c0, x0);
-                        tmem_wait_ld();
+                        float v[8];
+                        if (c0 < ly.Np) {
+                            tmem_ld16x256_x2(t_v + c0, v);
+                            tmem_wait_ld();
+                        } else {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int col = c0 + j;
-                            o[j] = col < ly.N ? fmaxf(x0[j] + bias[col < ly.N ? col : 0], 0.0f) : 0.0f;
+                            for (int e = 0; e < 8; ++e) v[e] = 0.0f;
                         }
-                        if (is_val) {
-                            st_row8<F16>(A0, r, c0, Kn, o);
-                            st_row8<F16>(A0, r, c0 + 8, Kn, o + 8);
+#pragma unroll
+                        for (int g8 = 0; g8 < 2; ++g8) {
+                            float o[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int col = c0 + 8 * g8 + fc + (e & 1);
+                                o[e] = col < ly.N ? fmaxf(v[4 * g8 + e] + bias[col], 0.0f) : 0.0f;
+                            }
+                            stmatrix2(row0 + (uint32_t)((c0 + 8 * g8) >> 3) * 128u, pack2<F16>(o[0], o[1]),
+                                      pack2<F16>(o[2], o[3]));
                         }
                     }
                 } else if (hf == 0) {
