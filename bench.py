@@ -36,6 +36,8 @@ WORKLOADS = {
     "view": "room 8x6x3m (20 boxes, 4 plates), 256^3 TSDF from 100x640x480 depth maps, 640x480 novel views",
     "panorama": "room 8x6x3m (20 boxes, 4 plates), 256^3 TSDF from 100x640x480 depth maps, 1024x512 equirect "
                 "panoramas from 4 in-room centres (ragged 1-64 samples, fallback 96)",
+    "large": "20x20x4m floor (4 rooms, 200 boxes, 40 plates), 512^3 fp16 TSDF from 300x1280x960 depth maps, "
+             "batch of 8 2048x1024 equirect panoramas (one panorama per step)",
 }
 WORKLOAD = WORKLOADS["view"]
 ALGO_FLOP_PER_SAMPLE = 2.25e6   # SDF fwd + minimal reverse-mode grad + colour, 8x256 / 4x256 networks
@@ -230,6 +232,45 @@ def build_scene(device, mlp, source="network", n_rays=0, workload="view"):
     return wl, grid, grid_an, mask, rays, fusion, depth
 
 
+def build_scene_large(device, n_rays=0):
+    """The large configuration: 300 analytic 1280x960 depth maps fused into the 512^3
+    fp16 grid (timed, three times), 8 panoramas of 2048x1024 from seeded centres."""
+    import torch
+    from paper_2311_17878_gb300 import synth
+    from paper_2311_17878_gb300 import tsdfs as T
+    t_gen = time.perf_counter()
+    wl = synth.large_workload_torch(device=device)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    grid = T.Grid(wl.grid, device=device).init()
+    depth = wl.views.depth.contiguous()
+    K = torch.tensor(wl.views.K, device=device)
+    P = torch.tensor(wl.views.c2w, device=device)
+    fuse_ms = []
+    for _ in range(3):
+        grid.init()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        grid.integrate(depth, K, P)
+        e1.record()
+        torch.cuda.synchronize()
+        fuse_ms.append(e0.elapsed_time(e1))
+    mask = grid.inside_mask(wl.bounds.nb_radius)
+    rays = []
+    for c in synth.large_panorama_centres(N_VIEWS_TIMED):
+        o, d = synth.room_panorama_rays(2048, 1024, center=tuple(c))
+        if n_rays:
+            idx = np.sort(synth.sub_sample(len(o), n_rays, seed=60 + len(rays)))
+            o, d = np.ascontiguousarray(o[idx]), np.ascontiguousarray(d[idx])
+        rays.append((torch.tensor(o, device=device), torch.tensor(d, device=device), o, d))
+    nvox = wl.grid.nx * wl.grid.ny * wl.grid.nz
+    fusion = {"workload": "300 analytic 1280x960 depth maps into 512^3 fp16", "ms": min(fuse_ms),
+              "voxels_per_s": nvox / (min(fuse_ms) / 1e3),
+              "voxel_views_per_s": nvox * depth.shape[0] / (min(fuse_ms) / 1e3),
+              "grid_for_render": f"fused from the analytic depth maps (generated in {t_gen:.1f} s)"}
+    return wl, grid, grid, mask, rays, fusion, depth
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_2311_17878_gb300 import build as B
@@ -244,11 +285,23 @@ def run_ours(args, ws, rank, local):
     PREC = {"f16": T.TSDFS_PREC_F16, "bf16": T.TSDFS_PREC_BF16, "f32": T.TSDFS_PREC_F32}
     mlp = T.Mlp(spec, PREC[prec], device=dev)
     mlp_depth = mlp if prec != "f32" else T.Mlp(spec, T.TSDFS_PREC_F16, device=dev)
-    wl, grid, grid_an, mask, rays, fusion, depth = build_scene(dev, mlp_depth, args.grid_source, args.rays,
-                                                               args.workload)
+    if args.workload == "large":
+        wl, grid, grid_an, mask, rays, fusion, depth = build_scene_large(dev, args.rays)
+    else:
+        wl, grid, grid_an, mask, rays, fusion, depth = build_scene(dev, mlp_depth, args.grid_source, args.rays,
+                                                                   args.workload)
     bp = synth.BoundsParams(**{**wl.bounds.__dict__, "d_s": args.ds_vox * wl.grid.voxel_size})
     n = rays[0][0].shape[0]
     max_samples = n * max(bp.n_max, bp.n_fallback)
+    if args.workload == "large":
+        # size the sample workspace from the batch's own counts (n x 96 would be 9.7 GB of records)
+        bcount = T.Bounds(n, device=dev)
+        tot = 0
+        for i in range(N_VIEWS_TIMED):
+            bcount.compute(grid, rays[i][0], rays[i][1], bp, mask)
+            tot = max(tot, int(bcount.offsets[-1].item()))
+        max_samples = tot if args.recovery_tau is None else n * max(bp.n_max, bp.n_fallback)
+        del bcount
     bounds = T.Bounds(n, device=dev)
     rend = T.Renderer(mlp, n, max_samples, device=dev)
     rec = T.Recovery(mlp, n, bp.n_fallback, device=dev) if args.recovery_tau is not None else None
@@ -354,19 +407,23 @@ def run_ours(args, ws, rank, local):
     e2e = None if lean else run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev)
     # hierarchical comparator on the same views
     hier = {} if lean else run_hier(args, mlp, grid, rays, bp, n, dev, flush)
-    quality = None if (args.no_quality or main_only or rank != 0) else run_quality(
+    # the room networks are not fitted to the large floor, so its images have no quality to score
+    quality = None if (args.no_quality or main_only or rank != 0 or args.workload == "large") else run_quality(
         spec, wl, grid, bounds, rend, hier.get("renderer"), rays, bp, mask, args.sweep, rec, args.recovery_tau)
     cpu = run_cpu_baseline(wl, grid, rays, bp, spec) if (rank == 0 and ws == 1 and not lean) else None
-    train = run_train(spec, wl, grid, mask, dev) if (rank == 0 and not lean) else None
+    train = run_train(spec, wl, grid, mask, dev, n_rays=65536 if args.workload == "large" else 8192) \
+        if (rank == 0 and not lean) else None
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": prec, "data": "synthetic (seeded room scene, fitted networks)",
         "config": {"workload": WORKLOAD, "rays_per_step": n, "views": N_VIEWS_TIMED,
-                   "samples_per_step": samples_timed / args.steps, "grid": "256^3 f32 + uint8",
+                   "samples_per_step": samples_timed / args.steps,
+                   "grid": f"{wl.grid.nx}^3 {wl.grid.dtype} + uint8",
                    "d_s_vox": args.ds_vox, "fallback_frac_per_view": fallback_per_view,
-                   "grid_source": args.grid_source, "ray_subset": args.rays or None,
+                   "grid_source": "analytic" if args.workload == "large" else args.grid_source,
+                   "ray_subset": args.rays or None,
                    "cuda_graph": bool(graphs), "train_pitch_deg": synth.TRAIN_PITCH_DEG,
                    "recovery_tau": args.recovery_tau,
                    "networks": "SDF 8x256 PE6 skip4 + colour 4x256 PE4", "l2": "flushed between steps (256 MB write)",
@@ -561,7 +618,7 @@ def run_cpu_baseline(wl, grid, rays, bp, spec, seconds=10.0, chunk=2048):
     from oracle import cgrid
     from oracle import render as orr
     from paper_2311_17878_gb300 import synth
-    V = grid.V.cpu().numpy()
+    V = grid.V.view(torch.int16).cpu().numpy().view(np.uint16) if grid.V.dtype == torch.float16 else grid.V.cpu().numpy()
     n_view = rays[0][2].shape[0]
     order = synth.sub_sample(n_view, n_view, seed=32)
     net = orr.Net(spec)
@@ -583,6 +640,9 @@ def run_cpu_baseline(wl, grid, rays, bp, spec, seconds=10.0, chunk=2048):
 def run_reference(args, ws, rank):
     """The CPU oracle as the reference arm: each step renders a bounded sample of
     the same workload (ref_rays seeded rays of a held-out view)."""
+    if args.workload == "large":
+        return {"impl": "reference", "unavailable": "the oracle's fusion of 300 1280x960 maps into 512^3 runs for "
+                                                   "hours on the host cores; the reference arm covers view and panorama"}
     import torch
     if rank != 0:
         return None
@@ -628,7 +688,7 @@ def main():
     global WORKLOAD, N_VIEWS_TIMED
     args = parse()
     WORKLOAD = WORKLOADS[args.workload]
-    N_VIEWS_TIMED = 4 if args.workload == "panorama" else 10
+    N_VIEWS_TIMED = {"panorama": 4, "large": 8}.get(args.workload, 10)
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         ws = int(os.environ.get("WORLD_SIZE", "1"))

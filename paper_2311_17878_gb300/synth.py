@@ -636,16 +636,18 @@ def sdf_torch(scene, x):
     return torch.minimum(d_room, torch.amin(sb, 1))
 
 
-def analytic_tsdf_torch(scene, grid: GridSpec, device="cuda"):
-    """analytic_tsdf on a torch device (float32 tensor (nz, ny, nx))."""
+def analytic_tsdf_torch(scene, grid: GridSpec, device="cuda", dtype=None):
+    """analytic_tsdf on a torch device (float32 tensor (nz, ny, nx)); ``dtype`` is the
+    arithmetic type (float64 by default, float32 for the 512^3 grid)."""
     import torch
-    o = torch.tensor(grid.origin, dtype=torch.float64, device=device)
+    dt = torch.float64 if dtype is None else dtype
+    o = torch.tensor(grid.origin, dtype=dt, device=device)
     jj, ii = torch.meshgrid(torch.arange(grid.ny, device=device), torch.arange(grid.nx, device=device), indexing="ij")
     out = torch.empty((grid.nz, grid.ny, grid.nx), dtype=torch.float32, device=device)
     for k in range(grid.nz):
         x = torch.stack([o[0] + (ii + 0.5) * grid.voxel_size, o[1] + (jj + 0.5) * grid.voxel_size,
-                         torch.full(ii.shape, float(o[2] + (k + 0.5) * grid.voxel_size), dtype=torch.float64,
-                                    device=device)], -1).reshape(-1, 3).to(torch.float64)
+                         torch.full(ii.shape, float(o[2] + (k + 0.5) * grid.voxel_size), dtype=dt,
+                                    device=device)], -1).reshape(-1, 3).to(dt)
         out[k] = torch.clamp(sdf_torch(scene, x) / grid.trunc, -1.0, 1.0).reshape(grid.ny, grid.nx).to(torch.float32)
     return out
 
@@ -661,3 +663,69 @@ def room_workload_torch(device="cuda", n_views=100, width=640, height=480, grid_
     wl.views = Views(np.tile(np.array([fx, fy, width / 2.0, height / 2.0], np.float32), (V, 1)),
                      np.asarray(c2ws, np.float32).reshape(V, 12), depth, width, height)
     return wl
+
+
+# ----------------------------------------------------------------------------
+# large: 20 x 20 x 4 m multi-room floor, 512^3 fp16 grid, 300 views of 1280x960
+# ----------------------------------------------------------------------------
+def large_scene(seed=SEED_SCENE + 10):
+    """20x20x4 m floor split into four rooms by two 10 cm walls with 2 m doorways,
+    200 random boxes (0.2-1.5 m sides) and 40 thin (2 cm) partition plates."""
+    walls = [((-0.05, -10.0, 0.0), (0.05, -1.0, 4.0)), ((-0.05, 1.0, 0.0), (0.05, 10.0, 4.0)),
+             ((-10.0, -0.05, 0.0), (-1.0, 0.05, 4.0)), ((1.0, -0.05, 0.0), (10.0, 0.05, 4.0))]
+    return make_box_room(seed, (-10.0, -10.0, 0.0), (10.0, 10.0, 4.0), n_boxes=200, n_plates=40, interior_walls=walls)
+
+
+def large_grid(n=512) -> GridSpec:
+    vs = 20.48 / n
+    return GridSpec(n, n, n, (-10.24, -10.24, 2.0 - 10.24), vs, 4 * vs, dtype="f16")
+
+
+def large_bounds(grid: GridSpec) -> BoundsParams:
+    vs = grid.voxel_size
+    return BoundsParams(d_s=vs, t_near=0.05, t_far=30.0, step=2 * vs, n_max=64)
+
+
+def large_poses(n=300):
+    return sample_free_poses(large_scene(), np.random.default_rng(SEED_POSES + 10), n, pitch_deg=TRAIN_PITCH_DEG)
+
+
+def large_panorama_centres(n=8):
+    poses = sample_free_poses(large_scene(), np.random.default_rng(SEED_HELDOUT + 110), n)
+    return poses.reshape(n, 3, 4)[:, :, 3].copy()
+
+
+def render_depth_maps_torch_f32(scene, c2ws, fx, fy, cx, cy, width, height, noise_std=0.0, seed=SEED_NOISE,
+                                device="cuda", chunk=1 << 18):
+    """Depth maps of a box scene computed in float32 on a torch device, in ray chunks
+    (for view counts and sizes where the float64 path is too slow)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    u, v = torch.meshgrid(torch.arange(width, dtype=torch.float32, device=device) + 0.5,
+                          torch.arange(height, dtype=torch.float32, device=device) + 0.5, indexing="xy")
+    dc = torch.stack([(u - cx) / fx, (v - cy) / fy, torch.ones_like(u)], -1).reshape(-1, 3)
+    out = torch.empty((len(c2ws), height, width), dtype=torch.float32, device=device)
+    flat = out.view(len(c2ws), -1)
+    for i, c2w in enumerate(c2ws):
+        P = torch.tensor(np.asarray(c2w), dtype=torch.float32, device=device)
+        d = dc @ P[:, :3].T
+        d = d / torch.linalg.norm(d, dim=1, keepdim=True)
+        o = P[:, 3].expand_as(d)
+        for a in range(0, d.shape[0], chunk):
+            flat[i, a:a + chunk] = ray_range_torch(scene, o[a:a + chunk], d[a:a + chunk]).to(torch.float32)
+        if noise_std > 0:
+            flat[i] += torch.tensor(rng.normal(0.0, noise_std, flat.shape[1]), dtype=torch.float32, device=device)
+    return out
+
+
+def large_workload_torch(device="cuda", n_views=300, width=1280, height=960, noise_std=0.005):
+    """The large configuration with its depth maps rendered on a torch device."""
+    scene = large_scene()
+    grid = large_grid()
+    c2ws = large_poses(n_views)
+    fx = fy = 1000.0 * width / 1280.0
+    depth = render_depth_maps_torch_f32(scene, c2ws, fx, fy, width / 2.0, height / 2.0, width, height, noise_std,
+                                        device=device)
+    views = _views(c2ws, fx, fy, width / 2.0, height / 2.0, width, height, depth)
+    return Workload("large", grid, large_bounds(grid), views, scene)
+
