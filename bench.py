@@ -571,6 +571,25 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=Fal
             ort = orr.render_bounded(net, on, dn, tn, tf, cnt)["rgb"].numpy()
     p_gpu, p_or = orr.psnr(gpu_rgb, dense), orr.psnr(ort, dense)
     p_h = orr.psnr(hier_rgb, dense) if hier_rgb is not None else None
+    # geometry metrics on pixels where the dense reference sees a surface (Sec. 4 metrics:
+    # depth error, normal angle error; the Tab. 1 failure statistic; mean sample spacing)
+    hit = dd["wsum"].numpy() > 0.5
+
+    def geometry(depth, normal):
+        if depth is None or not hit.any():
+            return None
+        n_ref = dd["normal"].numpy()[hit]
+        n_got = normal[hit]
+        cosang = np.sum(n_ref * n_got, 1) / np.maximum(np.linalg.norm(n_ref, axis=1) * np.linalg.norm(n_got, axis=1),
+                                                        1e-12)
+        return {"depth_mae_m": float(np.mean(np.abs(depth[hit] - dd["depth"].numpy()[hit]))),
+                "normal_angle_deg": float(np.degrees(np.mean(np.arccos(np.clip(cosang, -1.0, 1.0)))))}
+    gstat = geometry(out.depth[idx_t].cpu().numpy(), out.normal[idx_t].cpu().numpy())
+    hstat = geometry(hout.depth[idx_t].cpu().numpy(), hout.normal[idx_t].cpu().numpy()) if hout is not None else None
+    bnd = (ob["status"] == 1) & hit
+    t_star = dd["depth"].numpy()
+    failed = bnd & ((t_star < tn) | (t_star > tf))
+    spacing = (tf - tn)[ob["status"] == 1] / np.maximum(cnt[ob["status"] == 1], 1)
     # D_s sweep (surface criterion of Alg. 1) on the same pixels: GPU bounds + render
     from paper_2311_17878_gb300 import tsdfs as T
     vs = wl.grid.voxel_size
@@ -607,6 +626,9 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=Fal
             "recovery": None if rec is None else {
                 "tau": tau, "recovered_frac": float((rec.bounds.status == 2).float().mean().item()),
                 "recovered_frac_oracle_pixels": float(np.mean(again))},
+            "geometry_tsdf_gpu": gstat, "geometry_hier96_gpu": hstat,
+            "tab1_failed_frac": float(failed.sum() / max(bnd.sum(), 1)),
+            "mean_sample_spacing_m": float(spacing.mean()) if spacing.size else None,
             "oracle_s": time.perf_counter() - t_q}
 
 

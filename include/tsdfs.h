@@ -47,6 +47,7 @@ typedef struct CUstream_st* tsdfs_stream_t; /* identical to cudaStream_t */
 #define TSDFS_DEV_SAMPLES_OVERFLOW 1u /* offsets[n_rays] exceeded max_samples   */
 #define TSDFS_DEV_MARCH_CAP 2u        /* a ray hit the voxel-step cap            */
 #define TSDFS_DEV_TIMEOUT 4u          /* a bounded wait in a pipelined kernel expired */
+#define TSDFS_DEV_NONFINITE 8u        /* a network parameter is NaN or infinite         */
 
 /* ---- TSDF grid (Sec. 3.2; Sec. A.1: V initialised to -1 = unseen, W to 0) -
  * tsdf holds s / D_T in [-1, 1] (normalised truncated signed distance), as
@@ -270,6 +271,12 @@ int render_rays_backward(const tsdfs_mlp* mlp, const float* ray_o, const float* 
  * 16-byte aligned).  Repeat after every parameter update.                    */
 size_t tsdfs_packed_size(int32_t arch);
 int tsdfs_pack_mlp(const tsdfs_mlp* mlp, void* packed, tsdfs_stream_t stream);
+
+/* ---- parameter check (failure detection; no counterpart in the paper) --------
+ * Scans sdf_w and rgb_w (device, fp32) and sets TSDFS_DEV_NONFINITE in the
+ * status word (tsdfs_sync_status) if any parameter is NaN or infinite;
+ * tsdfs_pack_mlp sets the same bit for the values it packs.  Nothing traps.  */
+int tsdfs_check_mlp(const tsdfs_mlp* mlp, tsdfs_stream_t stream);
 
 /* ---- kernel timing (instrumentation; no counterpart in the paper) ------------
  * tsdfs_profile(1) clears the record and starts timing: every kernel launch

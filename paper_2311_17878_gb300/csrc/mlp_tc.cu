@@ -1066,7 +1066,8 @@ int launch_tc_value(const tsdfs_mlp* m, const SampleSource& src, float* f_out, c
 
 // ---- pack fp32 [N][K] weights into the bf16 chunked core-matrix layout ----
 template <int ARCH, bool F16>
-__global__ void k_pack(const float* __restrict__ sdf_w, const float* __restrict__ rgb_w, uint16_t* __restrict__ out) {
+__global__ void k_pack(const float* __restrict__ sdf_w, const float* __restrict__ rgb_w, uint16_t* __restrict__ out,
+                       uint32_t* status) {
     using TA = TcArch<ARCH>;
     const int64_t total = TA::packed_bytes() / 2;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -1088,6 +1089,7 @@ __global__ void k_pack(const float* __restrict__ sdf_w, const float* __restrict_
         const int k = c * kKChunk + (core % (kc / 8)) * 8 + within % 8;
         const float* W = (ly.sdf ? sdf_w : rgb_w) + TA::param_offset(L);
         const float v = (n < ly.N && k < ly.K) ? W[(int64_t)n * ly.K + k] : 0.0f;
+        if (!isfinite(v)) set_status(status, TSDFS_DEV_NONFINITE);
         if constexpr (F16) {
             __half h = __float2half_rn(v);
             out[e] = *reinterpret_cast<uint16_t*>(&h);
@@ -1175,11 +1177,35 @@ extern "C" int tsdfs_pack_mlp(const tsdfs_mlp* m, void* packed, tsdfs_stream_t s
     uint16_t* out = static_cast<uint16_t*>(packed);
     const bool f16 = m->precision == TSDFS_PREC_F16;
     if (m->arch == TSDFS_ARCH_TINY) {
-        if (f16) k_pack<TSDFS_ARCH_TINY, true><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out);
-        else k_pack<TSDFS_ARCH_TINY, false><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out);
+        if (f16) k_pack<TSDFS_ARCH_TINY, true><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out, device_status_word());
+        else k_pack<TSDFS_ARCH_TINY, false><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out, device_status_word());
     } else {
-        if (f16) k_pack<TSDFS_ARCH_ROOM, true><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out);
-        else k_pack<TSDFS_ARCH_ROOM, false><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out);
+        if (f16) k_pack<TSDFS_ARCH_ROOM, true><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out, device_status_word());
+        else k_pack<TSDFS_ARCH_ROOM, false><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out, device_status_word());
     }
     return cuda_check(cudaGetLastError(), "tsdfs_pack_mlp launch");
+}
+
+namespace tsdfs {
+namespace {
+__global__ void k_check_finite(const float* __restrict__ w, int64_t n, uint32_t* status) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(__ldg(w + i))) {
+            set_status(status, TSDFS_DEV_NONFINITE);
+            return;
+        }
+}
+}  // namespace
+}  // namespace tsdfs
+
+extern "C" int tsdfs_check_mlp(const tsdfs_mlp* m, tsdfs_stream_t stream) {
+    if (!m || !m->sdf_w || !m->rgb_w) return fail(TSDFS_E_INVALID, "mlp and its weights must be non-NULL");
+    if (m->arch != TSDFS_ARCH_TINY && m->arch != TSDFS_ARCH_ROOM) return fail(TSDFS_E_INVALID, "unknown arch %d", m->arch);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t ns = m->arch == TSDFS_ARCH_TINY ? sdf_param_count<TSDFS_ARCH_TINY>() : sdf_param_count<TSDFS_ARCH_ROOM>();
+    const int64_t nr = m->arch == TSDFS_ARCH_TINY ? rgb_param_count<TSDFS_ARCH_TINY>() : rgb_param_count<TSDFS_ARCH_ROOM>();
+    ProfScope ps("check_mlp", st);
+    k_check_finite<<<grid_1d(ns, 256), 256, 0, st>>>(m->sdf_w, ns, device_status_word());
+    k_check_finite<<<grid_1d(nr, 256), 256, 0, st>>>(m->rgb_w, nr, device_status_word());
+    return cuda_check(cudaGetLastError(), "tsdfs_check_mlp launch");
 }

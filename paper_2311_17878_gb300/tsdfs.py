@@ -11,6 +11,7 @@ call raises.
 from __future__ import annotations
 
 import ctypes as C
+from dataclasses import dataclass
 import os
 import threading
 
@@ -27,13 +28,14 @@ TSDFS_F32, TSDFS_F16 = 0, 1
 TSDFS_MISS, TSDFS_BOUNDED, TSDFS_FALLBACK = 0, 1, 2
 TSDFS_ARCH_TINY, TSDFS_ARCH_ROOM = 0, 1
 TSDFS_PREC_F32, TSDFS_PREC_BF16, TSDFS_PREC_F16 = 0, 1, 2
-TSDFS_DEV_SAMPLES_OVERFLOW, TSDFS_DEV_MARCH_CAP, TSDFS_DEV_TIMEOUT = 1, 2, 4
+TSDFS_DEV_SAMPLES_OVERFLOW, TSDFS_DEV_MARCH_CAP, TSDFS_DEV_TIMEOUT, TSDFS_DEV_NONFINITE = 1, 2, 4, 8
 
 EXPORTS = ["tsdfs_last_error", "tsdfs_sync_status", "tsdfs_grid_init", "tsdf_integrate", "tsdfs_inside_mask_words",
            "tsdfs_inside_mask", "tsdfs_bounds_workspace_size", "tsdf_ray_bounds", "tsdfs_render_workspace_size",
            "render_rays", "tsdfs_hier_workspace_size", "render_rays_hier96", "tsdfs_backward_workspace_size",
            "render_rays_backward", "tsdfs_packed_size", "tsdfs_pack_mlp", "tsdfs_sdf_param_count",
-           "tsdfs_rgb_param_count"]
+           "tsdfs_rgb_param_count", "tsdf_ray_bounds_noalloc", "tsdf_ray_bounds_noalloc_max_rays",
+           "tsdf_recovery_bounds", "tsdf_recovery_merge", "tsdfs_check_mlp", "tsdfs_profile", "tsdfs_profile_read"]
 
 
 class TsdfsError(RuntimeError):
@@ -233,6 +235,10 @@ def tsdfs_pack_mlp(mlp: "Mlp", packed):
     _check(lib().tsdfs_pack_mlp(C.byref(mlp.c), _p(packed), _stream()))
 
 
+def tsdfs_check_mlp(mlp: "Mlp"):
+    _check(lib().tsdfs_check_mlp(C.byref(mlp.c), _stream()))
+
+
 def tsdfs_sdf_param_count(arch: int) -> int:
     return int(lib().tsdfs_sdf_param_count(C.c_int32(arch)))
 
@@ -246,6 +252,18 @@ def tsdfs_rgb_param_count(arch: int) -> int:
 # ----------------------------------------------------------------------------
 def _bytes(n, device):
     return torch.empty(max(int(n), 1), dtype=torch.uint8, device=device)
+
+
+@dataclass
+class GridSpecLike:
+    """Grid geometry (the fields of ``tsdfs_grid`` besides the arrays)."""
+    nx: int
+    ny: int
+    nz: int
+    origin: tuple
+    voxel_size: float
+    trunc: float
+    dtype: str = "f32"
 
 
 class Grid:
@@ -270,6 +288,21 @@ class Grid:
     def integrate(self, depth, K, c2w):
         tsdf_integrate(self, depth, K, c2w)
         return self
+
+    def save(self, path):
+        """Checkpoint of the fused volume: geometry header plus V and W (V in its storage
+        type), so later sessions render novel views without fusing again."""
+        sp = self.spec
+        header = np.array([sp.nx, sp.ny, sp.nz, *sp.origin, sp.voxel_size, sp.trunc], np.float64)
+        np.savez(path, header=header, dtype=np.array(sp.dtype), V=self.V.cpu().numpy(), W=self.W.cpu().numpy())
+
+    @classmethod
+    def load(cls, path, device="cuda"):
+        z = np.load(path)
+        h = z["header"]
+        spec = GridSpecLike(int(h[0]), int(h[1]), int(h[2]), (float(h[3]), float(h[4]), float(h[5])), float(h[6]),
+                            float(h[7]), str(z["dtype"]))
+        return cls(spec, device=device, V=torch.as_tensor(z["V"]).to(device), W=torch.as_tensor(z["W"]).to(device))
 
     def inside_mask(self, nb_radius):
         bits = torch.empty(tsdfs_inside_mask_words(self), dtype=torch.int32, device=self.V.device)

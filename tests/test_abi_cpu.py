@@ -7,6 +7,7 @@ import re
 
 import numpy as np
 import pytest
+import torch
 
 from paper_2311_17878_gb300 import build, synth
 from paper_2311_17878_gb300 import tsdfs as T
@@ -108,3 +109,18 @@ def test_recovery_arguments_fail_on_host(L):
     assert L.tsdf_recovery_merge(C.c_int64(4), v, v, v, v, None, v, v, v, v, None) == T.TSDFS_E_INVALID
     assert L.tsdf_recovery_merge(C.c_int64(-1), v, v, v, v, v, v, v, v, v, None) == T.TSDFS_E_INVALID
     assert L.tsdf_recovery_merge(C.c_int64(0), None, None, None, None, None, None, None, None, None, None) == T.TSDFS_OK
+
+
+def test_grid_checkpoint_roundtrip(tmp_path):
+    from paper_2311_17878_gb300 import synth
+    for dtype, tdt in (("f32", torch.float32), ("f16", torch.float16)):
+        spec = synth.GridSpec(7, 5, 3, (-0.5, 0.25, 1.0), 0.125, 0.375, dtype)
+        g = T.Grid(spec, device="cpu", V=torch.linspace(-1, 1, 105).reshape(3, 5, 7).to(tdt),
+                   W=torch.arange(105, dtype=torch.uint8).reshape(3, 5, 7))
+        path = tmp_path / f"grid_{dtype}.npz"
+        g.save(path)
+        h = T.Grid.load(path, device="cpu")
+        assert (h.spec.nx, h.spec.ny, h.spec.nz, h.spec.dtype) == (7, 5, 3, dtype)
+        assert h.spec.origin == spec.origin and h.spec.voxel_size == spec.voxel_size and h.spec.trunc == spec.trunc
+        assert torch.equal(h.V, g.V) and torch.equal(h.W, g.W) and h.V.dtype == tdt
+        assert h.c.nx == 7 and h.c.dtype == (T.TSDFS_F16 if dtype == "f16" else T.TSDFS_F32)
