@@ -376,6 +376,8 @@ def run_ours(args, ws, rank, local):
     import ctypes as C
     ms_k, n_k = C.c_double(0), C.c_int64(0)
     T.lib().tsdfs_profile_read(mlp_name.encode(), C.byref(ms_k), C.byref(n_k))
+    ms_b, n_b = C.c_double(0), C.c_int64(0)
+    T.lib().tsdfs_profile_read(b"ray_bounds", C.byref(ms_b), C.byref(n_b))
     ms_all, n_all = C.c_double(0), C.c_int64(0)
     T.lib().tsdfs_profile_read(b"", C.byref(ms_all), C.byref(n_all))
     T.lib().tsdfs_profile(0)
@@ -429,11 +431,33 @@ def run_ours(args, ws, rank, local):
                    "networks": "SDF 8x256 PE6 skip4 + colour 4x256 PE4", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}, rays independent", "wall_s": t_wall},
         "e2e": e2e, "gpu_launches": int(n_all.value), "roofline": roof, "kernel_time": kernel_share,
+        "roofline_march": march_roofline(wl, grid, rays, bp, ms_b.value / max(n_b.value, 1), hbm, peak_src)
+        if rank == 0 else None,
         "comparator": {k: v for k, v in hier.items() if k != "renderer"},
         "fusion": fusion, "train_step": train,
         "quality": quality, "cpu_baseline": cpu, "clocks": clocks,
     }
     return line
+
+
+def march_roofline(wl, grid, rays, bp, ms_per_launch, hbm, peak_src, n_sample=4096):
+    """Roofline line of the ray march (Alg. 1, k_ray_bounds): every tested voxel reads one
+    32-bit word (its value in the near phase, its inside-mask word in the far phase), plus
+    24 B of ray in and 17 B of bounds out per ray.  The voxel counts come from the oracle's
+    walk of a seeded sample of image 0 on the same grid."""
+    import torch
+    from oracle import cgrid
+    from paper_2311_17878_gb300 import synth
+    V = grid.V.view(torch.int16).cpu().numpy().view(np.uint16) if grid.V.dtype == torch.float16 else grid.V.cpu().numpy()
+    o, d = rays[0][2], rays[0][3]
+    idx = synth.sub_sample(len(o), min(n_sample, len(o)), seed=33)
+    st = cgrid.ray_bounds(wl.grid, V, o[idx], d[idx], bp, "f32")["steps"]
+    bytes_per_ray = 4.0 * float(np.mean(st)) + 41.0
+    achieved = bytes_per_ray * len(o) / (ms_per_launch / 1e3) / 1e9 if ms_per_launch > 0 else 0.0
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "kernel": "ray_bounds", "voxels_per_ray": float(np.mean(st)),
+            "bytes_per_ray": bytes_per_ray, "ms_per_launch": ms_per_launch,
+            "peak_kind": f"HBM copy ({peak_src}); the grid is L2-resident, so this is a floor on the fraction"}
 
 
 def run_train(spec, wl, grid, mask, dev, n_rays=8192, iters=5):
