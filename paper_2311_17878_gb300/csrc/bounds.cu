@@ -59,8 +59,14 @@ __device__ __forceinline__ bool dda_next(Dda& s, const GridDev& g, const float o
     if (ty < tm) { a = 1; tm = ty; }
     if (tz < tm) { a = 2; tm = tz; }
     s.t = tm;
-    s.X[a] += s.step[a];
-    return s.X[a] >= 0 && s.X[a] < g.n[a];
+    // the axis is a run-time value: update the three components by selection, so the
+    // walk state stays in registers
+    s.X[0] += a == 0 ? s.step[0] : 0;
+    s.X[1] += a == 1 ? s.step[1] : 0;
+    s.X[2] += a == 2 ? s.step[2] : 0;
+    const int xa = a == 0 ? s.X[0] : (a == 1 ? s.X[1] : s.X[2]);
+    const int na = a == 0 ? g.n[0] : (a == 1 ? g.n[1] : g.n[2]);
+    return xa >= 0 && xa < na;
 }
 
 __device__ __forceinline__ float trilinear(const GridDev& g, const float p[3]) {
@@ -175,15 +181,44 @@ __global__ void __launch_bounds__(kBoundsBlock) k_ray_bounds(GridDev g, const ui
             s.X[a] = gg >= 0.0f ? (gg > (float)(g.n[a] - 1) ? g.n[a] - 1 : (int)gg) : 0;
         }
         // ---- near phase: first voxel with V(centre) <= D_s ----
+        // The walk does not depend on the values: the next kAhead voxels are stepped and
+        // their values requested before the current one is tested, so the loads are in
+        // flight together; the voxels, their order and every test are unchanged.
+        constexpr int kAhead = 4;
+        Dda wq[kAhead];
+        float qv[kAhead];
+        bool qok[kAhead];   // the loop condition of that step: still in the grid, t < t_end
+        bool live = true;   // the walk has not left the grid
+        wq[0] = s;
+        qok[0] = s.t < t_end;
+        qv[0] = gval(g, s.X[0], s.X[1], s.X[2]);
+#pragma unroll
+        for (int i = 1; i < kAhead; ++i) {
+            wq[i] = wq[i - 1];
+            live = live && dda_next(wq[i], g, o);
+            qok[i] = live && wq[i].t < t_end;
+            qv[i] = live ? gval(g, wq[i].X[0], wq[i].X[1], wq[i].X[2]) : 0.0f;
+        }
         bool found = false, in_grid = true;
         float t_before = t0;
         int steps = 0;
-        while (in_grid && s.t < t_end) {
+        while (qok[0]) {
             if (++steps > max_steps) { set_status(dev_status, TSDFS_DEV_MARCH_CAP); in_grid = false; break; }
-            if (gval(g, s.X[0], s.X[1], s.X[2]) <= ds_norm) { found = true; break; }
-            t_before = s.t;
-            in_grid = dda_next(s, g, o);
+            if (qv[0] <= ds_norm) { found = true; break; }
+            t_before = wq[0].t;
+            Dda nx = wq[kAhead - 1];
+#pragma unroll
+            for (int i = 0; i + 1 < kAhead; ++i) {
+                wq[i] = wq[i + 1];
+                qv[i] = qv[i + 1];
+                qok[i] = qok[i + 1];
+            }
+            live = live && dda_next(nx, g, o);
+            wq[kAhead - 1] = nx;
+            qok[kAhead - 1] = live && nx.t < t_end;
+            qv[kAhead - 1] = live ? gval(g, nx.X[0], nx.X[1], nx.X[2]) : 0.0f;
         }
+        s = wq[0];
         if (!found) {
             t_n_out[r] = t0; t_f_out[r] = t_end; n_out[r] = p.n_fallback; status_out[r] = TSDFS_FALLBACK;
             if (t_zero_out) t_zero_out[r] = kNaN;
