@@ -230,3 +230,45 @@ def test_bounds_zero_rays_and_all_miss():
     d = np.tile(np.array([[0.0, 0.0, 1.0]], np.float32), (10000, 1))
     got = run_bounds(wl.grid, V, o, d, wl.bounds, False)
     assert np.all(got["status"] == 0) and np.all(got["n"] == 0) and got["offsets"][-1] == 0
+
+
+def _degenerate_rays():
+    """Rays the voxel walk treats specially: axis-aligned in both senses (zero
+    direction components), exact diagonals, origins on voxel boundaries and grid
+    faces, origins inside the sphere, rays grazing the grid box, rays that miss."""
+    vs = 1.0 / 64
+    o, d = [], []
+    for a in range(3):
+        for sgn in (1.0, -1.0):
+            for off in (0.0, 0.5 * vs, vs, 0.123, -0.31):
+                p = np.array([off, -off, 0.25 * off])
+                p[a] = -sgn * 0.9
+                v = np.zeros(3)
+                v[a] = sgn
+                o.append(p); d.append(v)
+    for v in ([1, 1, 1], [1, -1, 1], [-1, -1, -1], [1, 1, 0], [0, 1, -1]):
+        v = np.asarray(v, np.float64)
+        v /= np.linalg.norm(v)
+        for p in ([-0.8, -0.8, -0.8], [0.0, 0.0, 0.0], [0.1, -0.2, 0.05], [-0.5, -0.5, -0.5], [8 * vs, 4 * vs, 0.0]):
+            o.append(np.asarray(p, np.float64) - 0.0 * v); d.append(v)
+    # grazing the box edges and faces, and parallel to a face just outside it
+    for p, v in (([-0.9, 0.5, 0.0], [1, 0, 0]), ([-0.9, 0.5 - 1e-7, 0.5 - 1e-7], [1, 0, 0]),
+                 ([-0.9, 0.5000001, 0.0], [1, 0, 0]), ([0.5, -0.9, 0.5], [0, 1, 0]),
+                 ([-0.9, -0.9, 0.0], [1, 1e-7, 0]), ([0.0, 0.0, 0.49], [0, 0, 1]), ([0.0, 0.0, 0.0], [0, 0, 1])):
+        v = np.asarray(v, np.float64)
+        o.append(np.asarray(p, np.float64)); d.append(v / np.linalg.norm(v))
+    return np.asarray(o, np.float32), np.asarray(d, np.float32)
+
+
+@pytest.mark.parametrize("use_mask", [False, True])
+def test_degenerate_rays_bit_exact(use_mask):
+    wl = synth.tiny_workload()
+    V, _ = cgrid.integrate_projective(wl.grid, wl.views, "f32")
+    o, d = _degenerate_rays()
+    for bp in (wl.bounds, synth.BoundsParams(**{**wl.bounds.__dict__, "t_near": 0.3})):
+        ref = cgrid.ray_bounds(wl.grid, V, o, d, bp, "f32")
+        got = run_bounds(wl.grid, V, o, d, bp, use_mask)
+        assert_bounds_equal(got, ref)
+        assert np.array_equal(got["offsets"], np.concatenate([[0], np.cumsum(ref["n"])]).astype(np.int32))
+    assert set(np.unique(ref["status"])) >= {0, 1}
+    check_status_clean()

@@ -240,3 +240,24 @@ def test_bf16_hier96_runs_and_tracks_f32():
         outs.append(o.rgb.cpu().numpy())
     assert np.max(np.abs(outs[0] - outs[1])) < 1e-2
     assert np.max(np.abs(outs[0] - outs[2])) < 5e-3
+
+
+@pytest.mark.parametrize("precision", [T.TSDFS_PREC_F32, T.TSDFS_PREC_F16])
+def test_degenerate_rays_render_matches_oracle(precision):
+    """Axis-aligned, diagonal, inside-the-sphere and grazing rays (the bounds
+    tests' set), rendered through the bounds the oracle computes."""
+    from test_gpu_fusion_bounds import _degenerate_rays
+    wl = synth.tiny_workload()
+    V, _ = cgrid.integrate_projective(wl.grid, wl.views, "f32")
+    o, d = _degenerate_rays()
+    b = cgrid.ray_bounds(wl.grid, V, o, d, wl.bounds, "f32")
+    spec = synth.scene_mlp("tiny")
+    got = gpu_render(spec, o, d, b, precision=precision)
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == 0, bits
+    ref, _ = oracle_render(spec, o, d, b)
+    if precision == T.TSDFS_PREC_F32:
+        compare(got, ref)
+    else:
+        er, ed = _errors(got, ref)
+        assert er.max() < RGB_ABS and (ed.size == 0 or ed.max() < 2e-3)
