@@ -479,65 +479,71 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
         constexpr float kInvSqrt2 = 0.70710678118654752f;
         uint32_t lc = 0, tab_ph = 0;
         bool ok = true;
-        for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-            // ---- per-tile sample table: epilogue thread et < 64 looks up sample et ----
-            const int et = threadIdx.x;
-            if (et < kTileS) {
-                const int64_t g = tile * kTileS + et;
-                float t = 0.0f, dl = 0.0f, xs[3] = {0.0f, 0.0f, 0.0f}, ds[3] = {0.0f, 0.0f, 0.0f};
-                if (g < total) {
-                    int64_t ray;
-                    if (p.src.mode == kUniform) {
-                        ray = p.src.sample_ray ? (int64_t)__ldg(p.src.sample_ray + g) : find_ray(p.src.offsets, p.src.n_rays, g);
-                        const int32_t o0 = __ldg(p.src.offsets + ray), o1 = __ldg(p.src.offsets + ray + 1);
-                        const float tn = __ldg(p.src.t_n + ray), tf = __ldg(p.src.t_f + ray);
-                        dl = (tf - tn) / (float)(o1 - o0);
-                        t = tn + ((float)(g - o0) + 0.5f) * dl;
-                    } else {
-                        ray = g / p.src.per_ray;
-                        t = __ldg(p.src.t + g);
-                        dl = __ldg(p.src.delta + g);
+        // per-tile sample table (coordinates, direction, t, delta, sin / cos of the encodings):
+        // epilogue thread et < 64 looks up sample et, thread et < 192 one (sample, axis)
+        const int et = threadIdx.x;
+        auto build_table = [&](int64_t tile) -> bool {
+                if (et < kTileS) {
+                    const int64_t g = tile * kTileS + et;
+                    float t = 0.0f, dl = 0.0f, xs[3] = {0.0f, 0.0f, 0.0f}, ds[3] = {0.0f, 0.0f, 0.0f};
+                    if (g < total) {
+                        int64_t ray;
+                        if (p.src.mode == kUniform) {
+                            ray = p.src.sample_ray ? (int64_t)__ldg(p.src.sample_ray + g) : find_ray(p.src.offsets, p.src.n_rays, g);
+                            const int32_t o0 = __ldg(p.src.offsets + ray), o1 = __ldg(p.src.offsets + ray + 1);
+                            const float tn = __ldg(p.src.t_n + ray), tf = __ldg(p.src.t_f + ray);
+                            dl = (tf - tn) / (float)(o1 - o0);
+                            t = tn + ((float)(g - o0) + 0.5f) * dl;
+                        } else {
+                            ray = g / p.src.per_ray;
+                            t = __ldg(p.src.t + g);
+                            dl = __ldg(p.src.delta + g);
+                        }
+    #pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            ds[a] = __ldg(p.src.ray_d + 3 * ray + a);
+                            xs[a] = (__ldg(p.src.ray_o + 3 * ray + a) + t * ds[a] - p.center[a]) * p.inv_scale;
+                        }
                     }
-#pragma unroll
+                    float* sx = s_x + et * 8;
+    #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        ds[a] = __ldg(p.src.ray_d + 3 * ray + a);
-                        xs[a] = (__ldg(p.src.ray_o + 3 * ray + a) + t * ds[a] - p.center[a]) * p.inv_scale;
+                        sx[a] = xs[a];
+                        sx[3 + a] = ds[a];
+                    }
+                    sx[6] = t;
+                    sx[7] = dl;
+                }
+                mbar_arrive(bar_tab);
+                if (!__all_sync(0xffffffffu, mbar_wait(bar_tab, tab_ph & 1u, abort_flag))) return false;
+                ++tab_ph;
+                // ---- sin / cos of the encodings: thread et < 192 -> (sample et / 3, axis et % 3) ----
+                if (et < 3 * kTileS) {
+                    const int sm = et / 3, a = et % 3;
+                    const float xv = s_x[sm * 8 + a], dv = s_x[sm * 8 + 3 + a];
+    #pragma unroll
+                    for (int oct = 0; oct < A::kPeSdf; ++oct) {
+                        float sn, cs;
+                        sincosf((float)(1 << oct) * xv, &sn, &cs);
+                        s_pe[((sm * A::kPeSdf + oct) * 3 + a) * 2] = sn;
+                        s_pe[((sm * A::kPeSdf + oct) * 3 + a) * 2 + 1] = cs;
+                    }
+    #pragma unroll
+                    for (int oct = 0; oct < A::kPeDir; ++oct) {
+                        float sn, cs;
+                        sincosf((float)(1 << oct) * dv, &sn, &cs);
+                        s_pd[((sm * A::kPeDir + oct) * 3 + a) * 2] = sn;
+                        s_pd[((sm * A::kPeDir + oct) * 3 + a) * 2 + 1] = cs;
                     }
                 }
-                float* sx = s_x + et * 8;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    sx[a] = xs[a];
-                    sx[3 + a] = ds[a];
-                }
-                sx[6] = t;
-                sx[7] = dl;
-            }
-            mbar_arrive(bar_tab);
-            if (!__all_sync(0xffffffffu, mbar_wait(bar_tab, tab_ph & 1u, abort_flag))) { ok = false; break; }
-            ++tab_ph;
-            // ---- sin / cos of the encodings: thread et < 192 -> (sample et / 3, axis et % 3) ----
-            if (et < 3 * kTileS) {
-                const int sm = et / 3, a = et % 3;
-                const float xv = s_x[sm * 8 + a], dv = s_x[sm * 8 + 3 + a];
-#pragma unroll
-                for (int oct = 0; oct < A::kPeSdf; ++oct) {
-                    float sn, cs;
-                    sincosf((float)(1 << oct) * xv, &sn, &cs);
-                    s_pe[((sm * A::kPeSdf + oct) * 3 + a) * 2] = sn;
-                    s_pe[((sm * A::kPeSdf + oct) * 3 + a) * 2 + 1] = cs;
-                }
-#pragma unroll
-                for (int oct = 0; oct < A::kPeDir; ++oct) {
-                    float sn, cs;
-                    sincosf((float)(1 << oct) * dv, &sn, &cs);
-                    s_pd[((sm * A::kPeDir + oct) * 3 + a) * 2] = sn;
-                    s_pd[((sm * A::kPeDir + oct) * 3 + a) * 2 + 1] = cs;
-                }
-            }
-            mbar_arrive(bar_tab);
-            if (!__all_sync(0xffffffffu, mbar_wait(bar_tab, tab_ph & 1u, abort_flag))) { ok = false; break; }
-            ++tab_ph;
+                mbar_arrive(bar_tab);
+                if (!__all_sync(0xffffffffu, mbar_wait(bar_tab, tab_ph & 1u, abort_flag))) return false;
+                ++tab_ph;
+            return true;
+        };
+        ok = build_table(blockIdx.x);
+        for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            // (the sample table of this tile was built before the loop or during the last one)
             // ---- layer-0 input: encoding rows, stored as 16x256b-ordered stmatrix fragments ----
             {
                 constexpr int Kp0 = TA::layer(0).Kp;
@@ -567,6 +573,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
             fence_proxy_async();
             mbar_arrive(bar_a);
             float f_out = 0.0f, dd_out = 0.0f, gn_out = 0.0f, nrm[3] = {0.0f, 0.0f, 0.0f};
+            float rec_t = 0.0f, rec_dl = 0.0f;   // this row's sample t and delta, for the record
             for (int L = 0; L < NL; ++L, ++lc) {
                 const TcLayer ly = TA::layer(L);
                 const bool w_ok = mbar_wait(bar_acc, lc & 1u, abort_flag);
@@ -731,6 +738,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                         nrm[0] = n_hat[0]; nrm[1] = n_hat[1]; nrm[2] = n_hat[2];
                         const float* ds = s_x + s * 8 + 3;
                         dd_out = gx * ds[0] + gy * ds[1] + gz * ds[2];
+                        rec_t = s_x[s * 8 + 6];
+                        rec_dl = s_x[s * 8 + 7];
 #pragma unroll
                         for (int e = 0; e < kDir; ++e) venc[e] = enc_tab(ds, s_pd + s * A::kPeDir * 6, A::kPeDir, e, 0);
                     }
@@ -811,7 +820,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                     tmem_wait_ld();
                     const int64_t g = tile * kTileS + s;
                     if (is_val && g < total) {
-                        const float t = s_x[s * 8 + 6], dl = s_x[s * 8 + 7];
+                        const float t = rec_t, dl = rec_dl;
                         float4* R4 = reinterpret_cast<float4*>(p.rec + g);
                         const float cr = __fdividef(1.0f, 1.0f + __expf(-(x0[0] + bias[0])));
                         const float cg = __fdividef(1.0f, 1.0f + __expf(-(x0[1] + bias[1])));
@@ -825,6 +834,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                 if (!last) {
                     fence_proxy_async();
                     mbar_arrive(bar_a);
+                }
+                // the next tile's table, while the colour layers' MMAs run: every warp
+                // has left the SDF output layer (the last reader of this tile's table)
+                // once colour layer 0's accumulator is complete
+                if (L == LS && tile + gridDim.x < n_tiles && !build_table(tile + gridDim.x)) {
+                    ok = false;
+                    break;
                 }
             }
         }
