@@ -30,6 +30,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+HIER_LADDER = ((32, 16), (16, 8), (8, 4), (4, 2))
 METRIC = "rays/s at PSNR≥oracle−0.1dB, TSDF-bounded vs 96-sample hierarchical, 1 GB300"
 UNIT = "rays/s"
 WORKLOADS = {
@@ -409,9 +410,10 @@ def run_ours(args, ws, rank, local):
     e2e = None if lean else run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev)
     # hierarchical comparator on the same views
     hier = {} if lean else run_hier(args, mlp, grid, rays, bp, n, dev, flush)
+    th = [] if (lean or args.workload == "large") else run_tsdf_hier(args, mlp, grid, rays, bp, mask, n, dev, flush)
     # the room networks are not fitted to the large floor, so its images have no quality to score
     quality = None if (args.no_quality or main_only or rank != 0 or args.workload == "large") else run_quality(
-        spec, wl, grid, bounds, rend, hier.get("renderer"), rays, bp, mask, args.sweep, rec, args.recovery_tau)
+        spec, wl, grid, bounds, rend, hier.get("renderer"), rays, bp, mask, args.sweep, rec, args.recovery_tau, th)
     cpu = run_cpu_baseline(wl, grid, rays, bp, spec) if (rank == 0 and ws == 1 and not lean) else None
     train = run_train(spec, wl, grid, mask, dev, n_rays=65536 if args.workload == "large" else 8192) \
         if (rank == 0 and not lean) else None
@@ -434,10 +436,28 @@ def run_ours(args, ws, rank, local):
         "roofline_march": march_roofline(wl, grid, rays, bp, ms_b.value / max(n_b.value, 1), hbm, peak_src)
         if rank == 0 else None,
         "comparator": {k: v for k, v in hier.items() if k != "renderer"},
+        "comparator_equal_psnr": equal_psnr_comparison(value, hier, quality),
+        "tsdf_hier": [{k: v for k, v in t.items() if k != "renderer"} for t in th] or None,
         "fusion": fusion, "train_step": train,
         "quality": quality, "cpu_baseline": cpu, "clocks": clocks,
     }
     return line
+
+
+def equal_psnr_comparison(value, hier, quality):
+    """The hierarchical sampler at the fewest samples (from the timed ladder and
+    64 + 32) whose PSNR on the quality pixels is at least the TSDF render's; its
+    rays/s beside the TSDF render's."""
+    if not hier or not quality or not quality.get("hier_ladder_psnr"):
+        return None
+    p_t = quality["psnr_tsdf_gpu"]
+    cands = [{"n_coarse": 64, "n_fine": 32, "value": hier["value"], "psnr": quality["psnr_hier96_gpu"]}]
+    for tl, ql in zip(hier["ladder"], quality["hier_ladder_psnr"]):
+        cands.append({"n_coarse": tl["n_coarse"], "n_fine": tl["n_fine"], "value": tl["value"], "psnr": ql["psnr"]})
+    ok = [c for c in cands if c["psnr"] >= p_t]
+    best = max(ok, key=lambda c: c["value"]) if ok else None
+    return {"psnr_tsdf_gpu": p_t, "tsdf_rays_s": value, "hier_at_ge_psnr": best,
+            "tsdf_over_hier": value / best["value"] if best else None, "candidates": cands}
 
 
 def march_roofline(wl, grid, rays, bp, ms_per_launch, hbm, peak_src, n_sample=4096):
@@ -552,11 +572,78 @@ def run_hier(args, mlp, grid, rays, bp, n, dev, flush):
         e1.record(st)
         torch.cuda.synchronize()
         tot += e0.elapsed_time(e1)
-    return {"impl": "hier 64+32 (same GPU, same network engine)", "value": n * steps / (tot / 1e3), "unit": UNIT,
-            "ms_per_step": tot / steps, "samples_per_ray": 96 + 64 * 0, "renderer": h}
+    line = {"impl": "hier 64+32 (same GPU, same network engine)", "value": n * steps / (tot / 1e3), "unit": UNIT,
+            "ms_per_step": tot / steps, "samples_per_ray": 96, "renderer": h, "ladder": []}
+    # smaller sample counts of the same sampler, for the equal-PSNR comparison (the large
+    # floor has no quality leg, so no ladder)
+    for nc, nf in (HIER_LADDER if args.workload != "large" else ()):
+        h.n_coarse, h.n_fine = nc, nf
+        h.render(grid, rays[0][0], rays[0][1], bp.t_near, bp.t_far)
+        tot = 0.0
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            h.render(grid, rays[k % N_VIEWS_TIMED][0], rays[k % N_VIEWS_TIMED][1], bp.t_near, bp.t_far)
+            e1.record(st)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        line["ladder"].append({"n_coarse": nc, "n_fine": nf, "value": n * steps / (tot / 1e3),
+                               "ms_per_step": tot / steps})
+    h.n_coarse, h.n_fine = 64, 32
+    return line
 
 
-def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=False, rec=None, tau=None):
+TSDF_HIER_VARIANTS = (  # name, mean coarse count, n_min, n_max, fine count (Tab. 2 "Ours" 6 + 8)
+    ("naive 6+8", 6.0, 6, 6, 8),
+    ("full 6+8", 6.0, 2, 64, 8),
+)
+
+
+def run_tsdf_hier(args, mlp, grid, rays, bp, mask, n, dev, flush):
+    """Coarse + fine inside the TSDF bound (Tab. 2 "Ours"): per step the timed path's
+    bounds, counts relative to the mean interval (fixed for "naive", adaptive for
+    "full"), then the coarse values, the inverse-CDF fine samples and the full
+    evaluation of the merged samples.  FALLBACK rays take 64 coarse samples."""
+    import torch
+    from paper_2311_17878_gb300 import tsdfs as T
+    b = T.Bounds(n, device=dev)
+    ac = T.AdaptiveCounts(n, device=dev)
+    out = []
+    steps = max(3, min(args.steps, 6))
+    st = torch.cuda.current_stream()
+    for name, n_mean, n_min, n_max, n_fine in TSDF_HIER_VARIANTS:
+        h = T.HierBoundedRenderer(mlp, n, n_fine, n * max(n_max, 64), device=dev)
+
+        def step(k):
+            o, d = rays[k % N_VIEWS_TIMED][:2]
+            b.compute(grid, o, d, bp, mask)
+            c = ac.apply(b, n_mean, n_min, n_max, 64)
+            h.render(o, d, c)
+            return c
+
+        for k in range(2):
+            step(k)
+        torch.cuda.synchronize()
+        tot, samples = 0.0, 0
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            c = step(k)
+            e1.record(st)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+            samples += int(c.offsets[-1].item()) + n_fine * int((c.n > 0).sum().item())
+        out.append({"name": name, "n_mean": n_mean, "n_min": n_min, "n_max": n_max, "n_fine": n_fine,
+                    "value": n * steps / (tot / 1e3), "ms_per_step": tot / steps,
+                    "samples_per_ray": samples / (n * steps), "renderer": (h, b, ac)})
+        del h
+    return out
+
+
+def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=False, rec=None, tau=None,
+                tsdf_hier=None):
     """PSNR against the oracle's dense reference (FP64, DENSE_SAMPLES midpoints
     over [t0, t_end]) on a seeded pixel subset of view 0.  The oracle's own TSDF
     render takes its bounds from its fp32 Alg. 1 on the same grid (and, with a
@@ -595,6 +682,24 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=Fal
             ort = orr.render_bounded(net, on, dn, tn, tf, cnt)["rgb"].numpy()
     p_gpu, p_or = orr.psnr(gpu_rgb, dense), orr.psnr(ort, dense)
     p_h = orr.psnr(hier_rgb, dense) if hier_rgb is not None else None
+    th_psnr = []
+    for v in (tsdf_hier or []):
+        h, b3, ac3 = v["renderer"]
+        b3.compute(grid, o, d, bp, mask)
+        c3 = ac3.apply(b3, v["n_mean"], v["n_min"], v["n_max"], 64)
+        ho = h.render(o, d, c3)
+        torch.cuda.synchronize()
+        th_psnr.append({"name": v["name"], "psnr": orr.psnr(ho.rgb[idx_t].cpu().numpy(), dense)})
+    ladder_psnr = []
+    if hier is not None:
+        for nc, nf in HIER_LADDER:
+            hier.n_coarse, hier.n_fine = nc, nf
+            ho = hier.render(grid, o, d, bp.t_near, bp.t_far)
+            torch.cuda.synchronize()
+            ladder_psnr.append({"n_coarse": nc, "n_fine": nf, "psnr": orr.psnr(ho.rgb[idx_t].cpu().numpy(), dense)})
+        hier.n_coarse, hier.n_fine = 64, 32
+        hout = hier.render(grid, o, d, bp.t_near, bp.t_far)
+        torch.cuda.synchronize()
     # geometry metrics on pixels where the dense reference sees a surface (Sec. 4 metrics:
     # depth error, normal angle error; the Tab. 1 failure statistic; mean sample spacing)
     hit = dd["wsum"].numpy() > 0.5
@@ -650,7 +755,8 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=Fal
             "recovery": None if rec is None else {
                 "tau": tau, "recovered_frac": float((rec.bounds.status == 2).float().mean().item()),
                 "recovered_frac_oracle_pixels": float(np.mean(again))},
-            "geometry_tsdf_gpu": gstat, "geometry_hier96_gpu": hstat,
+            "geometry_tsdf_gpu": gstat, "geometry_hier96_gpu": hstat, "hier_ladder_psnr": ladder_psnr,
+            "tsdf_hier_psnr": th_psnr,
             "tab1_failed_frac": float(failed.sum() / max(bnd.sum(), 1)),
             "mean_sample_spacing_m": float(spacing.mean()) if spacing.size else None,
             "oracle_s": time.perf_counter() - t_q}

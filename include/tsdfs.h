@@ -232,18 +232,68 @@ int tsdf_recovery_merge(int64_t n_rays, const uint8_t* status2, const float* rgb
                         const float* wsum2, const float* normal2, float* rgb, float* depth, float* wsum,
                         float* normal, tsdfs_stream_t stream);
 
-/* ---- hierarchical comparator (64 coarse + 32 inverse-CDF fine, Tab. 2 "HS") -
+/* ---- hierarchical comparator (n_c coarse + n_f inverse-CDF fine; 64 + 32 is
+ * the "HS" sampler of Tab. 2) ------------------------------------------------
  * Per ray over [t0, t_end] (t_near/t_far clipped to the grid box of `grid`;
- * only its geometry fields are read): 64 midpoints, SDF values only; section
+ * only its geometry fields are read): n_c midpoints, SDF values only; section
  * weights from the values (NeuS up-sampling opacity: slope min(own,
- * previous), clipped to [-1e3, 0]); 32 inverse-CDF samples at u = (k+1/2)/32
- * over pdf ~ w + 1e-5; all 96 sorted samples evaluated fully and composited
- * with section boundaries halfway between neighbours.  Outputs as render_rays.
- * workspace >= tsdfs_hier_workspace_size.                                    */
+ * previous), clipped to [-1e3, 0]); n_f inverse-CDF samples at
+ * u = (k+1/2)/n_f over pdf ~ w + 1e-5; all n_c + n_f sorted samples evaluated
+ * fully and composited with section boundaries halfway between neighbours.
+ * Outputs as render_rays.  2 <= n_coarse <= 64, 1 <= n_fine <= 32, else
+ * TSDFS_E_INVALID.  workspace >= tsdfs_hier_workspace_size (sized for 64 + 32,
+ * so it serves every count).  render_rays_hier96 is n_coarse = 64,
+ * n_fine = 32.                                                              */
 size_t tsdfs_hier_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays);
+int render_rays_hier(const tsdfs_mlp* mlp, const tsdfs_grid* grid, const float* ray_o, const float* ray_d,
+                     int64_t n_rays, int n_coarse, int n_fine, float t_near, float t_far, float* rgb, float* depth,
+                     float* wsum, float* normal, void* workspace, size_t ws_bytes, tsdfs_stream_t stream);
 int render_rays_hier96(const tsdfs_mlp* mlp, const tsdfs_grid* grid, const float* ray_o, const float* ray_d,
                        int64_t n_rays, float t_near, float t_far, float* rgb, float* depth, float* wsum,
                        float* normal, void* workspace, size_t ws_bytes, tsdfs_stream_t stream);
+
+/* ---- adaptive sample counts relative to the mean interval (Sec. 3.4) -------
+ * Samples sit at equal spacing inside [t_n, t_f], so a ray's count is
+ * proportional to its interval's length; the supplementary ray study scales it
+ * against the average interval (longer than average -> more samples, shorter
+ * -> fewer).  Two passes over the bounds of tsdf_ray_bounds (device arrays):
+ *   mean   = FP32 of the FP64 mean of L_r = t_f[r] - t_n[r] (FP32 subtraction)
+ *            over the BOUNDED rays (0 if there are none), summed in a fixed
+ *            order, so repeatable;
+ *   dl     = mean / n_mean (FP32, IEEE division);
+ *   n[r]   = BOUNDED: clamp(ceil(L_r / dl), n_min, n_max) (FP32 division;
+ *            n_min if dl == 0); FALLBACK: n_fallback; MISS: 0;
+ *   offsets: exclusive scan of n, n_rays + 1 entries.
+ * mean_len (device float[1]) receives the mean, or is NULL.  Requires
+ * 0 < n_mean <= 4096, 1 <= n_min <= n_max <= 4096, 0 <= n_fallback <= 4096,
+ * max(n_max, n_fallback) * n_rays < 2^31, else TSDFS_E_INVALID.  workspace >=
+ * tsdfs_adaptive_counts_workspace_size.  Ordered on `stream`.               */
+size_t tsdfs_adaptive_counts_workspace_size(int64_t n_rays);
+int tsdf_adaptive_counts(const float* t_n, const float* t_f, const uint8_t* status, int64_t n_rays, float n_mean,
+                         int32_t n_min, int32_t n_max, int32_t n_fallback, int32_t* n_samples, int32_t* offsets,
+                         float* mean_len, void* workspace, size_t ws_bytes, tsdfs_stream_t stream);
+
+/* ---- coarse + fine samples inside the TSDF bound (Tab. 2 "Ours", Sec. B) ---
+ * The hierarchical sampler restricted to each ray's [t_n, t_f]: ray r's
+ * c_r = offsets[r+1] - offsets[r] coarse midpoints of [t_n, t_f] (the counts of
+ * tsdf_ray_bounds, of tsdf_adaptive_counts, or any caller's) are evaluated for
+ * SDF values only; their sections give the NeuS up-sampling weights (as
+ * render_rays_hier) and n_fine inverse-CDF samples at u = (k+1/2)/n_fine over
+ * pdf ~ w + 1e-5; the c_r + n_fine sorted samples are evaluated fully and
+ * composited with section boundaries halfway between neighbours and the outer
+ * ones at t_n, t_f.  A ray with one coarse sample has no section: its fine
+ * samples are the midpoints of n_fine equal parts of [t_n, t_f].  A ray with
+ * no coarse sample (MISS) renders to zero.  Fixed counts over the bound are
+ * the "naive" variant of Tab. 2, adaptive counts the "full" one.
+ * 0 <= n_fine <= 32; max_coarse >= offsets[n_rays] (else the status word gets
+ * TSDFS_DEV_SAMPLES_OVERFLOW and the outputs are zero); max_coarse +
+ * n_rays * n_fine < 2^31.  Outputs as render_rays.  workspace >=
+ * tsdfs_hier_bounded_workspace_size.                                        */
+size_t tsdfs_hier_bounded_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays, int32_t n_fine, int64_t max_coarse);
+int render_rays_hier_bounded(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
+                             const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
+                             int32_t n_fine, int64_t max_coarse, float* rgb, float* depth, float* wsum, float* normal,
+                             void* workspace, size_t ws_bytes, tsdfs_stream_t stream);
 
 /* ---- backward of render_rays (training step of the networks) ---------------
  * Gradients of L = sum_r d_rgb_r . rgb_r + d_depth_r depth_r + d_eik_r eik_r

@@ -1,7 +1,8 @@
 """CPU oracle for the render half of TSDF-Sampling: sample placement, the SDF and
 colour MLPs with the analytic SDF gradient, NeuS opacity and volume-rendering
 compositing (Eq. 1, Eq. 2, the rendered normal of Sec. C.1), the 64+32
-hierarchical comparator, the dense reference render and the training loss.
+hierarchical comparator and the same sampler inside the TSDF bound, counts
+relative to the mean interval, the dense reference render and the training loss.
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
@@ -24,7 +25,10 @@ Readings taken here (numbered as in the design notes):
   R17 black background; R18 depth and normal are 0 when sum w < 1e-8;
   R19 hierarchical comparator as in :func:`render_hier`;
   R21 section widths: boundaries at the interval ends and halfway between
-      neighbouring samples (equal to (t_f - t_n)/n for midpoint placement).
+      neighbouring samples (equal to (t_f - t_n)/n for midpoint placement);
+  R23 coarse + fine inside the TSDF bound as in :func:`render_hier_bounded`;
+  R24 counts relative to the mean interval as in :func:`adaptive_counts`;
+  R25 the dense reference image is rendered without the opacity guard.
 """
 from __future__ import annotations
 
@@ -156,6 +160,9 @@ def neus_alpha(f, dd, delta, inv_s, eps):
     f_hi = f + 0.5 * delta * c
     p_lo = torch.sigmoid(inv_s * f_lo)
     p_hi = torch.sigmoid(inv_s * f_hi)
+    if eps == 0.0:  # no guard: a section whose near end underflows to Phi = 0 lies deep inside, opaque
+        ratio = torch.where(p_lo > 0, (p_lo - p_hi) / torch.where(p_lo > 0, p_lo, 1.0), torch.ones_like(p_lo))
+        return torch.clamp(ratio, 0.0, 1.0)
     return torch.clamp((p_lo - p_hi + eps) / (p_lo + eps), 0.0, 1.0)
 
 
@@ -199,8 +206,9 @@ def _padded(counts):
     return counts, S, mask
 
 
-def render_samples(net, o, d, t, delta, mask):
-    """Evaluate and composite padded samples t (R, S) with widths delta."""
+def render_samples(net, o, d, t, delta, mask, eps=None):
+    """Evaluate and composite padded samples t (R, S) with widths delta (opacity
+    guard eps: the network's own unless given)."""
     R, S = t.shape
     x = o.unsqueeze(1) + t.unsqueeze(2) * d.unsqueeze(1)
     sel = mask.reshape(-1)
@@ -219,7 +227,7 @@ def render_samples(net, o, d, t, delta, mask):
     dd = scatter(ev["dd"])
     rgb = scatter(ev["rgb"])
     nh = scatter(ev["n_hat"])
-    alpha = neus_alpha(f, dd, delta, spec.inv_s, spec.alpha_eps)
+    alpha = neus_alpha(f, dd, delta, spec.inv_s, spec.alpha_eps if eps is None else eps)
     out = composite(alpha, t, rgb, nh, mask)
     out["alpha"] = alpha
     out["eik"] = (ev["gnorm"] - 1.0) ** 2
@@ -241,16 +249,17 @@ def midpoint_samples(t_n, t_f, counts):
     return t, dl, mask
 
 
-def render_bounded(net, rays_o, rays_d, t_n, t_f, counts):
+def render_bounded(net, rays_o, rays_d, t_n, t_f, counts, eps=None):
     """The TSDF-bounded render: n_r midpoint samples in [t_n, t_f] per ray
     (Sec. 3.3-3.4), evaluated and composited (Eq. 1, Eq. 2, normal)."""
     o = torch.as_tensor(np.asarray(rays_o), dtype=DT)
     d = torch.as_tensor(np.asarray(rays_d), dtype=DT)
     t, dl, mask = midpoint_samples(t_n, t_f, counts)
-    return render_samples(net, o, d, t, dl, mask)
+    return render_samples(net, o, d, t, dl, mask, eps)
 
 
 STATUS_BOUNDED = 1   # ray status written by the bounds pass: 0 MISS, 1 BOUNDED, 2 FALLBACK
+STATUS_FALLBACK = 2
 
 
 def render_recovered(net, rays_o, rays_d, t_n, t_f, counts, status, t0, t_end, tau, n_fallback=96):
@@ -273,20 +282,23 @@ def render_recovered(net, rays_o, rays_d, t_n, t_f, counts, status, t0, t_end, t
     return out, again
 
 
-def render_uniform(net, rays_o, rays_d, t0, t_end, n):
+def render_uniform(net, rays_o, rays_d, t0, t_end, n, eps=None):
     """n midpoint samples over [t0, t_end] (the fallback and the dense reference)."""
-    return render_bounded(net, rays_o, rays_d, t0, t_end, np.full(len(np.asarray(t0)), n, np.int64))
+    return render_bounded(net, rays_o, rays_d, t0, t_end, np.full(len(np.asarray(t0)), n, np.int64), eps)
 
 
 def dense_reference(net, rays_o, rays_d, t0, t_end, n=2048, chunk=64):
-    """The reference image: n midpoint samples over the whole [t0, t_end]."""
+    """The reference image: n midpoint samples over the whole [t0, t_end], without
+    the opacity guard (R25): the guard gives every free-space section an opacity
+    of about eps, which over n samples adds up to n * eps (1 % at n = 1024), so
+    only the unguarded sum converges to the continuous render as n grows."""
     outs = []
     N = len(np.asarray(t0))
     for s in range(0, N, chunk):
         e = min(N, s + chunk)
         with torch.no_grad():
             r = render_uniform(net, np.asarray(rays_o)[s:e], np.asarray(rays_d)[s:e],
-                               np.asarray(t0)[s:e], np.asarray(t_end)[s:e], n)
+                               np.asarray(t0)[s:e], np.asarray(t_end)[s:e], n, eps=0.0)
         outs.append({k: r[k] for k in ("rgb", "depth", "wsum", "normal")})
     return {k: torch.cat([o[k] for o in outs]) for k in outs[0]}
 
@@ -330,7 +342,8 @@ def inverse_cdf(z, w, n_fine, pdf_floor=1e-5):
 
 
 def render_hier(net, rays_o, rays_d, t0, t_end, n_coarse=64, n_fine=32):
-    """Hierarchical 64 + 32 render over [t0, t_end] (the comparator of Tab. 2)."""
+    """Hierarchical render over [t0, t_end]: n_coarse midpoints, n_fine inverse-CDF samples
+    (64 + 32 is the comparator of Tab. 2)."""
     spec = net.spec
     o = torch.as_tensor(np.asarray(rays_o), dtype=DT)
     d = torch.as_tensor(np.asarray(rays_d), dtype=DT)
@@ -348,6 +361,81 @@ def render_hier(net, rays_o, rays_d, t0, t_end, n_coarse=64, n_fine=32):
     dl = section_widths(t, t0, te, mask)
     out = render_samples(net, o, d, t, dl, mask)
     out["t"] = t
+    return out
+
+
+# ----------------------------------------------------------------------------
+# coarse + fine inside the TSDF bound (R23) and counts relative to the mean (R24)
+# ----------------------------------------------------------------------------
+def adaptive_counts(t_n, t_f, status, n_mean, n_min, n_max, n_fallback):
+    """R24 (Sec. 3.4: equal spacing, so a count proportional to the interval's
+    length; the supplementary ray study scales it against the average bound).
+    In FP32 as the library states it: L = t_f - t_n, mean = the FP64 mean of L
+    over the BOUNDED rays rounded to FP32 (0 with none), dl = mean / n_mean,
+    n = clamp(ceil(L / dl), n_min, n_max) (n_min when dl = 0 or L / dl is NaN);
+    FALLBACK rays n_fallback, MISS rays 0.  Returns (counts int32, mean float32)."""
+    t_n = np.asarray(t_n, np.float32)
+    t_f = np.asarray(t_f, np.float32)
+    status = np.asarray(status)
+    L = np.subtract(t_f, t_n, dtype=np.float32)
+    bnd = status == STATUS_BOUNDED
+    mean = np.float32(np.mean(L[bnd].astype(np.float64))) if bnd.any() else np.float32(0.0)
+    dl = np.float32(mean / np.float32(n_mean))
+    n = np.zeros(len(L), np.int32)
+    if dl > 0:
+        with np.errstate(invalid="ignore", divide="ignore", over="ignore"):
+            q = np.ceil(np.divide(L, dl, dtype=np.float32))
+        q = np.where(np.isnan(q), n_min, np.clip(q, n_min, n_max))
+    else:
+        q = np.full(len(L), n_min, np.float32)
+    n[bnd] = q[bnd].astype(np.int32)
+    n[status == STATUS_FALLBACK] = n_fallback
+    return n, mean
+
+
+def render_hier_bounded(net, rays_o, rays_d, t_n, t_f, counts, n_fine):
+    """R23 (Tab. 2 "Ours", the supplementary ray study): the hierarchical sampler
+    inside each ray's [t_n, t_f].  counts[r] coarse midpoints of [t_n, t_f],
+    SDF values only; section weights as :func:`hier_coarse_weights`; n_fine
+    inverse-CDF samples (:func:`inverse_cdf`); with a single coarse sample (no
+    section) the fine samples are the midpoints of n_fine equal parts of the
+    interval; coarse and fine merged in order, section widths as R21 with the
+    outer boundaries at t_n and t_f; rays with no coarse sample render to zero."""
+    spec = net.spec
+    o = torch.as_tensor(np.asarray(rays_o), dtype=DT)
+    d = torch.as_tensor(np.asarray(rays_d), dtype=DT)
+    lo_all = torch.as_tensor(np.asarray(t_n), dtype=DT)
+    hi_all = torch.as_tensor(np.asarray(t_f), dtype=DT)
+    counts = np.asarray(counts, np.int64)
+    R = len(counts)
+    out = {"rgb": torch.zeros((R, 3), dtype=DT), "depth": torch.zeros(R, dtype=DT),
+           "wsum": torch.zeros(R, dtype=DT), "normal": torch.zeros((R, 3), dtype=DT)}
+    t_all = [None] * R
+    for c in np.unique(counts[counts > 0]):
+        idx = np.nonzero(counts == c)[0]
+        it = torch.as_tensor(idx)
+        lo, hi = lo_all[it], hi_all[it]
+        i = torch.arange(int(c), dtype=DT).unsqueeze(0)
+        zc = lo.unsqueeze(1) + (i + 0.5) * ((hi - lo) / int(c)).unsqueeze(1)
+        if n_fine == 0:
+            zf = zc[:, :0]
+        elif c >= 2:
+            xc = (o[it].unsqueeze(1) + zc.unsqueeze(2) * d[it].unsqueeze(1)).reshape(-1, 3)
+            fc, _, _ = sdf_forward(net, xc, with_grad=False)
+            w = hier_coarse_weights(fc.reshape(len(idx), int(c)), zc, spec.inv_s, spec.alpha_eps)
+            zf = inverse_cdf(zc, w, n_fine)
+        else:
+            k = torch.arange(n_fine, dtype=DT).unsqueeze(0)
+            zf = lo.unsqueeze(1) + (k + 0.5) * ((hi - lo) / n_fine).unsqueeze(1)
+        t, _ = torch.sort(torch.cat([zc, zf], 1), 1)
+        mask = torch.ones_like(t, dtype=torch.bool)
+        dl = section_widths(t, lo, hi, mask)
+        r = render_samples(net, o[it], d[it], t, dl, mask)
+        for key in out:
+            out[key][it] = r[key]
+        for j, rr in enumerate(idx):
+            t_all[rr] = t[j]
+    out["t"] = t_all
     return out
 
 

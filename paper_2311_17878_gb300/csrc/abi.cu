@@ -106,9 +106,15 @@ int launch_composite(const SampleRec* rec, const int32_t* offsets, int per_ray, 
                      const int32_t* total_dev, int64_t capacity, float inv_s, float eps, float* rgb, float* depth,
                      float* wsum, float* normal, float* eik, cudaStream_t st);
 int launch_hier_setup(const tsdfs_grid* g, const float* ray_o, const float* ray_d, int64_t n_rays, float t_near,
-                      float t_far, float* t0, float* te, uint8_t* status, float* tc, float* dc, cudaStream_t st);
+                      float t_far, float* t0, float* te, uint8_t* status, float* tc, float* dc, int n_c,
+                      cudaStream_t st);
 int launch_hier_fine(const float* fcoarse, const float* tc, const float* t0, const float* te, int64_t n_rays,
-                     float inv_s, float eps, float* t_out, float* d_out, cudaStream_t st);
+                     float inv_s, float eps, float* t_out, float* d_out, int n_c, int n_f, cudaStream_t st);
+int launch_bounded_counts(const int32_t* offsets, int64_t n_rays, int n_f, int64_t max_coarse, int32_t* n2,
+                          cudaStream_t st);
+int launch_bounded_fine(const float* fcoarse, const int32_t* offsets, const float* t_n, const float* t_f,
+                        const int32_t* offsets2, int64_t n_rays, int n_f, float inv_s, float eps, int64_t max_coarse,
+                        int64_t capacity2, float* t_out, float* d_out, int32_t* ray_out, cudaStream_t st);
 int grid_check(const tsdfs_grid* g);
 int mlp_tc_available(int arch);
 int launch_mlp_full_tc(const tsdfs_mlp* mlp, const SampleSource& src, SampleRec* rec, int64_t max_samples,
@@ -283,7 +289,7 @@ struct HierWs {
     size_t bytes;
 };
 
-static HierWs hier_layout(void* base, int64_t n) {
+static HierWs hier_layout(void* base, int64_t n, int n_c = 64, int n_f = 32) {
     HierWs w{};
     uintptr_t p = (reinterpret_cast<uintptr_t>(base) + 255) & ~uintptr_t(255);
     auto take = [&](size_t bytes) {
@@ -291,14 +297,15 @@ static HierWs hier_layout(void* base, int64_t n) {
         p = (p + bytes + 255) & ~uintptr_t(255);
         return q;
     };
-    w.rec = reinterpret_cast<SampleRec*>(take((size_t)n * 96 * sizeof(SampleRec)));
+    const size_t n_h = (size_t)(n_c + n_f);
+    w.rec = reinterpret_cast<SampleRec*>(take((size_t)n * n_h * sizeof(SampleRec)));
     w.t0 = reinterpret_cast<float*>(take((size_t)n * 4));
     w.te = reinterpret_cast<float*>(take((size_t)n * 4));
-    w.tc = reinterpret_cast<float*>(take((size_t)n * 64 * 4));
-    w.dc = reinterpret_cast<float*>(take((size_t)n * 64 * 4));
-    w.fc = reinterpret_cast<float*>(take((size_t)n * 64 * 4));
-    w.tf = reinterpret_cast<float*>(take((size_t)n * 96 * 4));
-    w.df = reinterpret_cast<float*>(take((size_t)n * 96 * 4));
+    w.tc = reinterpret_cast<float*>(take((size_t)n * n_c * 4));
+    w.dc = reinterpret_cast<float*>(take((size_t)n * n_c * 4));
+    w.fc = reinterpret_cast<float*>(take((size_t)n * n_c * 4));
+    w.tf = reinterpret_cast<float*>(take((size_t)n * n_h * 4));
+    w.df = reinterpret_cast<float*>(take((size_t)n * n_h * 4));
     w.status = reinterpret_cast<uint8_t*>(take((size_t)n));
     w.bytes = p - reinterpret_cast<uintptr_t>(base) + 256;
     return w;
@@ -310,26 +317,29 @@ extern "C" size_t tsdfs_hier_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays
     return hier_layout(nullptr, n_rays).bytes + 256;
 }
 
-extern "C" int render_rays_hier96(const tsdfs_mlp* mlp, const tsdfs_grid* grid, const float* ray_o,
-                                  const float* ray_d, int64_t n_rays, float t_near, float t_far, float* rgb,
-                                  float* depth, float* wsum, float* normal, void* ws, size_t ws_bytes,
-                                  tsdfs_stream_t stream) {
+extern "C" int render_rays_hier(const tsdfs_mlp* mlp, const tsdfs_grid* grid, const float* ray_o, const float* ray_d,
+                                int64_t n_rays, int n_coarse, int n_fine, float t_near, float t_far, float* rgb,
+                                float* depth, float* wsum, float* normal, void* ws, size_t ws_bytes,
+                                tsdfs_stream_t stream) {
     int rc = mlp_check(mlp);
     if (rc) return rc;
     if (!grid) return fail(TSDFS_E_INVALID, "grid is NULL");
     if (grid->nx <= 0 || grid->ny <= 0 || grid->nz <= 0 || !(grid->voxel_size > 0.0f))
         return fail(TSDFS_E_INVALID, "grid geometry invalid");
+    if (n_coarse < 2 || n_coarse > 64 || n_fine < 1 || n_fine > 32)
+        return fail(TSDFS_E_INVALID, "sample counts must be coarse in [2, 64], fine in [1, 32]");
     if (n_rays < 0) return fail(TSDFS_E_INVALID, "n_rays must be >= 0");
     if (n_rays == 0) return TSDFS_OK;
+    const int n_h = n_coarse + n_fine;
     if (n_rays * 96 > (int64_t)INT32_MAX) return fail(TSDFS_E_INVALID, "too many rays");
     if (!ray_o || !ray_d || !rgb || !depth || !wsum) return fail(TSDFS_E_INVALID, "ray and output pointers must be non-NULL");
     if (!(t_near < t_far)) return fail(TSDFS_E_INVALID, "t_near must be < t_far");
     if (!ws || ws_bytes < tsdfs_hier_workspace_size(mlp, n_rays)) return fail(TSDFS_E_WORKSPACE, "hier workspace too small");
     cudaStream_t st = (cudaStream_t)stream;
-    HierWs w = hier_layout(ws, n_rays);
+    HierWs w = hier_layout(ws, n_rays, n_coarse, n_fine);
     {
         ProfScope ps("hier_setup", st);
-        rc = launch_hier_setup(grid, ray_o, ray_d, n_rays, t_near, t_far, w.t0, w.te, w.status, w.tc, w.dc, st);
+        rc = launch_hier_setup(grid, ray_o, ray_d, n_rays, t_near, t_far, w.t0, w.te, w.status, w.tc, w.dc, n_coarse, st);
     }
     if (rc) return rc;
     const NetParams np = net_params(mlp);
@@ -339,9 +349,9 @@ extern "C" int render_rays_hier96(const tsdfs_mlp* mlp, const tsdfs_grid* grid, 
     cs.ray_d = ray_d;
     cs.t = w.tc;
     cs.delta = w.dc;
-    cs.per_ray = 64;
-    cs.total_host = n_rays * 64;
-    cs.capacity = n_rays * 64;
+    cs.per_ray = n_coarse;
+    cs.total_host = n_rays * n_coarse;
+    cs.capacity = n_rays * n_coarse;
     if (mlp->precision != TSDFS_PREC_F32) {
         ProfScope ps("mlp_value_tc", st);
         rc = launch_mlp_value_tc(mlp, cs, w.fc, st);
@@ -353,18 +363,142 @@ extern "C" int render_rays_hier96(const tsdfs_mlp* mlp, const tsdfs_grid* grid, 
     if (rc) return rc;
     {
         ProfScope ps("hier_fine", st);
-        rc = launch_hier_fine(w.fc, w.tc, w.t0, w.te, n_rays, mlp->inv_s, mlp->alpha_eps, w.tf, w.df, st);
+        rc = launch_hier_fine(w.fc, w.tc, w.t0, w.te, n_rays, mlp->inv_s, mlp->alpha_eps, w.tf, w.df, n_coarse, n_fine,
+                              st);
     }
     if (rc) return rc;
     SampleSource fs = cs;
     fs.t = w.tf;
     fs.delta = w.df;
-    fs.per_ray = 96;
-    fs.total_host = n_rays * 96;
-    fs.capacity = n_rays * 96;
-    rc = run_full_mlp(mlp, fs, w.rec, n_rays * 96, st);
+    fs.per_ray = n_h;
+    fs.total_host = n_rays * n_h;
+    fs.capacity = n_rays * n_h;
+    rc = run_full_mlp(mlp, fs, w.rec, n_rays * n_h, st);
     if (rc) return rc;
     ProfScope ps("composite", st);
-    return launch_composite(w.rec, nullptr, 96, w.status, n_rays, nullptr, n_rays * 96, mlp->inv_s, mlp->alpha_eps, rgb,
+    return launch_composite(w.rec, nullptr, n_h, w.status, n_rays, nullptr, n_rays * n_h, mlp->inv_s, mlp->alpha_eps,
+                            rgb, depth, wsum, normal, nullptr, st);
+}
+
+extern "C" int render_rays_hier96(const tsdfs_mlp* mlp, const tsdfs_grid* grid, const float* ray_o,
+                                  const float* ray_d, int64_t n_rays, float t_near, float t_far, float* rgb,
+                                  float* depth, float* wsum, float* normal, void* ws, size_t ws_bytes,
+                                  tsdfs_stream_t stream) {
+    return render_rays_hier(mlp, grid, ray_o, ray_d, n_rays, 64, 32, t_near, t_far, rgb, depth, wsum, normal, ws,
+                            ws_bytes, stream);
+}
+
+// ---- coarse + fine inside the TSDF bound ----------------------------------------
+struct BoundedHierWs {
+    int32_t *ray_c, *n2, *off2, *sums, *ray2;
+    float *fc, *t2, *d2;
+    SampleRec* rec;
+    size_t bytes;
+};
+
+static BoundedHierWs bounded_hier_layout(void* base, int64_t n, int64_t max_coarse, int64_t cap2) {
+    BoundedHierWs w{};
+    uintptr_t p = (reinterpret_cast<uintptr_t>(base) + 255) & ~uintptr_t(255);
+    auto take = [&](size_t bytes) {
+        uintptr_t q = p;
+        p = (p + bytes + 255) & ~uintptr_t(255);
+        return q;
+    };
+    w.rec = reinterpret_cast<SampleRec*>(take((size_t)cap2 * sizeof(SampleRec)));
+    w.ray_c = reinterpret_cast<int32_t*>(take((size_t)max_coarse * 4));
+    w.fc = reinterpret_cast<float*>(take((size_t)max_coarse * 4));
+    w.n2 = reinterpret_cast<int32_t*>(take((size_t)n * 4));
+    w.off2 = reinterpret_cast<int32_t*>(take((size_t)(n + 1) * 4));
+    w.sums = reinterpret_cast<int32_t*>(take((size_t)(scan_chunks(n) + 1) * 4));
+    w.t2 = reinterpret_cast<float*>(take((size_t)cap2 * 4));
+    w.d2 = reinterpret_cast<float*>(take((size_t)cap2 * 4));
+    w.ray2 = reinterpret_cast<int32_t*>(take((size_t)cap2 * 4));
+    w.bytes = p - reinterpret_cast<uintptr_t>(base) + 256;
+    return w;
+}
+
+extern "C" size_t tsdfs_hier_bounded_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays, int32_t n_fine,
+                                                    int64_t max_coarse) {
+    (void)mlp;
+    if (n_rays < 0 || max_coarse < 0 || n_fine < 0) return 0;
+    return bounded_hier_layout(nullptr, n_rays, max_coarse, max_coarse + n_rays * n_fine).bytes + 256;
+}
+
+extern "C" int render_rays_hier_bounded(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d,
+                                        const float* t_n, const float* t_f, const int32_t* offsets,
+                                        const uint8_t* status, int64_t n_rays, int32_t n_fine, int64_t max_coarse,
+                                        float* rgb, float* depth, float* wsum, float* normal, void* ws,
+                                        size_t ws_bytes, tsdfs_stream_t stream) {
+    int rc = mlp_check(mlp);
+    if (rc) return rc;
+    if (n_rays < 0 || max_coarse < 0) return fail(TSDFS_E_INVALID, "n_rays and max_coarse must be >= 0");
+    if (n_fine < 0 || n_fine > 32) return fail(TSDFS_E_INVALID, "fine sample count must be in [0, 32]");
+    if (n_rays == 0) return TSDFS_OK;
+    const int64_t cap2 = max_coarse + n_rays * (int64_t)n_fine;
+    if (cap2 > (int64_t)INT32_MAX) return fail(TSDFS_E_INVALID, "max_coarse + n_rays * n_fine must fit int32 offsets");
+    if (!ray_o || !ray_d || !t_n || !t_f || !offsets || !status || !rgb || !depth || !wsum)
+        return fail(TSDFS_E_INVALID, "ray, bound and output pointers must be non-NULL (normal may be NULL)");
+    if (!ws || ws_bytes < tsdfs_hier_bounded_workspace_size(mlp, n_rays, n_fine, max_coarse))
+        return fail(TSDFS_E_WORKSPACE, "bounded hierarchical workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    BoundedHierWs w = bounded_hier_layout(ws, n_rays, max_coarse, cap2);
+    // coarse pass: SDF values at the midpoints of the bounds' ragged counts
+    SampleSource cs{};
+    cs.mode = kUniform;
+    cs.ray_o = ray_o;
+    cs.ray_d = ray_d;
+    cs.offsets = offsets;
+    cs.t_n = t_n;
+    cs.t_f = t_f;
+    cs.n_rays = n_rays;
+    cs.total_dev = offsets + n_rays;
+    cs.capacity = max_coarse;
+    {
+        {
+            ProfScope ps("sample_ray", st);
+            k_sample_ray<<<grid_1d(n_rays, 256), 256, 0, st>>>(offsets, n_rays, max_coarse, w.ray_c);
+            rc = cuda_check(cudaGetLastError(), "sample_ray launch");
+            if (rc) return rc;
+        }
+        cs.sample_ray = w.ray_c;  // the value kernels flag a coarse total above max_coarse
+        if (mlp->precision != TSDFS_PREC_F32) {
+            ProfScope ps("mlp_value_tc", st);
+            rc = launch_mlp_value_tc(mlp, cs, w.fc, st);
+        } else {
+            ProfScope ps("mlp_value_simt", st);
+            const NetParams np = net_params(mlp);
+            rc = mlp->arch == TSDFS_ARCH_TINY ? launch_mlp_value_simt<TSDFS_ARCH_TINY>(np, cs, w.fc, st)
+                                              : launch_mlp_value_simt<TSDFS_ARCH_ROOM>(np, cs, w.fc, st);
+        }
+        if (rc) return rc;
+    }
+    // merged counts, their offsets, then the fine samples and the merged list
+    {
+        ProfScope ps("bounded_fine", st);
+        rc = launch_bounded_counts(offsets, n_rays, n_fine, max_coarse, w.n2, st);
+        if (rc) return rc;
+        rc = exclusive_scan(w.n2, n_rays, w.off2, w.sums, st);
+        if (rc) return rc;
+        rc = launch_bounded_fine(w.fc, offsets, t_n, t_f, w.off2, n_rays, n_fine, mlp->inv_s, mlp->alpha_eps,
+                                 max_coarse, cap2, w.t2, w.d2, w.ray2, st);
+        if (rc) return rc;
+    }
+    SampleSource fs{};
+    fs.mode = kExplicit;
+    fs.ray_o = ray_o;
+    fs.ray_d = ray_d;
+    fs.t = w.t2;
+    fs.delta = w.d2;
+    fs.sample_ray = w.ray2;
+    fs.per_ray = 1;
+    fs.n_rays = n_rays;
+    fs.total_dev = w.off2 + n_rays;
+    fs.capacity = cap2;
+    if (cap2 > 0) {
+        rc = run_full_mlp(mlp, fs, w.rec, cap2, st);
+        if (rc) return rc;
+    }
+    ProfScope ps("composite", st);
+    return launch_composite(w.rec, w.off2, 0, status, n_rays, w.off2 + n_rays, cap2, mlp->inv_s, mlp->alpha_eps, rgb,
                             depth, wsum, normal, nullptr, st);
 }

@@ -522,3 +522,140 @@ extern "C" int tsdf_ray_bounds_noalloc(const tsdfs_grid* g, const uint32_t* mask
     return tsdf_ray_bounds(g, mask, ray_o, ray_d, n_rays, p, t_n, t_f, n_samples, offsets, t_zero, status, scratch,
                            kNoAllocScratchBytes, stream);
 }
+
+// ---------------------------------------------------------------------------
+// Adaptive sample counts relative to the mean interval (Sec. 3.4: samples at
+// equal spacing inside [t_n, t_f], so the count is proportional to the
+// interval's length; the supplementary ray study: a ray whose bound is longer
+// than the average bound gets more samples, a shorter one fewer).  Two passes:
+// the mean length of the BOUNDED intervals over the batch, then per ray
+// n = clamp(ceil(L / (mean / n_mean)), n_min, n_max).  The mean is summed in
+// FP64 in a fixed order (a fixed grid of kMeanBlocks blocks, each a fixed tree),
+// so it does not depend on scheduling, and rounded once to FP32; the count
+// arithmetic is FP32 with IEEE division (this file is compiled without FMA
+// contraction), so an FP32 restatement on the host reproduces every count.
+// ---------------------------------------------------------------------------
+namespace tsdfs {
+namespace {
+constexpr int kMeanBlocks = 256;
+constexpr int kMeanThreads = 256;
+
+__global__ void __launch_bounds__(kMeanThreads) k_len_partials(const float* __restrict__ t_n,
+                                                                const float* __restrict__ t_f,
+                                                                const uint8_t* __restrict__ status, int64_t n_rays,
+                                                                double* __restrict__ part_sum,
+                                                                unsigned long long* __restrict__ part_cnt) {
+    __shared__ double s_sum[kMeanThreads];
+    __shared__ unsigned long long s_cnt[kMeanThreads];
+    double acc = 0.0;
+    unsigned long long cnt = 0;
+    for (int64_t r = blockIdx.x * (int64_t)kMeanThreads + threadIdx.x; r < n_rays; r += (int64_t)kMeanBlocks * kMeanThreads) {
+        if (__ldg(status + r) == TSDFS_BOUNDED) {
+            acc += (double)__fsub_rn(__ldg(t_f + r), __ldg(t_n + r));
+            ++cnt;
+        }
+    }
+    s_sum[threadIdx.x] = acc;
+    s_cnt[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int h = kMeanThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            s_sum[threadIdx.x] += s_sum[threadIdx.x + h];
+            s_cnt[threadIdx.x] += s_cnt[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part_sum[blockIdx.x] = s_sum[0];
+        part_cnt[blockIdx.x] = s_cnt[0];
+    }
+}
+
+// one block: the partials in a fixed tree -> mean (FP32) and the spacing mean / n_mean
+__global__ void __launch_bounds__(kMeanBlocks) k_len_mean(const double* __restrict__ part_sum,
+                                                          const unsigned long long* __restrict__ part_cnt,
+                                                          float n_mean, float* __restrict__ mean_out,
+                                                          float* __restrict__ spacing_out) {
+    __shared__ double s_sum[kMeanBlocks];
+    __shared__ unsigned long long s_cnt[kMeanBlocks];
+    s_sum[threadIdx.x] = part_sum[threadIdx.x];
+    s_cnt[threadIdx.x] = part_cnt[threadIdx.x];
+    __syncthreads();
+    for (int h = kMeanBlocks / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            s_sum[threadIdx.x] += s_sum[threadIdx.x + h];
+            s_cnt[threadIdx.x] += s_cnt[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float mean = s_cnt[0] > 0 ? (float)(s_sum[0] / (double)s_cnt[0]) : 0.0f;
+        *spacing_out = __fdiv_rn(mean, n_mean);
+        if (mean_out) *mean_out = mean;
+    }
+}
+
+__global__ void k_adaptive_counts(const float* __restrict__ t_n, const float* __restrict__ t_f,
+                                  const uint8_t* __restrict__ status, int64_t n_rays,
+                                  const float* __restrict__ spacing, int n_min, int n_max, int n_fallback,
+                                  int32_t* __restrict__ n_out) {
+    const float dl = __ldg(spacing);
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t st = __ldg(status + r);
+        int n = 0;
+        if (st == TSDFS_BOUNDED) {
+            const float len = __fsub_rn(__ldg(t_f + r), __ldg(t_n + r));
+            float q = dl > 0.0f ? ceilf(__fdiv_rn(len, dl)) : (float)n_min;
+            q = fminf(fmaxf(q, (float)n_min), (float)n_max);  // also maps NaN to n_min
+            n = (int)q;
+        } else if (st == TSDFS_FALLBACK) {
+            n = n_fallback;
+        }
+        n_out[r] = n;
+    }
+}
+}  // namespace
+}  // namespace tsdfs
+
+extern "C" size_t tsdfs_adaptive_counts_workspace_size(int64_t n_rays) {
+    if (n_rays < 0) return 0;
+    return tsdfs_bounds_workspace_size(n_rays) + (size_t)kMeanBlocks * (sizeof(double) + sizeof(unsigned long long)) +
+           3 * 256;
+}
+
+extern "C" int tsdf_adaptive_counts(const float* t_n, const float* t_f, const uint8_t* status, int64_t n_rays,
+                                    float n_mean, int32_t n_min, int32_t n_max, int32_t n_fallback,
+                                    int32_t* n_samples, int32_t* offsets, float* mean_len, void* ws, size_t ws_bytes,
+                                    tsdfs_stream_t stream) {
+    if (n_rays < 0 || n_rays > (int64_t)INT32_MAX) return fail(TSDFS_E_INVALID, "n_rays must be in [0, 2^31)");
+    if (!(n_mean > 0.0f) || !(n_mean <= 4096.0f)) return fail(TSDFS_E_INVALID, "n_mean must be in (0, 4096]");
+    if (n_min < 1 || n_max < n_min || n_max > 4096) return fail(TSDFS_E_INVALID, "need 1 <= n_min <= n_max <= 4096");
+    if (n_fallback < 0 || n_fallback > 4096) return fail(TSDFS_E_INVALID, "n_fallback must be in [0, 4096]");
+    if ((int64_t)(n_max > n_fallback ? n_max : n_fallback) * n_rays > (int64_t)INT32_MAX)
+        return fail(TSDFS_E_INVALID, "sample total could overflow int32 offsets");
+    if (n_rays > 0 && (!t_n || !t_f || !status || !n_samples))
+        return fail(TSDFS_E_INVALID, "bound, status and count pointers must be non-NULL");
+    if (!offsets) return fail(TSDFS_E_INVALID, "offsets is NULL");
+    if (!ws || ws_bytes < tsdfs_adaptive_counts_workspace_size(n_rays))
+        return fail(TSDFS_E_WORKSPACE, "adaptive counts workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    uintptr_t p = (reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255);
+    int32_t* sums = reinterpret_cast<int32_t*>(p);
+    p = (p + (size_t)(scan_chunks(n_rays) + 1) * sizeof(int32_t) + 255) & ~uintptr_t(255);
+    double* part_sum = reinterpret_cast<double*>(p);
+    unsigned long long* part_cnt = reinterpret_cast<unsigned long long*>(p + kMeanBlocks * sizeof(double));
+    float* spacing = reinterpret_cast<float*>(p + kMeanBlocks * (sizeof(double) + sizeof(unsigned long long)));
+    if (n_rays > 0) {
+        ProfScope ps("adaptive_counts", st);
+        k_len_partials<<<kMeanBlocks, kMeanThreads, 0, st>>>(t_n, t_f, status, n_rays, part_sum, part_cnt);
+        k_len_mean<<<1, kMeanBlocks, 0, st>>>(part_sum, part_cnt, n_mean, mean_len, spacing);
+        k_adaptive_counts<<<grid_1d(n_rays, 256), 256, 0, st>>>(t_n, t_f, status, n_rays, spacing, n_min, n_max,
+                                                                n_fallback, n_samples);
+        int rc = cuda_check(cudaGetLastError(), "adaptive counts launch");
+        if (rc) return rc;
+    } else if (mean_len) {
+        int rc = cuda_check(cudaMemsetAsync(mean_len, 0, sizeof(float), st), "adaptive counts memset");
+        if (rc) return rc;
+    }
+    return exclusive_scan(n_samples, n_rays, offsets, sums, st);
+}

@@ -18,6 +18,10 @@ int cuda_check(cudaError_t e, const char* what);
 // device status word of the current device (TSDFS_DEV_* bits), see abi.cu
 uint32_t* device_status_word();
 
+// exclusive scan of n counts into offsets[0..n]; `sums` needs scan_chunks(n) + 1 ints (bounds.cu)
+int64_t scan_chunks(int64_t n);
+int exclusive_scan(const int32_t* cnt, int64_t n, int32_t* offsets, int32_t* sums, cudaStream_t st);
+
 // kernel timing (tsdfs_profile): brackets the launches in its scope with events
 void prof_begin(const char* name, cudaStream_t st, void** token);
 void prof_end(void* token, cudaStream_t st);
@@ -107,7 +111,7 @@ static_assert(sizeof(SampleRec) == 48, "record layout");
 // how the network kernel finds a sample's ray, t and delta
 enum SampleMode : int {
     kUniform = 0,   // ragged offsets, midpoints of [t_n, t_f]
-    kExplicit = 1,  // t[g], delta[g] given, ray = g / per_ray
+    kExplicit = 1,  // t[g], delta[g] given, ray = sample_ray[g] if given, else g / per_ray
 };
 
 struct NetParams {
@@ -126,16 +130,28 @@ struct SampleSource {
     const float* t_n;
     const float* t_f;
     int64_t n_rays;
-    const int32_t* sample_ray;  // optional: ray of every sample (else a binary search of offsets)
+    const int32_t* sample_ray;  // optional: ray of every sample (else a binary search of offsets /
+                                // g / per_ray)
     // kExplicit
     const float* t;
     const float* delta;
     int per_ray;
-    // total sample count: *total_dev (uniform, = offsets[n_rays]) or total_host
+    // total sample count: *total_dev when given (uniform: = offsets[n_rays]), else total_host
     const int32_t* total_dev;
     int64_t total_host;
     int64_t capacity;  // records available in the workspace
 };
+
+__device__ __forceinline__ int64_t sample_total(const SampleSource& s) {
+    return s.total_dev ? (int64_t)__ldg(s.total_dev) : s.total_host;
+}
+
+// host-side upper bound on the sample total (sizes persistent grids)
+inline int64_t sample_bound(const SampleSource& s) { return s.total_dev ? s.capacity : s.total_host; }
+
+__device__ __forceinline__ int64_t explicit_ray(const SampleSource& s, int64_t g) {
+    return s.sample_ray ? (int64_t)__ldg(s.sample_ray + g) : g / s.per_ray;
+}
 
 __device__ __forceinline__ int64_t find_ray(const int32_t* __restrict__ offsets, int64_t n_rays, int64_t g) {
     // largest r with offsets[r] <= g (offsets non-decreasing, offsets[0] = 0)

@@ -1,5 +1,6 @@
 // Volume-rendering compositing (Eq. 1, Eq. 2, the rendered normal) with NeuS
-// opacity, and the per-ray steps of the 64 + 32 hierarchical comparator.
+// opacity, and the per-ray steps of the hierarchical comparator (n_c coarse +
+// n_f inverse-CDF fine samples; 64 + 32 is the comparator of Tab. 2).
 #include "common.cuh"
 
 namespace tsdfs {
@@ -7,9 +8,9 @@ namespace tsdfs {
 namespace {
 
 constexpr int kCompBlock = 128;
-constexpr int kCoarse = 64;
-constexpr int kFine = 32;
-constexpr int kHier = kCoarse + kFine;
+constexpr int kMaxCoarse = 64;
+constexpr int kMaxFine = 32;
+constexpr int kMaxHier = kMaxCoarse + kMaxFine;
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
 
@@ -102,7 +103,7 @@ struct BoxDev {
 __global__ void k_hier_setup(BoxDev box, const float* __restrict__ ray_o, const float* __restrict__ ray_d,
                              int64_t n_rays, float t_near, float t_far, float* __restrict__ t0_out,
                              float* __restrict__ te_out, uint8_t* __restrict__ status, float* __restrict__ tc,
-                             float* __restrict__ dc) {
+                             float* __restrict__ dc, int n_c) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
         float o[3], d[3];
 #pragma unroll
@@ -116,70 +117,152 @@ __global__ void k_hier_setup(BoxDev box, const float* __restrict__ ray_o, const 
         t0_out[r] = t0;
         te_out[r] = te;
         status[r] = ok ? TSDFS_FALLBACK : TSDFS_MISS;
-        const float dl = (te - t0) / (float)kCoarse;
-        for (int j = 0; j < kCoarse; ++j) {
-            tc[r * kCoarse + j] = t0 + ((float)j + 0.5f) * dl;
-            dc[r * kCoarse + j] = dl;
+        const float dl = (te - t0) / (float)n_c;
+        for (int j = 0; j < n_c; ++j) {
+            tc[r * n_c + j] = t0 + ((float)j + 0.5f) * dl;
+            dc[r * n_c + j] = dl;
         }
     }
 }
 
-// Section weights from the coarse SDF values, 32 inverse-CDF samples, merge,
-// and section widths with boundaries halfway between sorted neighbours.
+// Weight of the section [z0, z1] between two coarse samples from their SDF
+// values alone (NeuS up-sampling opacity): slope min(own, previous) clipped to
+// [-1e3, 0], section ends at mid -/+ slope * dz / 2; T carries the
+// transmittance, prev_slope the previous section's slope.
+__device__ __forceinline__ float section_weight(float f0, float f1, float z0, float z1, float inv_s, float eps,
+                                                float& T, float& prev_slope) {
+    const float dz = z1 - z0;
+    const float mid = 0.5f * (f0 + f1);
+    const float slope = dz > 0.0f ? (f1 - f0) / dz : 0.0f;
+    float c = fminf(slope, prev_slope);
+    c = fminf(fmaxf(c, -1e3f), 0.0f);
+    prev_slope = slope;
+    const float p_lo = sigmoidf_(inv_s * (mid - 0.5f * c * dz));
+    const float p_hi = sigmoidf_(inv_s * (mid + 0.5f * c * dz));
+    float alpha = (p_lo - p_hi + eps) / (p_lo + eps);
+    alpha = fminf(fmaxf(alpha, 0.0f), 1.0f);
+    const float w = alpha * T;
+    T *= 1.0f - alpha;
+    return w;
+}
+
+// n_f inverse-CDF samples at u_k = (k + 1/2)/n_f over the c - 1 sections of the
+// coarse samples zat(0) < ... < zat(c-1) (c >= 2), pdf ~ w + 1e-5, linear within
+// a section.  Two passes over the sections (the normaliser, then the samples
+// in increasing u) so that no per-ray table is kept.
+template <class Z, class F>
+__device__ __forceinline__ void fine_from_coarse(Z zat, F fat, int c, float inv_s, float eps, int n_f, float* fine) {
+    float T = 1.0f, prev_slope = 0.0f, psum = 0.0f;
+    for (int j = 0; j < c - 1; ++j)
+        psum += section_weight(fat(j), fat(j + 1), zat(j), zat(j + 1), inv_s, eps, T, prev_slope) + 1e-5f;
+    const float inv_sum = 1.0f / psum;
+    T = 1.0f;
+    prev_slope = 0.0f;
+    float cum = 0.0f;
+    int k = 0;
+    for (int j = 0; j < c - 1 && k < n_f; ++j) {
+        const float z0 = zat(j), z1 = zat(j + 1);
+        const float cnext = cum + (section_weight(fat(j), fat(j + 1), z0, z1, inv_s, eps, T, prev_slope) + 1e-5f);
+        const float c0 = cum * inv_sum, c1 = cnext * inv_sum;
+        const bool last = j == c - 2;
+        while (k < n_f) {
+            const float u = ((float)k + 0.5f) / (float)n_f;
+            if (!last && c1 <= u) break;
+            const float p = c1 - c0;
+            fine[k++] = p > 0.0f ? z0 + (u - c0) / p * (z1 - z0) : z0;
+        }
+        cum = cnext;
+    }
+}
+
+// Merge the ascending coarse (zat) and fine samples and hand each merged sample
+// with its section width (boundaries halfway between sorted neighbours, the
+// outer ones at lo and hi) to emit(i, t, delta).
+template <class Z, class E>
+__device__ __forceinline__ void merge_emit(Z zat, int c, const float* fine, int n_f, float lo, float hi, E emit) {
+    const int m = c + n_f;
+    int a = 0, b = 0;
+    auto pick = [&]() {
+        const bool take_c = b >= n_f || (a < c && zat(a) <= fine[b]);
+        return take_c ? zat(a++) : fine[b++];
+    };
+    float prev = 0.0f, cur = m > 0 ? pick() : 0.0f;
+    for (int i = 0; i < m; ++i) {
+        const float next = i + 1 < m ? pick() : 0.0f;
+        const float bl = i == 0 ? lo : 0.5f * (prev + cur);
+        const float bh = i == m - 1 ? hi : 0.5f * (cur + next);
+        emit(i, cur, bh - bl);
+        prev = cur;
+        cur = next;
+    }
+}
+
+// Comparator: n_c coarse values -> n_f fine samples -> n_c + n_f merged samples per ray.
 __global__ void k_hier_fine(const float* __restrict__ fcoarse, const float* __restrict__ tc,
                             const float* __restrict__ t0_in, const float* __restrict__ te_in, int64_t n_rays,
-                            float inv_s, float eps, float* __restrict__ t_out, float* __restrict__ d_out) {
+                            float inv_s, float eps, float* __restrict__ t_out, float* __restrict__ d_out, int n_c,
+                            int n_f) {
+    const int n_h = n_c + n_f;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
-        const float* f = fcoarse + r * kCoarse;
-        const float* z = tc + r * kCoarse;
-        float cdf[kCoarse];
-        // section weights w_j (j < 63) -> pdf ~ w + 1e-5 -> cdf[0..63]
-        float T = 1.0f, prev_slope = 0.0f, psum = 0.0f;
-        cdf[0] = 0.0f;
-        for (int j = 0; j < kCoarse - 1; ++j) {
-            const float f0 = __ldg(f + j), f1 = __ldg(f + j + 1);
-            const float z0 = __ldg(z + j), z1 = __ldg(z + j + 1);
-            const float dz = z1 - z0;
-            const float mid = 0.5f * (f0 + f1);
-            const float slope = dz > 0.0f ? (f1 - f0) / dz : 0.0f;
-            float c = fminf(slope, prev_slope);
-            c = fminf(fmaxf(c, -1e3f), 0.0f);
-            prev_slope = slope;
-            const float p_lo = sigmoidf_(inv_s * (mid - 0.5f * c * dz));
-            const float p_hi = sigmoidf_(inv_s * (mid + 0.5f * c * dz));
-            float alpha = (p_lo - p_hi + eps) / (p_lo + eps);
-            alpha = fminf(fmaxf(alpha, 0.0f), 1.0f);
-            const float w = alpha * T;
-            T *= 1.0f - alpha;
-            psum += w + 1e-5f;
-            cdf[j + 1] = psum;
+        const float* f = fcoarse + r * n_c;
+        const float* z = tc + r * n_c;
+        auto zat = [&](int j) { return __ldg(z + j); };
+        auto fat = [&](int j) { return __ldg(f + j); };
+        float fine[kMaxFine];
+        fine_from_coarse(zat, fat, n_c, inv_s, eps, n_f, fine);
+        float* to = t_out + r * n_h;
+        float* dout = d_out + r * n_h;
+        merge_emit(zat, n_c, fine, n_f, __ldg(t0_in + r), __ldg(te_in + r), [&](int i, float t, float dl) {
+            to[i] = t;
+            dout[i] = dl;
+        });
+    }
+}
+
+// Coarse + fine inside the TSDF bound: ray r has c = offsets[r+1] - offsets[r]
+// coarse midpoints of [t_n, t_f] (values in fcoarse[offsets[r] ..]); its
+// c + n_f merged samples go to offsets2[r] .. with their ray index.  With one
+// coarse sample there are no sections: the fine samples are the midpoints of
+// n_f equal parts of [t_n, t_f].
+__global__ void k_bounded_fine(const float* __restrict__ fcoarse, const int32_t* __restrict__ offsets,
+                               const float* __restrict__ t_n, const float* __restrict__ t_f,
+                               const int32_t* __restrict__ offsets2, int64_t n_rays, int n_f, float inv_s, float eps,
+                               int64_t max_coarse, int64_t capacity2, float* __restrict__ t_out,
+                               float* __restrict__ d_out, int32_t* __restrict__ ray_out) {
+    // over capacity: the network kernels flag it; nothing is written here
+    if ((int64_t)__ldg(offsets + n_rays) > max_coarse || (int64_t)__ldg(offsets2 + n_rays) > capacity2) return;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t base = __ldg(offsets + r);
+        const int c = __ldg(offsets + r + 1) - base;
+        if (c <= 0) continue;
+        const float lo = __ldg(t_n + r), hi = __ldg(t_f + r);
+        const float dl = (hi - lo) / (float)c;
+        auto zat = [&](int j) { return lo + ((float)j + 0.5f) * dl; };
+        auto fat = [&](int j) { return __ldg(fcoarse + base + j); };
+        float fine[kMaxFine];
+        if (c >= 2) {
+            fine_from_coarse(zat, fat, c, inv_s, eps, n_f, fine);
+        } else {
+            const float df = (hi - lo) / (float)n_f;
+            for (int k = 0; k < n_f; ++k) fine[k] = lo + ((float)k + 0.5f) * df;
         }
-        const float inv_sum = 1.0f / psum;
-        // inverse CDF at u_k = (k + 1/2)/32 (u increasing -> samples increasing)
-        float fine[kFine];
-        int j = 0;
-        for (int k = 0; k < kFine; ++k) {
-            const float u = ((float)k + 0.5f) / (float)kFine;
-            while (j < kCoarse - 2 && cdf[j + 1] * inv_sum <= u) ++j;
-            const float c0 = cdf[j] * inv_sum, c1 = cdf[j + 1] * inv_sum;
-            const float p = c1 - c0;
-            const float z0 = __ldg(z + j), z1 = __ldg(z + j + 1);
-            fine[k] = p > 0.0f ? z0 + (u - c0) / p * (z1 - z0) : z0;
-        }
-        // merge 64 coarse + 32 fine (both ascending)
-        float ts[kHier];
-        int a = 0, b = 0;
-        for (int i = 0; i < kHier; ++i) {
-            const bool take_c = b >= kFine || (a < kCoarse && __ldg(z + a) <= fine[b]);
-            ts[i] = take_c ? __ldg(z + a++) : fine[b++];
-        }
-        const float lo = __ldg(t0_in + r), hi = __ldg(te_in + r);
-        for (int i = 0; i < kHier; ++i) {
-            const float bl = i == 0 ? lo : 0.5f * (ts[i - 1] + ts[i]);
-            const float bh = i == kHier - 1 ? hi : 0.5f * (ts[i] + ts[i + 1]);
-            t_out[r * kHier + i] = ts[i];
-            d_out[r * kHier + i] = bh - bl;
-        }
+        const int64_t b2 = __ldg(offsets2 + r);
+        merge_emit(zat, c, fine, n_f, lo, hi, [&](int i, float t, float w) {
+            t_out[b2 + i] = t;
+            d_out[b2 + i] = w;
+            ray_out[b2 + i] = (int32_t)r;
+        });
+    }
+}
+
+// merged count per ray: c + n_f for rays with coarse samples, else 0; all 0 when
+// the coarse total exceeds max_coarse (the coarse pass flags that overflow)
+__global__ void k_bounded_counts(const int32_t* __restrict__ offsets, int64_t n_rays, int n_f, int64_t max_coarse,
+                                 int32_t* __restrict__ n2) {
+    const bool over = (int64_t)__ldg(offsets + n_rays) > max_coarse;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
+        const int c = __ldg(offsets + r + 1) - __ldg(offsets + r);
+        n2[r] = (!over && c > 0) ? c + n_f : 0;
     }
 }
 
@@ -213,16 +296,36 @@ int launch_composite(const SampleRec* rec, const int32_t* offsets, int per_ray, 
 }
 
 int launch_hier_setup(const tsdfs_grid* g, const float* ray_o, const float* ray_d, int64_t n_rays, float t_near,
-                      float t_far, float* t0, float* te, uint8_t* status, float* tc, float* dc, cudaStream_t st) {
+                      float t_far, float* t0, float* te, uint8_t* status, float* tc, float* dc, int n_c,
+                      cudaStream_t st) {
+    if (n_c < 2 || n_c > kMaxCoarse) return fail(TSDFS_E_INVALID, "coarse sample count must be in [2, 64]");
     BoxDev box{{g->origin[0], g->origin[1], g->origin[2]}, {g->nx, g->ny, g->nz}, g->voxel_size};
-    k_hier_setup<<<grid_1d(n_rays, 128), 128, 0, st>>>(box, ray_o, ray_d, n_rays, t_near, t_far, t0, te, status, tc, dc);
+    k_hier_setup<<<grid_1d(n_rays, 128), 128, 0, st>>>(box, ray_o, ray_d, n_rays, t_near, t_far, t0, te, status, tc, dc,
+                                                       n_c);
     return cuda_check(cudaGetLastError(), "hier setup launch");
 }
 
 int launch_hier_fine(const float* fcoarse, const float* tc, const float* t0, const float* te, int64_t n_rays,
-                     float inv_s, float eps, float* t_out, float* d_out, cudaStream_t st) {
-    k_hier_fine<<<grid_1d(n_rays, 128), 128, 0, st>>>(fcoarse, tc, t0, te, n_rays, inv_s, eps, t_out, d_out);
+                     float inv_s, float eps, float* t_out, float* d_out, int n_c, int n_f, cudaStream_t st) {
+    if (n_c < 2 || n_c > kMaxCoarse || n_f < 1 || n_f > kMaxFine)
+        return fail(TSDFS_E_INVALID, "sample counts must be coarse in [2, 64], fine in [1, 32]");
+    k_hier_fine<<<grid_1d(n_rays, 128), 128, 0, st>>>(fcoarse, tc, t0, te, n_rays, inv_s, eps, t_out, d_out, n_c, n_f);
     return cuda_check(cudaGetLastError(), "hier fine launch");
+}
+
+int launch_bounded_counts(const int32_t* offsets, int64_t n_rays, int n_f, int64_t max_coarse, int32_t* n2,
+                          cudaStream_t st) {
+    k_bounded_counts<<<grid_1d(n_rays, 256), 256, 0, st>>>(offsets, n_rays, n_f, max_coarse, n2);
+    return cuda_check(cudaGetLastError(), "bounded counts launch");
+}
+
+int launch_bounded_fine(const float* fcoarse, const int32_t* offsets, const float* t_n, const float* t_f,
+                        const int32_t* offsets2, int64_t n_rays, int n_f, float inv_s, float eps, int64_t max_coarse,
+                        int64_t capacity2, float* t_out, float* d_out, int32_t* ray_out, cudaStream_t st) {
+    if (n_f < 0 || n_f > kMaxFine) return fail(TSDFS_E_INVALID, "fine sample count must be in [0, 32]");
+    k_bounded_fine<<<grid_1d(n_rays, 128), 128, 0, st>>>(fcoarse, offsets, t_n, t_f, offsets2, n_rays, n_f, inv_s, eps,
+                                                         max_coarse, capacity2, t_out, d_out, ray_out);
+    return cuda_check(cudaGetLastError(), "bounded fine launch");
 }
 
 }  // namespace tsdfs

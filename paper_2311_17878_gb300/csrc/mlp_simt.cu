@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_full(NetParams np, SampleSo
     using A = Arch<ARCH>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
-    int64_t total = src.mode == kUniform ? (int64_t)__ldg(src.total_dev) : src.total_host;
+    int64_t total = sample_total(src);
     if (total > src.capacity) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(dev_status, TSDFS_DEV_SAMPLES_OVERFLOW);
         return;
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_full(NetParams np, SampleSo
                     dl = (tf - tn) / (float)n;
                     t = tn + ((float)i + 0.5f) * dl;
                 } else {
-                    r = g / src.per_ray;
+                    r = explicit_ray(src, g);
                     t = __ldg(src.t + g);
                     dl = __ldg(src.delta + g);
                 }
@@ -360,11 +360,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_full(NetParams np, SampleSo
 
 // SDF values only (hierarchical coarse pass): 4*kTS samples per tile, one row each.
 template <int ARCH>
-__global__ void __launch_bounds__(kThreads, 1) k_mlp_value(NetParams np, SampleSource src, float* __restrict__ f_out) {
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_value(NetParams np, SampleSource src, float* __restrict__ f_out,
+                                                           uint32_t* dev_status) {
     using A = Arch<ARCH>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
-    const int64_t total = src.total_host;
+    const int64_t total = sample_total(src);
+    if (total > src.capacity) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(dev_status, TSDFS_DEV_SAMPLES_OVERFLOW);
+        return;
+    }
     constexpr int TS = 4 * kTS;
     const int64_t n_tiles = (total + TS - 1) / TS;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -373,8 +378,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_value(NetParams np, SampleS
             const int s = threadIdx.x;
             const int64_t g = tile * TS + s;
             const bool ok = g < total;
-            const int64_t r = ok ? g / src.per_ray : 0;
-            const float t = ok ? __ldg(src.t + g) : 0.0f;
+            int64_t r = 0;
+            float t = 0.0f;
+            if (ok) {
+                if (src.mode == kUniform) {
+                    r = src.sample_ray ? (int64_t)__ldg(src.sample_ray + g) : find_ray(src.offsets, src.n_rays, g);
+                    const int i = (int)(g - __ldg(src.offsets + r));
+                    const int n = __ldg(src.offsets + r + 1) - __ldg(src.offsets + r);
+                    const float tn = __ldg(src.t_n + r), tf = __ldg(src.t_f + r);
+                    const float dl = (tf - tn) / (float)n;
+                    t = tn + ((float)i + 0.5f) * dl;
+                } else {
+                    r = explicit_ray(src, g);
+                    t = __ldg(src.t + g);
+                }
+            }
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const float x = __ldg(src.ray_o + 3 * r + a) + t * __ldg(src.ray_d + 3 * r + a);
@@ -444,8 +462,8 @@ template <int ARCH>
 int launch_mlp_value_simt(const NetParams& np, const SampleSource& src, float* f_out, cudaStream_t st) {
     int rc = ensure_attrs<ARCH>();
     if (rc) return rc;
-    k_mlp_value<ARCH><<<persistent_blocks((src.total_host + 4 * kTS - 1) / (4 * kTS)), kThreads, sizeof(Smem), st>>>(
-        np, src, f_out);
+    k_mlp_value<ARCH><<<persistent_blocks((sample_bound(src) + 4 * kTS - 1) / (4 * kTS)), kThreads, sizeof(Smem), st>>>(
+        np, src, f_out, device_status_word());
     return cuda_check(cudaGetLastError(), "mlp value launch");
 }
 

@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
     float* s_pd = s_pe + kTileS * A::kPeSdf * 6;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    const int64_t total = p.src.mode == kUniform ? (int64_t)__ldg(p.src.total_dev) : p.src.total_host;
+    const int64_t total = sample_total(p.src);
     if (total > p.src.capacity) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(p.status, TSDFS_DEV_SAMPLES_OVERFLOW);
         return;
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                             dl = (tf - tn) / (float)(o1 - o0);
                             t = tn + ((float)(g - o0) + 0.5f) * dl;
                         } else {
-                            ray = g / p.src.per_ray;
+                            ray = explicit_ray(p.src, g);
                             t = __ldg(p.src.t + g);
                             dl = __ldg(p.src.delta + g);
                         }
@@ -876,7 +876,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
     const uint32_t bar_acc = smem_u32(bars + 2 * kStages), bar_a = smem_u32(bars + 2 * kStages + 1);
     const uint32_t bar_drain = smem_u32(bars + 2 * kStages + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t total = p.src.total_host;
+    const int64_t total = sample_total(p.src);
+    if (total > p.src.capacity) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(p.status, TSDFS_DEV_SAMPLES_OVERFLOW);
+        return;
+    }
     const int64_t n_tiles = (total + kTileV - 1) / kTileV;
     if ((int64_t)blockIdx.x >= n_tiles) return;
     if (threadIdx.x == 0) {
@@ -979,8 +983,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
         for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
             const int64_t g = tile * kTileV + r;
             const bool valid = g < total;
-            const int64_t ray = valid ? g / p.src.per_ray : 0;
-            const float t = valid ? __ldg(p.src.t + g) : 0.0f;
+            int64_t ray = 0;
+            float t = 0.0f;
+            if (valid) {
+                if (p.src.mode == kUniform) {
+                    ray = __ldg(p.src.sample_ray + g);
+                    const int32_t o0 = __ldg(p.src.offsets + ray), o1 = __ldg(p.src.offsets + ray + 1);
+                    const float tn = __ldg(p.src.t_n + ray), tf = __ldg(p.src.t_f + ray);
+                    const float dl = (tf - tn) / (float)(o1 - o0);
+                    t = tn + ((float)(g - o0) + 0.5f) * dl;
+                } else {
+                    ray = explicit_ray(p.src, g);
+                    t = __ldg(p.src.t + g);
+                }
+            }
             float xt[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -1074,7 +1090,8 @@ int launch_tc_value(const tsdfs_mlp* m, const SampleSource& src, float* f_out, c
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t tiles = (src.total_host + kTileV - 1) / kTileV;
+    if (src.mode == kUniform && !src.sample_ray) return fail(TSDFS_E_INVALID, "value pass needs the sample ray index");
+    const int64_t tiles = (sample_bound(src) + kTileV - 1) / kTileV;
     const unsigned blocks = (unsigned)(tiles < sms ? (tiles < 1 ? 1 : tiles) : sms);
     k_mlp_tc_value<ARCH, F16><<<blocks, kThreads, smem, st>>>(p, f_out);
     return cuda_check(cudaGetLastError(), "mlp_tc_value launch");

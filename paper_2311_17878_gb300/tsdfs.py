@@ -32,10 +32,11 @@ TSDFS_DEV_SAMPLES_OVERFLOW, TSDFS_DEV_MARCH_CAP, TSDFS_DEV_TIMEOUT, TSDFS_DEV_NO
 
 EXPORTS = ["tsdfs_last_error", "tsdfs_sync_status", "tsdfs_grid_init", "tsdf_integrate", "tsdfs_inside_mask_words",
            "tsdfs_inside_mask", "tsdfs_bounds_workspace_size", "tsdf_ray_bounds", "tsdfs_render_workspace_size",
-           "render_rays", "tsdfs_hier_workspace_size", "render_rays_hier96", "tsdfs_backward_workspace_size",
+           "render_rays", "tsdfs_hier_workspace_size", "render_rays_hier", "render_rays_hier96", "tsdfs_backward_workspace_size",
            "render_rays_backward", "tsdfs_packed_size", "tsdfs_pack_mlp", "tsdfs_sdf_param_count",
            "tsdfs_rgb_param_count", "tsdf_ray_bounds_noalloc", "tsdf_ray_bounds_noalloc_max_rays",
-           "tsdf_recovery_bounds", "tsdf_recovery_merge", "tsdfs_check_mlp", "tsdfs_profile", "tsdfs_profile_read"]
+           "tsdf_recovery_bounds", "tsdf_recovery_merge", "tsdfs_check_mlp", "tsdfs_adaptive_counts_workspace_size",
+           "tsdf_adaptive_counts", "tsdfs_hier_bounded_workspace_size", "render_rays_hier_bounded", "tsdfs_profile", "tsdfs_profile_read"]
 
 
 class TsdfsError(RuntimeError):
@@ -70,13 +71,16 @@ def lib():
             L = C.CDLL(LIB_PATH)
             L.tsdfs_last_error.restype = C.c_char_p
             for name in ["tsdfs_bounds_workspace_size", "tsdfs_render_workspace_size", "tsdfs_hier_workspace_size",
-                         "tsdfs_backward_workspace_size", "tsdfs_packed_size"]:
+                         "tsdfs_backward_workspace_size", "tsdfs_packed_size", "tsdfs_adaptive_counts_workspace_size",
+                         "tsdfs_hier_bounded_workspace_size"]:
                 getattr(L, name).restype = C.c_size_t
             for name in ["tsdfs_inside_mask_words", "tsdfs_sdf_param_count", "tsdfs_rgb_param_count"]:
                 getattr(L, name).restype = C.c_int64
             L.tsdfs_bounds_workspace_size.argtypes = [C.c_int64]
             L.tsdfs_render_workspace_size.argtypes = [C.c_void_p, C.c_int64, C.c_int64]
             L.tsdfs_hier_workspace_size.argtypes = [C.c_void_p, C.c_int64]
+            L.tsdfs_adaptive_counts_workspace_size.argtypes = [C.c_int64]
+            L.tsdfs_hier_bounded_workspace_size.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_int64]
             L.tsdfs_backward_workspace_size.argtypes = [C.c_void_p, C.c_int64, C.c_int64]
             L.tsdfs_packed_size.argtypes = [C.c_int32]
             L.tsdfs_sdf_param_count.argtypes = [C.c_int32]
@@ -207,11 +211,45 @@ def tsdfs_hier_workspace_size(mlp: "Mlp", n_rays: int) -> int:
     return int(lib().tsdfs_hier_workspace_size(C.byref(mlp.c), C.c_int64(n_rays)))
 
 
+def render_rays_hier(mlp: "Mlp", grid: "Grid", ray_o, ray_d, n_coarse, n_fine, t_near, t_far, rgb, depth, wsum, normal,
+                     workspace):
+    n = ray_o.shape[0]
+    _check(lib().render_rays_hier(C.byref(mlp.c), C.byref(grid.c), _p(ray_o), _p(ray_d), C.c_int64(n),
+                                  C.c_int(n_coarse), C.c_int(n_fine), C.c_float(t_near), C.c_float(t_far), _p(rgb),
+                                  _p(depth), _p(wsum), _p(normal), _p(workspace), C.c_size_t(workspace.numel()),
+                                  _stream()))
+
+
 def render_rays_hier96(mlp: "Mlp", grid: "Grid", ray_o, ray_d, t_near, t_far, rgb, depth, wsum, normal, workspace):
     n = ray_o.shape[0]
     _check(lib().render_rays_hier96(C.byref(mlp.c), C.byref(grid.c), _p(ray_o), _p(ray_d), C.c_int64(n),
                                     C.c_float(t_near), C.c_float(t_far), _p(rgb), _p(depth), _p(wsum), _p(normal),
                                     _p(workspace), C.c_size_t(workspace.numel()), _stream()))
+
+
+def tsdfs_adaptive_counts_workspace_size(n_rays: int) -> int:
+    return int(lib().tsdfs_adaptive_counts_workspace_size(C.c_int64(n_rays)))
+
+
+def tsdf_adaptive_counts(t_n, t_f, status, n_mean, n_min, n_max, n_fallback, n_samples, offsets, mean_len, workspace):
+    n = t_n.shape[0]
+    _check(lib().tsdf_adaptive_counts(_p(t_n), _p(t_f), _p(status), C.c_int64(n), C.c_float(n_mean), C.c_int32(n_min),
+                                      C.c_int32(n_max), C.c_int32(n_fallback), _p(n_samples), _p(offsets),
+                                      _p(mean_len), _p(workspace), C.c_size_t(workspace.numel()), _stream()))
+
+
+def tsdfs_hier_bounded_workspace_size(mlp: "Mlp", n_rays: int, n_fine: int, max_coarse: int) -> int:
+    return int(lib().tsdfs_hier_bounded_workspace_size(C.byref(mlp.c), C.c_int64(n_rays), C.c_int32(n_fine),
+                                                       C.c_int64(max_coarse)))
+
+
+def render_rays_hier_bounded(mlp: "Mlp", ray_o, ray_d, t_n, t_f, offsets, status, n_fine, max_coarse, rgb, depth, wsum,
+                             normal, workspace):
+    n = ray_o.shape[0]
+    _check(lib().render_rays_hier_bounded(C.byref(mlp.c), _p(ray_o), _p(ray_d), _p(t_n), _p(t_f), _p(offsets),
+                                          _p(status), C.c_int64(n), C.c_int32(n_fine), C.c_int64(max_coarse), _p(rgb),
+                                          _p(depth), _p(wsum), _p(normal), _p(workspace),
+                                          C.c_size_t(workspace.numel()), _stream()))
 
 
 def tsdfs_backward_workspace_size(mlp: "Mlp", n_rays: int, max_samples: int) -> int:
@@ -400,16 +438,56 @@ class Recovery:
         return out
 
 
-class HierRenderer:
-    def __init__(self, mlp: Mlp, n_rays, device="cuda"):
+class AdaptiveCounts:
+    """Counts relative to the mean interval (tsdf_adaptive_counts) for the bounds
+    of a batch: ``apply`` returns a ``Bounds`` view sharing the input's t_n, t_f and
+    status with the new counts and offsets."""
+
+    def __init__(self, n, device="cuda"):
+        self.n = torch.empty(n, dtype=torch.int32, device=device)
+        self.offsets = torch.empty(n + 1, dtype=torch.int32, device=device)
+        self.mean_len = torch.empty(1, dtype=torch.float32, device=device)
+        self.workspace = _bytes(tsdfs_adaptive_counts_workspace_size(n), device)
+
+    def apply(self, b: Bounds, n_mean, n_min=2, n_max=64, n_fallback=64):
+        tsdf_adaptive_counts(b.t_n, b.t_f, b.status, n_mean, n_min, n_max, n_fallback, self.n, self.offsets,
+                             self.mean_len, self.workspace)
+        out = Bounds.__new__(Bounds)
+        out.t_n, out.t_f, out.status, out.t_zero = b.t_n, b.t_f, b.status, b.t_zero
+        out.n, out.offsets, out.workspace = self.n, self.offsets, None
+        return out
+
+
+class HierBoundedRenderer:
+    """Coarse + fine inside the TSDF bound (render_rays_hier_bounded): the bounds'
+    counts are the coarse samples, ``n_fine`` inverse-CDF samples are added per ray."""
+
+    def __init__(self, mlp: Mlp, n_rays, n_fine, max_coarse, device="cuda"):
         self.mlp = mlp
+        self.n_fine, self.max_coarse = int(n_fine), int(max_coarse)
+        self.out = RenderOut(n_rays, device)
+        self.workspace = _bytes(tsdfs_hier_bounded_workspace_size(mlp, n_rays, self.n_fine, self.max_coarse), device)
+
+    def render(self, rays_o, rays_d, b: Bounds):
+        o = self.out
+        render_rays_hier_bounded(self.mlp, rays_o, rays_d, b.t_n, b.t_f, b.offsets, b.status, self.n_fine,
+                                 self.max_coarse, o.rgb, o.depth, o.wsum, o.normal, self.workspace)
+        return o
+
+
+class HierRenderer:
+    """The hierarchical comparator: n_coarse uniform + n_fine inverse-CDF samples per ray (64 + 32 by default)."""
+
+    def __init__(self, mlp: Mlp, n_rays, device="cuda", n_coarse=64, n_fine=32):
+        self.mlp = mlp
+        self.n_coarse, self.n_fine = int(n_coarse), int(n_fine)
         self.out = RenderOut(n_rays, device)
         self.workspace = _bytes(tsdfs_hier_workspace_size(mlp, n_rays), device)
 
     def render(self, grid: Grid, rays_o, rays_d, t_near, t_far):
         o = self.out
-        render_rays_hier96(self.mlp, grid, rays_o, rays_d, t_near, t_far, o.rgb, o.depth, o.wsum, o.normal,
-                           self.workspace)
+        render_rays_hier(self.mlp, grid, rays_o, rays_d, self.n_coarse, self.n_fine, t_near, t_far, o.rgb, o.depth,
+                         o.wsum, o.normal, self.workspace)
         return o
 
 

@@ -92,6 +92,46 @@ def test_invalid_arguments_fail_on_host(L):
                          None) == T.TSDFS_OK
 
 
+def test_hier_counts_checked_on_host(L):
+    g = _grid_struct()
+    m = T.tsdfs_mlp(0, 0, 8, 8, None, (C.c_float * 3)(0, 0, 0), 1.0, 64.0, 100.0, 1e-5)
+    v = C.c_void_p(8)
+    ws = L.tsdfs_hier_workspace_size(C.byref(m), 100)
+    for nc, nf in [(1, 8), (65, 8), (16, 0), (16, 33)]:
+        assert L.render_rays_hier(C.byref(m), C.byref(g), v, v, C.c_int64(100), nc, nf, C.c_float(0.1),
+                                  C.c_float(5.0), v, v, v, None, v, C.c_size_t(ws), None) == T.TSDFS_E_INVALID
+        assert "sample counts" in T.tsdfs_last_error()
+    # zero rays with valid counts succeed without the device
+    assert L.render_rays_hier(C.byref(m), C.byref(g), None, None, C.c_int64(0), 16, 8, C.c_float(0.1), C.c_float(5.0),
+                              None, None, None, None, None, C.c_size_t(0), None) == T.TSDFS_OK
+
+
+def test_adaptive_counts_and_bounded_hier_arguments_fail_on_host(L):
+    v = C.c_void_p(8)
+    ws = T.tsdfs_adaptive_counts_workspace_size(100)
+    args = lambda n_mean, n_min, n_max, n_fb, wsb=ws: (v, v, v, C.c_int64(100), C.c_float(n_mean), C.c_int32(n_min),
+                                                       C.c_int32(n_max), C.c_int32(n_fb), v, v, None, v,
+                                                       C.c_size_t(wsb), None)
+    for bad in [(0.0, 1, 64, 96), (float("nan"), 1, 64, 96), (6.0, 0, 64, 96), (6.0, 9, 8, 96), (6.0, 1, 5000, 96),
+                (6.0, 1, 64, -1)]:
+        assert L.tsdf_adaptive_counts(*args(*bad)) == T.TSDFS_E_INVALID
+    assert L.tsdf_adaptive_counts(*args(6.0, 1, 64, 96, 1)) == T.TSDFS_E_WORKSPACE
+    # zero rays: offsets[0] = 0 is written on the stream (needs the device), so only the
+    # workspace-size function is checked here
+    assert T.tsdfs_adaptive_counts_workspace_size(0) > 0
+    assert T.tsdfs_adaptive_counts_workspace_size(10 ** 6) > T.tsdfs_adaptive_counts_workspace_size(10)
+    m = T.tsdfs_mlp(0, 0, 8, 8, None, (C.c_float * 3)(0, 0, 0), 1.0, 64.0, 100.0, 1e-5)
+    wsh = L.tsdfs_hier_bounded_workspace_size(C.byref(m), C.c_int64(100), C.c_int32(8), C.c_int64(1000))
+    assert wsh >= (1000 + 100 * 8) * 48
+    hb = lambda n_fine, wsb=wsh, n=100: L.render_rays_hier_bounded(C.byref(m), v, v, v, v, v, v, C.c_int64(n),
+                                                                  C.c_int32(n_fine), C.c_int64(1000), v, v, v, None,
+                                                                  v, C.c_size_t(wsb), None)
+    assert hb(-1) == T.TSDFS_E_INVALID and hb(33) == T.TSDFS_E_INVALID
+    assert "fine" in T.tsdfs_last_error()
+    assert hb(8, 16) == T.TSDFS_E_WORKSPACE
+    assert hb(8, 0, 0) == T.TSDFS_OK
+
+
 def test_recovery_arguments_fail_on_host(L):
     g = _grid_struct()
     p = T.tsdfs_bounds_params(0.1, 0.0, 10.0, 0.1, 2, 15, 32, 96)

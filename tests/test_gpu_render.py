@@ -134,7 +134,11 @@ def test_ragged_counts_single_and_large():
     compare(got, ref)
 
 
-def test_tiny_hier96_f32_matches_oracle():
+@pytest.mark.parametrize("n_coarse,n_fine", [(64, 32), (16, 8), (37, 5), (2, 1)])
+def test_tiny_hier_f32_matches_oracle(n_coarse, n_fine):
+    """The hierarchical comparator at its Tab. 2 counts (64 + 32) and at
+    smaller ones, including counts that are no multiple of a tile (37 + 5)
+    and the fewest the section weights allow (2 + 1)."""
     wl = synth.tiny_workload()
     spec = synth.scene_mlp("tiny")
     bp = wl.bounds
@@ -142,13 +146,13 @@ def test_tiny_hier96_f32_matches_oracle():
     mlp = T.Mlp(spec)
     g = T.Grid(wl.grid, V=torch.zeros(wl.grid.shape_zyx, device="cuda"),
                W=torch.zeros(wl.grid.shape_zyx, dtype=torch.uint8, device="cuda"))
-    h = T.HierRenderer(mlp, 4096)
+    h = T.HierRenderer(mlp, 4096, n_coarse=n_coarse, n_fine=n_fine)
     out = h.render(g, dev(wl.rays_o), dev(wl.rays_d), bp.t_near, bp.t_far)
     torch.cuda.synchronize()
     got = {k: getattr(out, k).cpu().numpy() for k in ("rgb", "depth", "wsum", "normal")}
     live = np.nonzero(ok)[0]
     ro = orr.render_hier(orr.Net(spec), wl.rays_o[live], wl.rays_d[live], t0[live].astype(np.float64),
-                         te[live].astype(np.float64))
+                         te[live].astype(np.float64), n_coarse=n_coarse, n_fine=n_fine)
     ref = {k: ro[k].detach().numpy() for k in ("rgb", "depth", "wsum", "normal")}
     sub = {k: v[live] for k, v in got.items()}
     compare(sub, ref)
@@ -227,18 +231,23 @@ def test_render_bf16_operands_match_oracle(scene):
     assert er.max() <= 2 * bf16_factor * RGB_ABS and ed.max() <= 2 * bf16_factor * DEPTH_REL_BF16
 
 
-def test_bf16_hier96_runs_and_tracks_f32():
+@pytest.mark.parametrize("n_coarse,n_fine", [(64, 32), (24, 9)])
+def test_bf16_hier_runs_and_tracks_f32(n_coarse, n_fine):
     wl = synth.tiny_workload()
     spec = synth.scene_mlp("tiny")
     g = T.Grid(wl.grid, V=torch.zeros(wl.grid.shape_zyx, device="cuda"),
                W=torch.zeros(wl.grid.shape_zyx, dtype=torch.uint8, device="cuda"))
     outs = []
     for prec in (T.TSDFS_PREC_F32, T.TSDFS_PREC_BF16, T.TSDFS_PREC_F16):
-        h = T.HierRenderer(T.Mlp(spec, prec), 4096)
+        h = T.HierRenderer(T.Mlp(spec, prec), 4096, n_coarse=n_coarse, n_fine=n_fine)
         o = h.render(g, dev(wl.rays_o), dev(wl.rays_d), wl.bounds.t_near, wl.bounds.t_far)
         torch.cuda.synchronize()
         outs.append(o.rgb.cpu().numpy())
-    assert np.max(np.abs(outs[0] - outs[1])) < 1e-2
+    # BF16 against FP32: the FP32 colour bar scaled by the unit-roundoff ratio 2^-8 / 2^-11 at
+    # the 99th percentile, twice that at the maximum (fewer coarse samples place the fine ones
+    # from fewer, so more sensitive, section weights)
+    e_bf16 = np.abs(outs[0] - outs[1])
+    assert np.percentile(e_bf16, 99) <= 8 * RGB_ABS and e_bf16.max() <= 16 * RGB_ABS
     assert np.max(np.abs(outs[0] - outs[2])) < 5e-3
 
 

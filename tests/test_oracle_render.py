@@ -186,15 +186,19 @@ def test_inverse_cdf_matches_quantile_table():
         assert np.max(np.abs(np.interp(s[r], grid, cg) - u)) < 1e-4  # one grid cell of mass
 
 
-def test_hier_samples_sorted_in_range_and_complete():
+@pytest.mark.parametrize("n_coarse,n_fine", [(64, 32), (16, 8), (2, 1)])
+def test_hier_samples_sorted_in_range_and_complete(n_coarse, n_fine):
     wl = synth.tiny_workload()
     net = orr.Net(synth.tiny_mlp())
     o, d = wl.rays_o[1000:1040], wl.rays_d[1000:1040]
     t0 = np.full(40, 1.0)
     te = np.full(40, 3.0)
-    out = orr.render_hier(net, o, d, t0, te)
+    out = orr.render_hier(net, o, d, t0, te, n_coarse=n_coarse, n_fine=n_fine)
     t = out["t"].numpy()
-    assert t.shape == (40, 96)
+    assert t.shape == (40, n_coarse + n_fine)
+    # the coarse midpoints are all among the samples
+    zc = 1.0 + (np.arange(n_coarse) + 0.5) * (2.0 / n_coarse)
+    assert all(np.isin(zc, t[r]).all() for r in range(40))
     assert np.all(np.diff(t, axis=1) >= 0) and np.all(t > 1.0) and np.all(t < 3.0)
     assert torch.all(out["w"] >= 0) and torch.all(out["wsum"] <= 1 + 1e-12)
 
