@@ -39,6 +39,12 @@ constexpr uint32_t kBarBytes = 256;  // mbarriers, TMEM slot and abort flag
 constexpr int kEpiThreads = 256;  // warps 0-7
 constexpr int kMmaWarp = 8;
 constexpr int kThreads = 32 * (kMmaWarp + 1 + kStages);
+// the full kernel: kEpiWarpsF epilogue warps (kPartsF per TMEM lane quarter, each writing one
+// column part of the next operand), then the MMA warp, then one producer warp per stage
+constexpr int kEpiWarpsF = 12;
+constexpr int kPartsF = kEpiWarpsF / 4;
+constexpr int kMmaWarpF = kEpiWarpsF;
+constexpr int kThreadsF = 32 * (kMmaWarpF + 1 + kStages);
 constexpr uint32_t kABytes = 64 * 1024;   // one A region (128 rows x 256 bf16)
 constexpr uint32_t kMaxSpin = 1u << 26;
 
@@ -53,6 +59,9 @@ __host__ __device__ constexpr int pad16(int x) { return (x + 15) / 16 * 16; }
 // the split is rounded up to 16 so every 16-column block stays inside K
 __host__ __device__ constexpr int half_lo(int K, int hf) { return hf ? pad16(K / 2) : 0; }
 __host__ __device__ constexpr int half_hi(int K, int hf) { return hf ? K : pad16(K / 2); }
+// the same for `parts` parts of whole 16-column blocks (K a multiple of 16)
+__host__ __device__ constexpr int part_lo(int K, int pt, int parts) { return ((K / 16) * pt / parts) * 16; }
+__host__ __device__ constexpr int part_hi(int K, int pt, int parts) { return pt + 1 == parts ? K : part_lo(K, pt + 1, parts); }
 
 template <int ARCH> struct TcArch {
     using A = Arch<ARCH>;
@@ -314,7 +323,7 @@ struct TcParams {
 };
 
 template <int ARCH, bool F16>
-__global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
+__global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
     using TA = TcArch<ARCH>;
     using A = Arch<ARCH>;
     constexpr int NL = TA::kLayers;
@@ -353,14 +362,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
             mbar_init(bar_empty0 + 8 * i, 1);
         }
         mbar_init(bar_acc, 1);
-        mbar_init(bar_a, kEpiThreads);
+        mbar_init(bar_a, 32 * kEpiWarpsF);
         mbar_init(bar_drain, 1);
-        mbar_init(bar_tab, kEpiThreads);
+        mbar_init(bar_tab, 32 * kEpiWarpsF);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // all biases of both networks, staged once
-    for (int i = threadIdx.x; i < TA::bias_total(); i += kThreads) {
+    for (int i = threadIdx.x; i < TA::bias_total(); i += kThreadsF) {
         int L = 0;
         while (L + 1 < NL && TA::bias_offset(L + 1) <= i) ++L;
         const TcLayer ly = TA::layer(L);
@@ -368,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
         const int j = i - TA::bias_offset(L);
         sbias[i] = j < ly.N ? __ldg(W + (int64_t)ly.N * ly.K + j) : 0.0f;
     }
-    if (warp == kMmaWarp) {
+    if (warp == kMmaWarpF) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -378,10 +387,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp > kMmaWarp) {
+    if (warp > kMmaWarpF) {
         // ------------------------------------------- producers (one per stage)
         if (lane == 0) {
-            const uint32_t own = (uint32_t)(warp - kMmaWarp - 1);
+            const uint32_t own = (uint32_t)(warp - kMmaWarpF - 1);
             uint32_t seq = 0, issued = 0;
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
@@ -404,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                 }
             }
         }
-    } else if (warp == kMmaWarp) {
+    } else if (warp == kMmaWarpF) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
             uint32_t seq = 0, lc = 0;
@@ -463,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int q = warp & 3, hf = warp >> 2;
+        const int q = warp & 3, pt = warp >> 2;   // lane quarter, column part
         const bool is_val = lane < 16;
         const int r = 32 * q + lane;                  // TMEM lane / A row of this thread
         const int s = 16 * q + (lane & 15);           // sample within the tile
@@ -554,7 +563,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                 const float* pb = s_pe + sb * A::kPeSdf * 6;
                 const uint32_t row0 = smem_u32(A0) + a_off(32 * q + lane, 0, Kp0);
                 const uint32_t row1 = smem_u32(A1) + a_off(32 * q + lane, 0, Kp0);
-                for (int c8 = hf * (Kp0 / 2); c8 < (hf + 1) * (Kp0 / 2); c8 += 8) {
+                for (int c8 = part_lo(Kp0, pt, kPartsF); c8 < part_hi(Kp0, pt, kPartsF); c8 += 8) {
                     float v[4][4];   // [component][(sample a, col 0), (a, 1), (b, 0), (b, 1)]
 #pragma unroll
                     for (int cp = 0; cp < 4; ++cp)
@@ -590,7 +599,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                     const float sc = ly.idx + 1 == A::kSkip ? kInvSqrt2 : 1.0f;
                     const uint32_t row0 = smem_u32(A0) + a_off(32 * q + lane, 0, Kn);
                     const uint32_t row1 = smem_u32(A1) + a_off(32 * q + lane, 0, Kn);
-                    const int c_lo = half_lo(Kn, hf), c_hi = half_hi(Kn, hf);
+                    const int c_lo = part_lo(Kn, pt, kPartsF), c_hi = part_hi(Kn, pt, kPartsF);
                     const int c_full = (ly.N / 16) * 16 < c_hi ? (ly.N / 16) * 16 : c_hi;
                     // 8-column groups, software-pipelined: the TMEM loads of group c + 8 are in
                     // flight while group c is computed.  buf = [value(4) | d/dx(4) | d/dy(4) | d/dz(4)],
@@ -723,7 +732,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                     const int Kc = TA::layer(L + 1).Kp;
                     float n_hat[3] = {0.0f, 0.0f, 0.0f};
                     float venc[kDir];
-                    if (hf == 0) {
+                    if (pt == 0) {
                         float x0[16], x1[16];
                         tmem_ld16(tmem + lane_addr, x0);
                         tmem_ld16(tmem + 256 + lane_addr, x1);
@@ -765,9 +774,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                             }
                         }
                     };
-                    const int lo = half_lo(Kc, hf), hi = half_hi(Kc, hf);
-                    int c_start = lo;
-                    if (hf == 0) {
+                    // part 0 writes the prefix blocks (x~, direction, normal); every part
+                    // writes the feature blocks of its column range beyond them
+                    const int lo = part_lo(Kc, pt, kPartsF), hi = part_hi(Kc, pt, kPartsF);
+                    const int c_start = lo > 16 * kPrefix ? lo : 16 * kPrefix;
+                    if (pt == 0) {
 #pragma unroll
                         for (int pb = 0; pb < kPrefix; ++pb) {
                             float o[16];
@@ -777,7 +788,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                                 st_row8<F16>(A0, r, 16 * pb + 8, Kc, o + 8);
                             }
                         }
-                        c_start = 16 * kPrefix;
                     }
                     for (int c0 = c_start; c0 < hi; c0 += 16) {
                         float o[16];
@@ -792,7 +802,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                     // lane 32q holds value rows only (samples 16q + fs and 16q + 8 + fs) ----
                     const int Kn = TA::layer(L + 1).Kp;
                     const uint32_t row0 = smem_u32(A0) + a_off(32 * q + (lane & 15), 0, Kn);
-                    for (int c0 = half_lo(Kn, hf); c0 < half_hi(Kn, hf); c0 += 16) {
+                    for (int c0 = part_lo(Kn, pt, kPartsF); c0 < part_hi(Kn, pt, kPartsF); c0 += 16) {
                         float v[8];
                         if (c0 < ly.Np) {
                             tmem_ld16x256_x2(t_v + c0, v);
@@ -813,7 +823,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
                                       pack2<F16>(o[2], o[3]));
                         }
                     }
-                } else if (hf == 0) {
+                } else if (pt == 0) {
                     // ---- colour output (sigmoid) -> record ----
                     float x0[16];
                     tmem_ld16(tmem + lane_addr, x0);
@@ -849,7 +859,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(TcParams p) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kMmaWarp) {
+    if (warp == kMmaWarpF) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
     }
 }
@@ -1161,7 +1171,7 @@ int launch_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int64_t tiles = (max_samples + kTileS - 1) / kTileS;
     unsigned blocks = (unsigned)(tiles < sms ? (tiles < 1 ? 1 : tiles) : sms);
-    k_mlp_tc<ARCH, F16><<<blocks, kThreads, smem, st>>>(p);
+    k_mlp_tc<ARCH, F16><<<blocks, kThreadsF, smem, st>>>(p);
     return cuda_check(cudaGetLastError(), "mlp_tc launch");
 }
 
