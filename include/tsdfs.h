@@ -95,9 +95,17 @@ typedef struct {
  *   TSDFS_ARCH_ROOM: SDF 39-256-256-256-217, skip, 256-256-256-(1+256), L = 6;
  *                    colour (3+27+3+256)-256-256-256-256-3, direction L = 4.
  * Packed fp32 parameters (sdf_w, rgb_w): for each layer in order, W[out][in]
- * row-major, then b[out].  Opacity (NeuS, the SDF-to-density transform of the
- * backbone in Eq. 1): alpha = clamp((Phi(f-) - Phi(f+) + eps)/(Phi(f-) + eps),
- * 0, 1), Phi(x) = sigmoid(inv_s x), f-/+ = f -/+ (delta/2) min(v . grad f, 0).  */
+ * row-major, then b[out].  Opacity of a sample's section (the SDF-to-density
+ * transform of the backbone in Eq. 1), by `opacity`:
+ *   TSDFS_OPACITY_NEUS:   alpha = clamp((Phi(f-) - Phi(f+) + eps)/(Phi(f-) + eps),
+ *                         0, 1), Phi(x) = sigmoid(inv_s x),
+ *                         f-/+ = f -/+ (delta/2) min(v . grad f, 0);
+ *   TSDFS_OPACITY_VOLSDF: alpha = 1 - exp(-sigma(f) delta) (Eq. 1 as printed) with
+ *                         the density of VolSDF / MonoSDF, sigma(f) = a Psi(-f),
+ *                         Psi the CDF of the zero-mean Laplace distribution of
+ *                         scale 1/a, a = inv_s (eps unused).                    */
+#define TSDFS_OPACITY_NEUS 0
+#define TSDFS_OPACITY_VOLSDF 1
 #define TSDFS_ARCH_TINY 0
 #define TSDFS_ARCH_ROOM 1
 #define TSDFS_PREC_F32 0  /* FP32 SIMT networks                                  */
@@ -111,9 +119,10 @@ typedef struct {
     const void* packed;  /* device, tsdfs_packed_size bytes from tsdfs_pack_mlp, or NULL */
     float center[3];
     float scale;
-    float inv_s;         /* s of Phi_s (64)                                             */
+    float inv_s;         /* NeuS: s of Phi_s (64); VolSDF: a = 1/beta of the density     */
     float beta;          /* softplus beta (100)                                         */
-    float alpha_eps;     /* eps of the opacity ratio (1e-5)                             */
+    float alpha_eps;     /* eps of the NeuS opacity ratio (1e-5)                        */
+    int32_t opacity;     /* TSDFS_OPACITY_NEUS (0) or TSDFS_OPACITY_VOLSDF (1)          */
 } tsdfs_mlp;
 
 /* ---- errors -------------------------------------------------------------- */

@@ -28,7 +28,10 @@ Readings taken here (numbered as in the design notes):
       neighbouring samples (equal to (t_f - t_n)/n for midpoint placement);
   R23 coarse + fine inside the TSDF bound as in :func:`render_hier_bounded`;
   R24 counts relative to the mean interval as in :func:`adaptive_counts`;
-  R25 the dense reference image is rendered without the opacity guard.
+  R25 the dense reference image is rendered without the opacity guard;
+  R26 VolSDF opacity: alpha = 1 - exp(-sigma delta) with sigma(f) = a Psi(-f),
+      Psi the Laplace CDF of scale 1/a (a = inv_s); the comparator's section
+      opacity uses the density at the section's mid value.
 """
 from __future__ import annotations
 
@@ -38,6 +41,7 @@ import numpy as np
 import torch
 
 DT = torch.float64
+OPACITY_NEUS, OPACITY_VOLSDF = 0, 1   # the network's SDF-to-opacity transform (R16 / R26)
 LOG_T_CLAMP = 1.0 - 2.0 ** -24
 WSUM_MIN = 1e-8
 
@@ -166,6 +170,24 @@ def neus_alpha(f, dd, delta, inv_s, eps):
     return torch.clamp((p_lo - p_hi + eps) / (p_lo + eps), 0.0, 1.0)
 
 
+def volsdf_density(f, a):
+    """R26: VolSDF / MonoSDF density sigma(f) = a Psi(-f), Psi the CDF of the zero-mean
+    Laplace law of scale 1/a."""
+    return a * torch.where(f >= 0, 0.5 * torch.exp(-a * f), 1.0 - 0.5 * torch.exp(a * f))
+
+
+def volsdf_alpha(f, delta, a):
+    """Eq. 1 as printed: alpha = 1 - exp(-sigma delta)."""
+    return -torch.expm1(-volsdf_density(f, a) * delta)
+
+
+def section_alpha(spec, f, dd, delta, eps=None):
+    """Opacity of the section of width delta around a sample, by the network's transform."""
+    if getattr(spec, "opacity", OPACITY_NEUS) == OPACITY_VOLSDF:
+        return volsdf_alpha(f, delta, spec.inv_s)
+    return neus_alpha(f, dd, delta, spec.inv_s, spec.alpha_eps if eps is None else eps)
+
+
 def composite(alpha, t, rgb, n_hat, mask):
     """Eq. 1/2 on padded (R, S) arrays; mask marks real samples.
 
@@ -227,7 +249,7 @@ def render_samples(net, o, d, t, delta, mask, eps=None):
     dd = scatter(ev["dd"])
     rgb = scatter(ev["rgb"])
     nh = scatter(ev["n_hat"])
-    alpha = neus_alpha(f, dd, delta, spec.inv_s, spec.alpha_eps if eps is None else eps)
+    alpha = section_alpha(spec, f, dd, delta, eps)
     out = composite(alpha, t, rgb, nh, mask)
     out["alpha"] = alpha
     out["eik"] = (ev["gnorm"] - 1.0) ** 2
@@ -306,13 +328,18 @@ def dense_reference(net, rays_o, rays_d, t0, t_end, n=2048, chunk=64):
 # ----------------------------------------------------------------------------
 # 64 + 32 hierarchical comparator (R19)
 # ----------------------------------------------------------------------------
-def hier_coarse_weights(f, z, inv_s, eps):
+def hier_coarse_weights(f, z, inv_s, eps, opacity=0):
     """Weights of the sections between consecutive coarse samples, from SDF
     values only: mid value, slope (f_{j+1} - f_j)/(z_{j+1} - z_j), slope taken as
     min(own, previous) (previous of the first = 0), clipped to [-1e3, 0];
-    opacity as R16 with the section's ends; w = alpha * prod (1 - alpha)."""
+    opacity as R16 with the section's ends (NeuS), or the density at the mid
+    value over the section (VolSDF, R26); w = alpha * prod (1 - alpha)."""
     mid = 0.5 * (f[:, 1:] + f[:, :-1])
     dz = z[:, 1:] - z[:, :-1]
+    if opacity == OPACITY_VOLSDF:
+        alpha = volsdf_alpha(mid, dz, inv_s)
+        T = torch.cumprod(torch.cat([torch.ones_like(alpha[:, :1]), 1.0 - alpha[:, :-1]], 1), 1)
+        return alpha * T
     slope = (f[:, 1:] - f[:, :-1]) / dz
     prev = torch.cat([torch.zeros_like(slope[:, :1]), slope[:, :-1]], 1)
     c = torch.clamp(torch.minimum(slope, prev), -1e3, 0.0)
@@ -354,7 +381,7 @@ def render_hier(net, rays_o, rays_d, t0, t_end, n_coarse=64, n_fine=32):
     zc = t0.unsqueeze(1) + (i + 0.5) * ((te - t0) / n_coarse).unsqueeze(1)
     xc = (o.unsqueeze(1) + zc.unsqueeze(2) * d.unsqueeze(1)).reshape(-1, 3)
     fc, _, _ = sdf_forward(net, xc, with_grad=False)
-    w = hier_coarse_weights(fc.reshape(R, n_coarse), zc, spec.inv_s, spec.alpha_eps)
+    w = hier_coarse_weights(fc.reshape(R, n_coarse), zc, spec.inv_s, spec.alpha_eps, spec.opacity)
     zf = inverse_cdf(zc, w, n_fine)
     t, _ = torch.sort(torch.cat([zc, zf], 1), 1)
     mask = torch.ones_like(t, dtype=torch.bool)
@@ -422,7 +449,7 @@ def render_hier_bounded(net, rays_o, rays_d, t_n, t_f, counts, n_fine):
         elif c >= 2:
             xc = (o[it].unsqueeze(1) + zc.unsqueeze(2) * d[it].unsqueeze(1)).reshape(-1, 3)
             fc, _, _ = sdf_forward(net, xc, with_grad=False)
-            w = hier_coarse_weights(fc.reshape(len(idx), int(c)), zc, spec.inv_s, spec.alpha_eps)
+            w = hier_coarse_weights(fc.reshape(len(idx), int(c)), zc, spec.inv_s, spec.alpha_eps, spec.opacity)
             zf = inverse_cdf(zc, w, n_fine)
         else:
             k = torch.arange(n_fine, dtype=DT).unsqueeze(0)

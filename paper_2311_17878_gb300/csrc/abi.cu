@@ -103,17 +103,17 @@ int launch_mlp_full_simt(const NetParams& np, const SampleSource& src, SampleRec
 template <int ARCH>
 int launch_mlp_value_simt(const NetParams& np, const SampleSource& src, float* f_out, cudaStream_t st);
 int launch_composite(const SampleRec* rec, const int32_t* offsets, int per_ray, const uint8_t* status, int64_t n_rays,
-                     const int32_t* total_dev, int64_t capacity, float inv_s, float eps, float* rgb, float* depth,
+                     const int32_t* total_dev, int64_t capacity, Opacity op, float* rgb, float* depth,
                      float* wsum, float* normal, float* eik, cudaStream_t st);
 int launch_hier_setup(const tsdfs_grid* g, const float* ray_o, const float* ray_d, int64_t n_rays, float t_near,
                       float t_far, float* t0, float* te, uint8_t* status, float* tc, float* dc, int n_c,
                       cudaStream_t st);
 int launch_hier_fine(const float* fcoarse, const float* tc, const float* t0, const float* te, int64_t n_rays,
-                     float inv_s, float eps, float* t_out, float* d_out, int n_c, int n_f, cudaStream_t st);
+                     Opacity op, float* t_out, float* d_out, int n_c, int n_f, cudaStream_t st);
 int launch_bounded_counts(const int32_t* offsets, int64_t n_rays, int n_f, int64_t max_coarse, int32_t* n2,
                           cudaStream_t st);
 int launch_bounded_fine(const float* fcoarse, const int32_t* offsets, const float* t_n, const float* t_f,
-                        const int32_t* offsets2, int64_t n_rays, int n_f, float inv_s, float eps, int64_t max_coarse,
+                        const int32_t* offsets2, int64_t n_rays, int n_f, Opacity op, int64_t max_coarse,
                         int64_t capacity2, float* t_out, float* d_out, int32_t* ray_out, cudaStream_t st);
 int grid_check(const tsdfs_grid* g);
 int mlp_tc_available(int arch);
@@ -131,12 +131,16 @@ static int mlp_check(const tsdfs_mlp* m) {
     if (!m->sdf_w || !m->rgb_w) return fail(TSDFS_E_INVALID, "sdf_w and rgb_w must be non-NULL");
     if (!(m->scale > 0.0f) || !(m->beta > 0.0f) || !(m->inv_s > 0.0f) || !(m->alpha_eps >= 0.0f))
         return fail(TSDFS_E_INVALID, "scale, beta and inv_s must be > 0, alpha_eps >= 0");
+    if (m->opacity != TSDFS_OPACITY_NEUS && m->opacity != TSDFS_OPACITY_VOLSDF)
+        return fail(TSDFS_E_INVALID, "unknown opacity %d", m->opacity);
     if (m->precision != TSDFS_PREC_F32) {
         if (!m->packed) return fail(TSDFS_E_INVALID, "16-bit precisions need packed weights (tsdfs_pack_mlp)");
         if (!mlp_tc_available(m->arch)) return fail(TSDFS_E_UNSUPPORTED, "BF16 tensor-core path not available for arch %d", m->arch);
     }
     return TSDFS_OK;
 }
+
+static Opacity opacity_of(const tsdfs_mlp* m) { return Opacity{m->opacity, m->inv_s, m->alpha_eps}; }
 
 static NetParams net_params(const tsdfs_mlp* m) {
     NetParams np;
@@ -277,7 +281,7 @@ extern "C" int render_rays(const tsdfs_mlp* mlp, const float* ray_o, const float
         if (rc) return rc;
     }
     ProfScope ps("composite", st);
-    return launch_composite(rec, offsets, 0, status, n_rays, offsets + n_rays, max_samples, mlp->inv_s, mlp->alpha_eps,
+    return launch_composite(rec, offsets, 0, status, n_rays, offsets + n_rays, max_samples, opacity_of(mlp),
                             rgb, depth, wsum, normal, eik, st);
 }
 
@@ -363,7 +367,7 @@ extern "C" int render_rays_hier(const tsdfs_mlp* mlp, const tsdfs_grid* grid, co
     if (rc) return rc;
     {
         ProfScope ps("hier_fine", st);
-        rc = launch_hier_fine(w.fc, w.tc, w.t0, w.te, n_rays, mlp->inv_s, mlp->alpha_eps, w.tf, w.df, n_coarse, n_fine,
+        rc = launch_hier_fine(w.fc, w.tc, w.t0, w.te, n_rays, opacity_of(mlp), w.tf, w.df, n_coarse, n_fine,
                               st);
     }
     if (rc) return rc;
@@ -376,7 +380,7 @@ extern "C" int render_rays_hier(const tsdfs_mlp* mlp, const tsdfs_grid* grid, co
     rc = run_full_mlp(mlp, fs, w.rec, n_rays * n_h, st);
     if (rc) return rc;
     ProfScope ps("composite", st);
-    return launch_composite(w.rec, nullptr, n_h, w.status, n_rays, nullptr, n_rays * n_h, mlp->inv_s, mlp->alpha_eps,
+    return launch_composite(w.rec, nullptr, n_h, w.status, n_rays, nullptr, n_rays * n_h, opacity_of(mlp),
                             rgb, depth, wsum, normal, nullptr, st);
 }
 
@@ -479,7 +483,7 @@ extern "C" int render_rays_hier_bounded(const tsdfs_mlp* mlp, const float* ray_o
         if (rc) return rc;
         rc = exclusive_scan(w.n2, n_rays, w.off2, w.sums, st);
         if (rc) return rc;
-        rc = launch_bounded_fine(w.fc, offsets, t_n, t_f, w.off2, n_rays, n_fine, mlp->inv_s, mlp->alpha_eps,
+        rc = launch_bounded_fine(w.fc, offsets, t_n, t_f, w.off2, n_rays, n_fine, opacity_of(mlp),
                                  max_coarse, cap2, w.t2, w.d2, w.ray2, st);
         if (rc) return rc;
     }
@@ -499,6 +503,6 @@ extern "C" int render_rays_hier_bounded(const tsdfs_mlp* mlp, const float* ray_o
         if (rc) return rc;
     }
     ProfScope ps("composite", st);
-    return launch_composite(w.rec, w.off2, 0, status, n_rays, w.off2 + n_rays, cap2, mlp->inv_s, mlp->alpha_eps, rgb,
+    return launch_composite(w.rec, w.off2, 0, status, n_rays, w.off2 + n_rays, cap2, opacity_of(mlp), rgb,
                             depth, wsum, normal, nullptr, st);
 }

@@ -38,7 +38,7 @@ __device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + expf(-x))
 // ---- 2. compositing backward ------------------------------------------------
 __global__ void k_comp_bwd(const SampleRec* __restrict__ rec, const int32_t* __restrict__ offsets,
                            const uint8_t* __restrict__ status, const float* __restrict__ ray_d, int64_t n_rays,
-                           float inv_s, float eps, const float* __restrict__ d_rgb, const float* __restrict__ d_depth,
+                           Opacity op, const float* __restrict__ d_rgb, const float* __restrict__ d_depth,
                            const float* __restrict__ d_eik, SampleAdj* __restrict__ adj) {
     const float kClamp = 1.0f - 5.9604645e-8f;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
@@ -48,7 +48,17 @@ __global__ void k_comp_bwd(const SampleRec* __restrict__ rec, const int32_t* __r
         const float dd_r = d_depth ? d_depth[r] : 0.0f;
         const float de_r = d_eik ? d_eik[r] : 0.0f;
         const float v[3] = {ray_d[3 * r], ray_d[3 * r + 1], ray_d[3 * r + 2]};
+        const float inv_s = op.inv_s, eps = op.eps;
+        const bool volsdf = op.kind == TSDFS_OPACITY_VOLSDF;
+        // NeuS: plo / phi = Phi at the section ends, araw = the unclamped ratio;
+        // VolSDF: plo = the density, phi = exp(-density * delta) = 1 - alpha, araw = alpha
         auto alpha_of = [&](const SampleRec& R, float& plo, float& phi, float& araw) {
+            if (volsdf) {
+                plo = laplace_density(R.f, inv_s);
+                phi = expf(-plo * R.delta);
+                araw = -expm1f(-plo * R.delta);
+                return araw;
+            }
             const float c = fminf(R.dd, 0.0f);
             plo = sigm(inv_s * (R.f - 0.5f * R.delta * c));
             phi = sigm(inv_s * (R.f + 0.5f * R.delta * c));
@@ -94,15 +104,22 @@ __global__ void k_comp_bwd(const SampleRec* __restrict__ rec, const int32_t* __r
             const float S = G - P;  // sum over later samples of dL/dw_k w_k
             const float dlt = a < kClamp ? -1.0f / (1.0f - a) : 0.0f;
             const float ga = gw * T + S * dlt;
-            const float ga_raw = (araw > 0.0f && araw < 1.0f) ? ga : 0.0f;
-            const float Dn = plo + eps;
-            const float g_plo = ga_raw * phi / (Dn * Dn);
-            const float g_phi = -ga_raw / Dn;
-            const float g_xlo = g_plo * inv_s * plo * (1.0f - plo);
-            const float g_xhi = g_phi * inv_s * phi * (1.0f - phi);
-            const float gf = g_xlo + g_xhi;
-            const float gc = 0.5f * R.delta * (g_xhi - g_xlo);
-            const float gdd = R.dd < 0.0f ? gc : 0.0f;
+            float gf, gdd;
+            if (volsdf) {
+                // d alpha / d f = exp(-sigma delta) delta d sigma / d f
+                gf = ga * phi * R.delta * laplace_density_slope(R.f, inv_s);
+                gdd = 0.0f;
+            } else {
+                const float ga_raw = (araw > 0.0f && araw < 1.0f) ? ga : 0.0f;
+                const float Dn = plo + eps;
+                const float g_plo = ga_raw * phi / (Dn * Dn);
+                const float g_phi = -ga_raw / Dn;
+                const float g_xlo = g_plo * inv_s * plo * (1.0f - plo);
+                const float g_xhi = g_phi * inv_s * phi * (1.0f - phi);
+                gf = g_xlo + g_xhi;
+                const float gc = 0.5f * R.delta * (g_xhi - g_xlo);
+                gdd = R.dd < 0.0f ? gc : 0.0f;
+            }
             float ggx = gdd * v[0], ggy = gdd * v[1], ggz = gdd * v[2];
             if (bounded && de_r != 0.0f) {
                 // d/dg of (|g| - 1)^2 = 2 (|g| - 1) g / |g| = 2 (|g| - 1) n^
@@ -554,6 +571,8 @@ extern "C" int render_rays_backward(const tsdfs_mlp* mlp, const float* ray_o, co
     if (mlp->arch != TSDFS_ARCH_TINY && mlp->arch != TSDFS_ARCH_ROOM) return fail(TSDFS_E_INVALID, "unknown arch %d", mlp->arch);
     if (!mlp->sdf_w || !mlp->rgb_w) return fail(TSDFS_E_INVALID, "sdf_w and rgb_w must be non-NULL");
     if (!(mlp->scale > 0.0f) || !(mlp->beta > 0.0f) || !(mlp->inv_s > 0.0f)) return fail(TSDFS_E_INVALID, "bad mlp scalars");
+    if (mlp->opacity != TSDFS_OPACITY_NEUS && mlp->opacity != TSDFS_OPACITY_VOLSDF)
+        return fail(TSDFS_E_INVALID, "unknown opacity %d", mlp->opacity);
     if (n_rays < 0 || max_samples < 0) return fail(TSDFS_E_INVALID, "n_rays and max_samples must be >= 0");
     if (n_rays == 0) return TSDFS_OK;
     if (!ray_o || !ray_d || !t_n || !t_f || !offsets || !status || !d_rgb || !d_sdf_w || !d_rgb_w)
@@ -585,7 +604,7 @@ extern "C" int render_rays_backward(const tsdfs_mlp* mlp, const float* ray_o, co
     int rc = mlp->arch == TSDFS_ARCH_TINY ? launch_mlp_full_simt<TSDFS_ARCH_TINY>(np, src, w.rec, max_samples, st)
                                           : launch_mlp_full_simt<TSDFS_ARCH_ROOM>(np, src, w.rec, max_samples, st);
     if (rc) return rc;
-    k_comp_bwd<<<grid_1d(n_rays, 128), 128, 0, st>>>(w.rec, offsets, status, ray_d, n_rays, mlp->inv_s, mlp->alpha_eps,
+    k_comp_bwd<<<grid_1d(n_rays, 128), 128, 0, st>>>(w.rec, offsets, status, ray_d, n_rays, Opacity{mlp->opacity, mlp->inv_s, mlp->alpha_eps},
                                                      d_rgb, d_depth, d_eik, w.adj);
     rc = cuda_check(cudaGetLastError(), "backward composite launch");
     if (rc) return rc;

@@ -142,6 +142,34 @@ struct SampleSource {
     int64_t capacity;  // records available in the workspace
 };
 
+// opacity of a sample's section (Eq. 1 with the backbone's SDF-to-density transform)
+struct Opacity {
+    int kind;     // TSDFS_OPACITY_NEUS / TSDFS_OPACITY_VOLSDF
+    float inv_s;  // NeuS: s of Phi_s; VolSDF: a = 1 / beta (density scale and Laplace rate)
+    float eps;    // NeuS ratio guard
+};
+
+__device__ __forceinline__ float sigmoid_acc(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// VolSDF density sigma(f) = a Psi(-f), Psi the CDF of the zero-mean Laplace law of scale 1/a
+__device__ __forceinline__ float laplace_density(float f, float a) {
+    const float e = 0.5f * expf(-fabsf(f) * a);
+    return a * (f >= 0.0f ? e : 1.0f - e);
+}
+
+// d sigma / d f = -a * (a / 2) exp(-a |f|)
+__device__ __forceinline__ float laplace_density_slope(float f, float a) { return -0.5f * a * a * expf(-fabsf(f) * a); }
+
+// opacity of the section of width dl around a sample of SDF f and slope dd = v . grad f
+__device__ __forceinline__ float section_opacity(const Opacity& op, float f, float dd, float dl) {
+    if (op.kind == TSDFS_OPACITY_VOLSDF) return -expm1f(-laplace_density(f, op.inv_s) * dl);
+    const float c = fminf(dd, 0.0f);
+    const float p_lo = sigmoid_acc(op.inv_s * (f - 0.5f * dl * c));
+    const float p_hi = sigmoid_acc(op.inv_s * (f + 0.5f * dl * c));
+    const float alpha = (p_lo - p_hi + op.eps) / (p_lo + op.eps);
+    return fminf(fmaxf(alpha, 0.0f), 1.0f);
+}
+
 __device__ __forceinline__ int64_t sample_total(const SampleSource& s) {
     return s.total_dev ? (int64_t)__ldg(s.total_dev) : s.total_host;
 }

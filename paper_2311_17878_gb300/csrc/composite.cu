@@ -12,15 +12,14 @@ constexpr int kMaxCoarse = 64;
 constexpr int kMaxFine = 32;
 constexpr int kMaxHier = kMaxCoarse + kMaxFine;
 
-__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
 
 // One thread per ray.  Uniform rays: samples offsets[r]..offsets[r+1]; explicit
 // rays: r*per_ray .. (r+1)*per_ray.  eik: sum (|grad f| - 1)^2 for BOUNDED rays.
 __global__ void __launch_bounds__(kCompBlock) k_composite(const SampleRec* __restrict__ rec,
                                                           const int32_t* __restrict__ offsets, int per_ray,
                                                           const uint8_t* __restrict__ status, int64_t n_rays,
-                                                          const int32_t* total_dev, int64_t capacity, float inv_s,
-                                                          float eps, float* __restrict__ rgb, float* __restrict__ depth,
+                                                          const int32_t* total_dev, int64_t capacity, Opacity op,
+                                                          float* __restrict__ rgb, float* __restrict__ depth,
                                                           float* __restrict__ wsum_out, float* __restrict__ normal,
                                                           float* __restrict__ eik_out) {
     const bool overflow = total_dev && (int64_t)__ldg(total_dev) > capacity;
@@ -42,11 +41,7 @@ __global__ void __launch_bounds__(kCompBlock) k_composite(const SampleRec* __res
             const float4 q1 = reinterpret_cast<const float4*>(rec + g)[1];
             const float4 q2 = reinterpret_cast<const float4*>(rec + g)[2];
             const float f = q0.x, dd = q0.y, t = q0.z, dl = q0.w;
-            const float c = fminf(dd, 0.0f);
-            const float p_lo = sigmoidf_(inv_s * (f - 0.5f * dl * c));
-            const float p_hi = sigmoidf_(inv_s * (f + 0.5f * dl * c));
-            float alpha = (p_lo - p_hi + eps) / (p_lo + eps);
-            alpha = fminf(fmaxf(alpha, 0.0f), 1.0f);
+            const float alpha = section_opacity(op, f, dd, dl);
             const float w = expf(logT) * alpha;
             ws += w;
             cr += w * q1.x; cg += w * q1.y; cb += w * q1.z;
@@ -126,21 +121,20 @@ __global__ void k_hier_setup(BoxDev box, const float* __restrict__ ray_o, const 
 }
 
 // Weight of the section [z0, z1] between two coarse samples from their SDF
-// values alone (NeuS up-sampling opacity): slope min(own, previous) clipped to
-// [-1e3, 0], section ends at mid -/+ slope * dz / 2; T carries the
-// transmittance, prev_slope the previous section's slope.
-__device__ __forceinline__ float section_weight(float f0, float f1, float z0, float z1, float inv_s, float eps,
-                                                float& T, float& prev_slope) {
+// values alone.  NeuS (up-sampling opacity): slope min(own, previous) clipped
+// to [-1e3, 0], section ends at mid -/+ slope * dz / 2.  VolSDF: the density
+// at the mid value over the section.  T carries the transmittance, prev_slope
+// the previous section's slope.
+__device__ __forceinline__ float section_weight(float f0, float f1, float z0, float z1, const Opacity& op, float& T,
+                                                float& prev_slope) {
     const float dz = z1 - z0;
     const float mid = 0.5f * (f0 + f1);
     const float slope = dz > 0.0f ? (f1 - f0) / dz : 0.0f;
     float c = fminf(slope, prev_slope);
     c = fminf(fmaxf(c, -1e3f), 0.0f);
     prev_slope = slope;
-    const float p_lo = sigmoidf_(inv_s * (mid - 0.5f * c * dz));
-    const float p_hi = sigmoidf_(inv_s * (mid + 0.5f * c * dz));
-    float alpha = (p_lo - p_hi + eps) / (p_lo + eps);
-    alpha = fminf(fmaxf(alpha, 0.0f), 1.0f);
+    // the opacity of a section of width dz around the mid value with slope c
+    const float alpha = section_opacity(op, mid, c, dz);
     const float w = alpha * T;
     T *= 1.0f - alpha;
     return w;
@@ -151,10 +145,10 @@ __device__ __forceinline__ float section_weight(float f0, float f1, float z0, fl
 // a section.  Two passes over the sections (the normaliser, then the samples
 // in increasing u) so that no per-ray table is kept.
 template <class Z, class F>
-__device__ __forceinline__ void fine_from_coarse(Z zat, F fat, int c, float inv_s, float eps, int n_f, float* fine) {
+__device__ __forceinline__ void fine_from_coarse(Z zat, F fat, int c, const Opacity& op, int n_f, float* fine) {
     float T = 1.0f, prev_slope = 0.0f, psum = 0.0f;
     for (int j = 0; j < c - 1; ++j)
-        psum += section_weight(fat(j), fat(j + 1), zat(j), zat(j + 1), inv_s, eps, T, prev_slope) + 1e-5f;
+        psum += section_weight(fat(j), fat(j + 1), zat(j), zat(j + 1), op, T, prev_slope) + 1e-5f;
     const float inv_sum = 1.0f / psum;
     T = 1.0f;
     prev_slope = 0.0f;
@@ -162,7 +156,7 @@ __device__ __forceinline__ void fine_from_coarse(Z zat, F fat, int c, float inv_
     int k = 0;
     for (int j = 0; j < c - 1 && k < n_f; ++j) {
         const float z0 = zat(j), z1 = zat(j + 1);
-        const float cnext = cum + (section_weight(fat(j), fat(j + 1), z0, z1, inv_s, eps, T, prev_slope) + 1e-5f);
+        const float cnext = cum + (section_weight(fat(j), fat(j + 1), z0, z1, op, T, prev_slope) + 1e-5f);
         const float c0 = cum * inv_sum, c1 = cnext * inv_sum;
         const bool last = j == c - 2;
         while (k < n_f) {
@@ -200,8 +194,7 @@ __device__ __forceinline__ void merge_emit(Z zat, int c, const float* fine, int 
 // Comparator: n_c coarse values -> n_f fine samples -> n_c + n_f merged samples per ray.
 __global__ void k_hier_fine(const float* __restrict__ fcoarse, const float* __restrict__ tc,
                             const float* __restrict__ t0_in, const float* __restrict__ te_in, int64_t n_rays,
-                            float inv_s, float eps, float* __restrict__ t_out, float* __restrict__ d_out, int n_c,
-                            int n_f) {
+                            Opacity op, float* __restrict__ t_out, float* __restrict__ d_out, int n_c, int n_f) {
     const int n_h = n_c + n_f;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
         const float* f = fcoarse + r * n_c;
@@ -209,7 +202,7 @@ __global__ void k_hier_fine(const float* __restrict__ fcoarse, const float* __re
         auto zat = [&](int j) { return __ldg(z + j); };
         auto fat = [&](int j) { return __ldg(f + j); };
         float fine[kMaxFine];
-        fine_from_coarse(zat, fat, n_c, inv_s, eps, n_f, fine);
+        fine_from_coarse(zat, fat, n_c, op, n_f, fine);
         float* to = t_out + r * n_h;
         float* dout = d_out + r * n_h;
         merge_emit(zat, n_c, fine, n_f, __ldg(t0_in + r), __ldg(te_in + r), [&](int i, float t, float dl) {
@@ -226,7 +219,7 @@ __global__ void k_hier_fine(const float* __restrict__ fcoarse, const float* __re
 // n_f equal parts of [t_n, t_f].
 __global__ void k_bounded_fine(const float* __restrict__ fcoarse, const int32_t* __restrict__ offsets,
                                const float* __restrict__ t_n, const float* __restrict__ t_f,
-                               const int32_t* __restrict__ offsets2, int64_t n_rays, int n_f, float inv_s, float eps,
+                               const int32_t* __restrict__ offsets2, int64_t n_rays, int n_f, Opacity op,
                                int64_t max_coarse, int64_t capacity2, float* __restrict__ t_out,
                                float* __restrict__ d_out, int32_t* __restrict__ ray_out) {
     // over capacity: the network kernels flag it; nothing is written here
@@ -241,7 +234,7 @@ __global__ void k_bounded_fine(const float* __restrict__ fcoarse, const int32_t*
         auto fat = [&](int j) { return __ldg(fcoarse + base + j); };
         float fine[kMaxFine];
         if (c >= 2) {
-            fine_from_coarse(zat, fat, c, inv_s, eps, n_f, fine);
+            fine_from_coarse(zat, fat, c, op, n_f, fine);
         } else {
             const float df = (hi - lo) / (float)n_f;
             for (int k = 0; k < n_f; ++k) fine[k] = lo + ((float)k + 0.5f) * df;
@@ -287,11 +280,11 @@ __global__ void k_recovery_merge(int64_t n_rays, const uint8_t* __restrict__ sta
 }  // namespace
 
 int launch_composite(const SampleRec* rec, const int32_t* offsets, int per_ray, const uint8_t* status, int64_t n_rays,
-                     const int32_t* total_dev, int64_t capacity, float inv_s, float eps, float* rgb, float* depth,
+                     const int32_t* total_dev, int64_t capacity, Opacity op, float* rgb, float* depth,
                      float* wsum, float* normal, float* eik, cudaStream_t st) {
     if (n_rays == 0) return TSDFS_OK;
     k_composite<<<grid_1d(n_rays, kCompBlock), kCompBlock, 0, st>>>(rec, offsets, per_ray, status, n_rays, total_dev,
-                                                                    capacity, inv_s, eps, rgb, depth, wsum, normal, eik);
+                                                                    capacity, op, rgb, depth, wsum, normal, eik);
     return cuda_check(cudaGetLastError(), "composite launch");
 }
 
@@ -306,10 +299,10 @@ int launch_hier_setup(const tsdfs_grid* g, const float* ray_o, const float* ray_
 }
 
 int launch_hier_fine(const float* fcoarse, const float* tc, const float* t0, const float* te, int64_t n_rays,
-                     float inv_s, float eps, float* t_out, float* d_out, int n_c, int n_f, cudaStream_t st) {
+                     Opacity op, float* t_out, float* d_out, int n_c, int n_f, cudaStream_t st) {
     if (n_c < 2 || n_c > kMaxCoarse || n_f < 1 || n_f > kMaxFine)
         return fail(TSDFS_E_INVALID, "sample counts must be coarse in [2, 64], fine in [1, 32]");
-    k_hier_fine<<<grid_1d(n_rays, 128), 128, 0, st>>>(fcoarse, tc, t0, te, n_rays, inv_s, eps, t_out, d_out, n_c, n_f);
+    k_hier_fine<<<grid_1d(n_rays, 128), 128, 0, st>>>(fcoarse, tc, t0, te, n_rays, op, t_out, d_out, n_c, n_f);
     return cuda_check(cudaGetLastError(), "hier fine launch");
 }
 
@@ -320,10 +313,10 @@ int launch_bounded_counts(const int32_t* offsets, int64_t n_rays, int n_f, int64
 }
 
 int launch_bounded_fine(const float* fcoarse, const int32_t* offsets, const float* t_n, const float* t_f,
-                        const int32_t* offsets2, int64_t n_rays, int n_f, float inv_s, float eps, int64_t max_coarse,
+                        const int32_t* offsets2, int64_t n_rays, int n_f, Opacity op, int64_t max_coarse,
                         int64_t capacity2, float* t_out, float* d_out, int32_t* ray_out, cudaStream_t st) {
     if (n_f < 0 || n_f > kMaxFine) return fail(TSDFS_E_INVALID, "fine sample count must be in [0, 32]");
-    k_bounded_fine<<<grid_1d(n_rays, 128), 128, 0, st>>>(fcoarse, offsets, t_n, t_f, offsets2, n_rays, n_f, inv_s, eps,
+    k_bounded_fine<<<grid_1d(n_rays, 128), 128, 0, st>>>(fcoarse, offsets, t_n, t_f, offsets2, n_rays, n_f, op,
                                                          max_coarse, capacity2, t_out, d_out, ray_out);
     return cuda_check(cudaGetLastError(), "bounded fine launch");
 }

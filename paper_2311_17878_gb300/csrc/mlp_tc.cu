@@ -45,6 +45,10 @@ constexpr int kEpiWarpsF = 12;
 constexpr int kPartsF = kEpiWarpsF / 4;
 constexpr int kMmaWarpF = kEpiWarpsF;
 constexpr int kThreadsF = 32 * (kMmaWarpF + 1 + kStages);
+// CTAs per cluster of the full kernel: each weight chunk is read from L2 once per cluster, each
+// CTA copying 1/kCluster of it to every CTA of the cluster (multicast); the CTAs of a cluster
+// run the same number of tiles (the last may be empty) so that their weight rings stay in step
+constexpr int kCluster = 1;
 constexpr uint32_t kABytes = 64 * 1024;   // one A region (128 rows x 256 bf16)
 constexpr uint32_t kMaxSpin = 1u << 26;
 
@@ -152,6 +156,23 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
+// the same copy multicast to the CTAs of `mask` in the cluster (same smem offsets, each
+// CTA's mbarrier at `bar` receives the bytes that land in that CTA)
+__device__ __forceinline__ void bulk_g2s_mc(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -177,6 +198,13 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// arrive on the mbarrier at offset `bar` of every CTA in `mask` once this thread's MMAs complete
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                     bar),
+                 "h"(mask)
+                 : "memory");
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
@@ -323,7 +351,7 @@ struct TcParams {
 };
 
 template <int ARCH, bool F16>
-__global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
+__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
     using TA = TcArch<ARCH>;
     using A = Arch<ARCH>;
     constexpr int NL = TA::kLayers;
@@ -354,12 +382,15 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
         return;
     }
     const int64_t n_tiles = (total + kTileS - 1) / kTileS;
-    if ((int64_t)blockIdx.x >= n_tiles) return;
+    if (n_tiles == 0) return;
+    // every CTA runs the same number of rounds; tiles >= n_tiles are empty (no sample valid)
+    const int64_t n_tiles_pad = (n_tiles + gridDim.x - 1) / gridDim.x * gridDim.x;
+    constexpr uint16_t kMask = (uint16_t)((1u << kCluster) - 1u);
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; ++i) {
             mbar_init(bar_full0 + 8 * i, 1);
-            mbar_init(bar_empty0 + 8 * i, 1);
+            mbar_init(bar_empty0 + 8 * i, kCluster);   // one MMA commit per CTA of the cluster
         }
         mbar_init(bar_acc, 1);
         mbar_init(bar_a, 32 * kEpiWarpsF);
@@ -383,7 +414,8 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
-    __syncthreads();
+    if constexpr (kCluster > 1) cluster_sync();   // the peers' barriers exist before any remote arrive
+    else __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -393,7 +425,8 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
             const uint32_t own = (uint32_t)(warp - kMmaWarpF - 1);
             uint32_t seq = 0, issued = 0;
             bool ok = true;
-            for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            const uint32_t crank = kCluster > 1 ? cluster_rank() : 0u;
+            for (int64_t tile = blockIdx.x; tile < n_tiles_pad && ok; tile += gridDim.x) {
                 for (int L = 0; L < NL && ok; ++L) {
                     for (int c = 0; c < TA::chunks(L); ++c, ++seq) {
                         if (seq % kStages != own) continue;
@@ -401,8 +434,16 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                         if (!mbar_wait(bar_empty0 + 8 * own, ph ^ 1u, abort_flag)) { ok = false; break; }
                         const uint32_t bytes = (uint32_t)TA::chunk_bytes(L, c);
                         mbar_expect_tx(bar_full0 + 8 * own, bytes);
-                        bulk_g2s(smem_u32(stage_base + own * kStage), p.packed + TA::packed_offset(L, c), bytes,
-                                 bar_full0 + 8 * own);
+                        if constexpr (kCluster == 1) {
+                            bulk_g2s(smem_u32(stage_base + own * kStage), p.packed + TA::packed_offset(L, c), bytes,
+                                     bar_full0 + 8 * own);
+                        } else {
+                            // this CTA's 1/kCluster of the chunk, to the same offsets in every CTA
+                            const uint32_t part = bytes / kCluster;
+                            bulk_g2s_mc(smem_u32(stage_base + own * kStage) + crank * part,
+                                        p.packed + TA::packed_offset(L, c) + crank * part, part, bar_full0 + 8 * own,
+                                        kMask);
+                        }
                         ++issued;
                     }
                 }
@@ -412,13 +453,18 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                 for (uint32_t it = 0; it < kMaxSpin && !mbar_try(bar_full0 + 8 * own, (issued - 1) & 1u); ++it) {
                 }
             }
+            if (kCluster > 1 && ok && issued > 0) {
+                // the last use of this stage released by every CTA's MMAs: no peer commit is
+                // still on its way to this CTA's barrier when it exits
+                if (!mbar_wait(bar_empty0 + 8 * own, (issued - 1) & 1u, abort_flag)) set_status(p.status, TSDFS_DEV_TIMEOUT);
+            }
         }
     } else if (warp == kMmaWarpF) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
             uint32_t seq = 0, lc = 0;
             bool ok = true;
-            for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            for (int64_t tile = blockIdx.x; tile < n_tiles_pad && ok; tile += gridDim.x) {
                 for (int L = 0; L < NL && ok; ++L, ++lc) {
                     const TcLayer ly = TA::layer(L);
                     if (!mbar_wait(bar_a, lc & 1u, abort_flag)) { ok = false; break; }
@@ -456,7 +502,8 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                                 mma_bf16(tmem, ad0, bd, idesc_mma<F16>(128, ly.Np), acc);
                             }
                         }
-                        mma_commit(bar_empty0 + 8 * s);
+                        if constexpr (kCluster > 1) mma_commit_mc(bar_empty0 + 8 * s, kMask);
+                        else mma_commit(bar_empty0 + 8 * s);
                         ++seq;
                     }
                     if (!ok) break;
@@ -551,7 +598,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
             return true;
         };
         ok = build_table(blockIdx.x);
-        for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        for (int64_t tile = blockIdx.x; tile < n_tiles_pad && ok; tile += gridDim.x) {
             // (the sample table of this tile was built before the loop or during the last one)
             // ---- layer-0 input: encoding rows, stored as 16x256b-ordered stmatrix fragments ----
             {
@@ -848,7 +895,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                 // the next tile's table, while the colour layers' MMAs run: every warp
                 // has left the SDF output layer (the last reader of this tile's table)
                 // once colour layer 0's accumulator is complete
-                if (L == LS && tile + gridDim.x < n_tiles && !build_table(tile + gridDim.x)) {
+                if (L == LS && tile + gridDim.x < n_tiles_pad && !build_table(tile + gridDim.x)) {
                     ok = false;
                     break;
                 }
@@ -857,7 +904,8 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
         if (!ok) set_status(p.status, TSDFS_DEV_TIMEOUT);
     }
     tc_fence_before();
-    __syncthreads();
+    if constexpr (kCluster > 1) cluster_sync();   // no peer copy or arrive is still aimed at this CTA
+    else __syncthreads();
     tc_fence_after();
     if (warp == kMmaWarpF) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
@@ -1169,9 +1217,30 @@ int launch_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t tiles = (max_samples + kTileS - 1) / kTileS;
-    unsigned blocks = (unsigned)(tiles < sms ? (tiles < 1 ? 1 : tiles) : sms);
-    k_mlp_tc<ARCH, F16><<<blocks, kThreadsF, smem, st>>>(p);
+    // persistent grid: as many clusters as are resident at once (two SMs of one GPC each)
+    static int max_clusters[2][2] = {{0, 0}, {0, 0}};
+    int& mc = max_clusters[ARCH][F16 ? 1 : 0];
+    if (mc == 0) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)(sms / kCluster * kCluster), 1, 1);
+        cfg.blockDim = dim3(kThreadsF, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = kCluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int rc = cuda_check(cudaOccupancyMaxActiveClusters(&mc, k_mlp_tc<ARCH, F16>, &cfg), "mlp_tc cluster occupancy");
+        if (rc) return rc;
+        if (mc < 1) return fail(TSDFS_E_UNSUPPORTED, "mlp_tc: no cluster of %d CTAs fits on the device", kCluster);
+    }
+    const int64_t tiles = (max_samples + kTileS - 1) / kTileS;
+    int64_t blocks = tiles < (int64_t)mc * kCluster ? tiles : (int64_t)mc * kCluster;
+    blocks = (blocks + kCluster - 1) / kCluster * kCluster;
+    if (blocks < kCluster) blocks = kCluster;
+    k_mlp_tc<ARCH, F16><<<(unsigned)blocks, kThreadsF, smem, st>>>(p);
     return cuda_check(cudaGetLastError(), "mlp_tc launch");
 }
 

@@ -289,6 +289,7 @@ class MLPSpec:
     pe_sdf: int = 0            # positional-encoding octaves of the SDF input
     pe_dir: int = 0            # positional-encoding octaves of the view direction
     skip_layer: int = -1       # SDF layer whose input is concat(h, gamma(x)) / sqrt(2)
+    opacity: int = 0           # SDF-to-opacity transform: 0 NeuS, 1 VolSDF Laplace density (a = inv_s)
 
     def packed(self, which):
         layers = self.sdf if which == "sdf" else self.rgb

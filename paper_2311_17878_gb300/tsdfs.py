@@ -28,6 +28,7 @@ TSDFS_F32, TSDFS_F16 = 0, 1
 TSDFS_MISS, TSDFS_BOUNDED, TSDFS_FALLBACK = 0, 1, 2
 TSDFS_ARCH_TINY, TSDFS_ARCH_ROOM = 0, 1
 TSDFS_PREC_F32, TSDFS_PREC_BF16, TSDFS_PREC_F16 = 0, 1, 2
+TSDFS_OPACITY_NEUS, TSDFS_OPACITY_VOLSDF = 0, 1
 TSDFS_DEV_SAMPLES_OVERFLOW, TSDFS_DEV_MARCH_CAP, TSDFS_DEV_TIMEOUT, TSDFS_DEV_NONFINITE = 1, 2, 4, 8
 
 EXPORTS = ["tsdfs_last_error", "tsdfs_sync_status", "tsdfs_grid_init", "tsdf_integrate", "tsdfs_inside_mask_words",
@@ -59,7 +60,7 @@ class tsdfs_bounds_params(C.Structure):
 class tsdfs_mlp(C.Structure):
     _fields_ = [("arch", C.c_int32), ("precision", C.c_int32), ("sdf_w", C.c_void_p), ("rgb_w", C.c_void_p),
                 ("packed", C.c_void_p), ("center", C.c_float * 3), ("scale", C.c_float), ("inv_s", C.c_float),
-                ("beta", C.c_float), ("alpha_eps", C.c_float)]
+                ("beta", C.c_float), ("alpha_eps", C.c_float), ("opacity", C.c_int32)]
 
 
 def lib():
@@ -385,7 +386,8 @@ class Mlp:
             self.packed = torch.zeros(max(tsdfs_packed_size(spec.arch), 1), dtype=torch.uint8, device=device)
         self.c = tsdfs_mlp(spec.arch, precision, self.sdf_w.data_ptr(), self.rgb_w.data_ptr(),
                            self.packed.data_ptr() if self.packed is not None else None,
-                           (C.c_float * 3)(*spec.center), spec.scale, spec.inv_s, spec.beta, spec.alpha_eps)
+                           (C.c_float * 3)(*spec.center), spec.scale, spec.inv_s, spec.beta, spec.alpha_eps,
+                           spec.opacity)
         if precision != TSDFS_PREC_F32:
             tsdfs_pack_mlp(self, self.packed)
 

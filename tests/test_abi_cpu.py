@@ -86,6 +86,13 @@ def test_invalid_arguments_fail_on_host(L):
     m.precision = T.TSDFS_PREC_BF16
     assert L.render_rays(C.byref(m), *([C.c_void_p(8)] * 7), C.c_int64(1), C.c_int64(1), *([C.c_void_p(8)] * 5),
                          C.c_void_p(8), C.c_size_t(1 << 20), None) == T.TSDFS_E_INVALID  # packed is NULL
+    # unknown opacity transform
+    m.precision = 0
+    m.opacity = 5
+    assert L.render_rays(C.byref(m), *([C.c_void_p(8)] * 7), C.c_int64(1), C.c_int64(1), *([C.c_void_p(8)] * 5),
+                         C.c_void_p(8), C.c_size_t(1 << 20), None) == T.TSDFS_E_INVALID
+    assert "opacity" in T.tsdfs_last_error()
+    m.opacity = T.TSDFS_OPACITY_VOLSDF
     # zero rays is a no-op that succeeds without touching the device
     m.precision = 0
     assert L.render_rays(C.byref(m), *([None] * 6), C.c_int64(0), C.c_int64(0), *([None] * 5), None, C.c_size_t(0),

@@ -6,6 +6,7 @@ Each pin compares with something independent: finite differences, the
 composition of affine maps, numpy's sin/cos, the telescoping closed form of
 NeuS weights on a plane, invariants of Eq. 1, a brute-force quantile table.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -210,12 +211,13 @@ def test_midpoint_section_widths_are_uniform():
     assert torch.allclose(t[0], torch.tensor([1.125, 1.375, 1.625, 1.875], dtype=DT))
 
 
-def test_training_loss_gradient_matches_central_differences():
+@pytest.mark.parametrize("opacity", [orr.OPACITY_NEUS, orr.OPACITY_VOLSDF])
+def test_training_loss_gradient_matches_central_differences(opacity):
     """Reverse-mode gradient of L1 colour + 0.1 eikonal (through grad f in the
     opacity, the colour-network normal and the eikonal term) against FP64
-    central differences, h = 1e-6, on 64 rays."""
+    central differences, h = 1e-6, on 64 rays; NeuS and VolSDF opacity."""
     wl = synth.tiny_workload()
-    spec = synth.tiny_mlp()
+    spec = dataclasses.replace(synth.tiny_mlp(), opacity=opacity)
     rng = np.random.default_rng(12)
     idx = rng.choice(4096, 64, replace=False)
     o, d = wl.rays_o[idx], wl.rays_d[idx]
