@@ -304,6 +304,8 @@ def run_ours(args, ws, rank, local):
         max_samples = tot if args.recovery_tau is None else n * max(bp.n_max, bp.n_fallback)
         del bcount
     bounds = T.Bounds(n, device=dev)
+    # the march's launch shape, picked by the library's autotuner on the first view's rays
+    tuned = bounds.autotune(grid, rays[0][0], rays[0][1], bp, mask, reps=3)
     rend = T.Renderer(mlp, n, max_samples, device=dev)
     rec = T.Recovery(mlp, n, bp.n_fallback, device=dev) if args.recovery_tau is not None else None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
@@ -429,6 +431,7 @@ def run_ours(args, ws, rank, local):
                    "grid_source": "analytic" if args.workload == "large" else args.grid_source,
                    "ray_subset": args.rays or None,
                    "cuda_graph": bool(graphs), "train_pitch_deg": synth.TRAIN_PITCH_DEG,
+                   "march_launch": {"block": tuned[0], "blocks_per_sm": tuned[1], "autotuned_ms": tuned[2]},
                    "recovery_tau": args.recovery_tau,
                    "networks": "SDF 8x256 PE6 skip4 + colour 4x256 PE4", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}, rays independent", "wall_s": t_wall},

@@ -261,6 +261,27 @@ int render_rays_hier96(const tsdfs_mlp* mlp, const tsdfs_grid* grid, const float
                        int64_t n_rays, float t_near, float t_far, float* rgb, float* depth, float* wsum,
                        float* normal, void* workspace, size_t ws_bytes, tsdfs_stream_t stream);
 
+/* ---- launch shape of the march and its autotuner --------------------------
+ * tsdf_ray_bounds and tsdf_recovery_bounds launch a grid-stride march of
+ * `block` threads per block and at most `blocks_per_sm` blocks per SM (default
+ * 128 and 64).  Outputs do not depend on the shape (rays are independent);
+ * speed does.  tsdfs_autotune_bounds times every candidate (block in {64, 128,
+ * 256} x blocks_per_sm in {4, 8, 16, 32, 64}) with CUDA events on `stream`,
+ * `reps` launches each of tsdf_ray_bounds on the caller's rays and buffers
+ * (arguments as tsdf_ray_bounds; the outputs hold the last run's results), and
+ * keeps the fastest as this device's shape; best_ms (host, or NULL) receives
+ * its time per launch.  It synchronises the stream: call it at set-up, not
+ * inside a captured step.  tsdfs_set_bounds_launch_shape sets a shape
+ * directly (0, 0 = the default; block a multiple of 32 in [32, 256],
+ * blocks_per_sm in [1, 1024]); tsdfs_bounds_launch_shape reads it.  The shape
+ * is per device and process-wide.                                            */
+int tsdfs_autotune_bounds(const tsdfs_grid* grid, const uint32_t* inside_mask, const float* ray_o, const float* ray_d,
+                          int64_t n_rays, const tsdfs_bounds_params* params, float* t_n, float* t_f,
+                          int32_t* n_samples, int32_t* offsets, float* t_zero, uint8_t* status, void* workspace,
+                          size_t ws_bytes, int32_t reps, float* best_ms, tsdfs_stream_t stream);
+int tsdfs_set_bounds_launch_shape(int32_t block, int32_t blocks_per_sm);
+int tsdfs_bounds_launch_shape(int32_t* block, int32_t* blocks_per_sm);
+
 /* ---- adaptive sample counts relative to the mean interval (Sec. 3.4) -------
  * Samples sit at equal spacing inside [t_n, t_f], so a ray's count is
  * proportional to its interval's length; the supplementary ray study scales it

@@ -15,7 +15,8 @@ int grid_check(const tsdfs_grid* g);
 
 namespace {
 
-constexpr int kBoundsBlock = 128;
+constexpr int kBoundsBlock = 128;      // default threads per block of the march
+constexpr int kBoundsMaxBlock = 256;   // largest block the autotuner may pick
 constexpr int kScanBlock = 1024;
 constexpr int kScanItems = 8;
 constexpr int kScanChunk = kScanBlock * kScanItems;
@@ -144,7 +145,7 @@ __device__ __forceinline__ bool clip_box(const GridDev& g, const float o[3], con
     return hit && t0 < t_end;
 }
 
-__global__ void __launch_bounds__(kBoundsBlock) k_ray_bounds(GridDev g, const uint32_t* __restrict__ mask,
+__global__ void __launch_bounds__(kBoundsMaxBlock) k_ray_bounds(GridDev g, const uint32_t* __restrict__ mask,
                                                              const float* __restrict__ ray_o,
                                                              const float* __restrict__ ray_d, int64_t n_rays,
                                                              BoundsDev p, float* __restrict__ t_n_out,
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(kBoundsBlock) k_ray_bounds(GridDev g, const ui
 
 // ---- recovery (Sec. 4.5): BOUNDED rays whose weight sum stayed below tau are
 // rendered again over the whole [t0, t_end] with n_fallback samples ----
-__global__ void __launch_bounds__(kBoundsBlock) k_recovery_bounds(GridDev g, const float* __restrict__ ray_o,
+__global__ void __launch_bounds__(kBoundsMaxBlock) k_recovery_bounds(GridDev g, const float* __restrict__ ray_o,
                                                                   const float* __restrict__ ray_d, int64_t n_rays,
                                                                   BoundsDev p, float tau,
                                                                   const float* __restrict__ wsum,
@@ -379,6 +380,31 @@ __global__ void __launch_bounds__(kScanBlock) k_chunk_scan(const int32_t* __rest
 
 int64_t scan_chunks(int64_t n) { return (n + kScanChunk - 1) / kScanChunk; }
 
+// ---- launch shape of the march (threads per block, resident blocks per SM of the
+// grid-stride grid): the default, or what tsdfs_autotune_bounds measured, per device
+namespace {
+struct MarchShape {
+    int block = kBoundsBlock;
+    int blocks_per_sm = 64;
+};
+std::mutex g_shape_mu;
+MarchShape g_shape[64];
+
+MarchShape march_shape() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MarchShape{};
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    return g_shape[dev];
+}
+
+unsigned march_grid(int64_t n_rays, const MarchShape& sh) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return grid_1d(n_rays, sh.block, sms * sh.blocks_per_sm);
+}
+}  // namespace
+
 // exclusive scan of n counts into offsets[0..n]; `sums` needs scan_chunks(n) ints
 int exclusive_scan(const int32_t* cnt, int64_t n, int32_t* offsets, int32_t* sums, cudaStream_t st) {
     const int64_t chunks = scan_chunks(n);
@@ -426,9 +452,10 @@ extern "C" int tsdf_ray_bounds(const tsdfs_grid* g, const uint32_t* mask, const 
         GridDev gd{g->tsdf, g->dtype == TSDFS_F16, {g->nx, g->ny, g->nz}, {g->origin[0], g->origin[1], g->origin[2]},
                    g->voxel_size, g->trunc};
         BoundsDev bd{p->d_s, p->t_near, p->t_far, p->step, p->nb_radius, p->m_confirm, p->n_max, p->n_fallback};
+        const MarchShape sh = march_shape();
         ProfScope ps("ray_bounds", st);
-        k_ray_bounds<<<grid_1d(n_rays, kBoundsBlock, 152 * 64), kBoundsBlock, 0, st>>>(
-            gd, mask, ray_o, ray_d, n_rays, bd, t_n, t_f, n_samples, t_zero, status, device_status_word());
+        k_ray_bounds<<<march_grid(n_rays, sh), sh.block, 0, st>>>(gd, mask, ray_o, ray_d, n_rays, bd, t_n, t_f,
+                                                                  n_samples, t_zero, status, device_status_word());
         rc = cuda_check(cudaGetLastError(), "tsdf_ray_bounds launch");
         if (rc) return rc;
     }
@@ -458,8 +485,9 @@ extern "C" int tsdf_recovery_bounds(const tsdfs_grid* g, const float* ray_o, con
         GridDev gd{g->tsdf, g->dtype == TSDFS_F16, {g->nx, g->ny, g->nz}, {g->origin[0], g->origin[1], g->origin[2]},
                    g->voxel_size, g->trunc};
         BoundsDev bd{p->d_s, p->t_near, p->t_far, p->step, p->nb_radius, p->m_confirm, p->n_max, p->n_fallback};
+        const MarchShape sh = march_shape();
         ProfScope ps("recovery_bounds", st);
-        k_recovery_bounds<<<grid_1d(n_rays, kBoundsBlock, 152 * 64), kBoundsBlock, 0, st>>>(
+        k_recovery_bounds<<<march_grid(n_rays, sh), sh.block, 0, st>>>(
             gd, ray_o, ray_d, n_rays, bd, tau, wsum, status, t_n2, t_f2, n2, status2);
         rc = cuda_check(cudaGetLastError(), "tsdf_recovery_bounds launch");
         if (rc) return rc;
@@ -658,4 +686,88 @@ extern "C" int tsdf_adaptive_counts(const float* t_n, const float* t_f, const ui
         if (rc) return rc;
     }
     return exclusive_scan(n_samples, n_rays, offsets, sums, st);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the march's launch shape.  The march is latency-bound (a DDA per
+// thread, scattered reads of an L2-resident grid), so its speed depends on how
+// many rays are in flight per SM and how rays are grouped into blocks; the best
+// shape depends on the grid, the ray batch and the device.  The candidates are
+// every (threads per block, resident blocks per SM) pair below; each is timed
+// with CUDA events on the caller's stream over `reps` launches on the caller's
+// own rays (outputs are identical for every shape: rays are independent), and
+// the fastest becomes this device's shape for tsdf_ray_bounds and
+// tsdf_recovery_bounds.  It synchronises the stream: a set-up call.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kTuneBlocks[] = {64, 128, 256};
+constexpr int kTunePerSm[] = {4, 8, 16, 32, 64};
+}  // namespace
+
+extern "C" int tsdfs_bounds_launch_shape(int32_t* block, int32_t* blocks_per_sm) {
+    if (!block || !blocks_per_sm) return fail(TSDFS_E_INVALID, "block and blocks_per_sm must be non-NULL");
+    const MarchShape sh = march_shape();
+    *block = sh.block;
+    *blocks_per_sm = sh.blocks_per_sm;
+    return TSDFS_OK;
+}
+
+extern "C" int tsdfs_set_bounds_launch_shape(int32_t block, int32_t blocks_per_sm) {
+    if (block == 0 && blocks_per_sm == 0) {
+        block = kBoundsBlock;
+        blocks_per_sm = 64;
+    }
+    if (block < 32 || block > kBoundsMaxBlock || block % 32 != 0 || blocks_per_sm < 1 || blocks_per_sm > 1024)
+        return fail(TSDFS_E_INVALID, "block must be a multiple of 32 in [32, %d], blocks_per_sm in [1, 1024]",
+                    kBoundsMaxBlock);
+    int dev = 0;
+    int rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc) return rc;
+    if (dev < 0 || dev >= 64) return fail(TSDFS_E_UNSUPPORTED, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shape[dev].block = block;
+    g_shape[dev].blocks_per_sm = blocks_per_sm;
+    return TSDFS_OK;
+}
+
+extern "C" int tsdfs_autotune_bounds(const tsdfs_grid* g, const uint32_t* mask, const float* ray_o, const float* ray_d,
+                                     int64_t n_rays, const tsdfs_bounds_params* p, float* t_n, float* t_f,
+                                     int32_t* n_samples, int32_t* offsets, float* t_zero, uint8_t* status, void* ws,
+                                     size_t ws_bytes, int32_t reps, float* best_ms, tsdfs_stream_t stream) {
+    if (reps < 1 || reps > 1000) return fail(TSDFS_E_INVALID, "reps must be in [1, 1000]");
+    if (n_rays < 1) return fail(TSDFS_E_INVALID, "autotuning needs at least one ray");
+    int32_t b0 = 0, s0 = 0;
+    tsdfs_bounds_launch_shape(&b0, &s0);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = cuda_check(cudaEventCreate(&e0), "autotune event");
+    if (!rc) rc = cuda_check(cudaEventCreate(&e1), "autotune event");
+    float best = 1e30f;
+    int best_b = b0, best_s = s0;
+    for (int bi = 0; !rc && bi < (int)(sizeof(kTuneBlocks) / sizeof(int)); ++bi)
+        for (int si = 0; !rc && si < (int)(sizeof(kTunePerSm) / sizeof(int)); ++si) {
+            rc = tsdfs_set_bounds_launch_shape(kTuneBlocks[bi], kTunePerSm[si]);
+            // one untimed launch (argument checks, caches), then `reps` timed
+            if (!rc) rc = tsdf_ray_bounds(g, mask, ray_o, ray_d, n_rays, p, t_n, t_f, n_samples, offsets, t_zero,
+                                          status, ws, ws_bytes, stream);
+            if (!rc) rc = cuda_check(cudaEventRecord(e0, st), "autotune event record");
+            for (int r = 0; !rc && r < reps; ++r)
+                rc = tsdf_ray_bounds(g, mask, ray_o, ray_d, n_rays, p, t_n, t_f, n_samples, offsets, t_zero, status,
+                                     ws, ws_bytes, stream);
+            if (!rc) rc = cuda_check(cudaEventRecord(e1, st), "autotune event record");
+            if (!rc) rc = cuda_check(cudaEventSynchronize(e1), "autotune event sync");
+            float ms = 0.0f;
+            if (!rc) rc = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "autotune elapsed");
+            if (!rc && ms < best) {
+                best = ms;
+                best_b = kTuneBlocks[bi];
+                best_s = kTunePerSm[si];
+            }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    const int rc2 = tsdfs_set_bounds_launch_shape(rc ? b0 : best_b, rc ? s0 : best_s);
+    if (rc) return rc;
+    if (best_ms) *best_ms = best / (float)reps;
+    return rc2;
 }

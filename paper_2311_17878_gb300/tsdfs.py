@@ -37,7 +37,8 @@ EXPORTS = ["tsdfs_last_error", "tsdfs_sync_status", "tsdfs_grid_init", "tsdf_int
            "render_rays_backward", "tsdfs_packed_size", "tsdfs_pack_mlp", "tsdfs_sdf_param_count",
            "tsdfs_rgb_param_count", "tsdf_ray_bounds_noalloc", "tsdf_ray_bounds_noalloc_max_rays",
            "tsdf_recovery_bounds", "tsdf_recovery_merge", "tsdfs_check_mlp", "tsdfs_adaptive_counts_workspace_size",
-           "tsdf_adaptive_counts", "tsdfs_hier_bounded_workspace_size", "render_rays_hier_bounded", "tsdfs_profile", "tsdfs_profile_read"]
+           "tsdf_adaptive_counts", "tsdfs_hier_bounded_workspace_size", "render_rays_hier_bounded",
+           "tsdfs_autotune_bounds", "tsdfs_set_bounds_launch_shape", "tsdfs_bounds_launch_shape", "tsdfs_profile", "tsdfs_profile_read"]
 
 
 class TsdfsError(RuntimeError):
@@ -228,6 +229,30 @@ def render_rays_hier96(mlp: "Mlp", grid: "Grid", ray_o, ray_d, t_near, t_far, rg
                                     _p(workspace), C.c_size_t(workspace.numel()), _stream()))
 
 
+def tsdfs_autotune_bounds(grid: "Grid", inside_mask, ray_o, ray_d, p, t_n, t_f, n_samples, offsets, t_zero, status,
+                          workspace, reps=3):
+    """Time the march's candidate launch shapes on these rays and keep the fastest; returns
+    (block, blocks_per_sm, ms per launch)."""
+    n = ray_o.shape[0]
+    best = C.c_float(0.0)
+    _check(lib().tsdfs_autotune_bounds(C.byref(grid.c), _p(inside_mask), _p(ray_o), _p(ray_d), C.c_int64(n),
+                                       C.byref(p), _p(t_n), _p(t_f), _p(n_samples), _p(offsets), _p(t_zero),
+                                       _p(status), _p(workspace), C.c_size_t(workspace.numel()), C.c_int32(reps),
+                                       C.byref(best), _stream()))
+    b, s = tsdfs_bounds_launch_shape()
+    return b, s, best.value
+
+
+def tsdfs_set_bounds_launch_shape(block=0, blocks_per_sm=0):
+    _check(lib().tsdfs_set_bounds_launch_shape(C.c_int32(block), C.c_int32(blocks_per_sm)))
+
+
+def tsdfs_bounds_launch_shape():
+    b, s = C.c_int32(0), C.c_int32(0)
+    _check(lib().tsdfs_bounds_launch_shape(C.byref(b), C.byref(s)))
+    return b.value, s.value
+
+
 def tsdfs_adaptive_counts_workspace_size(n_rays: int) -> int:
     return int(lib().tsdfs_adaptive_counts_workspace_size(C.c_int64(n_rays)))
 
@@ -365,6 +390,12 @@ class Bounds:
         self.t_zero = torch.empty(n, dtype=torch.float32, device=device)
         self.status = torch.empty(n, dtype=torch.uint8, device=device)
         self.workspace = _bytes(tsdfs_bounds_workspace_size(n), device)
+
+    def autotune(self, grid: Grid, rays_o, rays_d, bp, inside_mask=None, reps=3):
+        """Pick the march's launch shape on these rays (tsdfs_autotune_bounds); fills the outputs."""
+        p = bp if isinstance(bp, tsdfs_bounds_params) else bounds_params(bp)
+        return tsdfs_autotune_bounds(grid, inside_mask, rays_o, rays_d, p, self.t_n, self.t_f, self.n, self.offsets,
+                                     self.t_zero, self.status, self.workspace, reps)
 
     def compute(self, grid: Grid, rays_o, rays_d, bp, inside_mask=None):
         p = bp if isinstance(bp, tsdfs_bounds_params) else bounds_params(bp)

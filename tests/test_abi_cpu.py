@@ -139,6 +139,19 @@ def test_adaptive_counts_and_bounded_hier_arguments_fail_on_host(L):
     assert hb(8, 0, 0) == T.TSDFS_OK
 
 
+def test_bounds_launch_shape_arguments(L):
+    for b, sm in [(16, 8), (96 + 1, 8), (512, 8), (128, 0), (128, 2000)]:
+        assert L.tsdfs_set_bounds_launch_shape(C.c_int32(b), C.c_int32(sm)) == T.TSDFS_E_INVALID
+    assert L.tsdfs_bounds_launch_shape(None, None) == T.TSDFS_E_INVALID
+    v = C.c_void_p(8)
+    p = T.tsdfs_bounds_params(0.1, 0.0, 10.0, 0.1, 2, 15, 32, 96)
+    g = _grid_struct()
+    assert L.tsdfs_autotune_bounds(C.byref(g), None, v, v, C.c_int64(10), C.byref(p), v, v, v, v, None, v, v,
+                                   C.c_size_t(1 << 20), C.c_int32(0), None, None) == T.TSDFS_E_INVALID
+    assert L.tsdfs_autotune_bounds(C.byref(g), None, v, v, C.c_int64(0), C.byref(p), v, v, v, v, None, v, v,
+                                   C.c_size_t(1 << 20), C.c_int32(3), None, None) == T.TSDFS_E_INVALID
+
+
 def test_recovery_arguments_fail_on_host(L):
     g = _grid_struct()
     p = T.tsdfs_bounds_params(0.1, 0.0, 10.0, 0.1, 2, 15, 32, 96)

@@ -272,3 +272,33 @@ def test_degenerate_rays_bit_exact(use_mask):
         assert np.array_equal(got["offsets"], np.concatenate([[0], np.cumsum(ref["n"])]).astype(np.int32))
     assert set(np.unique(ref["status"])) >= {0, 1}
     check_status_clean()
+
+
+def test_every_march_launch_shape_bit_exact_and_autotune():
+    """The march's outputs do not depend on its launch shape: every shape the
+    autotuner may pick reproduces the oracle bit for bit on a ragged ray count
+    (several blocks and a partial one for each shape); the autotuner picks one of
+    them and leaves correct outputs behind."""
+    wl = synth.tiny_workload()
+    V, _ = cgrid.integrate_projective(wl.grid, wl.views, "f32")
+    n = 3001
+    o, d = wl.rays_o[:n], wl.rays_d[:n]
+    ref = cgrid.ray_bounds(wl.grid, V, o, d, wl.bounds, "f32")
+    try:
+        for block in (64, 128, 256):
+            for per_sm in (1, 4, 64):
+                T.tsdfs_set_bounds_launch_shape(block, per_sm)
+                assert T.tsdfs_bounds_launch_shape() == (block, per_sm)
+                for use_mask in (False, True):
+                    assert_bounds_equal(run_bounds(wl.grid, V, o, d, wl.bounds, use_mask), ref)
+        g = T.Grid(wl.grid, V=dev(V), W=torch.zeros(V.shape, dtype=torch.uint8, device="cuda"))
+        b = T.Bounds(n)
+        block, per_sm, ms = b.autotune(g, dev(o), dev(d), wl.bounds, g.inside_mask(wl.bounds.nb_radius), reps=2)
+        torch.cuda.synchronize()
+        assert block in (64, 128, 256) and per_sm in (4, 8, 16, 32, 64) and ms > 0
+        assert T.tsdfs_bounds_launch_shape() == (block, per_sm)
+        assert_bounds_equal({k: getattr(b, k).cpu().numpy() for k in ("t_n", "t_f", "n", "t_zero", "status")}, ref)
+    finally:
+        T.tsdfs_set_bounds_launch_shape(0, 0)
+    assert T.tsdfs_bounds_launch_shape() == (128, 64)
+    check_status_clean()
