@@ -149,6 +149,28 @@ int tsdfs_grid_init(const tsdfs_grid* grid, tsdfs_stream_t stream);
 int tsdf_integrate(const tsdfs_grid* grid, const float* depth, int32_t n_views, int32_t height, int32_t width,
                    const float* K, const float* c2w, tsdfs_stream_t stream);
 
+/* tsdf_integrate_raycast: Alg. 2 as printed, marching every training ray.
+ *   Views in order; for each pixel of a view: v = the unit ray through the
+ *   pixel centre, normalise(R ((px + 1/2 - cx)/fx, (py + 1/2 - cy)/fy, 1)),
+ *   o = the camera centre, p* = o + D v (D = the stored range); the ray is
+ *   clipped to the grid box from t = 0 and walked voxel by voxel (the walk of
+ *   tsdf_ray_bounds); at each voxel s = clamp(v . (p* - c), -D_T, D_T)
+ *   (D = +inf: s = D_T); the walk stops at the first s <= -D_T, else the voxel
+ *   records s / D_T and one visit.  The rays of one view are applied together:
+ *   every voxel with k > 0 visits gets V <- (W V + sum) / (W + k),
+ *   W <- min(W + k, 255) (for w = 1 and no saturation this equals the one-ray-
+ *   at-a-time running mean).  Each s / D_T is summed as an integer number of
+ *   2^-32 units (round to nearest even), exactly and in any order, and the
+ *   update is done in FP64 and rounded once (to half, per view, for half
+ *   storage): results are reproducible bit for bit.  Rays and walk in fp32
+ *   with round-to-nearest and no contraction.  At most 2^21 pixels per view.
+ *   Arguments as tsdf_integrate; workspace >= tsdfs_raycast_workspace_size
+ *   (12 bytes per voxel).                                                   */
+size_t tsdfs_raycast_workspace_size(const tsdfs_grid* grid);
+int tsdf_integrate_raycast(const tsdfs_grid* grid, const float* depth, int32_t n_views, int32_t height,
+                           int32_t width, const float* K, const float* c2w, void* workspace, size_t ws_bytes,
+                           tsdfs_stream_t stream);
+
 /* ---- far-phase neighbourhood test, precomputed (Alg. 1) ---------------------
  * bit (k*ny + j)*nx + i of mask_bits (uint32 words, little bit order) is 1 iff
  * every voxel within Chebyshev radius nb_radius of (i, j, k) has V < 0 (out of

@@ -99,6 +99,28 @@ def integrate_raycast(grid, views):
     return V, W
 
 
+def integrate_raycast_batched(grid, views, mode="f32", V=None, W=None):
+    """Alg. 2 as printed with each view's rays applied together (reading R27).
+
+    mode "f64": FP64 reference (sums in FP64); "f32": fp32-exact mode (binary32
+    rays and walk, fixed-point sums in 2^-32 units, FP64 update rounded once).
+    ``grid.dtype`` "f16" stores V as IEEE half (uint16 bits), rounded once per view.
+    V/W: initial state (default V = -1, W = 0).  Returns (V, W)."""
+    f16 = grid.dtype == "f16"
+    if V is None:
+        V = np.full(grid.shape_zyx, 0xBC00, np.uint16) if f16 else \
+            np.full(grid.shape_zyx, -1.0, np.float64 if mode == "f64" else np.float32)
+    else:
+        V = np.array(V, np.uint16 if f16 else (np.float64 if mode == "f64" else np.float32), copy=True)
+    W = np.zeros(grid.shape_zyx, np.uint8) if W is None else np.array(W, np.uint8, copy=True)
+    fn = lib().orc_integrate_raycast_batched_f64 if mode == "f64" else lib().orc_integrate_raycast_batched_f32
+    dep, K, P = _f(views.depth), _f(views.K), _f(views.c2w)
+    fn(C.c_int(grid.nx), C.c_int(grid.ny), C.c_int(grid.nz), _p(_origin(grid)), C.c_double(grid.voxel_size),
+       C.c_double(grid.trunc), _p(dep), C.c_int(dep.shape[0]), C.c_int(dep.shape[1]), C.c_int(dep.shape[2]),
+       _p(K), _p(P), _p(V), _p(W), C.c_int(int(f16)))
+    return V, W
+
+
 def _grid_values(V, f16):
     if f16:
         return np.ascontiguousarray(V, np.uint16)

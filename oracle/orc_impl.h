@@ -339,3 +339,84 @@ void SFX(orc_clip_rays)(int nx, int ny, int nz, const double* origin, double vs_
         t_end_out[r] = te;
     }
 }
+
+/* ---- Alg. 2 as printed, the rays of one view applied together (reading R27) --
+ * Views in order.  For every pixel (row-major) of a view: unit ray through the
+ * pixel centre, v = normalise(R ((px + 1/2 - cx)/fx, (py + 1/2 - cy)/fy, 1)),
+ * o = the camera centre, p* = o + D v (D = the stored range); clip to the grid
+ * box from t = 0; voxel walk (above); at each voxel s = clamp(v . (p* - c),
+ * -D_T, D_T) (D = +inf: s = D_T); stop at the first s <= -D_T, else the voxel
+ * records s / D_T and one visit.  After all the view's rays, every voxel with
+ * k > 0 visits: V <- (W V + sum) / (W + k), W <- min(W + k, 255).
+ * FP64 mode: sum in FP64.  fp32-exact mode: s / D_T in binary32, each turned
+ * into an integer number of 2^-32 units (round to nearest even) and summed
+ * exactly, then the update in FP64 and one rounding to binary32 (or to half for
+ * half storage, once per view).  V is R* or uint16 half bits, W uint8.       */
+void SFX(orc_integrate_raycast_batched)(int nx, int ny, int nz, const double* origin, double vs_d, double trunc_d,
+                                        const float* depth, int nv, int H, int Wd, const float* K, const float* c2w,
+                                        void* V, uint8_t* Wt, int f16)
+{
+    const int n[3] = {nx, ny, nz};
+    const size_t nvox = (size_t)nx * ny * nz;
+    R vs = (R)vs_d, trunc = (R)trunc_d, org[3] = {(R)origin[0], (R)origin[1], (R)origin[2]}, lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) { lo[a] = org[a]; hi[a] = org[a] + (R)n[a] * vs; }
+    const int fixed = sizeof(R) == sizeof(float);
+    double* dsum = fixed ? NULL : (double*)calloc(nvox, sizeof(double));
+    int64_t* qsum = fixed ? (int64_t*)calloc(nvox, sizeof(int64_t)) : NULL;
+    uint32_t* cnt = (uint32_t*)calloc(nvox, sizeof(uint32_t));
+    if ((!dsum && !qsum) || !cnt) { free(dsum); free(qsum); free(cnt); return; }
+    for (int view = 0; view < nv; ++view) {
+        const float* P = c2w + 12 * view;
+        R fx = (R)K[4 * view], fy = (R)K[4 * view + 1], cx = (R)K[4 * view + 2], cy = (R)K[4 * view + 3];
+        R o[3] = {(R)P[3], (R)P[7], (R)P[11]};
+        for (int py = 0; py < H; ++py)
+            for (int px = 0; px < Wd; ++px) {
+                R a = (((R)px + (R)0.5) - cx) / fx, b = (((R)py + (R)0.5) - cy) / fy;
+                R d[3];
+                for (int k = 0; k < 3; ++k) d[k] = ((R)P[4 * k] * a + (R)P[4 * k + 1] * b) + (R)P[4 * k + 2];
+                R nn = R_SQRT((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+                for (int k = 0; k < 3; ++k) d[k] = d[k] / nn;
+                R D = (R)depth[((size_t)view * H + py) * Wd + px];
+                R t0, t_end;
+                if (!SFX(clip_aabb)(o, d, lo, hi, (R)0, (R)INFINITY, &t0, &t_end)) continue;
+                R ps[3];
+                for (int k = 0; k < 3; ++k) ps[k] = o[k] + D * d[k];
+                SFX(dda_t) s;
+                SFX(dda_init)(&s, o, d, org, vs, n, t0);
+                int ok = 1;
+                while (ok && s.t < t_end) {
+                    R sx = trunc;
+                    if (!isinf(D)) {
+                        R e[3];
+                        for (int k = 0; k < 3; ++k) e[k] = ps[k] - (org[k] + ((R)s.X[k] + (R)0.5) * vs);
+                        R dot = (d[0] * e[0] + d[1] * e[1]) + d[2] * e[2];
+                        sx = dot > trunc ? trunc : (dot < -trunc ? -trunc : dot);
+                    }
+                    if (!(sx > -trunc)) break;
+                    size_t idx = ((size_t)s.X[2] * ny + s.X[1]) * nx + s.X[0];
+                    R x = sx / trunc;
+                    if (fixed) qsum[idx] += (int64_t)llrint((double)x * 4294967296.0);
+                    else dsum[idx] += (double)x;
+                    cnt[idx] += 1;
+                    ok = SFX(dda_next)(&s);
+                }
+            }
+        for (size_t q = 0; q < nvox; ++q) {
+            if (!cnt[q]) continue;
+            double v = f16 ? (double)orc_f16_to_f32(((uint16_t*)V)[q]) : (double)((R*)V)[q];
+            double sum = fixed ? (double)qsum[q] / 4294967296.0 : dsum[q];
+            double w = (double)Wt[q];
+            double vn = (w * v + sum) / (w + (double)cnt[q]);
+            if (f16) ((uint16_t*)V)[q] = orc_f32_to_f16((float)vn);
+            else ((R*)V)[q] = (R)vn;
+            uint32_t wn = (uint32_t)Wt[q] + cnt[q];
+            Wt[q] = (uint8_t)(wn > 255u ? 255u : wn);
+            cnt[q] = 0;
+            if (fixed) qsum[q] = 0;
+            else dsum[q] = 0.0;
+        }
+    }
+    free(dsum);
+    free(qsum);
+    free(cnt);
+}

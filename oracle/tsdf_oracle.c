@@ -8,6 +8,7 @@
  * second time in the fp32-exact mode described in orc_impl.h):
  *   orc_integrate_projective_{f64,f32}  Eq. 3 + Alg. 2, per-voxel projective form
  *   orc_integrate_raycast_f64           Alg. 2 as printed: march each training ray
+ *   orc_integrate_raycast_batched_{f64,f32}  the same, each view's rays applied together
  *   orc_ray_bounds_{f64,f32}            Alg. 1 (near / far phases) + Sec. 3.4 count
  *   orc_dda_sequence_{f64,f32}          the voxel walk of Alg. 1 ("NextVoxel")
  *   orc_inside_mask_{f64,f32}           Alg. 1's neighbourhood test for every voxel
@@ -17,6 +18,7 @@
  * are listed in the design notes of the repository.
  */
 #include <math.h>
+#include <stdlib.h>
 #include <stddef.h>
 #include <stdint.h>
 #include <string.h>

@@ -9,6 +9,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "march.cuh"
 
 namespace tsdfs {
 int grid_check(const tsdfs_grid* g);
@@ -21,54 +22,10 @@ constexpr int kScanBlock = 1024;
 constexpr int kScanItems = 8;
 constexpr int kScanChunk = kScanBlock * kScanItems;
 
-struct GridDev {
-    const void* V;
-    int f16;
-    int n[3];
-    float org[3];
-    float vs;
-    float trunc;
-};
-
 struct BoundsDev {
     float d_s, t_near, t_far, step;
     int nb_radius, m_confirm, n_max, n_fallback;
 };
-
-__device__ __forceinline__ float gval(const GridDev& g, int i, int j, int k) {
-    if (i < 0 || j < 0 || k < 0 || i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return -1.0f;
-    const int64_t idx = ((int64_t)k * g.n[1] + j) * g.n[0] + i;
-    return g.f16 ? __half2float(__ldg(reinterpret_cast<const __half*>(g.V) + idx))
-                 : __ldg(reinterpret_cast<const float*>(g.V) + idx);
-}
-
-struct Dda {
-    int X[3], step[3];
-    float t, inv[3];
-};
-
-__device__ __forceinline__ float dda_cross(const Dda& s, const GridDev& g, const float o[3], int a) {
-    if (s.step[a] == 0) return __int_as_float(0x7f800000);
-    const float b = (float)(s.X[a] + (s.step[a] > 0 ? 1 : 0));
-    return __fmul_rn(__fsub_rn(__fadd_rn(g.org[a], __fmul_rn(b, g.vs)), o[a]), s.inv[a]);
-}
-
-__device__ __forceinline__ bool dda_next(Dda& s, const GridDev& g, const float o[3]) {
-    const float tx = dda_cross(s, g, o, 0), ty = dda_cross(s, g, o, 1), tz = dda_cross(s, g, o, 2);
-    int a = 0;
-    float tm = tx;
-    if (ty < tm) { a = 1; tm = ty; }
-    if (tz < tm) { a = 2; tm = tz; }
-    s.t = tm;
-    // the axis is a run-time value: update the three components by selection, so the
-    // walk state stays in registers
-    s.X[0] += a == 0 ? s.step[0] : 0;
-    s.X[1] += a == 1 ? s.step[1] : 0;
-    s.X[2] += a == 2 ? s.step[2] : 0;
-    const int xa = a == 0 ? s.X[0] : (a == 1 ? s.X[1] : s.X[2]);
-    const int na = a == 0 ? g.n[0] : (a == 1 ? g.n[1] : g.n[2]);
-    return xa >= 0 && xa < na;
-}
 
 __device__ __forceinline__ float trilinear(const GridDev& g, const float p[3]) {
     int i0[3];
@@ -116,35 +73,6 @@ __device__ __forceinline__ bool inside_bit(const uint32_t* __restrict__ mask, co
     return (__ldg(mask + (idx >> 5)) >> (idx & 31)) & 1u;
 }
 
-__device__ __forceinline__ void point_at(const float o[3], const float d[3], float t, float p[3]) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) p[a] = __fadd_rn(o[a], __fmul_rn(t, d[a]));
-}
-
-// clip a ray to the grid box ("RenderingCube") within [t_near, t_far]: [t0, t_end]
-__device__ __forceinline__ bool clip_box(const GridDev& g, const float o[3], const float d[3], float t_near, float t_far,
-                                         float& t0, float& t_end) {
-    const float kInf = __int_as_float(0x7f800000);
-    float tmin = -kInf, tmax = kInf;
-    bool hit = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float lo = g.org[a], hi = __fadd_rn(g.org[a], __fmul_rn((float)g.n[a], g.vs));
-        if (d[a] == 0.0f) {
-            if (o[a] < lo || o[a] > hi) hit = false;
-            continue;
-        }
-        const float inv = __fdiv_rn(1.0f, d[a]);
-        const float t1 = __fmul_rn(__fsub_rn(lo, o[a]), inv), t2 = __fmul_rn(__fsub_rn(hi, o[a]), inv);
-        const float tl = t1 < t2 ? t1 : t2, th = t1 < t2 ? t2 : t1;
-        if (tl > tmin) tmin = tl;
-        if (th < tmax) tmax = th;
-    }
-    t0 = t_near > tmin ? t_near : tmin;
-    t_end = t_far < tmax ? t_far : tmax;
-    return hit && t0 < t_end;
-}
-
 __global__ void __launch_bounds__(kBoundsMaxBlock) k_ray_bounds(GridDev g, const uint32_t* __restrict__ mask,
                                                              const float* __restrict__ ray_o,
                                                              const float* __restrict__ ray_d, int64_t n_rays,
@@ -172,15 +100,7 @@ __global__ void __launch_bounds__(kBoundsMaxBlock) k_ray_bounds(GridDev g, const
         }
         // ---- voxel walk init ----
         Dda s;
-        s.t = t0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            s.step[a] = d[a] > 0.0f ? 1 : (d[a] < 0.0f ? -1 : 0);
-            s.inv[a] = d[a] != 0.0f ? __fdiv_rn(1.0f, d[a]) : kInf;
-            const float pa = __fadd_rn(o[a], __fmul_rn(t0, d[a]));
-            const float gg = floorf(__fdiv_rn(__fsub_rn(pa, g.org[a]), g.vs));
-            s.X[a] = gg >= 0.0f ? (gg > (float)(g.n[a] - 1) ? g.n[a] - 1 : (int)gg) : 0;
-        }
+        dda_init(s, g, o, d, t0);
         // ---- near phase: first voxel with V(centre) <= D_s ----
         // The walk does not depend on the values: the next kAhead voxels are stepped and
         // their values requested before the current one is tested, so the loads are in

@@ -6,6 +6,7 @@
 // operation order that tsdfs.h documents, so pixel choices, weights and
 // values are reproducible bit for bit.
 #include "common.cuh"
+#include "march.cuh"
 
 namespace tsdfs {
 
@@ -139,6 +140,84 @@ __global__ void __launch_bounds__(kMTX * kMTY) k_inside_mask(const void* __restr
     }
 }
 
+// ---- Alg. 2 as printed, one view at a time: march every pixel's ray ---------------
+// Thread per pixel of view `view`: unit ray through the pixel centre, clipped to the grid
+// box from t = 0; voxel walk of Alg. 1; at each voxel s = clamp(v . (p* - c), -D_T, D_T),
+// p* = o + D v (D = +inf: s = D_T); stop at the first s <= -D_T, else add s / D_T in fixed
+// point (2^-32 units: integer sums, so the result does not depend on the order in which
+// the rays arrive) and one count to the voxel.  k_raycast_apply folds the view's sums in.
+constexpr double kFix = 4294967296.0;   // 2^32
+
+__global__ void __launch_bounds__(kFuseBlock) k_raycast_view(GridDev g, const float* __restrict__ depth, int H, int Wd,
+                                                             const float* __restrict__ Kc, const float* __restrict__ c2w,
+                                                             int view, unsigned long long* __restrict__ qsum,
+                                                             uint32_t* __restrict__ cnt) {
+    const float kInf = __int_as_float(0x7f800000);
+    const float* P = c2w + 12 * view;
+    const float fx = __ldg(Kc + 4 * view), fy = __ldg(Kc + 4 * view + 1);
+    const float cx = __ldg(Kc + 4 * view + 2), cy = __ldg(Kc + 4 * view + 3);
+    const float o[3] = {__ldg(P + 3), __ldg(P + 7), __ldg(P + 11)};
+    const int max_steps = g.n[0] + g.n[1] + g.n[2] + 8;
+    const int64_t n_pix = (int64_t)H * Wd;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_pix; q += (int64_t)gridDim.x * blockDim.x) {
+        const int px = (int)(q % Wd), py = (int)(q / Wd);
+        const float a = __fdiv_rn(__fsub_rn(__fadd_rn((float)px, 0.5f), cx), fx);
+        const float b = __fdiv_rn(__fsub_rn(__fadd_rn((float)py, 0.5f), cy), fy);
+        float d[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            d[k] = __fadd_rn(__fadd_rn(__fmul_rn(__ldg(P + 4 * k), a), __fmul_rn(__ldg(P + 4 * k + 1), b)),
+                             __ldg(P + 4 * k + 2));
+        const float nn = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2])));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d[k] = __fdiv_rn(d[k], nn);
+        const float D = __ldg(depth + ((int64_t)view * H + py) * Wd + px);
+        float t0, t_end;
+        if (!clip_box(g, o, d, 0.0f, kInf, t0, t_end)) continue;
+        float ps[3];   // p* = o + D v
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ps[k] = __fadd_rn(o[k], __fmul_rn(D, d[k]));
+        const bool free_ray = isinf(D);
+        Dda s;
+        dda_init(s, g, o, d, t0);
+        for (int st = 0; st < max_steps && s.t < t_end; ++st) {
+            float sx = g.trunc;
+            if (!free_ray) {
+                float e[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    e[k] = __fsub_rn(ps[k], __fadd_rn(g.org[k], __fmul_rn(__fadd_rn((float)s.X[k], 0.5f), g.vs)));
+                const float dot = __fadd_rn(__fadd_rn(__fmul_rn(d[0], e[0]), __fmul_rn(d[1], e[1])), __fmul_rn(d[2], e[2]));
+                sx = dot > g.trunc ? g.trunc : (dot < -g.trunc ? -g.trunc : dot);
+            }
+            if (!(sx > -g.trunc)) break;
+            const long long qv = __double2ll_rn((double)__fdiv_rn(sx, g.trunc) * kFix);
+            const int64_t idx = ((int64_t)s.X[2] * g.n[1] + s.X[1]) * g.n[0] + s.X[0];
+            atomicAdd(qsum + idx, (unsigned long long)qv);
+            atomicAdd(cnt + idx, 1u);
+            if (!dda_next(s, g, o)) break;
+        }
+    }
+}
+
+// the view's k visits of a voxel: V <- (W V + sum) / (W + k) in FP64, rounded once to the
+// storage type; W <- min(W + k, 255); the accumulators are cleared for the next view
+__global__ void k_raycast_apply(void* V, int f16, uint8_t* W, unsigned long long* __restrict__ qsum,
+                                uint32_t* __restrict__ cnt, int64_t n) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = cnt[q];
+        if (k == 0) continue;
+        const long long sum = (long long)qsum[q];
+        const float v = load_v(V, f16, q);
+        const uint32_t w = W[q];
+        const double vn = ((double)w * (double)v + (double)sum / kFix) / (double)(w + k);
+        store_v(V, f16, q, (float)vn);
+        W[q] = (uint8_t)(w + k > 255u ? 255u : w + k);
+        qsum[q] = 0ull;
+        cnt[q] = 0u;
+    }
+}
+
 }  // namespace
 
 int grid_check(const tsdfs_grid* g) {
@@ -185,6 +264,44 @@ extern "C" int tsdf_integrate(const tsdfs_grid* g, const float* depth, int32_t n
         g->nx, g->ny, g->nz, g->origin[0], g->origin[1], g->origin[2], g->voxel_size, g->trunc, g->tsdf,
         g->dtype == TSDFS_F16, g->weight, depth, n_views, H, W, K, c2w);
     return cuda_check(cudaGetLastError(), "tsdf_integrate launch");
+}
+
+extern "C" size_t tsdfs_raycast_workspace_size(const tsdfs_grid* g) {
+    if (!g || g->nx <= 0 || g->ny <= 0 || g->nz <= 0) return 0;
+    const int64_t n = (int64_t)g->nx * g->ny * g->nz;
+    return (size_t)n * (sizeof(unsigned long long) + sizeof(uint32_t)) + 512;
+}
+
+extern "C" int tsdf_integrate_raycast(const tsdfs_grid* g, const float* depth, int32_t n_views, int32_t H, int32_t W,
+                                      const float* K, const float* c2w, void* ws, size_t ws_bytes,
+                                      tsdfs_stream_t stream) {
+    int rc = grid_check(g);
+    if (rc) return rc;
+    if (!g->weight) return fail(TSDFS_E_INVALID, "grid weight pointer is NULL");
+    if (n_views < 0 || H <= 0 || W <= 0) return fail(TSDFS_E_INVALID, "n_views must be >= 0 and H, W > 0");
+    if (n_views == 0) return TSDFS_OK;
+    if (!depth || !K || !c2w) return fail(TSDFS_E_INVALID, "depth, K and c2w must be non-NULL");
+    if ((int64_t)H * W > (int64_t)1 << 21)
+        return fail(TSDFS_E_INVALID, "at most 2^21 pixels per view (the fixed-point sums hold 2^21 visits)");
+    if (!ws || ws_bytes < tsdfs_raycast_workspace_size(g)) return fail(TSDFS_E_WORKSPACE, "raycast workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = (int64_t)g->nx * g->ny * g->nz;
+    uintptr_t p = (reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255);
+    unsigned long long* qsum = reinterpret_cast<unsigned long long*>(p);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(p + (size_t)n * sizeof(unsigned long long));
+    ProfScope ps("integrate_raycast", st);
+    rc = cuda_check(cudaMemsetAsync(qsum, 0, (size_t)n * (sizeof(unsigned long long) + sizeof(uint32_t)), st),
+                    "raycast workspace clear");
+    if (rc) return rc;
+    GridDev gd{g->tsdf, g->dtype == TSDFS_F16, {g->nx, g->ny, g->nz}, {g->origin[0], g->origin[1], g->origin[2]},
+               g->voxel_size, g->trunc};
+    const int f16 = g->dtype == TSDFS_F16;
+    for (int v = 0; v < n_views; ++v) {
+        k_raycast_view<<<grid_1d((int64_t)H * W, kFuseBlock, 152 * 16), kFuseBlock, 0, st>>>(gd, depth, H, W, K, c2w, v,
+                                                                                            qsum, cnt);
+        k_raycast_apply<<<grid_1d(n, 256, 152 * 16), 256, 0, st>>>(g->tsdf, f16, g->weight, qsum, cnt, n);
+    }
+    return cuda_check(cudaGetLastError(), "tsdf_integrate_raycast launch");
 }
 
 extern "C" int64_t tsdfs_inside_mask_words(const tsdfs_grid* g) {

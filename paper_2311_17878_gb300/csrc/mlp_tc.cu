@@ -44,11 +44,18 @@ constexpr int kThreads = 32 * (kMmaWarp + 1 + kStages);
 constexpr int kEpiWarpsF = 12;
 constexpr int kPartsF = kEpiWarpsF / 4;
 constexpr int kMmaWarpF = kEpiWarpsF;
-constexpr int kThreadsF = 32 * (kMmaWarpF + 1 + kStages);
+// weight slots of the full kernel: the kStages ring stages, and during the colour layers also
+// one slot in the A1 operand region (the tangent rows, which the colour layers do not use
+// beyond the spill of their input rows), so that more chunks are in flight while the colour
+// layers' single-accumulator MMAs consume them; one producer warp per slot
+constexpr bool kA1Slots = true;
+constexpr int kSlots = kA1Slots ? kStages + 1 : kStages;
+constexpr int kThreadsF = 32 * (kMmaWarpF + 1 + kSlots);
 // CTAs per cluster of the full kernel: each weight chunk is read from L2 once per cluster, each
 // CTA copying 1/kCluster of it to every CTA of the cluster (multicast); the CTAs of a cluster
 // run the same number of tiles (the last may be empty) so that their weight rings stay in step
 constexpr int kCluster = 1;
+static_assert(!kA1Slots || (kStages == 2 && kCluster == 1), "the A1 weight slot assumes the 2-stage ring, no multicast");
 constexpr uint32_t kABytes = 64 * 1024;   // one A region (128 rows x 256 bf16)
 constexpr uint32_t kMaxSpin = 1u << 26;
 
@@ -108,6 +115,35 @@ template <int ARCH> struct TcArch {
     }
     __host__ __device__ static constexpr size_t full_smem_bytes() {
         return 2 * (size_t)kABytes + kStages * (size_t)stage_bytes() + bias_bytes() + kBarBytes + table_bytes();
+    }
+    // index of chunk c of layer L within a tile's chunk sequence; chunks of the SDF layers
+    __host__ __device__ static constexpr int chunk_index(int L, int c) {
+        int j = 0;
+        for (int l = 0; l < L; ++l) j += chunks(l);
+        return j + c;
+    }
+    __host__ __device__ static constexpr int sdf_chunks() { return chunk_index(A::kSdfLayers, 0); }
+    __host__ __device__ static constexpr int rgb_chunks() { return chunk_index(kLayers, 0) - sdf_chunks(); }
+    __host__ __device__ static constexpr int64_t max_rgb_chunk_bytes() {
+        int64_t m = 0;
+        for (int l = A::kSdfLayers; l < kLayers; ++l)
+            for (int c = 0; c < chunks(l); ++c) m = chunk_bytes(l, c) > m ? chunk_bytes(l, c) : m;
+        return m;
+    }
+    // bytes of the A1 region the colour layers' input rows spill into (A0 holds 128 rows of
+    // 256 columns; a wider colour input continues into A1), rounded up to 1 KB
+    __host__ __device__ static constexpr uint32_t a1_spill() {
+        int64_t m = 0;
+        for (int l = A::kSdfLayers; l < kLayers; ++l) {
+            const int64_t b = 256 * (int64_t)layer(l).Kp - (int64_t)kABytes;
+            m = b > m ? b : m;
+        }
+        return (uint32_t)((m + 1023) / 1024 * 1024);
+    }
+    // weight slots that fit in the rest of A1 while the colour layers run (at most one)
+    __host__ __device__ static constexpr int a1_slots() {
+        const int64_t n = ((int64_t)kABytes - a1_spill()) / max_rgb_chunk_bytes();
+        return n > 1 ? 1 : (int)n;
     }
     __host__ __device__ static constexpr uint32_t stage_bytes() {
         int64_t m = 0;
@@ -363,12 +399,25 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
     uint8_t* stage_base = smem + 2 * kABytes;
     float* sbias = reinterpret_cast<float*>(stage_base + kStages * kStage);
     uint64_t* bars = reinterpret_cast<uint64_t*>(stage_base + kStages * kStage + TA::bias_bytes());
-    // bars: full[2], empty[2], acc_ready, a_ready, drain
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4);
+    // bars: full[kSlots], empty[kSlots], acc_ready, a_ready, drain, table
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kSlots + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    const uint32_t bar_full0 = smem_u32(bars + 0), bar_empty0 = smem_u32(bars + kStages);
-    const uint32_t bar_acc = smem_u32(bars + 2 * kStages), bar_a = smem_u32(bars + 2 * kStages + 1);
-    const uint32_t bar_drain = smem_u32(bars + 2 * kStages + 2), bar_tab = smem_u32(bars + 2 * kStages + 3);
+    const uint32_t bar_full0 = smem_u32(bars + 0), bar_empty0 = smem_u32(bars + kSlots);
+    const uint32_t bar_acc = smem_u32(bars + 2 * kSlots), bar_a = smem_u32(bars + 2 * kSlots + 1);
+    const uint32_t bar_drain = smem_u32(bars + 2 * kSlots + 2), bar_tab = smem_u32(bars + 2 * kSlots + 3);
+    // weight slot of chunk c of layer L: SDF chunks alternate over the ring stages, colour
+    // chunks cycle over the ring stages and the free part of A1; and the slot's shared address
+    constexpr int kColSlots = kA1Slots ? kStages + TA::a1_slots() : kStages;
+    static_assert(kColSlots <= kSlots, "weight slot count");
+    auto slot_of = [&](int L, int c) -> uint32_t {
+        const int j = TA::chunk_index(L, c);
+        if (L < LS) return (uint32_t)(j % kStages);
+        return (uint32_t)((j - TA::sdf_chunks()) % kColSlots);
+    };
+    auto slot_addr = [&](uint32_t sl) -> uint32_t {
+        return sl < (uint32_t)kStages ? smem_u32(stage_base + sl * kStage)
+                                      : smem_u32(A1) + TA::a1_spill() + (sl - kStages) * (uint32_t)TA::max_rgb_chunk_bytes();
+    };
     // per-tile sample table: [x~ (3), direction (3), t, delta] per sample, then sin / cos of the
     // positional encodings of x~ (kPeSdf octaves) and of the direction (kPeDir octaves)
     float* s_x = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + kBarBytes);
@@ -388,7 +437,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
     constexpr uint16_t kMask = (uint16_t)((1u << kCluster) - 1u);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kStages; ++i) {
+        for (int i = 0; i < kSlots; ++i) {
             mbar_init(bar_full0 + 8 * i, 1);
             mbar_init(bar_empty0 + 8 * i, kCluster);   // one MMA commit per CTA of the cluster
         }
@@ -420,29 +469,30 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
     const uint32_t tmem = *tmem_slot;
 
     if (warp > kMmaWarpF) {
-        // ------------------------------------------- producers (one per stage)
-        if (lane == 0) {
+        // ------------------ producers: one warp per weight slot (one thread's bulk copies
+        // do not overlap each other, and a second spinning lane would stall the first)
+        if (lane == 0 && warp - kMmaWarpF - 1 < kColSlots) {
             const uint32_t own = (uint32_t)(warp - kMmaWarpF - 1);
-            uint32_t seq = 0, issued = 0;
+            // ring stages: use u waits for the release of use u - 1; the A1 slot: use u waits
+            // for release u (release 0 of a tile is the end of the SDF MMAs, which read A1)
+            const uint32_t first = own < (uint32_t)kStages ? 1u : 0u;
+            uint32_t issued = 0;
             bool ok = true;
             const uint32_t crank = kCluster > 1 ? cluster_rank() : 0u;
             for (int64_t tile = blockIdx.x; tile < n_tiles_pad && ok; tile += gridDim.x) {
                 for (int L = 0; L < NL && ok; ++L) {
-                    for (int c = 0; c < TA::chunks(L); ++c, ++seq) {
-                        if (seq % kStages != own) continue;
-                        const uint32_t ph = (seq / kStages) & 1u;
-                        if (!mbar_wait(bar_empty0 + 8 * own, ph ^ 1u, abort_flag)) { ok = false; break; }
+                    for (int c = 0; c < TA::chunks(L); ++c) {
+                        if (slot_of(L, c) != own) continue;
+                        if (!mbar_wait(bar_empty0 + 8 * own, (issued & 1u) ^ first, abort_flag)) { ok = false; break; }
                         const uint32_t bytes = (uint32_t)TA::chunk_bytes(L, c);
                         mbar_expect_tx(bar_full0 + 8 * own, bytes);
                         if constexpr (kCluster == 1) {
-                            bulk_g2s(smem_u32(stage_base + own * kStage), p.packed + TA::packed_offset(L, c), bytes,
-                                     bar_full0 + 8 * own);
+                            bulk_g2s(slot_addr(own), p.packed + TA::packed_offset(L, c), bytes, bar_full0 + 8 * own);
                         } else {
                             // this CTA's 1/kCluster of the chunk, to the same offsets in every CTA
                             const uint32_t part = bytes / kCluster;
-                            bulk_g2s_mc(smem_u32(stage_base + own * kStage) + crank * part,
-                                        p.packed + TA::packed_offset(L, c) + crank * part, part, bar_full0 + 8 * own,
-                                        kMask);
+                            bulk_g2s_mc(slot_addr(own) + crank * part, p.packed + TA::packed_offset(L, c) + crank * part,
+                                        part, bar_full0 + 8 * own, kMask);
                         }
                         ++issued;
                     }
@@ -453,7 +503,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
                 for (uint32_t it = 0; it < kMaxSpin && !mbar_try(bar_full0 + 8 * own, (issued - 1) & 1u); ++it) {
                 }
             }
-            if (kCluster > 1 && ok && issued > 0) {
+            if (kCluster > 1 && ok && issued > 0) {   // (ring stages only: kA1Slots is off with clusters)
                 // the last use of this stage released by every CTA's MMAs: no peer commit is
                 // still on its way to this CTA's barrier when it exits
                 if (!mbar_wait(bar_empty0 + 8 * own, (issued - 1) & 1u, abort_flag)) set_status(p.status, TSDFS_DEV_TIMEOUT);
@@ -462,7 +512,10 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
     } else if (warp == kMmaWarpF) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            uint32_t seq = 0, lc = 0;
+            uint32_t uses[kSlots];
+#pragma unroll
+            for (int i = 0; i < kSlots; ++i) uses[i] = 0;
+            uint32_t lc = 0;
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < n_tiles_pad && ok; tile += gridDim.x) {
                 for (int L = 0; L < NL && ok; ++L, ++lc) {
@@ -473,11 +526,15 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
                     const uint32_t a0 = smem_u32(A0), a1 = smem_u32(A1);
                     const bool last_sdf = ly.sdf && ly.idx == LS - 1;
                     for (int c = 0; c < TA::chunks(L); ++c) {
-                        const uint32_t s = seq % kStages, ph = (seq / kStages) & 1u;
+                        const uint32_t s = slot_of(L, c);
+                        uint32_t ph = 0;
+#pragma unroll
+                        for (int i = 0; i < kSlots; ++i)
+                            if ((uint32_t)i == s) ph = uses[i]++ & 1u;
                         if (!mbar_wait(bar_full0 + 8 * s, ph, abort_flag)) { ok = false; break; }
                         tc_fence_after();
                         const int kc = TA::chunk_k(L, c);
-                        const uint32_t b0 = smem_u32(stage_base + s * kStage);
+                        const uint32_t b0 = slot_addr(s);
                         const uint32_t b_sbo = (uint32_t)(kc / 8) * 128u;
                         for (int kk = 0; kk < kc / 16; ++kk) {
                             const int k = c * kKChunk + kk * 16;
@@ -502,12 +559,19 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
                                 mma_bf16(tmem, ad0, bd, idesc_mma<F16>(128, ly.Np), acc);
                             }
                         }
+                        // release the slot, except the A1 slot after its last colour chunk of the
+                        // tile: the next tile's SDF layers own A1 until their MMAs are done
+                        const bool keep = s >= (uint32_t)kStages &&
+                                          TA::chunk_index(L, c) - TA::sdf_chunks() + kColSlots >= TA::rgb_chunks();
                         if constexpr (kCluster > 1) mma_commit_mc(bar_empty0 + 8 * s, kMask);
-                        else mma_commit(bar_empty0 + 8 * s);
-                        ++seq;
+                        else if (!keep) mma_commit(bar_empty0 + 8 * s);
                     }
                     if (!ok) break;
                     mma_commit(bar_acc);
+                    if (L == LS - 1) {
+                        // the SDF MMAs are the last readers of A1 in this tile: release its slots
+                        for (int i = kStages; i < kColSlots; ++i) mma_commit(bar_empty0 + 8 * i);
+                    }
                 }
             }
             if (!ok) {

@@ -38,7 +38,8 @@ EXPORTS = ["tsdfs_last_error", "tsdfs_sync_status", "tsdfs_grid_init", "tsdf_int
            "tsdfs_rgb_param_count", "tsdf_ray_bounds_noalloc", "tsdf_ray_bounds_noalloc_max_rays",
            "tsdf_recovery_bounds", "tsdf_recovery_merge", "tsdfs_check_mlp", "tsdfs_adaptive_counts_workspace_size",
            "tsdf_adaptive_counts", "tsdfs_hier_bounded_workspace_size", "render_rays_hier_bounded",
-           "tsdfs_autotune_bounds", "tsdfs_set_bounds_launch_shape", "tsdfs_bounds_launch_shape", "tsdfs_profile", "tsdfs_profile_read"]
+           "tsdfs_autotune_bounds", "tsdfs_set_bounds_launch_shape", "tsdfs_bounds_launch_shape",
+           "tsdfs_raycast_workspace_size", "tsdf_integrate_raycast", "tsdfs_profile", "tsdfs_profile_read"]
 
 
 class TsdfsError(RuntimeError):
@@ -74,7 +75,7 @@ def lib():
             L.tsdfs_last_error.restype = C.c_char_p
             for name in ["tsdfs_bounds_workspace_size", "tsdfs_render_workspace_size", "tsdfs_hier_workspace_size",
                          "tsdfs_backward_workspace_size", "tsdfs_packed_size", "tsdfs_adaptive_counts_workspace_size",
-                         "tsdfs_hier_bounded_workspace_size"]:
+                         "tsdfs_hier_bounded_workspace_size", "tsdfs_raycast_workspace_size"]:
                 getattr(L, name).restype = C.c_size_t
             for name in ["tsdfs_inside_mask_words", "tsdfs_sdf_param_count", "tsdfs_rgb_param_count"]:
                 getattr(L, name).restype = C.c_int64
@@ -82,6 +83,7 @@ def lib():
             L.tsdfs_render_workspace_size.argtypes = [C.c_void_p, C.c_int64, C.c_int64]
             L.tsdfs_hier_workspace_size.argtypes = [C.c_void_p, C.c_int64]
             L.tsdfs_adaptive_counts_workspace_size.argtypes = [C.c_int64]
+            L.tsdfs_raycast_workspace_size.argtypes = [C.c_void_p]
             L.tsdfs_hier_bounded_workspace_size.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_int64]
             L.tsdfs_backward_workspace_size.argtypes = [C.c_void_p, C.c_int64, C.c_int64]
             L.tsdfs_packed_size.argtypes = [C.c_int32]
@@ -135,6 +137,17 @@ def tsdfs_sync_status():
 
 def tsdfs_grid_init(grid: "Grid"):
     _check(lib().tsdfs_grid_init(C.byref(grid.c), _stream()))
+
+
+def tsdfs_raycast_workspace_size(grid: "Grid") -> int:
+    return int(lib().tsdfs_raycast_workspace_size(C.byref(grid.c)))
+
+
+def tsdf_integrate_raycast(grid: "Grid", depth, K, c2w, workspace):
+    _cuda(depth, torch.float32, "depth"), _cuda(K, torch.float32, "K"), _cuda(c2w, torch.float32, "c2w")
+    nv, H, W = depth.shape
+    _check(lib().tsdf_integrate_raycast(C.byref(grid.c), _p(depth), C.c_int32(nv), C.c_int32(H), C.c_int32(W), _p(K),
+                                        _p(c2w), _p(workspace), C.c_size_t(workspace.numel()), _stream()))
 
 
 def tsdf_integrate(grid: "Grid", depth, K, c2w):
@@ -351,6 +364,12 @@ class Grid:
 
     def integrate(self, depth, K, c2w):
         tsdf_integrate(self, depth, K, c2w)
+        return self
+
+    def integrate_raycast(self, depth, K, c2w, workspace=None):
+        """Alg. 2 as printed (every pixel's ray marched), each view's rays applied together."""
+        ws = workspace if workspace is not None else _bytes(tsdfs_raycast_workspace_size(self), self.V.device)
+        tsdf_integrate_raycast(self, depth, K, c2w, ws)
         return self
 
     def save(self, path):

@@ -152,6 +152,22 @@ def test_bounds_launch_shape_arguments(L):
                                    C.c_size_t(1 << 20), C.c_int32(3), None, None) == T.TSDFS_E_INVALID
 
 
+def test_raycast_fusion_arguments_fail_on_host(L):
+    g = _grid_struct()
+    v = C.c_void_p(8)
+    ws = L.tsdfs_raycast_workspace_size(C.byref(g))
+    assert ws >= 8 * 8 * 8 * 12
+    call = lambda nv, H, W, wsb: L.tsdf_integrate_raycast(C.byref(g), v, C.c_int32(nv), C.c_int32(H), C.c_int32(W),
+                                                         v, v, v, C.c_size_t(wsb), None)
+    assert call(-1, 4, 4, ws) == T.TSDFS_E_INVALID
+    assert call(1, 0, 4, ws) == T.TSDFS_E_INVALID
+    assert call(1, 2048, 2048, ws) == T.TSDFS_E_INVALID and "2^21" in T.tsdfs_last_error()
+    assert call(1, 4, 4, ws - 1) == T.TSDFS_E_WORKSPACE
+    assert call(0, 4, 4, 0) == T.TSDFS_OK   # no views: nothing to do, no device touched
+    g.weight = None
+    assert call(1, 4, 4, ws) == T.TSDFS_E_INVALID
+
+
 def test_recovery_arguments_fail_on_host(L):
     g = _grid_struct()
     p = T.tsdfs_bounds_params(0.1, 0.0, 10.0, 0.1, 2, 15, 32, 96)
