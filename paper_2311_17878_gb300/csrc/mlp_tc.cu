@@ -51,11 +51,7 @@ constexpr int kMmaWarpF = kEpiWarpsF;
 constexpr bool kA1Slots = true;
 constexpr int kSlots = kA1Slots ? kStages + 1 : kStages;
 constexpr int kThreadsF = 32 * (kMmaWarpF + 1 + kSlots);
-// CTAs per cluster of the full kernel: each weight chunk is read from L2 once per cluster, each
-// CTA copying 1/kCluster of it to every CTA of the cluster (multicast); the CTAs of a cluster
-// run the same number of tiles (the last may be empty) so that their weight rings stay in step
-constexpr int kCluster = 1;
-static_assert(!kA1Slots || (kStages == 2 && kCluster == 1), "the A1 weight slot assumes the 2-stage ring, no multicast");
+static_assert(!kA1Slots || kStages == 2, "the A1 weight slot assumes the 2-stage ring");
 constexpr uint32_t kABytes = 64 * 1024;   // one A region (128 rows x 256 bf16)
 constexpr uint32_t kMaxSpin = 1u << 26;
 
@@ -192,23 +188,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
-// the same copy multicast to the CTAs of `mask` in the cluster (same smem offsets, each
-// CTA's mbarrier at `bar` receives the bytes that land in that CTA)
-__device__ __forceinline__ void bulk_g2s_mc(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;" ::"r"(
-            dst),
-        "l"(src), "r"(bytes), "r"(bar), "h"(mask)
-        : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -234,13 +213,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-// arrive on the mbarrier at offset `bar` of every CTA in `mask` once this thread's MMAs complete
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                     bar),
-                 "h"(mask)
-                 : "memory");
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
@@ -345,6 +317,43 @@ __device__ __forceinline__ void softplus_slope_tanh(float z, float half_beta, fl
     sg = fmaf(0.5f, t, 0.5f);
     h = fmaxf(z, 0.0f) + (0.69314718055994531f - log1p_unit(fabsf(t))) * inv_beta;
 }
+// the same for two pre-activations at once in FP16 arithmetic, for the FP16-operand path
+// (its activation and tangent rows are rounded to FP16 for the next layer anyway): one
+// tanh.approx.f16x2 for both, the polynomial and the products in half2 (the correction
+// term is below ln 2 / beta, so its FP16 rounding is below that of the activation)
+__device__ __forceinline__ __half2 tanh_h2(__half2 x) {
+    uint32_t xi = *reinterpret_cast<uint32_t*>(&x), yi;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(yi) : "r"(xi));
+    return *reinterpret_cast<__half2*>(&yi);
+}
+struct SoftplusH2 {
+    __half2 half_beta, neg_inv_beta, ln2_inv_beta, c4, c3, c2, c1, half, zero;
+};
+__device__ __forceinline__ SoftplusH2 softplus_h2_consts(float half_beta, float inv_beta) {
+    SoftplusH2 k;
+    k.half_beta = __float2half2_rn(half_beta);
+    k.neg_inv_beta = __float2half2_rn(-inv_beta);
+    k.ln2_inv_beta = __float2half2_rn(0.69314718055994531f * inv_beta);
+    k.c4 = __float2half2_rn(-0.05692862346768379f);
+    k.c3 = __float2half2_rn(0.22263112664222717f);
+    k.c2 = __float2half2_rn(-0.4698040187358856f);
+    k.c1 = __float2half2_rn(0.9972487092018127f);
+    k.half = __float2half2_rn(0.5f);
+    k.zero = __float2half2_rn(0.0f);
+    return k;
+}
+__device__ __forceinline__ void softplus_slope_h2(float z0, float z1, const SoftplusH2& k, __half2& h, __half2& sg) {
+    const __half2 z = __floats2half2_rn(z0, z1);
+    const __half2 t = tanh_h2(__hmul2(z, k.half_beta));
+    sg = __hfma2(k.half, t, k.half);
+    const __half2 u = __habs2(t);
+    __half2 p = __hfma2(k.c4, u, k.c3);
+    p = __hfma2(p, u, k.c2);
+    p = __hfma2(p, u, k.c1);
+    p = __hmul2(p, u);
+    h = __hadd2(__hmax2(z, k.zero), __hfma2(p, k.neg_inv_beta, k.ln2_inv_beta));
+}
+__device__ __forceinline__ uint32_t h2u(__half2 v) { return *reinterpret_cast<uint32_t*>(&v); }
 
 // positional encoding entry j of coordinate vector xt, and its derivative along axis a
 __device__ __forceinline__ float enc_val(const float* xt, int j, int pe, int a, bool deriv) {
@@ -387,7 +396,7 @@ struct TcParams {
 };
 
 template <int ARCH, bool F16>
-__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
+__global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
     using TA = TcArch<ARCH>;
     using A = Arch<ARCH>;
     constexpr int NL = TA::kLayers;
@@ -431,15 +440,12 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
         return;
     }
     const int64_t n_tiles = (total + kTileS - 1) / kTileS;
-    if (n_tiles == 0) return;
-    // every CTA runs the same number of rounds; tiles >= n_tiles are empty (no sample valid)
-    const int64_t n_tiles_pad = (n_tiles + gridDim.x - 1) / gridDim.x * gridDim.x;
-    constexpr uint16_t kMask = (uint16_t)((1u << kCluster) - 1u);
+    if ((int64_t)blockIdx.x >= n_tiles) return;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kSlots; ++i) {
             mbar_init(bar_full0 + 8 * i, 1);
-            mbar_init(bar_empty0 + 8 * i, kCluster);   // one MMA commit per CTA of the cluster
+            mbar_init(bar_empty0 + 8 * i, 1);
         }
         mbar_init(bar_acc, 1);
         mbar_init(bar_a, 32 * kEpiWarpsF);
@@ -463,8 +469,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
-    if constexpr (kCluster > 1) cluster_sync();   // the peers' barriers exist before any remote arrive
-    else __syncthreads();
+    __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -478,22 +483,14 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
             const uint32_t first = own < (uint32_t)kStages ? 1u : 0u;
             uint32_t issued = 0;
             bool ok = true;
-            const uint32_t crank = kCluster > 1 ? cluster_rank() : 0u;
-            for (int64_t tile = blockIdx.x; tile < n_tiles_pad && ok; tile += gridDim.x) {
+            for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
                 for (int L = 0; L < NL && ok; ++L) {
                     for (int c = 0; c < TA::chunks(L); ++c) {
                         if (slot_of(L, c) != own) continue;
                         if (!mbar_wait(bar_empty0 + 8 * own, (issued & 1u) ^ first, abort_flag)) { ok = false; break; }
                         const uint32_t bytes = (uint32_t)TA::chunk_bytes(L, c);
                         mbar_expect_tx(bar_full0 + 8 * own, bytes);
-                        if constexpr (kCluster == 1) {
-                            bulk_g2s(slot_addr(own), p.packed + TA::packed_offset(L, c), bytes, bar_full0 + 8 * own);
-                        } else {
-                            // this CTA's 1/kCluster of the chunk, to the same offsets in every CTA
-                            const uint32_t part = bytes / kCluster;
-                            bulk_g2s_mc(slot_addr(own) + crank * part, p.packed + TA::packed_offset(L, c) + crank * part,
-                                        part, bar_full0 + 8 * own, kMask);
-                        }
+                        bulk_g2s(slot_addr(own), p.packed + TA::packed_offset(L, c), bytes, bar_full0 + 8 * own);
                         ++issued;
                     }
                 }
@@ -502,11 +499,6 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
                 // let the copy in flight into this stage land before the CTA exits
                 for (uint32_t it = 0; it < kMaxSpin && !mbar_try(bar_full0 + 8 * own, (issued - 1) & 1u); ++it) {
                 }
-            }
-            if (kCluster > 1 && ok && issued > 0) {   // (ring stages only: kA1Slots is off with clusters)
-                // the last use of this stage released by every CTA's MMAs: no peer commit is
-                // still on its way to this CTA's barrier when it exits
-                if (!mbar_wait(bar_empty0 + 8 * own, (issued - 1) & 1u, abort_flag)) set_status(p.status, TSDFS_DEV_TIMEOUT);
             }
         }
     } else if (warp == kMmaWarpF) {
@@ -517,7 +509,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
             for (int i = 0; i < kSlots; ++i) uses[i] = 0;
             uint32_t lc = 0;
             bool ok = true;
-            for (int64_t tile = blockIdx.x; tile < n_tiles_pad && ok; tile += gridDim.x) {
+            for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
                 for (int L = 0; L < NL && ok; ++L, ++lc) {
                     const TcLayer ly = TA::layer(L);
                     if (!mbar_wait(bar_a, lc & 1u, abort_flag)) { ok = false; break; }
@@ -563,8 +555,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
                         // tile: the next tile's SDF layers own A1 until their MMAs are done
                         const bool keep = s >= (uint32_t)kStages &&
                                           TA::chunk_index(L, c) - TA::sdf_chunks() + kColSlots >= TA::rgb_chunks();
-                        if constexpr (kCluster > 1) mma_commit_mc(bar_empty0 + 8 * s, kMask);
-                        else if (!keep) mma_commit(bar_empty0 + 8 * s);
+                        if (!keep) mma_commit(bar_empty0 + 8 * s);
                     }
                     if (!ok) break;
                     mma_commit(bar_acc);
@@ -597,6 +588,8 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
         const uint32_t t_y = t_v + 256, t_z = t_x + 256;
         const float half_beta = 0.5f * p.beta, inv_beta = 1.0f / p.beta;
         constexpr float kInvSqrt2 = 0.70710678118654752f;
+        const SoftplusH2 spk = softplus_h2_consts(half_beta, inv_beta);
+        const __half2 inv_sqrt2_h2 = __float2half2_rn(kInvSqrt2);
         uint32_t lc = 0, tab_ph = 0;
         bool ok = true;
         // per-tile sample table (coordinates, direction, t, delta, sin / cos of the encodings):
@@ -662,7 +655,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
             return true;
         };
         ok = build_table(blockIdx.x);
-        for (int64_t tile = blockIdx.x; tile < n_tiles_pad && ok; tile += gridDim.x) {
+        for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
             // (the sample table of this tile was built before the loop or during the last one)
             // ---- layer-0 input: encoding rows, stored as 16x256b-ordered stmatrix fragments ----
             {
@@ -724,6 +717,27 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
                     auto group = [&](int c, const float (&d)[16], auto skip_tag) {
                         constexpr bool kSkipIn = decltype(skip_tag)::value;
                         const float2 b = *reinterpret_cast<const float2*>(bias + c + fc);
+                        if constexpr (F16) {
+                            // pairs (sample a, columns c, c+1) and (sample b, columns c, c+1)
+                            __half2 hv2[2], xv2[2], yv2[2], zv2[2];
+#pragma unroll
+                            for (int pr = 0; pr < 2; ++pr) {
+                                __half2 h, sg;
+                                softplus_slope_h2(d[2 * pr] + b.x, d[2 * pr + 1] + b.y, spk, h, sg);
+                                if constexpr (kSkipIn) {
+                                    sg = __hmul2(sg, inv_sqrt2_h2);
+                                    h = __hmul2(h, inv_sqrt2_h2);
+                                }
+                                hv2[pr] = h;
+                                xv2[pr] = __hmul2(sg, __floats2half2_rn(d[4 + 2 * pr], d[5 + 2 * pr]));
+                                yv2[pr] = __hmul2(sg, __floats2half2_rn(d[8 + 2 * pr], d[9 + 2 * pr]));
+                                zv2[pr] = __hmul2(sg, __floats2half2_rn(d[12 + 2 * pr], d[13 + 2 * pr]));
+                            }
+                            const uint32_t co = (uint32_t)(c >> 3) * 128u;
+                            stmatrix4(row0 + co, h2u(hv2[0]), h2u(hv2[1]), h2u(xv2[0]), h2u(xv2[1]));
+                            stmatrix4(row1 + co, h2u(yv2[0]), h2u(yv2[1]), h2u(zv2[0]), h2u(zv2[1]));
+                            return;
+                        }
                         float hv[4], xv[4], yv[4], zv[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
@@ -959,7 +973,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
                 // the next tile's table, while the colour layers' MMAs run: every warp
                 // has left the SDF output layer (the last reader of this tile's table)
                 // once colour layer 0's accumulator is complete
-                if (L == LS && tile + gridDim.x < n_tiles_pad && !build_table(tile + gridDim.x)) {
+                if (L == LS && tile + gridDim.x < n_tiles && !build_table(tile + gridDim.x)) {
                     ok = false;
                     break;
                 }
@@ -968,8 +982,7 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreadsF, 1)
         if (!ok) set_status(p.status, TSDFS_DEV_TIMEOUT);
     }
     tc_fence_before();
-    if constexpr (kCluster > 1) cluster_sync();   // no peer copy or arrive is still aimed at this CTA
-    else __syncthreads();
+    __syncthreads();
     tc_fence_after();
     if (warp == kMmaWarpF) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
@@ -1281,29 +1294,8 @@ int launch_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // persistent grid: as many clusters as are resident at once (two SMs of one GPC each)
-    static int max_clusters[2][2] = {{0, 0}, {0, 0}};
-    int& mc = max_clusters[ARCH][F16 ? 1 : 0];
-    if (mc == 0) {
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3((unsigned)(sms / kCluster * kCluster), 1, 1);
-        cfg.blockDim = dim3(kThreadsF, 1, 1);
-        cfg.dynamicSmemBytes = smem;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = kCluster;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int rc = cuda_check(cudaOccupancyMaxActiveClusters(&mc, k_mlp_tc<ARCH, F16>, &cfg), "mlp_tc cluster occupancy");
-        if (rc) return rc;
-        if (mc < 1) return fail(TSDFS_E_UNSUPPORTED, "mlp_tc: no cluster of %d CTAs fits on the device", kCluster);
-    }
     const int64_t tiles = (max_samples + kTileS - 1) / kTileS;
-    int64_t blocks = tiles < (int64_t)mc * kCluster ? tiles : (int64_t)mc * kCluster;
-    blocks = (blocks + kCluster - 1) / kCluster * kCluster;
-    if (blocks < kCluster) blocks = kCluster;
+    const unsigned blocks = (unsigned)(tiles < sms ? (tiles < 1 ? 1 : tiles) : sms);
     k_mlp_tc<ARCH, F16><<<(unsigned)blocks, kThreadsF, smem, st>>>(p);
     return cuda_check(cudaGetLastError(), "mlp_tc launch");
 }
