@@ -51,6 +51,8 @@ constexpr int kMmaWarpF = kEpiWarpsF;
 constexpr bool kA1Slots = true;
 constexpr int kSlots = kA1Slots ? kStages + 1 : kStages;
 constexpr int kThreadsF = 32 * (kMmaWarpF + 1 + kSlots);
+constexpr bool kWarpArrive = true;   // one epilogue arrival per warp on the operand / table barriers
+constexpr int kEpiArrivals = kWarpArrive ? kEpiWarpsF : 32 * kEpiWarpsF;
 static_assert(!kA1Slots || kStages == 2, "the A1 weight slot assumes the 2-stage ring");
 constexpr uint32_t kABytes = 64 * 1024;   // one A region (128 rows x 256 bf16)
 constexpr uint32_t kMaxSpin = 1u << 26;
@@ -448,9 +450,9 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
             mbar_init(bar_empty0 + 8 * i, 1);
         }
         mbar_init(bar_acc, 1);
-        mbar_init(bar_a, 32 * kEpiWarpsF);
+        mbar_init(bar_a, kEpiArrivals);
         mbar_init(bar_drain, 1);
-        mbar_init(bar_tab, 32 * kEpiWarpsF);
+        mbar_init(bar_tab, kEpiArrivals);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -595,6 +597,12 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
         // per-tile sample table (coordinates, direction, t, delta, sin / cos of the encodings):
         // epilogue thread et < 64 looks up sample et, thread et < 192 one (sample, axis)
         const int et = threadIdx.x;
+        // the epilogue's arrivals on the operand and table barriers: one per warp once all its
+        // lanes are past their writes (and TMEM reads), instead of one per thread
+        auto epi_arrive = [&](uint32_t bar) {
+            __syncwarp();
+            if (!kWarpArrive || lane == 0) mbar_arrive(bar);
+        };
         auto build_table = [&](int64_t tile) -> bool {
                 if (et < kTileS) {
                     const int64_t g = tile * kTileS + et;
@@ -627,7 +635,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                     sx[6] = t;
                     sx[7] = dl;
                 }
-                mbar_arrive(bar_tab);
+                epi_arrive(bar_tab);
                 if (!__all_sync(0xffffffffu, mbar_wait(bar_tab, tab_ph & 1u, abort_flag))) return false;
                 ++tab_ph;
                 // ---- sin / cos of the encodings: thread et < 192 -> (sample et / 3, axis et % 3) ----
@@ -649,7 +657,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                         s_pd[((sm * A::kPeDir + oct) * 3 + a) * 2 + 1] = cs;
                     }
                 }
-                mbar_arrive(bar_tab);
+                epi_arrive(bar_tab);
                 if (!__all_sync(0xffffffffu, mbar_wait(bar_tab, tab_ph & 1u, abort_flag))) return false;
                 ++tab_ph;
             return true;
@@ -684,7 +692,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                 }
             }
             fence_proxy_async();
-            mbar_arrive(bar_a);
+            epi_arrive(bar_a);
             float f_out = 0.0f, dd_out = 0.0f, gn_out = 0.0f, nrm[3] = {0.0f, 0.0f, 0.0f};
             float rec_t = 0.0f, rec_dl = 0.0f;   // this row's sample t and delta, for the record
             for (int L = 0; L < NL; ++L, ++lc) {
@@ -968,7 +976,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                 tc_fence_before();
                 if (!last) {
                     fence_proxy_async();
-                    mbar_arrive(bar_a);
+                    epi_arrive(bar_a);
                 }
                 // the next tile's table, while the colour layers' MMAs run: every warp
                 // has left the SDF output layer (the last reader of this tile's table)
