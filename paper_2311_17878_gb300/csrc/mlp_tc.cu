@@ -71,6 +71,9 @@ __host__ __device__ constexpr int half_hi(int K, int hf) { return hf ? K : pad16
 // the same for `parts` parts of whole 16-column blocks (K a multiple of 16)
 __host__ __device__ constexpr int part_lo(int K, int pt, int parts) { return ((K / 16) * pt / parts) * 16; }
 __host__ __device__ constexpr int part_hi(int K, int pt, int parts) { return pt + 1 == parts ? K : part_lo(K, pt + 1, parts); }
+// the same in 8-column groups (K a multiple of 8): parts differ by at most one group
+__host__ __device__ constexpr int part8_lo(int K, int pt, int parts) { return ((K / 8) * pt / parts) * 8; }
+__host__ __device__ constexpr int part8_hi(int K, int pt, int parts) { return pt + 1 == parts ? K : part8_lo(K, pt + 1, parts); }
 
 template <int ARCH> struct TcArch {
     using A = Arch<ARCH>;
@@ -711,7 +714,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                     const float sc = ly.idx + 1 == A::kSkip ? kInvSqrt2 : 1.0f;
                     const uint32_t row0 = smem_u32(A0) + a_off(32 * q + lane, 0, Kn);
                     const uint32_t row1 = smem_u32(A1) + a_off(32 * q + lane, 0, Kn);
-                    const int c_lo = part_lo(Kn, pt, kPartsF), c_hi = part_hi(Kn, pt, kPartsF);
+                    const int c_lo = part8_lo(Kn, pt, kPartsF), c_hi = part8_hi(Kn, pt, kPartsF);
                     const int c_full = (ly.N / 16) * 16 < c_hi ? (ly.N / 16) * 16 : c_hi;
                     // 8-column groups, software-pipelined: the TMEM loads of group c + 8 are in
                     // flight while group c is computed.  buf = [value(4) | d/dx(4) | d/dy(4) | d/dz(4)],
@@ -768,18 +771,22 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                     };
                     auto body = [&](auto skip_tag) {
                         if (c_full <= c_lo) return;
+                        const int ng = (c_full - c_lo) / 8;   // groups of this part below c_full
                         float bufA[16], bufB[16];
                         ld8(c_lo, bufA);
                         tmem_wait_ld16(bufA);
-                        for (int c0 = c_lo; c0 < c_full; c0 += 16) {
+                        int gi = 0;
+                        for (; gi + 1 < ng; gi += 2) {
+                            const int c0 = c_lo + 8 * gi;
                             ld8(c0 + 8, bufB);
                             group(c0, bufA, skip_tag);
                             tmem_wait_ld16(bufB);
-                            const bool more = c0 + 16 < c_full;
+                            const bool more = gi + 2 < ng;
                             if (more) ld8(c0 + 16, bufA);
                             group(c0 + 8, bufB, skip_tag);
                             if (more) tmem_wait_ld16(bufA);
                         }
+                        if (gi < ng) group(c_lo + 8 * gi, bufA, skip_tag);   // an odd count: the last group
                     };
                     if (sc != 1.0f) body(std::integral_constant<bool, true>{});
                     else body(std::integral_constant<bool, false>{});
@@ -788,70 +795,63 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                     const float* sxb = sxa + 8 * 8;
                     const float* spa = s_pe + (16 * q + fs) * A::kPeSdf * 6;
                     const float* spb = spa + 8 * A::kPeSdf * 6;
-                    for (int c0 = c_full > c_lo ? c_full : c_lo; c0 < c_hi; c0 += 16) {
-                        float v[8], x[8], y[8], z[8];
+                    for (int c8 = c_full > c_lo ? c_full : c_lo; c8 < c_hi; c8 += 8) {
+                        float d[16];   // [value(4) | d/dx(4) | d/dy(4) | d/dz(4)], as ld8
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) { v[j] = 0.0f; x[j] = 0.0f; y[j] = 0.0f; z[j] = 0.0f; }
-                        if (c0 < ly.Np) {
-                            tmem_ld16x256_x2(t_v + c0, v);
-                            tmem_ld16x256_x2(t_x + c0, x);
-                            tmem_ld16x256_x2(t_y + c0, y);
-                            tmem_ld16x256_x2(t_z + c0, z);
-                            tmem_wait_ld();
+                        for (int j = 0; j < 16; ++j) d[j] = 0.0f;
+                        if (c8 < ly.Np) {
+                            ld8(c8, d);
+                            tmem_wait_ld16(d);
                         }
+                        float hv[4], xv[4], yv[4], zv[4];
 #pragma unroll
-                        for (int g8 = 0; g8 < 2; ++g8) {
-                            float hv[4], xv[4], yv[4], zv[4];
+                        for (int cc = 0; cc < 2; ++cc) {
+                            const int col = c8 + fc + cc;
+                            if (col < ly.N) {
 #pragma unroll
-                            for (int cc = 0; cc < 2; ++cc) {
-                                const int col = c0 + 8 * g8 + fc + cc;
-                                if (col < ly.N) {
+                                for (int e = cc; e < 4; e += 2) {
+                                    float h, sg;
+                                    softplus_slope_tanh(d[e] + bias[col], half_beta, inv_beta, h, sg);
+                                    sg *= sc;
+                                    hv[e] = h * sc;
+                                    xv[e] = sg * d[4 + e];
+                                    yv[e] = sg * d[8 + e];
+                                    zv[e] = sg * d[12 + e];
+                                }
+                            } else {
+                                // encoding entry en of both samples: decoded once per column
+                                const int en = col - ly.N;
+                                const int qq = en - 3, oct = qq / 6, part = (qq % 6) / 3, b = en < 3 ? en : qq % 3;
+                                const bool coord = en < 3, in = en < A::kEnc && (coord || oct < A::kPeSdf);
+                                const float f = coord ? 1.0f : (float)(1 << (oct > 0 ? oct : 0)) * sc;
+                                const int ti = ((coord ? 0 : oct) * 3 + b) * 2;
 #pragma unroll
-                                    for (int e = cc; e < 4; e += 2) {
-                                        const int k = 4 * g8 + e;
-                                        float h, sg;
-                                        softplus_slope_tanh(v[k] + bias[col], half_beta, inv_beta, h, sg);
-                                        sg *= sc;
-                                        hv[e] = h * sc;
-                                        xv[e] = sg * x[k];
-                                        yv[e] = sg * y[k];
-                                        zv[e] = sg * z[k];
-                                    }
-                                } else {
-                                    // encoding entry en of both samples: decoded once per column
-                                    const int en = col - ly.N;
-                                    const int qq = en - 3, oct = qq / 6, part = (qq % 6) / 3, b = en < 3 ? en : qq % 3;
-                                    const bool coord = en < 3, in = en < A::kEnc && (coord || oct < A::kPeSdf);
-                                    const float f = coord ? 1.0f : (float)(1 << (oct > 0 ? oct : 0)) * sc;
-                                    const int ti = ((coord ? 0 : oct) * 3 + b) * 2;
-#pragma unroll
-                                    for (int e = cc; e < 4; e += 2) {
-                                        const float* sx = (e & 2) ? sxb : sxa;
-                                        const float* sp = (e & 2) ? spb : spa;
-                                        float val = 0.0f, der = 0.0f;
-                                        if (in) {
-                                            if (coord) {
-                                                val = sx[b] * sc;
-                                                der = sc;
-                                            } else {
-                                                const float sn = sp[ti], cs = sp[ti + 1];
-                                                val = (part == 0 ? sn : cs) * sc;
-                                                der = part == 0 ? f * cs : -f * sn;
-                                            }
+                                for (int e = cc; e < 4; e += 2) {
+                                    const float* sx = (e & 2) ? sxb : sxa;
+                                    const float* sp = (e & 2) ? spb : spa;
+                                    float val = 0.0f, der = 0.0f;
+                                    if (in) {
+                                        if (coord) {
+                                            val = sx[b] * sc;
+                                            der = sc;
+                                        } else {
+                                            const float sn = sp[ti], cs = sp[ti + 1];
+                                            val = (part == 0 ? sn : cs) * sc;
+                                            der = part == 0 ? f * cs : -f * sn;
                                         }
-                                        hv[e] = val;
-                                        xv[e] = b == 0 ? der : 0.0f;
-                                        yv[e] = b == 1 ? der : 0.0f;
-                                        zv[e] = b == 2 ? der : 0.0f;
                                     }
+                                    hv[e] = val;
+                                    xv[e] = b == 0 ? der : 0.0f;
+                                    yv[e] = b == 1 ? der : 0.0f;
+                                    zv[e] = b == 2 ? der : 0.0f;
                                 }
                             }
-                            const uint32_t co = (uint32_t)((c0 + 8 * g8) >> 3) * 128u;
-                            stmatrix4(row0 + co, pack2<F16>(hv[0], hv[1]), pack2<F16>(hv[2], hv[3]),
-                                      pack2<F16>(xv[0], xv[1]), pack2<F16>(xv[2], xv[3]));
-                            stmatrix4(row1 + co, pack2<F16>(yv[0], yv[1]), pack2<F16>(yv[2], yv[3]),
-                                      pack2<F16>(zv[0], zv[1]), pack2<F16>(zv[2], zv[3]));
                         }
+                        const uint32_t co = (uint32_t)(c8 >> 3) * 128u;
+                        stmatrix4(row0 + co, pack2<F16>(hv[0], hv[1]), pack2<F16>(hv[2], hv[3]),
+                                  pack2<F16>(xv[0], xv[1]), pack2<F16>(xv[2], xv[3]));
+                        stmatrix4(row1 + co, pack2<F16>(yv[0], yv[1]), pack2<F16>(yv[2], yv[3]),
+                                  pack2<F16>(zv[0], zv[1]), pack2<F16>(zv[2], zv[3]));
                     }
                 } else if (ly.sdf) {
                     // ---- output layer: f, grad f, feature -> colour input rows ----
