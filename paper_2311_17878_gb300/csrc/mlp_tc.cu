@@ -71,8 +71,9 @@ __host__ __device__ constexpr int half_hi(int K, int hf) { return hf ? K : pad16
 // the same for `parts` parts of whole 16-column blocks (K a multiple of 16)
 __host__ __device__ constexpr int part_lo(int K, int pt, int parts) { return ((K / 16) * pt / parts) * 16; }
 __host__ __device__ constexpr int part_hi(int K, int pt, int parts) { return pt + 1 == parts ? K : part_lo(K, pt + 1, parts); }
-// the same in 8-column groups (K a multiple of 8): parts differ by at most one group
-__host__ __device__ constexpr int part8_lo(int K, int pt, int parts) { return ((K / 8) * pt / parts) * 8; }
+// the same in 8-column groups (K a multiple of 8): parts differ by at most one group, the
+// last part (which also writes the skip input's encoding columns) being the smaller
+__host__ __device__ constexpr int part8_lo(int K, int pt, int parts) { return ((K / 8) * pt + parts - 1) / parts * 8; }
 __host__ __device__ constexpr int part8_hi(int K, int pt, int parts) { return pt + 1 == parts ? K : part8_lo(K, pt + 1, parts); }
 
 template <int ARCH> struct TcArch {
