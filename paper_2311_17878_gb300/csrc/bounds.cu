@@ -102,62 +102,49 @@ __global__ void __launch_bounds__(kBoundsMaxBlock) k_ray_bounds(GridDev g, const
         Dda s;
         dda_init(s, g, o, d, t0);
         // ---- near phase: first voxel with V(centre) <= D_s ----
-        // The walk does not depend on the values: a leading walker runs kAhead - 1 voxels
-        // ahead and the values of the pending voxels are requested before the current one
-        // is tested, so the loads are in flight together; the voxels, their order and every
-        // test are unchanged.  The four pending slots are used in rotation (the loop body
-        // is unrolled over them), so nothing is shifted.
-        struct Pend {
-            int X[3];
-            float t, v;
-            bool ok;   // the loop condition of that step: still in the grid, t < t_end
-        };
-        Dda lead = s;
-        bool live = true;   // the leading walker has not left the grid
-        auto take = [&](Pend& e) {
-            e.X[0] = lead.X[0]; e.X[1] = lead.X[1]; e.X[2] = lead.X[2];
-            e.t = lead.t;
-            e.ok = live && lead.t < t_end;
-            e.v = live ? gval(g, lead.X[0], lead.X[1], lead.X[2]) : 0.0f;
-        };
-        Pend e0, e1, e2, e3;
-        take(e0);
-        live = dda_next(lead, g, o);
-        take(e1);
-        live = live && dda_next(lead, g, o);
-        take(e2);
-        live = live && dda_next(lead, g, o);
-        take(e3);
+        // The walk does not depend on the values: the next kAhead voxels are stepped and
+        // their values requested before the current one is tested, so the loads are in
+        // flight together; the voxels, their order and every test are unchanged.
+        constexpr int kAhead = 4;
+        Dda wq[kAhead];
+        float qv[kAhead];
+        bool qok[kAhead];   // the loop condition of that step: still in the grid, t < t_end
+        bool live = true;   // the walk has not left the grid
+        wq[0] = s;
+        qok[0] = s.t < t_end;
+        qv[0] = gval(g, s.X[0], s.X[1], s.X[2]);
+#pragma unroll
+        for (int i = 1; i < kAhead; ++i) {
+            wq[i] = wq[i - 1];
+            live = live && dda_next(wq[i], g, o);
+            qok[i] = live && wq[i].t < t_end;
+            qv[i] = live ? gval(g, wq[i].X[0], wq[i].X[1], wq[i].X[2]) : 0.0f;
+        }
         bool found = false, in_grid = true;
         float t_before = t0;
         int steps = 0;
-        Pend hit{};
-        // one step on slot e: 0 = go on, 1 = found (hit = e), 2 = the walk ended without
-        auto step = [&](Pend& e) -> int {
-            if (!e.ok) return 2;
-            if (++steps > max_steps) { set_status(dev_status, TSDFS_DEV_MARCH_CAP); in_grid = false; return 2; }
-            if (e.v <= ds_norm) { hit = e; return 1; }
-            t_before = e.t;
-            live = live && dda_next(lead, g, o);
-            take(e);
-            return 0;
-        };
-        for (;;) {
-            int rc = step(e0);
-            if (rc == 0) rc = step(e1);
-            if (rc == 0) rc = step(e2);
-            if (rc == 0) rc = step(e3);
-            if (rc == 1) found = true;
-            if (rc != 0) break;
+        while (qok[0]) {
+            if (++steps > max_steps) { set_status(dev_status, TSDFS_DEV_MARCH_CAP); in_grid = false; break; }
+            if (qv[0] <= ds_norm) { found = true; break; }
+            t_before = wq[0].t;
+            Dda nx = wq[kAhead - 1];
+#pragma unroll
+            for (int i = 0; i + 1 < kAhead; ++i) {
+                wq[i] = wq[i + 1];
+                qv[i] = qv[i + 1];
+                qok[i] = qok[i + 1];
+            }
+            live = live && dda_next(nx, g, o);
+            wq[kAhead - 1] = nx;
+            qok[kAhead - 1] = live && nx.t < t_end;
+            qv[kAhead - 1] = live ? gval(g, nx.X[0], nx.X[1], nx.X[2]) : 0.0f;
         }
+        s = wq[0];
         if (!found) {
             t_n_out[r] = t0; t_f_out[r] = t_end; n_out[r] = p.n_fallback; status_out[r] = TSDFS_FALLBACK;
             if (t_zero_out) t_zero_out[r] = kNaN;
             continue;
         }
-        // the walk state at the near voxel (step and 1/d are those of every voxel of the ray)
-        s.X[0] = hit.X[0]; s.X[1] = hit.X[1]; s.X[2] = hit.X[2];
-        s.t = hit.t;
         const float tn = s.t;
         float tf = t_end;
         // ---- zero-crossing search, starting at the entry of the voxel before ----
