@@ -642,23 +642,25 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                 epi_arrive(bar_tab);
                 if (!__all_sync(0xffffffffu, mbar_wait(bar_tab, tab_ph & 1u, abort_flag))) return false;
                 ++tab_ph;
-                // ---- sin / cos of the encodings: thread et < 192 -> (sample et / 3, axis et % 3) ----
-                if (et < 3 * kTileS) {
-                    const int sm = et / 3, a = et % 3;
-                    const float xv = s_x[sm * 8 + a], dv = s_x[sm * 8 + 3 + a];
-    #pragma unroll
-                    for (int oct = 0; oct < A::kPeSdf; ++oct) {
+                // ---- sin / cos of the encodings: thread et < 384 -> (sample et / 6, axis (et / 2) % 3,
+                // position or direction encoding et % 2); one sincos at octave 0, then the
+                // angle doubled per octave (sin 2x = 2 sin x cos x, cos 2x = (cos x - sin x)
+                // (cos x + sin x)): the error grows about twofold per octave, to a few 1e-6
+                // at the sixth, far below the FP16 / BF16 rounding of the operands ----
+                if (et < 6 * kTileS) {
+                    const int sm = et / 6, a = (et >> 1) % 3, which = et & 1;
+                    const int n_oct = which ? A::kPeDir : A::kPeSdf;
+                    float* dst = which ? s_pd + (sm * A::kPeDir * 3 + a) * 2 : s_pe + (sm * A::kPeSdf * 3 + a) * 2;
+                    if (n_oct > 0) {
                         float sn, cs;
-                        sincosf((float)(1 << oct) * xv, &sn, &cs);
-                        s_pe[((sm * A::kPeSdf + oct) * 3 + a) * 2] = sn;
-                        s_pe[((sm * A::kPeSdf + oct) * 3 + a) * 2 + 1] = cs;
-                    }
-    #pragma unroll
-                    for (int oct = 0; oct < A::kPeDir; ++oct) {
-                        float sn, cs;
-                        sincosf((float)(1 << oct) * dv, &sn, &cs);
-                        s_pd[((sm * A::kPeDir + oct) * 3 + a) * 2] = sn;
-                        s_pd[((sm * A::kPeDir + oct) * 3 + a) * 2 + 1] = cs;
+                        sincosf(s_x[sm * 8 + 3 * which + a], &sn, &cs);
+                        for (int oct = 0; oct < n_oct; ++oct) {
+                            dst[oct * 6] = sn;
+                            dst[oct * 6 + 1] = cs;
+                            const float s2 = 2.0f * sn * cs, c2 = (cs - sn) * (cs + sn);
+                            sn = s2;
+                            cs = c2;
+                        }
                     }
                 }
                 epi_arrive(bar_tab);
