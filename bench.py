@@ -532,6 +532,8 @@ def run_train(spec, wl, grid, mask, dev, n_rays=8192, iters=5):
     for _ in range(2):
         step()
     torch.cuda.synchronize()
+    import ctypes as C
+    T.lib().tsdfs_profile(1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(iters):
@@ -539,8 +541,14 @@ def run_train(spec, wl, grid, mask, dev, n_rays=8192, iters=5):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / iters
+    split = {}
+    for name in ("mlp_simt", "composite", "backward", "ray_bounds"):
+        t, c = C.c_double(0), C.c_int64(0)
+        T.lib().tsdfs_profile_read(name.encode(), C.byref(t), C.byref(c))
+        split[name + "_ms"] = t.value / iters
+    T.lib().tsdfs_profile(0)
     return {"rays": n_rays, "ms_per_step": ms, "rays_per_s": n_rays / (ms / 1e3),
-            "samples": int(b.offsets[-1].item()), "loss": float(loss.item()),
+            "samples": int(b.offsets[-1].item()), "loss": float(loss.item()), "kernel_ms": split,
             "what": "bounds + render (fp32) + L1 + 0.1 eikonal + backward through both networks"}
 
 
