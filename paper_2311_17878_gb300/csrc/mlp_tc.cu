@@ -115,8 +115,12 @@ template <int ARCH> struct TcArch {
     __host__ __device__ static constexpr uint32_t table_bytes() {
         return (uint32_t)(kTileS * (8 + 6 * (A::kPeSdf + A::kPeDir)) * 4);
     }
+    __host__ __device__ static constexpr int total_chunks() { return chunk_index(kLayers, 0); }
+    // per-tile weight-chunk schedule of the full kernel, built once per CTA: 12 bytes a chunk
+    __host__ __device__ static constexpr uint32_t chunk_tab_bytes() { return (uint32_t)((total_chunks() * 12 + 15) / 16 * 16); }
     __host__ __device__ static constexpr size_t full_smem_bytes() {
-        return 2 * (size_t)kABytes + kStages * (size_t)stage_bytes() + bias_bytes() + kBarBytes + table_bytes();
+        return 2 * (size_t)kABytes + kStages * (size_t)stage_bytes() + bias_bytes() + kBarBytes + table_bytes() +
+               chunk_tab_bytes();
     }
     // index of chunk c of layer L within a tile's chunk sequence; chunks of the SDF layers
     __host__ __device__ static constexpr int chunk_index(int L, int c) {
@@ -390,6 +394,15 @@ __device__ __forceinline__ float enc_tab(const float* sx, const float* spe, int 
     return part == 0 ? f * cs : -f * sn;
 }
 
+// one weight chunk of a tile's schedule: its offset and size in the packed weights, the
+// weight slot it goes through, its K columns, and whether its slot (an A1 slot after the
+// tile's last colour chunk in it) stays with the MMA warp instead of returning to its producer
+struct ChunkInfo {
+    uint32_t off, bytes;
+    uint16_t slot, kc_keep;   // kc_keep: K columns | 0x8000 when the slot is kept
+};
+static_assert(sizeof(ChunkInfo) == 12, "chunk table entry");
+
 struct TcParams {
     const uint8_t* packed;
     const float* sdf_w;
@@ -438,6 +451,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
     float* s_x = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + kBarBytes);
     float* s_pe = s_x + kTileS * 8;
     float* s_pd = s_pe + kTileS * A::kPeSdf * 6;
+    ChunkInfo* s_chunks = reinterpret_cast<ChunkInfo*>(reinterpret_cast<uint8_t*>(s_x) + TA::table_bytes());
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const int64_t total = sample_total(p.src);
@@ -459,6 +473,17 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
         mbar_init(bar_tab, kEpiArrivals);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // the tile's chunk schedule, computed once (the producers and the MMA warp read it
+        // instead of re-deriving offsets and slots in their loops)
+        uint32_t off = 0;
+        for (int L = 0, j = 0; L < NL; ++L)
+            for (int c = 0; c < TA::chunks(L); ++c, ++j) {
+                const uint32_t sl = slot_of(L, c);
+                const bool keep = sl >= (uint32_t)kStages && j - TA::sdf_chunks() + kColSlots >= TA::rgb_chunks();
+                s_chunks[j] = ChunkInfo{off, (uint32_t)TA::chunk_bytes(L, c), (uint16_t)sl,
+                                        (uint16_t)(TA::chunk_k(L, c) | (keep ? 0x8000 : 0))};
+                off += (uint32_t)TA::chunk_bytes(L, c);
+            }
     }
     // all biases of both networks, staged once
     for (int i = threadIdx.x; i < TA::bias_total(); i += kThreadsF) {
@@ -489,16 +514,15 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
             const uint32_t first = own < (uint32_t)kStages ? 1u : 0u;
             uint32_t issued = 0;
             bool ok = true;
+            const uint32_t dst = slot_addr(own);
             for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-                for (int L = 0; L < NL && ok; ++L) {
-                    for (int c = 0; c < TA::chunks(L); ++c) {
-                        if (slot_of(L, c) != own) continue;
-                        if (!mbar_wait(bar_empty0 + 8 * own, (issued & 1u) ^ first, abort_flag)) { ok = false; break; }
-                        const uint32_t bytes = (uint32_t)TA::chunk_bytes(L, c);
-                        mbar_expect_tx(bar_full0 + 8 * own, bytes);
-                        bulk_g2s(slot_addr(own), p.packed + TA::packed_offset(L, c), bytes, bar_full0 + 8 * own);
-                        ++issued;
-                    }
+                for (int j = 0; j < TA::total_chunks(); ++j) {
+                    const ChunkInfo ci = s_chunks[j];
+                    if (ci.slot != own) continue;
+                    if (!mbar_wait(bar_empty0 + 8 * own, (issued & 1u) ^ first, abort_flag)) { ok = false; break; }
+                    mbar_expect_tx(bar_full0 + 8 * own, ci.bytes);
+                    bulk_g2s(dst, p.packed + ci.off, ci.bytes, bar_full0 + 8 * own);
+                    ++issued;
                 }
             }
             if (!ok && issued > 0) {
@@ -516,6 +540,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
             uint32_t lc = 0;
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                int j = 0;   // chunk of the tile's schedule
                 for (int L = 0; L < NL && ok; ++L, ++lc) {
                     const TcLayer ly = TA::layer(L);
                     if (!mbar_wait(bar_a, lc & 1u, abort_flag)) { ok = false; break; }
@@ -523,15 +548,16 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                     const uint32_t a_sbo = (uint32_t)(ly.Kp / 8) * 128u;
                     const uint32_t a0 = smem_u32(A0), a1 = smem_u32(A1);
                     const bool last_sdf = ly.sdf && ly.idx == LS - 1;
-                    for (int c = 0; c < TA::chunks(L); ++c) {
-                        const uint32_t s = slot_of(L, c);
+                    for (int c = 0; c < TA::chunks(L); ++c, ++j) {
+                        const ChunkInfo ci = s_chunks[j];
+                        const uint32_t s = ci.slot;
                         uint32_t ph = 0;
 #pragma unroll
                         for (int i = 0; i < kSlots; ++i)
                             if ((uint32_t)i == s) ph = uses[i]++ & 1u;
                         if (!mbar_wait(bar_full0 + 8 * s, ph, abort_flag)) { ok = false; break; }
                         tc_fence_after();
-                        const int kc = TA::chunk_k(L, c);
+                        const int kc = ci.kc_keep & 0x7fff;
                         const uint32_t b0 = slot_addr(s);
                         const uint32_t b_sbo = (uint32_t)(kc / 8) * 128u;
                         for (int kk = 0; kk < kc / 16; ++kk) {
@@ -559,9 +585,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                         }
                         // release the slot, except the A1 slot after its last colour chunk of the
                         // tile: the next tile's SDF layers own A1 until their MMAs are done
-                        const bool keep = s >= (uint32_t)kStages &&
-                                          TA::chunk_index(L, c) - TA::sdf_chunks() + kColSlots >= TA::rgb_chunks();
-                        if (!keep) mma_commit(bar_empty0 + 8 * s);
+                        if (!(ci.kc_keep & 0x8000)) mma_commit(bar_empty0 + 8 * s);
                     }
                     if (!ok) break;
                     mma_commit(bar_acc);
