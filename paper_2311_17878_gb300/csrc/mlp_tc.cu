@@ -725,12 +725,14 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
             epi_arrive(bar_a);
             float f_out = 0.0f, dd_out = 0.0f, gn_out = 0.0f, nrm[3] = {0.0f, 0.0f, 0.0f};
             float rec_t = 0.0f, rec_dl = 0.0f;   // this row's sample t and delta, for the record
+            int boff = 0;                        // this layer's first bias (running, not re-derived)
             for (int L = 0; L < NL; ++L, ++lc) {
                 const TcLayer ly = TA::layer(L);
                 const bool w_ok = mbar_wait(bar_acc, lc & 1u, abort_flag);
                 if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
                 tc_fence_after();
-                const float* bias = sbias + TA::bias_offset(L);
+                const float* bias = sbias + boff;
+                boff += ly.Np;
                 const bool last = L == NL - 1;
                 if (ly.sdf && ly.idx < LS - 1) {
                     // ---- hidden SDF layer -> next layer's input (skip concat when due) ----
@@ -1087,15 +1089,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
             uint32_t seq = 0, issued = 0;
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                uint32_t off = 0;   // packed offset of chunk (L, c), kept running
                 for (int L = 0; L < LS && ok; ++L) {
                     for (int c = 0; c < TA::chunks(L); ++c, ++seq) {
+                        const uint32_t bytes = (uint32_t)TA::chunk_bytes(L, c);
+                        const uint32_t at = off;
+                        off += bytes;
                         if (seq % kStages != own) continue;
                         const uint32_t ph = (seq / kStages) & 1u;
                         if (!mbar_wait(bar_empty0 + 8 * own, ph ^ 1u, abort_flag)) { ok = false; break; }
-                        const uint32_t bytes = (uint32_t)TA::chunk_bytes(L, c);
                         mbar_expect_tx(bar_full0 + 8 * own, bytes);
-                        bulk_g2s(smem_u32(stage_base + own * kStage), p.packed + TA::packed_offset(L, c), bytes,
-                                 bar_full0 + 8 * own);
+                        bulk_g2s(smem_u32(stage_base + own * kStage), p.packed + at, bytes, bar_full0 + 8 * own);
                         ++issued;
                     }
                 }
@@ -1182,12 +1186,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
             }
             fence_proxy_async();
             mbar_arrive(bar_a);
+            int boff = 0;
             for (int L = 0; L < LS; ++L, ++lc) {
                 const TcLayer ly = TA::layer(L);
                 const bool w_ok = mbar_wait(bar_acc, lc & 1u, abort_flag);
                 if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
                 tc_fence_after();
-                const float* bias = sbias + TA::bias_offset(L);
+                const float* bias = sbias + boff;
+                boff += ly.Np;
                 if (L < LS - 1) {
                     const int Kn = TA::layer(L + 1).Kp;
                     const float sc = ly.idx + 1 == A::kSkip ? kInvSqrt2 : 1.0f;
