@@ -1,4 +1,4 @@
-// BF16 tensor-core (tcgen05) evaluation of the SDF and colour networks.
+// FP16 / BF16 tensor-core (tcgen05) evaluation of the SDF and colour networks.
 //
 // Tile: 64 samples.  The SDF gradient is carried in forward mode as tangent
 // rows.  Two M = 128 accumulators live in tensor memory (TMEM, 2 x 256 fp32
@@ -14,13 +14,15 @@
 // (kKChunk columns of K) with 1-D bulk TMA copies through a kStages-deep ring.
 // The colour network reuses acc0 with the value rows only.
 //
-// Warp roles: warps 0-7 epilogue (warp w: TMEM lane quarter w % 4, column
-// half w / 4), warp 8 lane 0 MMA issuer (warp 8 also allocates / frees TMEM),
-// warps 9 .. 8 + kStages lane 0 TMA producers, one per ring stage: bulk copies
-// issued by one thread towards different mbarriers do not overlap (measured),
-// so each stage has a thread of its own.  All hand-offs are mbarriers; every
-// wait is bounded and on timeout the kernel records TSDFS_DEV_TIMEOUT, drains
-// its own copies / MMAs and returns.
+// The full kernel (SDF value, gradient and colour): 16 warps, one persistent CTA per SM.
+// Warps 0-11 are the epilogue (warp w: TMEM lane quarter w % 4, column part w / 4 of three),
+// warp 12 lane 0 issues the MMAs (warp 12 also allocates / frees TMEM), warps 13-15 lane 0
+// stream weight chunks, one per slot (two ring stages, and a slot in the free part of A1 while
+// the colour layers run): bulk copies issued by one thread towards different mbarriers do not
+// overlap (measured), so each slot has a thread of its own.  The value kernel (the
+// comparator's coarse pass) has 8 epilogue warps, one MMA warp and one producer warp per ring
+// stage.  All hand-offs are mbarriers; every wait is bounded and on timeout the kernel
+// records TSDFS_DEV_TIMEOUT, drains its own copies / MMAs and returns.
 #include <type_traits>
 
 #include "common.cuh"
