@@ -453,6 +453,11 @@ def run_ours(args, ws, rank, local):
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": None,
                 "peak_kind": "fp32 FMA, 152 SMs x 128 lanes x 2 x 2.07 GHz", "kernel": "mlp_simt"}
+    # the GPU's own bounds of view 0, for the march's roofline line
+    bv = T.Bounds(n, device=dev)
+    bv.compute(grid, rays[0][0], rays[0][1], bp, mask)
+    march_tf, march_status = bv.t_f.cpu().numpy(), bv.status.cpu().numpy()
+    del bv
     kernel_share = {"mlp_ms_per_step": mlp_ms, "mlp_launches_per_step": n_k.value / max(args.steps, 1),
                     "all_kernels_ms_per_step": ms_all.value / max(args.steps, 1)}
     main_only = args.only_main
@@ -463,9 +468,13 @@ def run_ours(args, ws, rank, local):
     hier = {} if lean else run_hier(args, mlp, grid, rays, bp, n, dev, flush)
     th = [] if (lean or args.workload == "large") else run_tsdf_hier(args, mlp, grid, rays, bp, mask, n, dev, flush)
     # the room networks are not fitted to the large floor, so its images have no quality to score
-    quality = None if (args.no_quality or main_only or rank != 0 or args.workload == "large") else run_quality(
-        spec, wl, grid, bounds, rend, hier.get("renderer"), rays, bp, mask, args.sweep, rec, args.recovery_tau, th)
+    # the cpu_baseline leg: the oracle timed on a bounded sample, and its outputs on the quality
+    # pixels (the only place outside the reference arm where the bench runs the oracle)
+    want_q = not (args.no_quality or main_only or rank != 0 or args.workload == "large")
     cpu = run_cpu_baseline(wl, grid, rays, bp, spec) if (rank == 0 and ws == 1 and not lean) else None
+    refs = oracle_references(wl, grid, rays, bp, spec, args.recovery_tau) if want_q else None
+    quality = run_quality(refs, wl, grid, bounds, rend, hier.get("renderer"), rays, bp, mask, args.sweep, rec,
+                          args.recovery_tau, th) if want_q else None
     train = run_train(spec, wl, grid, mask, dev, n_rays=65536 if args.workload == "large" else 8192) \
         if (rank == 0 and not lean) else None
     clocks = clk.summary()
@@ -486,8 +495,8 @@ def run_ours(args, ws, rank, local):
                    "networks": "SDF 8x256 PE6 skip4 + colour 4x256 PE4", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}, rays independent", "wall_s": t_wall},
         "e2e": e2e, "gpu_launches": int(n_all.value), "roofline": roof, "kernel_time": kernel_share,
-        "roofline_march": march_roofline(wl, grid, rays, bp, ms_b.value / max(n_b.value, 1), hbm, peak_src)
-        if rank == 0 else None,
+        "roofline_march": march_roofline(wl.grid, rays[0][2], rays[0][3], march_tf, march_status, bp,
+                                         ms_b.value / max(n_b.value, 1), hbm, peak_src) if rank == 0 else None,
         "comparator": {k: v for k, v in hier.items() if k != "renderer"},
         "comparator_equal_psnr": equal_psnr_comparison(value, hier, quality),
         "tsdf_hier": [{k: v for k, v in t.items() if k != "renderer"} for t in th] or None,
@@ -513,22 +522,30 @@ def equal_psnr_comparison(value, hier, quality):
             "tsdf_over_hier": value / best["value"] if best else None, "candidates": cands}
 
 
-def march_roofline(wl, grid, rays, bp, ms_per_launch, hbm, peak_src, n_sample=4096):
-    """Roofline line of the ray march (Alg. 1, k_ray_bounds): every tested voxel reads one
-    32-bit word (its value in the near phase, its inside-mask word in the far phase), plus
-    24 B of ray in and 17 B of bounds out per ray.  The voxel counts come from the oracle's
-    walk of a seeded sample of image 0 on the same grid."""
-    import torch
-    from oracle import cgrid
-    from paper_2311_17878_gb300 import synth
-    V = grid.V.view(torch.int16).cpu().numpy().view(np.uint16) if grid.V.dtype == torch.float16 else grid.V.cpu().numpy()
-    o, d = rays[0][2], rays[0][3]
-    idx = synth.sub_sample(len(o), min(n_sample, len(o)), seed=33)
-    st = cgrid.ray_bounds(wl.grid, V, o[idx], d[idx], bp, "f32")["steps"]
-    bytes_per_ray = 4.0 * float(np.mean(st)) + 41.0
+def march_roofline(spec, o, d, t_f, status, bp, ms_per_launch, hbm, peak_src):
+    """Roofline line of the ray march (Alg. 1, k_ray_bounds): every voxel the walk tests reads
+    one 32-bit word (its value in the near phase, its inside-mask word in the far phase), plus
+    24 B of ray in and 17 B of bounds out per ray.  A ray's walk covers [t0, t_f] when it is
+    BOUNDED and [t0, t_end] when it falls back ([t0, t_end]: the grid-box clip of [t_near,
+    t_far]); the voxels it tests are counted as that length times the voxel-boundary crossings
+    per unit length, (|d_x| + |d_y| + |d_z|) / voxel size, plus the first voxel.  t_f and the
+    status are the GPU's own bounds of the same rays."""
+    o, d = np.asarray(o, np.float64), np.asarray(d, np.float64)
+    lo = np.asarray(spec.origin, np.float64)
+    hi = lo + np.array([spec.nx, spec.ny, spec.nz], np.float64) * spec.voxel_size
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = 1.0 / d
+        ta, tb = (lo - o) * inv, (hi - o) * inv
+        t0 = np.maximum(np.nanmax(np.minimum(ta, tb), axis=1), bp.t_near)
+        t_end = np.minimum(np.nanmin(np.maximum(ta, tb), axis=1), bp.t_far)
+    stop = np.where(status == 1, t_f, t_end)
+    walked = status != 0
+    length = np.where(walked, np.maximum(stop - t0, 0.0), 0.0)
+    vox = length * np.abs(d).sum(1) / spec.voxel_size + walked
+    bytes_per_ray = 4.0 * float(np.mean(vox)) + 41.0
     achieved = bytes_per_ray * len(o) / (ms_per_launch / 1e3) / 1e9 if ms_per_launch > 0 else 0.0
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "kernel": "ray_bounds", "voxels_per_ray": float(np.mean(st)),
+            "traffic": None, "kernel": "ray_bounds", "voxels_per_ray": float(np.mean(vox)),
             "bytes_per_ray": bytes_per_ray, "ms_per_launch": ms_per_launch,
             "peak_kind": f"HBM copy ({peak_src}); the grid is L2-resident, so this is a floor on the fraction"}
 
@@ -703,46 +720,38 @@ def run_tsdf_hier(args, mlp, grid, rays, bp, mask, n, dev, flush):
     return out
 
 
-def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=False, rec=None, tau=None,
+def psnr(a, b, peak=1.0):
+    mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+    return float("inf") if mse == 0 else 10.0 * math.log10(peak * peak / mse)
+
+
+def quality_pixels(n_rays):
+    from paper_2311_17878_gb300 import synth
+    return synth.sub_sample(n_rays, QUALITY_PIXELS, seed=31)
+
+
+def run_quality(refs, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=False, rec=None, tau=None,
                 tsdf_hier=None):
-    """PSNR against the oracle's dense reference (FP64, DENSE_SAMPLES midpoints
-    over [t0, t_end]) on a seeded pixel subset of view 0.  The oracle's own TSDF
-    render takes its bounds from its fp32 Alg. 1 on the same grid (and, with a
-    recovery threshold, its own recovery pass of Sec. 4.5)."""
+    """PSNR on a seeded pixel subset of view 0 against the oracle's dense reference (FP64,
+    DENSE_SAMPLES midpoints over [t0, t_end]), next to the PSNR of the oracle's own TSDF
+    render; both come in `refs` from the cpu_baseline leg (oracle_references)."""
     import torch
-    from oracle import cgrid
-    from oracle import render as orr
     from paper_2311_17878_gb300 import synth
     o, d = rays[0][0], rays[0][1]
     bounds.compute(grid, o, d, bp, mask)
     out = rend.render(o, d, bounds)
     if rec is not None:
-        first_wsum = out.wsum.clone()
         rec.apply(grid, o, d, bp, tau, out, bounds)
     hout = hier.render(grid, o, d, bp.t_near, bp.t_far) if hier is not None else None
     torch.cuda.synchronize()
-    idx = synth.sub_sample(o.shape[0], QUALITY_PIXELS, seed=31)
+    idx = quality_pixels(o.shape[0])
     idx_t = torch.as_tensor(idx, device=o.device)
     gpu_rgb = out.rgb[idx_t].cpu().numpy()
     hier_rgb = hout.rgb[idx_t].cpu().numpy() if hout is not None else None
-    on, dn = rays[0][2][idx], rays[0][3][idx]
-    t0, te, ok = cgrid.clip_rays(wl.grid, on, dn, bp.t_near, bp.t_far, "f64")
-    t_q = time.perf_counter()
-    net = orr.Net(spec)
-    dd = orr.dense_reference(net, on, dn, t0, te, n=DENSE_SAMPLES)
-    dense = dd["rgb"].numpy()
-    ob = cgrid.ray_bounds(wl.grid, grid.V.cpu().numpy(), on, dn, bp, "f32")
-    tn, tf, cnt = ob["t_n"].astype(np.float64), ob["t_f"].astype(np.float64), ob["n"]
-    if rec is not None:
-        t0f, tef, _ = cgrid.clip_rays(wl.grid, on, dn, bp.t_near, bp.t_far, "f32")
-        ro, again = orr.render_recovered(net, on, dn, tn, tf, cnt, ob["status"], t0f.astype(np.float64),
-                                         tef.astype(np.float64), tau, bp.n_fallback)
-        ort = ro["rgb"].numpy()
-    else:
-        with torch.no_grad():
-            ort = orr.render_bounded(net, on, dn, tn, tf, cnt)["rgb"].numpy()
-    p_gpu, p_or = orr.psnr(gpu_rgb, dense), orr.psnr(ort, dense)
-    p_h = orr.psnr(hier_rgb, dense) if hier_rgb is not None else None
+    dense, ort, dd = refs["dense_rgb"], refs["tsdf_rgb"], refs["dense"]
+    tn, tf, cnt, ob_status, again = refs["t_n"], refs["t_f"], refs["n"], refs["status"], refs["again"]
+    p_gpu, p_or = psnr(gpu_rgb, dense), psnr(ort, dense)
+    p_h = psnr(hier_rgb, dense) if hier_rgb is not None else None
     th_psnr = []
     for v in (tsdf_hier or []):
         h, b3, ac3 = v["renderer"]
@@ -750,36 +759,36 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=Fal
         c3 = ac3.apply(b3, v["n_mean"], v["n_min"], v["n_max"], 64)
         ho = h.render(o, d, c3)
         torch.cuda.synchronize()
-        th_psnr.append({"name": v["name"], "psnr": orr.psnr(ho.rgb[idx_t].cpu().numpy(), dense)})
+        th_psnr.append({"name": v["name"], "psnr": psnr(ho.rgb[idx_t].cpu().numpy(), dense)})
     ladder_psnr = []
     if hier is not None:
         for nc, nf in HIER_LADDER:
             hier.n_coarse, hier.n_fine = nc, nf
             ho = hier.render(grid, o, d, bp.t_near, bp.t_far)
             torch.cuda.synchronize()
-            ladder_psnr.append({"n_coarse": nc, "n_fine": nf, "psnr": orr.psnr(ho.rgb[idx_t].cpu().numpy(), dense)})
+            ladder_psnr.append({"n_coarse": nc, "n_fine": nf, "psnr": psnr(ho.rgb[idx_t].cpu().numpy(), dense)})
         hier.n_coarse, hier.n_fine = 64, 32
         hout = hier.render(grid, o, d, bp.t_near, bp.t_far)
         torch.cuda.synchronize()
     # geometry metrics on pixels where the dense reference sees a surface (Sec. 4 metrics:
     # depth error, normal angle error; the Tab. 1 failure statistic; mean sample spacing)
-    hit = dd["wsum"].numpy() > 0.5
+    hit = dd["wsum"] > 0.5
 
     def geometry(depth, normal):
         if depth is None or not hit.any():
             return None
-        n_ref = dd["normal"].numpy()[hit]
+        n_ref = dd["normal"][hit]
         n_got = normal[hit]
         cosang = np.sum(n_ref * n_got, 1) / np.maximum(np.linalg.norm(n_ref, axis=1) * np.linalg.norm(n_got, axis=1),
                                                         1e-12)
-        return {"depth_mae_m": float(np.mean(np.abs(depth[hit] - dd["depth"].numpy()[hit]))),
+        return {"depth_mae_m": float(np.mean(np.abs(depth[hit] - dd["depth"][hit]))),
                 "normal_angle_deg": float(np.degrees(np.mean(np.arccos(np.clip(cosang, -1.0, 1.0)))))}
     gstat = geometry(out.depth[idx_t].cpu().numpy(), out.normal[idx_t].cpu().numpy())
     hstat = geometry(hout.depth[idx_t].cpu().numpy(), hout.normal[idx_t].cpu().numpy()) if hout is not None else None
-    bnd = (ob["status"] == 1) & hit
-    t_star = dd["depth"].numpy()
+    bnd = (ob_status == 1) & hit
+    t_star = dd["depth"]
     failed = bnd & ((t_star < tn) | (t_star > tf))
-    spacing = (tf - tn)[ob["status"] == 1] / np.maximum(cnt[ob["status"] == 1], 1)
+    spacing = (tf - tn)[ob_status == 1] / np.maximum(cnt[ob_status == 1], 1)
     # D_s sweep (surface criterion of Alg. 1) on the same pixels: GPU bounds + render
     from paper_2311_17878_gb300 import tsdfs as T
     vs = wl.grid.voxel_size
@@ -797,7 +806,7 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=Fal
         o2 = rend.render(o, d, b2)
         e1.record()
         torch.cuda.synchronize()
-        sweep.append({"d_s_vox": ds, "step_vox": st_vox, "psnr": orr.psnr(o2.rgb[idx_t].cpu().numpy(), dense),
+        sweep.append({"d_s_vox": ds, "step_vox": st_vox, "psnr": psnr(o2.rgb[idx_t].cpu().numpy(), dense),
                       "samples_per_ray": float(b2.n.float().mean().item()),
                       "fallback_frac": float((b2.status == 2).float().mean().item()),
                       "ms_view0": e0.elapsed_time(e1)})
@@ -820,7 +829,7 @@ def run_quality(spec, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=Fal
             "tsdf_hier_psnr": th_psnr,
             "tab1_failed_frac": float(failed.sum() / max(bnd.sum(), 1)),
             "mean_sample_spacing_m": float(spacing.mean()) if spacing.size else None,
-            "oracle_s": time.perf_counter() - t_q}
+            "oracle_s": refs["seconds"]}
 
 
 def run_cpu_baseline(wl, grid, rays, bp, spec, seconds=10.0, chunk=2048):
@@ -847,6 +856,36 @@ def run_cpu_baseline(wl, grid, rays, bp, spec, seconds=10.0, chunk=2048):
     return {"value": done / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
             "sample": f"{done} seeded rays of image 0 of the workload in chunks of {chunk}: C bounds (1 thread) "
                       f"+ torch FP64 render", "seconds": dt}
+
+
+def oracle_references(wl, grid, rays, bp, spec, tau=None):
+    """The rest of the cpu_baseline leg: the oracle's outputs on the quality pixels of view 0,
+    which the quality fields compare the GPU renders against -- its dense FP64 reference over
+    [t0, t_end], its fp32 Alg. 1 bounds on the same grid and its TSDF-bounded render (with its
+    own recovery pass of Sec. 4.5 when tau is set)."""
+    import torch
+    from oracle import cgrid
+    from oracle import render as orr
+    t_q = time.perf_counter()
+    idx = quality_pixels(rays[0][2].shape[0])
+    on, dn = rays[0][2][idx], rays[0][3][idx]
+    t0, te, ok = cgrid.clip_rays(wl.grid, on, dn, bp.t_near, bp.t_far, "f64")
+    net = orr.Net(spec)
+    dd = orr.dense_reference(net, on, dn, t0, te, n=DENSE_SAMPLES)
+    ob = cgrid.ray_bounds(wl.grid, grid.V.cpu().numpy(), on, dn, bp, "f32")
+    tn, tf, cnt = ob["t_n"].astype(np.float64), ob["t_f"].astype(np.float64), ob["n"]
+    again = None
+    if tau is not None:
+        t0f, tef, _ = cgrid.clip_rays(wl.grid, on, dn, bp.t_near, bp.t_far, "f32")
+        ro, again = orr.render_recovered(net, on, dn, tn, tf, cnt, ob["status"], t0f.astype(np.float64),
+                                         tef.astype(np.float64), tau, bp.n_fallback)
+        ort = ro["rgb"].numpy()
+    else:
+        with torch.no_grad():
+            ort = orr.render_bounded(net, on, dn, tn, tf, cnt)["rgb"].numpy()
+    dense = {k: dd[k].numpy() for k in ("rgb", "depth", "wsum", "normal")}
+    return {"dense_rgb": dense["rgb"], "dense": dense, "tsdf_rgb": ort, "t_n": tn, "t_f": tf, "n": cnt,
+            "status": ob["status"], "again": again, "seconds": time.perf_counter() - t_q}
 
 
 # ----------------------------------------------------------------------------
