@@ -47,6 +47,9 @@ WORKLOAD = WORKLOADS["view"]
 # configuration and while the kernel sources hash to the ones it was captured on
 MLP_TC_TRAFFIC = {"sha256": "ba0400f966c61f635448f92c6329d13ccd2215e34715a1c36e3c19373196f2c8", "bytes_per_launch": 257857075,
                   "profile": "profiles/k_mlp_tc_room_view_traffic.md"}
+# the same for k_ray_bounds (the march of Alg. 1) on the same ten timed views
+MARCH_TRAFFIC = {"sha256": "b0949ace8b80982bc36c712a3e070b510fd14704b852a0badbb755be355d62a2", "bytes_per_launch": 9985254,
+                 "profile": "profiles/k_ray_bounds_room_view_traffic.md"}
 ALGO_FLOP_PER_SAMPLE = 2.25e6   # SDF fwd + minimal reverse-mode grad + colour, 8x256 / 4x256 networks
 EXEC_FLOP_PER_SAMPLE = 4.75e6   # what the tensor-core kernel issues: value + 3 tangent rows, padded colour rows
 N_VIEWS_TIMED = 10   # views cycled by the timed steps (4 for the panorama workload)
@@ -166,24 +169,27 @@ def max_over_ranks(x, ws):
     return float(t.item())
 
 
-def mlp_tc_source_hash() -> str:
-    """SHA-256 over the sources the tensor-core network kernel is compiled from."""
+def source_hash(files) -> str:
+    """SHA-256 over the library sources a kernel is compiled from."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("mlp_tc.cu", "common.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2311_17878_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def mlp_tc_traffic(args, prec):
-    """The captured per-launch DRAM traffic of k_mlp_tc, or None when this run is not the
-    captured configuration or the kernel has changed since."""
-    t = MLP_TC_TRAFFIC
+MLP_TC_SOURCES = ("mlp_tc.cu", "common.cuh")
+MARCH_SOURCES = ("bounds.cu", "march.cuh", "common.cuh")
+
+
+def captured_traffic(t, files, args, prec):
+    """A captured per-launch DRAM traffic, or None when this run is not the captured
+    configuration or the kernel has changed since."""
     same_run = (args.workload == "view" and args.grid_source == "network" and args.fusion == "projective"
                 and prec == "f16" and args.steps % N_VIEWS_TIMED == 0 and not args.rays
                 and args.recovery_tau is None and not args.graph)
-    if not same_run or t["bytes_per_launch"] is None or t["sha256"] != mlp_tc_source_hash():
+    if not same_run or t["bytes_per_launch"] is None or t["sha256"] != source_hash(files):
         return None
     return t["bytes_per_launch"]
 
@@ -445,7 +451,7 @@ def run_ours(args, ws, rank, local):
     achieved = ALGO_FLOP_PER_SAMPLE * samples_timed / (ms_k.value / 1e3) / 1e12 if ms_k.value > 0 else 0.0
     if prec != "f32":
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_burst, "unit": "TFLOP/s",
-                "frac": achieved / bf16_burst, "traffic": mlp_tc_traffic(args, prec),
+                "frac": achieved / bf16_burst, "traffic": captured_traffic(MLP_TC_TRAFFIC, MLP_TC_SOURCES, args, prec),
                 "peak_kind": f"bf16 dense burst ({peak_src}); fp16 dense has the same nominal rate",
                 "kernel": "mlp_tc", "executed_tflops": achieved * EXEC_FLOP_PER_SAMPLE / ALGO_FLOP_PER_SAMPLE}
     else:
@@ -495,8 +501,10 @@ def run_ours(args, ws, rank, local):
                    "networks": "SDF 8x256 PE6 skip4 + colour 4x256 PE4", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}, rays independent", "wall_s": t_wall},
         "e2e": e2e, "gpu_launches": int(n_all.value), "roofline": roof, "kernel_time": kernel_share,
-        "roofline_march": march_roofline(wl.grid, rays[0][2], rays[0][3], march_tf, march_status, bp,
-                                         ms_b.value / max(n_b.value, 1), hbm, peak_src) if rank == 0 else None,
+        "roofline_march": dict(march_roofline(wl.grid, rays[0][2], rays[0][3], march_tf, march_status, bp,
+                                              ms_b.value / max(n_b.value, 1), hbm, peak_src),
+                               traffic=captured_traffic(MARCH_TRAFFIC, MARCH_SOURCES, args, prec))
+        if rank == 0 else None,
         "comparator": {k: v for k, v in hier.items() if k != "renderer"},
         "comparator_equal_psnr": equal_psnr_comparison(value, hier, quality),
         "tsdf_hier": [{k: v for k, v in t.items() if k != "renderer"} for t in th] or None,
