@@ -99,6 +99,116 @@ def test_colour_network_constant_output():
     assert torch.allclose(c, torch.tensor([0.5, 0.75, 0.25], dtype=DT).expand(5, 3), atol=1e-15)
 
 
+def _colour_numpy(spec, x, v, n_hat, feat):
+    """The colour network written out per sample with numpy: the input row assembled
+    by hand as (x_tilde, v, sin 2^k v, cos 2^k v for k < L, unit normal, feature),
+    ReLU hidden layers, sigmoid output."""
+    out = np.zeros((len(x), 3))
+    for i in range(len(x)):
+        row = list((x[i] - np.asarray(spec.center)) / spec.scale)
+        row += list(v[i])
+        for k in range(spec.pe_dir):
+            row += [math.sin(2.0 ** k * v[i][a]) for a in range(3)]
+            row += [math.cos(2.0 ** k * v[i][a]) for a in range(3)]
+        row += list(n_hat[i]) + list(feat[i])
+        h = np.array(row)
+        for l, (W, b) in enumerate(spec.rgb):
+            z = np.asarray(W, np.float64).dot(h) + np.asarray(b, np.float64)
+            h = np.maximum(z, 0.0) if l + 1 < len(spec.rgb) else 1.0 / (1.0 + np.exp(-z))
+        out[i] = h
+    return out
+
+
+def _colour_inputs(spec, n, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-2.0, 2.0, (n, 3)) + np.asarray(spec.center)
+    v = rng.normal(size=(n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    nh = rng.normal(size=(n, 3))
+    nh /= np.linalg.norm(nh, axis=1, keepdims=True)
+    feat = rng.normal(0.0, 0.5, (n, spec.n_feat))
+    return x, v, nh, feat
+
+
+def _random_colour_layers(spec, rng, mode):
+    """Random colour layers: 'mixed' (about half of the hidden units active), 'active'
+    (every hidden unit above zero: non-negative weights on non-negative inputs beyond the
+    first layer, unit biases) or 'inactive' (every hidden unit below zero)."""
+    layers = []
+    for l, (W, b) in enumerate(spec.rgb):
+        fan_in = W.shape[1]
+        W2 = rng.normal(0.0, 1.0 / math.sqrt(fan_in), W.shape)
+        b2 = rng.normal(0.0, 0.1, b.shape)
+        hidden = l + 1 < len(spec.rgb)
+        if mode == "active" and hidden:
+            # first layer: small weights on the signed input and a unit bias; later layers:
+            # non-negative weights of mean 1 / fan_in on non-negative inputs
+            W2 = np.abs(W2) / (0.8 * math.sqrt(fan_in)) if l > 0 else W2 * 0.05
+            b2 = np.full(b.shape, 1.0)
+        if mode == "inactive" and hidden:
+            b2 = np.full(b.shape, -1e3)
+        layers.append((W2, b2))
+    return layers
+
+
+@pytest.mark.parametrize("arch", ["tiny", "room"])
+@pytest.mark.parametrize("mode", ["mixed", "active", "inactive"])
+def test_colour_network_matches_numpy_matvec(arch, mode):
+    """rgb_forward against the per-sample numpy matvec of the documented input row, on
+    random weights; with every hidden unit active the network is the sigmoid of the
+    composed affine map, with every hidden unit inactive the sigmoid of the output bias."""
+    s = specs()[arch]
+    rng = np.random.default_rng({"mixed": 11, "active": 12, "inactive": 13}[mode])
+    s.rgb = _random_colour_layers(s, rng, mode)
+    net = orr.Net(s)
+    x, v, nh, feat = _colour_inputs(s, 24, seed=14)
+    got = orr.rgb_forward(net, torch.tensor(x, dtype=DT), torch.tensor(v, dtype=DT), torch.tensor(nh, dtype=DT),
+                          torch.tensor(feat, dtype=DT)).numpy()
+    want = _colour_numpy(s, x, v, nh, feat)
+    assert np.max(np.abs(got - want)) < 1e-13
+    if mode == "inactive":
+        b_last = np.asarray(s.rgb[-1][1], np.float64)
+        assert np.max(np.abs(got - 1.0 / (1.0 + np.exp(-b_last)))) < 1e-15
+    if mode == "active":
+        # composed affine map of the input row: no unit may be clipped
+        rows = np.stack([np.concatenate([(x[i] - np.asarray(s.center)) / s.scale, v[i]] +
+                                        [f(2.0 ** k * v[i]) for k in range(s.pe_dir) for f in (np.sin, np.cos)] +
+                                        [nh[i], feat[i]]) for i in range(len(x))])
+        A, c = np.eye(rows.shape[1]), np.zeros(rows.shape[1])
+        for W, b in s.rgb:
+            A, c = np.asarray(W) @ A, np.asarray(W) @ c + np.asarray(b)
+        assert np.max(np.abs(got - 1.0 / (1.0 + np.exp(-(rows @ A.T + c))))) < 1e-12
+    if mode == "mixed":
+        # the hidden layers really are mixed: each first-layer unit is active on some
+        # samples and inactive on others, so a wrong activation would show
+        z0 = np.stack([np.asarray(s.rgb[0][0]) @ np.concatenate(
+            [(x[i] - np.asarray(s.center)) / s.scale, v[i]] +
+            [f(2.0 ** k * v[i]) for k in range(s.pe_dir) for f in (np.sin, np.cos)] + [nh[i], feat[i]])
+            for i in range(len(x))]) + np.asarray(s.rgb[0][1])
+        frac = float((z0 > 0).mean())
+        assert 0.3 < frac < 0.7
+
+
+@pytest.mark.parametrize("arch", ["tiny", "room"])
+def test_colour_network_reads_each_input_part(arch):
+    """Changing any one part of the input row (position, direction, normal, feature)
+    changes the colour exactly as the numpy matvec says, so no part is dropped or
+    exchanged with another (the direction is encoded, not the position)."""
+    s = specs()[arch]
+    s.rgb = _random_colour_layers(s, np.random.default_rng(15), "mixed")
+    net = orr.Net(s)
+    x, v, nh, feat = _colour_inputs(s, 8, seed=16)
+    rng = np.random.default_rng(17)
+    for part in range(4):
+        args = [a.copy() for a in (x, v, nh, feat)]
+        args[part] = args[part] + rng.normal(0.0, s.scale if part == 0 else 0.3, args[part].shape)
+        got = orr.rgb_forward(net, *[torch.tensor(a, dtype=DT) for a in args]).numpy()
+        want = _colour_numpy(s, *args)
+        base = _colour_numpy(s, x, v, nh, feat)
+        assert np.max(np.abs(got - want)) < 1e-13
+        assert np.max(np.abs(want - base)) > 1e-4
+
+
 def test_plane_weights_telescoping_closed_form():
     """For f(t) = f0 + c t (c < 0) the section ends are exact, and with eps = 0
     T_i = Phi(f(b_i)) / Phi(f(b_0)), so sum w = 1 - Phi(f(b_n)) / Phi(f(b_0))."""
