@@ -424,12 +424,23 @@ class Bounds:
 
 
 class Mlp:
-    """Network parameters on the device and their ``tsdfs_mlp`` descriptor."""
+    """Network parameters on the device and their ``tsdfs_mlp`` descriptor.
 
-    def __init__(self, spec, precision=TSDFS_PREC_F32, device="cuda"):
+    By default the parameters are copied from ``spec`` into new device tensors.  Given
+    ``sdf_w`` / ``rgb_w`` (contiguous float32 device tensors of the packed parameter
+    layout), the descriptor points at those tensors instead, without a copy; 16-bit
+    precisions then pack them into a buffer of their own at construction, so a later
+    change of the tensors needs :meth:`repack`."""
+
+    def __init__(self, spec, precision=TSDFS_PREC_F32, device="cuda", sdf_w=None, rgb_w=None):
         self.spec = spec
-        self.sdf_w = torch.tensor(spec.packed("sdf"), device=device)
-        self.rgb_w = torch.tensor(spec.packed("rgb"), device=device)
+        self.sdf_w = torch.tensor(spec.packed("sdf"), device=device) if sdf_w is None else \
+            _param_tensor(sdf_w, tsdfs_sdf_param_count(spec.arch), "sdf_w")
+        self.rgb_w = torch.tensor(spec.packed("rgb"), device=device) if rgb_w is None else \
+            _param_tensor(rgb_w, tsdfs_rgb_param_count(spec.arch), "rgb_w")
+        if self.sdf_w.device != self.rgb_w.device:
+            raise ValueError("sdf_w and rgb_w must be on the same device")
+        device = self.sdf_w.device
         self.packed = None
         self.precision = precision
         if precision != TSDFS_PREC_F32:
@@ -441,9 +452,25 @@ class Mlp:
         if precision != TSDFS_PREC_F32:
             tsdfs_pack_mlp(self, self.packed)
 
+    def with_params(self, sdf_w, rgb_w):
+        """The same networks (architecture, precision, constants) over the given
+        parameter tensors, which the returned descriptor reads in place."""
+        return Mlp(self.spec, self.precision, sdf_w=sdf_w, rgb_w=rgb_w)
+
     def repack(self):
         if self.packed is not None:
             tsdfs_pack_mlp(self, self.packed)
+
+
+def _param_tensor(w, count, name):
+    """A caller's parameter tensor, checked: float32, contiguous, on a CUDA device,
+    `count` elements (the packed (W, b) layout of the network's layers)."""
+    w = w.detach()
+    if w.dtype != torch.float32 or not w.is_contiguous() or not w.is_cuda:
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if w.numel() != count:
+        raise ValueError(f"{name} has {w.numel()} elements, the network has {count} parameters")
+    return w
 
 
 class RenderOut:
@@ -546,18 +573,25 @@ class HierRenderer:
 class RenderFunction(torch.autograd.Function):
     """render_rays as a differentiable torch op over the packed fp32 parameters.
 
-    forward(sdf_w, rgb_w, mlp, rays_o, rays_d, bounds, max_samples) -> (rgb, depth, eik);
-    backward calls render_rays_backward (FP32 networks, activations recomputed).
+    forward(sdf_w, rgb_w, mlp, rays_o, rays_d, bounds, max_samples) -> (rgb, depth, eik)
+    renders with ``mlp``'s architecture, precision and constants over the parameter
+    tensors ``sdf_w`` / ``rgb_w`` themselves (read in place; 16-bit precisions pack them
+    on every call), so an optimizer stepping those tensors changes the next render;
+    backward calls render_rays_backward (FP32 networks, activations recomputed) at the
+    same tensors and returns their gradients.
     """
 
     @staticmethod
     def forward(ctx, sdf_w, rgb_w, mlp, rays_o, rays_d, b, max_samples):
         n = rays_o.shape[0]
+        m = mlp.with_params(sdf_w, rgb_w)
         out = RenderOut(n, device=rays_o.device)
-        ws = _bytes(tsdfs_render_workspace_size(mlp, n, max_samples), rays_o.device)
-        render_rays(mlp, rays_o, rays_d, b.t_n, b.t_f, b.offsets, b.status, max_samples, out.rgb, out.depth,
+        ws = _bytes(tsdfs_render_workspace_size(m, n, max_samples), rays_o.device)
+        render_rays(m, rays_o, rays_d, b.t_n, b.t_f, b.offsets, b.status, max_samples, out.rgb, out.depth,
                     out.wsum, out.normal, out.eik, ws)
-        ctx.mlp, ctx.b, ctx.max_samples = mlp, b, max_samples
+        # the backward runs the FP32 networks over the same parameter tensors
+        ctx.mlp = m if m.precision == TSDFS_PREC_F32 else Mlp(mlp.spec, TSDFS_PREC_F32, sdf_w=sdf_w, rgb_w=rgb_w)
+        ctx.b, ctx.max_samples = b, max_samples
         ctx.save_for_backward(rays_o, rays_d)
         return out.rgb, out.depth, out.eik
 

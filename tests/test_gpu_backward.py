@@ -87,21 +87,73 @@ def test_backward_matches_oracle_gradient(scene, n_rays):
         assert err < 2e-3, name
 
 
-def test_autograd_function_accumulates_and_matches_direct_call():
-    o, d, b = case("tiny", 64, seed=5)
-    spec = synth.scene_mlp("tiny")
-    mlp = T.Mlp(spec)
+def _bounds_of(o, b):
     offsets = np.concatenate([[0], np.cumsum(b["n"])]).astype(np.int32)
     bb = T.Bounds(len(o))
     bb.t_n.copy_(dev(b["t_n"].astype(np.float32)))
     bb.t_f.copy_(dev(b["t_f"].astype(np.float32)))
     bb.offsets.copy_(dev(offsets))
     bb.status.copy_(dev(b["status"]))
+    return bb, int(offsets[-1])
+
+
+@pytest.mark.parametrize("precision", [T.TSDFS_PREC_F32, T.TSDFS_PREC_F16])
+def test_autograd_function_matches_direct_call(precision):
+    """RenderFunction renders from the parameter tensors it is given and returns the
+    gradients that a direct render_rays_backward call gives at those tensors."""
+    o, d, b = case("tiny", 64, seed=5)
+    spec = synth.scene_mlp("tiny")
+    mlp = T.Mlp(spec, precision)
+    bb, total = _bounds_of(o, b)
+    # leaves that differ from the descriptor's own parameters: the render must follow them
+    g = torch.Generator(device="cuda").manual_seed(3)
+    sdf_w = (mlp.sdf_w * (1.0 + 0.01 * torch.randn(mlp.sdf_w.shape, device="cuda", generator=g))).requires_grad_(True)
+    rgb_w = (mlp.rgb_w * (1.0 + 0.01 * torch.randn(mlp.rgb_w.shape, device="cuda", generator=g))).requires_grad_(True)
+    ro, rd = dev(o), dev(d)
+    rgb, depth, eik = T.RenderFunction.apply(sdf_w, rgb_w, mlp, ro, rd, bb, total)
+    # the same render through a descriptor built directly on the leaves' values
+    ref = T.Mlp(spec, precision, sdf_w=sdf_w.detach().clone(), rgb_w=rgb_w.detach().clone())
+    out = T.Renderer(ref, len(o), total).render(ro, rd, bb)
+    torch.cuda.synchronize()
+    assert torch.equal(rgb, out.rgb) and torch.equal(depth, out.depth)
+    own = T.Renderer(mlp, len(o), total).render(ro, rd, bb)
+    assert not torch.equal(rgb, own.rgb)
+    # seeded output gradients, given to autograd and to a direct call at the same parameters
+    g_rgb = torch.randn(rgb.shape, device="cuda", generator=g)
+    g_depth = torch.randn(depth.shape, device="cuda", generator=g)
+    g_eik = torch.full_like(eik, 0.01)
+    torch.autograd.backward((rgb, depth, eik), (g_rgb, g_depth, g_eik))
+    m32 = T.Mlp(spec, T.TSDFS_PREC_F32, sdf_w=sdf_w.detach().clone(), rgb_w=rgb_w.detach().clone())
+    d_sdf = torch.zeros_like(m32.sdf_w)
+    d_rw = torch.zeros_like(m32.rgb_w)
+    ws = torch.empty(T.tsdfs_backward_workspace_size(m32, len(o), total), dtype=torch.uint8, device="cuda")
+    T.render_rays_backward(m32, ro, rd, bb.t_n, bb.t_f, bb.offsets, bb.status, total, g_rgb, g_depth, g_eik, d_sdf,
+                           d_rw, ws)
+    torch.cuda.synchronize()
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == 0, bits
+    assert torch.equal(sdf_w.grad, d_sdf) and torch.equal(rgb_w.grad, d_rw)
+    assert sdf_w.grad.abs().sum() > 0 and rgb_w.grad.abs().sum() > 0
+
+
+def test_optimizer_step_on_the_leaves_changes_the_render():
+    o, d, b = case("tiny", 64, seed=6)
+    spec = synth.scene_mlp("tiny")
+    mlp = T.Mlp(spec)
+    bb, total = _bounds_of(o, b)
     sdf_w = mlp.sdf_w.clone().requires_grad_(True)
     rgb_w = mlp.rgb_w.clone().requires_grad_(True)
-    rgb, depth, eik = T.RenderFunction.apply(sdf_w, rgb_w, mlp, dev(o), dev(d), bb, int(offsets[-1]))
-    target = torch.rand_like(rgb)
-    loss = (rgb - target).abs().mean() + 0.1 * eik.sum() / max(int(b["n"][b["status"] == 1].sum()), 1)
-    loss.backward()
-    assert torch.isfinite(sdf_w.grad).all() and torch.isfinite(rgb_w.grad).all()
-    assert sdf_w.grad.abs().sum() > 0 and rgb_w.grad.abs().sum() > 0
+    opt = torch.optim.SGD([sdf_w, rgb_w], lr=1e-2)
+    ro, rd = dev(o), dev(d)
+    target = torch.zeros((len(o), 3), device="cuda")
+    rgb0, _, _ = T.RenderFunction.apply(sdf_w, rgb_w, mlp, ro, rd, bb, total)
+    loss0 = (rgb0 - target).abs().mean()
+    loss0.backward()
+    opt.step()
+    opt.zero_grad()
+    rgb1, _, _ = T.RenderFunction.apply(sdf_w, rgb_w, mlp, ro, rd, bb, total)
+    loss1 = (rgb1 - target).abs().mean()
+    assert not torch.equal(rgb0, rgb1)
+    assert loss1.item() < loss0.item()
+    # the descriptor's own copy is untouched
+    assert torch.equal(mlp.sdf_w, torch.tensor(spec.packed("sdf"), device="cuda"))
