@@ -27,22 +27,78 @@ int cuda_check(cudaError_t e, const char* what) {
     return fail(TSDFS_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-// one status word per device (a __device__ variable has one instance per
-// device context); its device address is looked up once per device
+// ---------------------------------------------------------------------------
+// device addresses of the library's __device__ variables
+//
+// A __device__ variable has one instance per CUDA context, so its address is
+// looked up with cudaGetSymbolAddress in the context that is current.  The
+// lookup is cached per device together with the id of the context it was made
+// in (cuCtxGetId: unique within the process, never reused); after a
+// cudaDeviceReset the device's next context has another id, and the address is
+// looked up again instead of reusing the stale one.  The two driver calls are
+// reached through the runtime's driver entry point, so the library does not
+// link the driver library itself.
+// ---------------------------------------------------------------------------
+namespace {
+using CtxGetCurrentFn = int (*)(void**);
+using CtxGetIdFn = int (*)(void*, unsigned long long*);
+std::once_flag g_ctx_fn_once;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// id of the current context of the calling thread; 0 when there is none yet or the
+// driver lacks the query (the cache then keys on the device alone)
+unsigned long long current_context_id() {
+    std::call_once(g_ctx_fn_once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    });
+    if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) != 0 || !ctx) return 0;
+    if (g_ctx_get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+}  // namespace
+
+int symbol_address(SymbolCache& cache, const void* symbol, void** out, const char* what) {
+    int dev = 0;
+    int rc = cuda_check(cudaGetDevice(&dev), what);
+    if (rc) return rc;
+    if (dev < 0 || dev >= SymbolCache::kDevices) return fail(TSDFS_E_UNSUPPORTED, "%s: device index %d out of range", what, dev);
+    std::lock_guard<std::mutex> lk(cache.mu);
+    unsigned long long id = current_context_id();
+    if (cache.addr[dev] && id != 0 && id == cache.ctx[dev]) {
+        *out = cache.addr[dev];
+        return TSDFS_OK;
+    }
+    void* p = nullptr;
+    rc = cuda_check(cudaGetSymbolAddress(&p, symbol), what);
+    if (rc) return rc;
+    if (id == 0) id = current_context_id();   // the lookup made the device's context current
+    cache.addr[dev] = p;
+    cache.ctx[dev] = id;
+    *out = p;
+    return TSDFS_OK;
+}
+
+// one status word per device context
 static __device__ uint32_t g_status_word;
-static std::mutex g_status_mu;
-static uint32_t* g_status_addr[64] = {nullptr};
+static SymbolCache g_status_cache;
 
 uint32_t* device_status_word() {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    std::lock_guard<std::mutex> lk(g_status_mu);
-    if (!g_status_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
-        g_status_addr[dev] = static_cast<uint32_t*>(p);
-    }
-    return g_status_addr[dev];
+    void* p = nullptr;
+    if (symbol_address(g_status_cache, (const void*)&g_status_word, &p, "status word address")) return nullptr;
+    return static_cast<uint32_t*>(p);
 }
 
 // ---------------------------------------------------------------------------

@@ -434,24 +434,13 @@ constexpr int64_t kNoAllocMaxRays = (int64_t)1 << 24;
 constexpr size_t kNoAllocScratchBytes = (size_t)(((kNoAllocMaxRays + kScanChunk - 1) / kScanChunk) + 1) * sizeof(int32_t) + 256;
 static __device__ __align__(256) unsigned char g_bounds_scratch[kNoAllocScratchBytes];
 
-std::mutex g_scratch_mu;
-void* g_scratch_addr[64] = {nullptr};
+SymbolCache g_scratch_cache;
 
-// device address of g_bounds_scratch on the current device (looked up once per device)
+// device address of g_bounds_scratch in the current context (looked up on the first call
+// in each context, so the first call on a device belongs before any stream capture)
 int bounds_scratch(void** out) {
-    int dev = 0;
-    int rc = cuda_check(cudaGetDevice(&dev), "tsdf_ray_bounds_noalloc cudaGetDevice");
-    if (rc) return rc;
-    if (dev < 0 || dev >= 64) return fail(TSDFS_E_UNSUPPORTED, "device index %d out of range", dev);
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        rc = cuda_check(cudaGetSymbolAddress(&p, g_bounds_scratch), "tsdf_ray_bounds_noalloc cudaGetSymbolAddress");
-        if (rc) return rc;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
-    return TSDFS_OK;
+    return symbol_address(g_scratch_cache, (const void*)&g_bounds_scratch, out,
+                          "tsdf_ray_bounds_noalloc cudaGetSymbolAddress");
 }
 }  // namespace
 

@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 #include <cstddef>
+#include <mutex>
 
 #include "tsdfs.h"
 
@@ -17,6 +18,16 @@ int fail(int code, const char* fmt, ...);
 int cuda_check(cudaError_t e, const char* what);
 // device status word of the current device (TSDFS_DEV_* bits), see abi.cu
 uint32_t* device_status_word();
+// cached device address of a __device__ variable in the current context: looked up
+// again when the device's context has changed since the last lookup (after a
+// cudaDeviceReset, for example)
+struct SymbolCache {
+    static constexpr int kDevices = 64;
+    std::mutex mu;
+    void* addr[kDevices] = {};
+    unsigned long long ctx[kDevices] = {};
+};
+int symbol_address(SymbolCache& cache, const void* symbol, void** out, const char* what);
 
 // exclusive scan of n counts into offsets[0..n]; `sums` needs scan_chunks(n) + 1 ints (bounds.cu)
 int64_t scan_chunks(int64_t n);
