@@ -53,8 +53,33 @@ MARCH_TRAFFIC = {"sha256": "b0949ace8b80982bc36c712a3e070b510fd14704b852a0badbb7
 ALGO_FLOP_PER_SAMPLE = 2.25e6   # SDF fwd + minimal reverse-mode grad + colour, 8x256 / 4x256 networks
 EXEC_FLOP_PER_SAMPLE = 4.75e6   # what the tensor-core kernel issues: value + 3 tangent rows, padded colour rows
 N_VIEWS_TIMED = 10   # views cycled by the timed steps (4 for the panorama workload)
-QUALITY_PIXELS = 256
+QUALITY_PIXELS = 4096          # seeded pixels spread over every timed view (synth.quality_pixels)
+QUALITY_PIXELS_LIVE = 1024     # when the dense reference is rendered during the run (panorama workload)
 DENSE_SAMPLES = 1024
+DENSE_REF = os.path.join(ROOT, "oracle", "data", "room_view_dense_reference.npz")
+# operating points of the quality leg: the paper's own knobs around the timed default (Alg. 1's
+# D_s, M and far-test neighbourhood, Sec. 3.4's spacing and cap, the mean-relative count of
+# Tab. 2 "full", coarse + fine inside the bound, the recovery pass of Sec. 4.5).  Keys: d_s and
+# step in voxels, m (M), nb (neighbourhood radius), n_max, tau (recovery), sampler: "mid"
+# (midpoints, counts from the spacing), "rel" (midpoints, counts relative to the mean interval,
+# mean n_mean), "cf" (coarse + fine: n_mean coarse relative to the mean, n_fine inverse-CDF)
+SWEEP = (
+    {"name": "M=2 (Fig. 2)", "m": 2},
+    {"name": "M=2 3^3", "m": 2, "nb": 1},
+    {"name": "M=4 3^3", "m": 4, "nb": 1},
+    {"name": "D_s=2", "d_s": 2.0},
+    {"name": "D_s=2 M=2 3^3", "d_s": 2.0, "m": 2, "nb": 1},
+    {"name": "D_s=2 M=2 3^3 step 1", "d_s": 2.0, "m": 2, "nb": 1, "step": 1.0},
+    {"name": "D_s=3 M=2 3^3 step 1", "d_s": 3.0, "m": 2, "nb": 1, "step": 1.0},
+    {"name": "n_max=16", "n_max": 16},
+    {"name": "rel n=8", "sampler": "rel", "n_mean": 8.0},
+    {"name": "D_s=2 M=2 3^3 rel n=8", "d_s": 2.0, "m": 2, "nb": 1, "sampler": "rel", "n_mean": 8.0},
+    {"name": "cf 6+8", "sampler": "cf", "n_mean": 6.0, "n_fine": 8},
+    {"name": "D_s=2 M=2 3^3 cf 6+8", "d_s": 2.0, "m": 2, "nb": 1, "sampler": "cf", "n_mean": 6.0, "n_fine": 8},
+    {"name": "D_s=2 M=2 3^3 cf 4+4", "d_s": 2.0, "m": 2, "nb": 1, "sampler": "cf", "n_mean": 4.0, "n_fine": 4},
+    {"name": "recovery 0.95", "tau": 0.95},
+    {"name": "D_s=2 M=2 3^3 recovery 0.95", "d_s": 2.0, "m": 2, "nb": 1, "tau": 0.95},
+)
 
 
 def parse():
@@ -65,7 +90,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["f16", "bf16", "f32"], default="f16")
     ap.add_argument("--no-quality", action="store_true")
-    ap.add_argument("--sweep", action="store_true", help="add the D_s / spacing quality sweep")
+    ap.add_argument("--no-sweep", dest="sweep", action="store_false", default=True,
+                    help="skip the operating-point sweep of the quality leg (D_s, M, neighbourhood, spacing, "
+                         "count rule, recovery)")
     ap.add_argument("--grid-source", choices=["network", "analytic"], default="network",
                     help="depth maps the marched grid is fused from (analytic: the exact scene, no network pre-pass)")
     ap.add_argument("--fusion", choices=["projective", "raycast"], default="projective",
@@ -73,7 +100,9 @@ def parse():
     ap.add_argument("--rays", type=int, default=0, help="seeded subset of each view's rays (0: all 307200)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="view",
                     help="view: 640x480 held-out views; panorama: 1024x512 equirect panoramas")
-    ap.add_argument("--graph", action="store_true", help="replay each view's bounds + render as a captured CUDA graph")
+    ap.add_argument("--graph", dest="graph", action="store_true", default=True,
+                    help="replay each view's bounds + render as a captured CUDA graph (the default)")
+    ap.add_argument("--no-graph", dest="graph", action="store_false", help="launch each step's kernels eagerly")
     ap.add_argument("--train-pitch", type=float, default=None,
                     help="largest pitch (degrees) of the random training poses (default: the synthetic recipe's)")
     ap.add_argument("--recovery-tau", type=float, default=None,
@@ -84,6 +113,9 @@ def parse():
                                                                   "quality / cpu / training legs): the small profiling case")
     ap.add_argument("--ref-rays", type=int, default=2048, help="rays per reference-arm step")
     ap.add_argument("--ds-vox", type=float, default=1.0, help="D_s of Alg. 1 in voxels (Sec. 4.2 uses 1)")
+    ap.add_argument("--m-confirm", type=int, default=None, help="M of Alg. 1 (Sec. 4.2 uses 15)")
+    ap.add_argument("--nb-radius", type=int, default=None, help="far-test neighbourhood radius (2: 5^3, Sec. 4.2)")
+    ap.add_argument("--step-vox", type=float, default=None, help="sample spacing of Sec. 3.4 in voxels (2)")
     return ap.parse_args()
 
 
@@ -344,7 +376,17 @@ def run_ours(args, ws, rank, local):
     else:
         wl, grid, grid_an, mask, rays, fusion, depth = build_scene(dev, mlp_depth, args.grid_source, args.rays,
                                                                    args.workload, args.fusion)
-    bp = synth.BoundsParams(**{**wl.bounds.__dict__, "d_s": args.ds_vox * wl.grid.voxel_size})
+    vs = wl.grid.voxel_size
+    bp = synth.BoundsParams(**{**wl.bounds.__dict__, "d_s": args.ds_vox * vs})
+    if args.m_confirm is not None:
+        bp.m_confirm = args.m_confirm
+    if args.nb_radius is not None:
+        bp.nb_radius = args.nb_radius
+    if args.step_vox is not None:
+        bp.n_max = max(bp.n_max, int(round(bp.n_max * bp.step / (args.step_vox * vs))))
+        bp.step = args.step_vox * vs
+    if bp.nb_radius != wl.bounds.nb_radius:
+        mask = grid.inside_mask(bp.nb_radius)
     n = rays[0][0].shape[0]
     max_samples = n * max(bp.n_max, bp.n_fallback)
     if args.workload == "large":
@@ -469,18 +511,25 @@ def run_ours(args, ws, rank, local):
     main_only = args.only_main
     lean = main_only or args.quality_only
     # end to end through the public API with host buffers
-    e2e = None if lean else run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev)
-    # hierarchical comparator on the same views
-    hier = {} if lean else run_hier(args, mlp, grid, rays, bp, n, dev, flush)
-    th = [] if (lean or args.workload == "large") else run_tsdf_hier(args, mlp, grid, rays, bp, mask, n, dev, flush)
-    # the room networks are not fitted to the large floor, so its images have no quality to score
+    e2e = None if lean else run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev, flush)
     # the cpu_baseline leg: the oracle timed on a bounded sample, and its outputs on the quality
-    # pixels (the only place outside the reference arm where the bench runs the oracle)
+    # pixels (the only place outside the reference arm where the bench runs the oracle); the room
+    # networks are not fitted to the large floor, so its images have no quality to score
     want_q = not (args.no_quality or main_only or rank != 0 or args.workload == "large")
     cpu = run_cpu_baseline(wl, grid, rays, bp, spec) if (rank == 0 and ws == 1 and not lean) else None
     refs = oracle_references(wl, grid, rays, bp, spec, args.recovery_tau) if want_q else None
-    quality = run_quality(refs, wl, grid, bounds, rend, hier.get("renderer"), rays, bp, mask, args.sweep, rec,
-                          args.recovery_tau, th) if want_q else None
+    # the hierarchical comparator (K7) and the operating points, timed and scored alike
+    hier_r = None if lean else T.HierRenderer(mlp, n, device=dev)
+    quality = QualityLeg(refs, args, wl, grid, mask, bounds, rend, rec, mlp, rays, bp, n, dev, flush).run_all(
+        hier_r, args.sweep) if (want_q and hier_r is not None) else None
+    comparator = None
+    if quality is not None:
+        comparator = {"impl": "hier n_c + n_f (same GPU, same network engine)",
+                      "ladder": [{k: h[k] for k in ("name", "rays_s", "ms_per_view", "psnr", "samples_per_ray")}
+                                 for h in quality["hier"]]}
+    elif hier_r is not None:
+        comparator = time_hier_only(hier_r, grid, rays, bp, n, flush)
+    del hier_r
     train = run_train(spec, wl, grid, mask, dev, n_rays=65536 if args.workload == "large" else 8192) \
         if (rank == 0 and not lean) else None
     clocks = clk.summary()
@@ -491,7 +540,9 @@ def run_ours(args, ws, rank, local):
         "config": {"workload": WORKLOAD, "rays_per_step": n, "views": N_VIEWS_TIMED,
                    "samples_per_step": samples_timed / args.steps,
                    "grid": f"{wl.grid.nx}^3 {wl.grid.dtype} + uint8",
-                   "d_s_vox": args.ds_vox, "fallback_frac_per_view": fallback_per_view,
+                   "alg1": {"d_s_vox": bp.d_s / vs, "m_confirm": bp.m_confirm, "nb_radius": bp.nb_radius,
+                            "step_vox": bp.step / vs, "n_max": bp.n_max, "n_fallback": bp.n_fallback},
+                   "fallback_frac_per_view": fallback_per_view,
                    "grid_source": "analytic" if args.workload == "large" else args.grid_source,
                    "fusion_form": args.fusion,
                    "ray_subset": args.rays or None,
@@ -500,34 +551,94 @@ def run_ours(args, ws, rank, local):
                    "recovery_tau": args.recovery_tau,
                    "networks": "SDF 8x256 PE6 skip4 + colour 4x256 PE4", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}, rays independent", "wall_s": t_wall},
-        "e2e": e2e, "gpu_launches": int(n_all.value), "roofline": roof, "kernel_time": kernel_share,
+        "comparator_equal_psnr": equal_psnr_comparison(quality),
+        "pareto": pareto_front(quality),
+        "e2e": e2e, "gpu_launches": int(n_all.value), "roofline": roof,
         "roofline_march": dict(march_roofline(wl.grid, rays[0][2], rays[0][3], march_tf, march_status, bp,
                                               ms_b.value / max(n_b.value, 1), hbm, peak_src),
                                traffic=captured_traffic(MARCH_TRAFFIC, MARCH_SOURCES, args, prec))
         if rank == 0 else None,
-        "comparator": {k: v for k, v in hier.items() if k != "renderer"},
-        "comparator_equal_psnr": equal_psnr_comparison(value, hier, quality),
-        "tsdf_hier": [{k: v for k, v in t.items() if k != "renderer"} for t in th] or None,
-        "fusion": fusion, "train_step": train,
-        "quality": quality, "cpu_baseline": cpu, "clocks": clocks,
+        "cpu_baseline": cpu, "clocks": clocks, "kernel_time": kernel_share,
+        "psnr_gate": None if quality is None else {k: quality[k] for k in (
+            "pixels", "psnr_tsdf_gpu", "psnr_tsdf_oracle", "meets_oracle_minus_0p1dB", "psnr_hier96_gpu")},
+        "comparator": comparator, "fusion": fusion, "train_step": train,
+        "quality": quality,
     }
     return line
 
 
-def equal_psnr_comparison(value, hier, quality):
-    """The hierarchical sampler at the fewest samples (from the timed ladder and
-    64 + 32) whose PSNR on the quality pixels is at least the TSDF render's; its
-    rays/s beside the TSDF render's."""
-    if not hier or not quality or not quality.get("hier_ladder_psnr"):
+def time_hier_only(h, grid, rays, bp, n, flush):
+    """The 64 + 32 comparator alone (the large floor has no quality leg): one pass over the
+    timed views, L2 flushed before each."""
+    import torch
+    st = torch.cuda.current_stream()
+    h.render(grid, rays[0][0], rays[0][1], bp.t_near, bp.t_far)
+    torch.cuda.synchronize()
+    ms = []
+    for v in range(N_VIEWS_TIMED):
+        flush.fill_(float(v))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        h.render(grid, rays[v][0], rays[v][1], bp.t_near, bp.t_far)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return {"impl": "hier 64+32 (same GPU, same network engine)",
+            "ladder": [{"name": "hier 64+32", "rays_s": n * len(ms) / (sum(ms) / 1e3), "ms_per_view": float(np.mean(ms)),
+                        "psnr": None, "samples_per_ray": 96}]}
+
+
+def _best_hier(hier, p):
+    ok = [h for h in hier if h["psnr"] >= p]
+    return max(ok, key=lambda h: h["rays_s"]) if ok else None
+
+
+def equal_psnr_comparison(q):
+    """The target's comparison: the TSDF render (the timed default) against the fastest
+    hierarchical configuration (64 + 32 and the smaller ladder) whose PSNR on the quality
+    pixels is at least as high, every configuration timed the same way (one pass over the
+    timed views, L2 flushed before each view); then the same for each operating point of the
+    sweep, and the best of them."""
+    if not q:
         return None
-    p_t = quality["psnr_tsdf_gpu"]
-    cands = [{"n_coarse": 64, "n_fine": 32, "value": hier["value"], "psnr": quality["psnr_hier96_gpu"]}]
-    for tl, ql in zip(hier["ladder"], quality["hier_ladder_psnr"]):
-        cands.append({"n_coarse": tl["n_coarse"], "n_fine": tl["n_fine"], "value": tl["value"], "psnr": ql["psnr"]})
-    ok = [c for c in cands if c["psnr"] >= p_t]
-    best = max(ok, key=lambda c: c["value"]) if ok else None
-    return {"psnr_tsdf_gpu": p_t, "tsdf_rays_s": value, "hier_at_ge_psnr": best,
-            "tsdf_over_hier": value / best["value"] if best else None, "candidates": cands}
+    hier, t = q["hier"], q["tsdf"]
+    b = _best_hier(hier, t["psnr"])
+    out = {"tsdf": {"rays_s": t["rays_s"], "psnr": t["psnr"], "samples_per_ray": t["samples_per_ray"]},
+           "hier_at_ge_psnr": None if b is None else {k: b[k] for k in ("name", "rays_s", "psnr")},
+           "tsdf_over_hier": t["rays_s"] / b["rays_s"] if b else None}
+    best = None
+    for c in [t] + q.get("sweep", []):
+        bh = _best_hier(hier, c["psnr"])
+        # no hierarchical configuration reaches this PSNR: compare with the most accurate one
+        ref = bh if bh is not None else max(hier, key=lambda h: h["psnr"])
+        r = c["rays_s"] / ref["rays_s"]
+        if bh is not None and (best is None or r > best["tsdf_over_hier"]):
+            best = {"name": c["name"], "rays_s": c["rays_s"], "psnr": c["psnr"],
+                    "samples_per_ray": c["samples_per_ray"], "hier": bh["name"], "hier_rays_s": bh["rays_s"],
+                    "hier_psnr": bh["psnr"], "tsdf_over_hier": r}
+    out["best_operating_point"] = best
+    return out
+
+
+def pareto_front(q):
+    """Every configuration of the quality leg as (rays/s, PSNR), fastest first; `front`
+    marks those that no other configuration beats on both."""
+    if not q:
+        return None
+    pts = [dict(kind="tsdf", name=q["tsdf"]["name"], rays_s=q["tsdf"]["rays_s"], psnr=q["tsdf"]["psnr"],
+                spr=q["tsdf"]["samples_per_ray"])]
+    pts += [dict(kind="tsdf", name=c["name"], rays_s=c["rays_s"], psnr=c["psnr"], spr=c["samples_per_ray"])
+            for c in q.get("sweep", [])]
+    pts += [dict(kind="hier", name=h["name"], rays_s=h["rays_s"], psnr=h["psnr"], spr=h["samples_per_ray"])
+            for h in q["hier"]]
+    for p_ in pts:
+        p_["front"] = not any(o is not p_ and o["rays_s"] >= p_["rays_s"] and o["psnr"] >= p_["psnr"] and
+                              (o["rays_s"] > p_["rays_s"] or o["psnr"] > p_["psnr"]) for o in pts)
+    for p_ in pts:
+        p_["rays_s"] = round(p_["rays_s"] / 1e6, 3)   # M rays/s
+        p_["psnr"] = round(p_["psnr"], 2)
+        p_["spr"] = round(p_["spr"], 1)
+    return sorted(pts, key=lambda p_: -p_["rays_s"])
 
 
 def march_roofline(spec, o, d, t_f, status, bp, ms_per_launch, hbm, peak_src):
@@ -607,7 +718,11 @@ def run_train(spec, wl, grid, mask, dev, n_rays=8192, iters=5):
             "what": "bounds + render (fp32) + L1 + 0.1 eikonal + backward through both networks"}
 
 
-def run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev):
+def run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev, flush):
+    """The metric end to end through the public Python API over the C ABI: each step copies
+    the view's rays in from pinned host memory, runs bounds + render and copies rgb and depth
+    out, between CUDA events on the launching stream; L2 is flushed before each step (outside
+    the timed region), as in the device-timed leg."""
     import torch
     st = torch.cuda.current_stream()
     h_o = [torch.tensor(r[2]).pin_memory() for r in rays]
@@ -629,103 +744,18 @@ def run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev):
     for k in range(max(2, args.warmup)):
         step(k)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for k in range(args.steps):
-        step(k)
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    return {"value": n * args.steps / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": n * 24,
-            "d2h_bytes_per_step": n * 16, "ms_per_step": ms / args.steps}
-
-
-def run_hier(args, mlp, grid, rays, bp, n, dev, flush):
-    import torch
-    from paper_2311_17878_gb300 import tsdfs as T
-    h = T.HierRenderer(mlp, n, device=dev)
-    for i in range(2):
-        h.render(grid, rays[i][0], rays[i][1], bp.t_near, bp.t_far)
-    torch.cuda.synchronize()
-    steps = max(3, min(args.steps, 6))
-    st = torch.cuda.current_stream()
-    tot = 0.0
-    for k in range(steps):
         flush.fill_(float(k))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        h.render(grid, rays[k % N_VIEWS_TIMED][0], rays[k % N_VIEWS_TIMED][1], bp.t_near, bp.t_far)
-        e1.record(st)
-        torch.cuda.synchronize()
-        tot += e0.elapsed_time(e1)
-    line = {"impl": "hier 64+32 (same GPU, same network engine)", "value": n * steps / (tot / 1e3), "unit": UNIT,
-            "ms_per_step": tot / steps, "samples_per_ray": 96, "renderer": h, "ladder": []}
-    # smaller sample counts of the same sampler, for the equal-PSNR comparison (the large
-    # floor has no quality leg, so no ladder)
-    for nc, nf in (HIER_LADDER if args.workload != "large" else ()):
-        h.n_coarse, h.n_fine = nc, nf
-        h.render(grid, rays[0][0], rays[0][1], bp.t_near, bp.t_far)
-        tot = 0.0
-        for k in range(steps):
-            flush.fill_(float(k))
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            h.render(grid, rays[k % N_VIEWS_TIMED][0], rays[k % N_VIEWS_TIMED][1], bp.t_near, bp.t_far)
-            e1.record(st)
-            torch.cuda.synchronize()
-            tot += e0.elapsed_time(e1)
-        line["ladder"].append({"n_coarse": nc, "n_fine": nf, "value": n * steps / (tot / 1e3),
-                               "ms_per_step": tot / steps})
-    h.n_coarse, h.n_fine = 64, 32
-    return line
-
-
-TSDF_HIER_VARIANTS = (  # name, mean coarse count, n_min, n_max, fine count (Tab. 2 "Ours" 6 + 8)
-    ("naive 6+8", 6.0, 6, 6, 8),
-    ("full 6+8", 6.0, 2, 64, 8),
-)
-
-
-def run_tsdf_hier(args, mlp, grid, rays, bp, mask, n, dev, flush):
-    """Coarse + fine inside the TSDF bound (Tab. 2 "Ours"): per step the timed path's
-    bounds, counts relative to the mean interval (fixed for "naive", adaptive for
-    "full"), then the coarse values, the inverse-CDF fine samples and the full
-    evaluation of the merged samples.  FALLBACK rays take 64 coarse samples."""
-    import torch
-    from paper_2311_17878_gb300 import tsdfs as T
-    b = T.Bounds(n, device=dev)
-    ac = T.AdaptiveCounts(n, device=dev)
-    out = []
-    steps = max(3, min(args.steps, 6))
-    st = torch.cuda.current_stream()
-    for name, n_mean, n_min, n_max, n_fine in TSDF_HIER_VARIANTS:
-        h = T.HierBoundedRenderer(mlp, n, n_fine, n * max(n_max, 64), device=dev)
-
-        def step(k):
-            o, d = rays[k % N_VIEWS_TIMED][:2]
-            b.compute(grid, o, d, bp, mask)
-            c = ac.apply(b, n_mean, n_min, n_max, 64)
-            h.render(o, d, c)
-            return c
-
-        for k in range(2):
-            step(k)
-        torch.cuda.synchronize()
-        tot, samples = 0.0, 0
-        for k in range(steps):
-            flush.fill_(float(k))
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            c = step(k)
-            e1.record(st)
-            torch.cuda.synchronize()
-            tot += e0.elapsed_time(e1)
-            samples += int(c.offsets[-1].item()) + n_fine * int((c.n > 0).sum().item())
-        out.append({"name": name, "n_mean": n_mean, "n_min": n_min, "n_max": n_max, "n_fine": n_fine,
-                    "value": n * steps / (tot / 1e3), "ms_per_step": tot / steps,
-                    "samples_per_ray": samples / (n * steps), "renderer": (h, b, ac)})
-        del h
-    return out
+        evs[k][0].record(st)
+        step(k)
+        evs[k][1].record(st)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    return {"value": n * args.steps / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": n * 24,
+            "d2h_bytes_per_step": n * 16, "ms_per_step": ms / args.steps,
+            "api": "tsdfs.py binding over the C ABI (Bounds.compute + Renderer.render), pinned host buffers",
+            "l2": "flushed before each step (256 MB write, outside the timed region)"}
 
 
 def psnr(a, b, peak=1.0):
@@ -733,111 +763,246 @@ def psnr(a, b, peak=1.0):
     return float("inf") if mse == 0 else 10.0 * math.log10(peak * peak / mse)
 
 
-def quality_pixels(n_rays):
-    from paper_2311_17878_gb300 import synth
-    return synth.sub_sample(n_rays, QUALITY_PIXELS, seed=31)
+class QualityLeg:
+    """Image quality and throughput of every configuration on the same footing: one pass over
+    the timed views, each view rendered between CUDA events on the launching stream with L2
+    flushed before it, the quality pixels (seeded, spread over all views) gathered after and
+    scored against the oracle's dense reference (`refs`, from the cpu_baseline leg)."""
 
+    def __init__(self, refs, args, wl, grid, mask, bounds, rend, rec, mlp, rays, bp, n, dev, flush):
+        import torch
+        self.refs, self.args, self.wl, self.grid, self.mask = refs, args, wl, grid, mask
+        self.bounds, self.rend, self.rec, self.mlp, self.rays, self.bp = bounds, rend, rec, mlp, rays, bp
+        self.n, self.dev, self.flush = n, dev, flush
+        self.idx_t = [torch.as_tensor(ix, device=dev) for ix in refs["pixels"]]
+        self.cuts = np.cumsum([0] + [len(ix) for ix in refs["pixels"]])
+        self.dense = refs["dense"]
+        self.masks = {bp.nb_radius: mask}
 
-def run_quality(refs, wl, grid, bounds, rend, hier, rays, bp, mask, sweep_on=False, rec=None, tau=None,
-                tsdf_hier=None):
-    """PSNR on a seeded pixel subset of view 0 against the oracle's dense reference (FP64,
-    DENSE_SAMPLES midpoints over [t0, t_end]), next to the PSNR of the oracle's own TSDF
-    render; both come in `refs` from the cpu_baseline leg (oracle_references)."""
-    import torch
-    from paper_2311_17878_gb300 import synth
-    o, d = rays[0][0], rays[0][1]
-    bounds.compute(grid, o, d, bp, mask)
-    out = rend.render(o, d, bounds)
-    if rec is not None:
-        rec.apply(grid, o, d, bp, tau, out, bounds)
-    hout = hier.render(grid, o, d, bp.t_near, bp.t_far) if hier is not None else None
-    torch.cuda.synchronize()
-    idx = quality_pixels(o.shape[0])
-    idx_t = torch.as_tensor(idx, device=o.device)
-    gpu_rgb = out.rgb[idx_t].cpu().numpy()
-    hier_rgb = hout.rgb[idx_t].cpu().numpy() if hout is not None else None
-    dense, ort, dd = refs["dense_rgb"], refs["tsdf_rgb"], refs["dense"]
-    tn, tf, cnt, ob_status, again = refs["t_n"], refs["t_f"], refs["n"], refs["status"], refs["again"]
-    p_gpu, p_or = psnr(gpu_rgb, dense), psnr(ort, dense)
-    p_h = psnr(hier_rgb, dense) if hier_rgb is not None else None
-    th_psnr = []
-    for v in (tsdf_hier or []):
-        h, b3, ac3 = v["renderer"]
-        b3.compute(grid, o, d, bp, mask)
-        c3 = ac3.apply(b3, v["n_mean"], v["n_min"], v["n_max"], 64)
-        ho = h.render(o, d, c3)
+    def mask_for(self, nb):
+        if nb not in self.masks:
+            self.masks[nb] = self.grid.inside_mask(nb)
+        return self.masks[nb]
+
+    def run(self, name, render_view, evals=None, keep=None):
+        """render_view(v) -> outputs with rgb / depth / wsum / normal; evals(v) -> network
+        evaluations of view v (read after the pass); keep(v, out) saves tensors for later."""
+        import torch
+        st = torch.cuda.current_stream()
+        render_view(0)
         torch.cuda.synchronize()
-        th_psnr.append({"name": v["name"], "psnr": psnr(ho.rgb[idx_t].cpu().numpy(), dense)})
-    ladder_psnr = []
-    if hier is not None:
-        for nc, nf in HIER_LADDER:
-            hier.n_coarse, hier.n_fine = nc, nf
-            ho = hier.render(grid, o, d, bp.t_near, bp.t_far)
+        ms, rgb, depth, ev = [], [], [], 0
+        for v in range(N_VIEWS_TIMED):
+            self.flush.fill_(float(v))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            out = render_view(v)
+            e1.record(st)
             torch.cuda.synchronize()
-            ladder_psnr.append({"n_coarse": nc, "n_fine": nf, "psnr": psnr(ho.rgb[idx_t].cpu().numpy(), dense)})
-        hier.n_coarse, hier.n_fine = 64, 32
-        hout = hier.render(grid, o, d, bp.t_near, bp.t_far)
-        torch.cuda.synchronize()
-    # geometry metrics on pixels where the dense reference sees a surface (Sec. 4 metrics:
-    # depth error, normal angle error; the Tab. 1 failure statistic; mean sample spacing)
-    hit = dd["wsum"] > 0.5
+            ms.append(e0.elapsed_time(e1))
+            rgb.append(out.rgb[self.idx_t[v]].cpu().numpy())
+            depth.append(out.depth[self.idx_t[v]].cpu().numpy())
+            if evals is not None:
+                ev += evals(v)
+            if keep is not None:
+                keep(v, out)
+        rgb = np.concatenate(rgb)
+        c = self.cuts
+        return {"name": name, "rays_s": self.n * N_VIEWS_TIMED / (sum(ms) / 1e3), "ms_per_view": float(np.mean(ms)),
+                "psnr": psnr(rgb, self.dense["rgb"]),
+                "psnr_per_view": [round(psnr(rgb[c[v]:c[v + 1]], self.dense["rgb"][c[v]:c[v + 1]]), 2)
+                                  for v in range(N_VIEWS_TIMED)],
+                "ms_per_view_list": [round(m, 3) for m in ms],
+                "samples_per_ray": ev / (self.n * N_VIEWS_TIMED) if evals is not None else None,
+                "_rgb": rgb, "_depth": np.concatenate(depth)}
 
-    def geometry(depth, normal):
-        if depth is None or not hit.any():
-            return None
-        n_ref = dd["normal"][hit]
-        n_got = normal[hit]
-        cosang = np.sum(n_ref * n_got, 1) / np.maximum(np.linalg.norm(n_ref, axis=1) * np.linalg.norm(n_got, axis=1),
-                                                        1e-12)
-        return {"depth_mae_m": float(np.mean(np.abs(depth[hit] - dd["depth"][hit]))),
-                "normal_angle_deg": float(np.degrees(np.mean(np.arccos(np.clip(cosang, -1.0, 1.0)))))}
-    gstat = geometry(out.depth[idx_t].cpu().numpy(), out.normal[idx_t].cpu().numpy())
-    hstat = geometry(hout.depth[idx_t].cpu().numpy(), hout.normal[idx_t].cpu().numpy()) if hout is not None else None
-    bnd = (ob_status == 1) & hit
-    t_star = dd["depth"]
-    failed = bnd & ((t_star < tn) | (t_star > tf))
-    spacing = (tf - tn)[ob_status == 1] / np.maximum(cnt[ob_status == 1], 1)
-    # D_s sweep (surface criterion of Alg. 1) on the same pixels: GPU bounds + render
-    from paper_2311_17878_gb300 import tsdfs as T
-    vs = wl.grid.voxel_size
-    sweep = []
-    b2 = T.Bounds(o.shape[0], device=o.device)
-    grid_sweep = ((1.0, 2.0), (2.0, 2.0), (3.0, 2.0), (2.0, 1.0), (3.0, 1.0), (2.0, 0.5), (3.0, 0.5), (3.0, 0.25))
-    for ds, st_vox in (grid_sweep if sweep_on else ()):
-        bp2 = synth.BoundsParams(**{**bp.__dict__, "d_s": ds * vs, "step": st_vox * vs,
-                                    "n_max": int(bp.n_max * max(1.0, bp.step / (st_vox * vs)))})
-        b2.compute(grid, o, d, bp2, mask)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        b2.compute(grid, o, d, bp2, mask)
-        o2 = rend.render(o, d, b2)
-        e1.record()
-        torch.cuda.synchronize()
-        sweep.append({"d_s_vox": ds, "step_vox": st_vox, "psnr": psnr(o2.rgb[idx_t].cpu().numpy(), dense),
-                      "samples_per_ray": float(b2.n.float().mean().item()),
-                      "fallback_frac": float((b2.status == 2).float().mean().item()),
-                      "ms_view0": e0.elapsed_time(e1)})
-    err = np.abs(gpu_rgb - dense).max(1)
-    worst = []
-    for i in np.argsort(-err)[:8]:
-        worst.append({"err": float(err[i]), "wsum": float(out.wsum[idx_t][i].item()),
-                      "depth": float(out.depth[idx_t][i].item()), "depth_dense": float(dd["depth"][i]),
-                      "t_n": float(tn[i]), "t_f": float(tf[i]), "n": int(cnt[i]),
-                      "status": int(bounds.status[idx_t][i].item())})
-    return {"pixels": QUALITY_PIXELS, "reference": f"oracle FP64 dense {DENSE_SAMPLES} samples over [t0,t_end]",
-            "worst": worst, "d_s_vox": bp.d_s / vs, "psnr_tsdf_gpu": p_gpu, "psnr_tsdf_oracle": p_or, "psnr_hier96_gpu": p_h,
-            "meets_oracle_minus_0p1dB": bool(p_gpu >= p_or - 0.1), "tsdf_ge_hier96": bool(p_gpu >= p_h) if p_h is not None else None,
-            "samples_per_ray_tsdf": float(bounds.n.float().mean().item()),
-            "fallback_frac": float((bounds.status == 2).float().mean().item()), "d_s_sweep": sweep,
-            "recovery": None if rec is None else {
-                "tau": tau, "recovered_frac": float((rec.bounds.status == 2).float().mean().item()),
-                "recovered_frac_oracle_pixels": float(np.mean(again))},
-            "geometry_tsdf_gpu": gstat, "geometry_hier96_gpu": hstat, "hier_ladder_psnr": ladder_psnr,
-            "tsdf_hier_psnr": th_psnr,
-            "tab1_failed_frac": float(failed.sum() / max(bnd.sum(), 1)),
-            "mean_sample_spacing_m": float(spacing.mean()) if spacing.size else None,
-            "oracle_s": refs["seconds"]}
+    # ---- the timed default -------------------------------------------------
+    def tsdf_default(self):
+        import torch
+        b, rend, rec, kept = self.bounds, self.rend, self.rec, {}
+
+        def render_view(v):
+            o, d = self.rays[v][:2]
+            b.compute(self.grid, o, d, self.bp, self.mask)
+            out = rend.render(o, d, b)
+            if rec is not None:
+                rec.apply(self.grid, o, d, self.bp, self.args.recovery_tau, out, b)
+            return out
+
+        def evals(v):
+            e = int(b.offsets[-1].item())
+            return e + (int(rec.bounds.offsets[-1].item()) if rec is not None else 0)
+
+        def keep(v, out):
+            kept[v] = {"t_n": b.t_n.clone(), "t_f": b.t_f.clone(), "n": b.n.clone(), "status": b.status.clone(),
+                       "wsum": out.wsum.clone()}
+        r = self.run("default", render_view, evals, keep)
+        r["_kept"] = kept
+        return r
+
+    # ---- the hierarchical comparator (K7) ------------------------------------
+    def hier(self, h):
+        import torch
+        out, kept = [], {}
+        for nc, nf in ((64, 32),) + HIER_LADDER:
+            h.n_coarse, h.n_fine = nc, nf
+
+            def render_view(v):
+                o, d = self.rays[v][:2]
+                return h.render(self.grid, o, d, self.bp.t_near, self.bp.t_far)
+
+            def keep(v, o_):
+                if nc == 64:
+                    kept[v] = {"depth": o_.depth.clone(), "wsum": o_.wsum.clone()}
+            r = self.run(f"hier {nc}+{nf}", render_view, lambda v: self.n * (nc + nf), keep)
+            r.update(n_coarse=nc, n_fine=nf, value_evals_per_ray=nc)
+            out.append(r)
+        h.n_coarse, h.n_fine = 64, 32
+        return out, kept
+
+    # ---- one operating point of the sweep --------------------------------------
+    def operating_point(self, cfg, pools):
+        import torch
+        from paper_2311_17878_gb300 import synth
+        from paper_2311_17878_gb300 import tsdfs as T
+        vs = self.wl.grid.voxel_size
+        bp = synth.BoundsParams(**{**self.bp.__dict__, "d_s": cfg.get("d_s", self.bp.d_s / vs) * vs,
+                                   "step": cfg.get("step", self.bp.step / vs) * vs,
+                                   "m_confirm": cfg.get("m", self.bp.m_confirm),
+                                   "nb_radius": cfg.get("nb", self.bp.nb_radius),
+                                   "n_max": cfg.get("n_max", self.bp.n_max)})
+        if cfg.get("step", None) is not None:
+            bp.n_max = max(bp.n_max, int(round(self.bp.n_max * self.bp.step / bp.step)))
+        mask = self.mask_for(bp.nb_radius)
+        b = pools["bounds"]
+        sampler = cfg.get("sampler", "mid")
+        tau = cfg.get("tau")
+        n = self.n
+        if sampler == "mid":
+            need = n * max(bp.n_max, bp.n_fallback)
+            if pools.get("rend_cap", 0) < need:
+                pools["rend"] = T.Renderer(self.mlp, n, need, device=self.dev)
+                pools["rend_cap"] = need
+            rend = pools["rend"]
+        elif sampler == "rel":
+            rend = pools["rend"]
+            ac = pools["ac"]
+        else:
+            ac = pools["ac"]
+            key = ("cf", cfg["n_fine"])
+            if key not in pools:
+                pools[key] = T.HierBoundedRenderer(self.mlp, n, cfg["n_fine"], n * 64, device=self.dev)
+            hb = pools[key]
+        rec = pools["rec"] if tau is not None else None
+        n_mean = cfg.get("n_mean", 6.0)
+        n_min, n_cap = cfg.get("n_min", 2), cfg.get("n_cap", 64)
+        used = {}
+
+        def render_view(v):
+            o, d = self.rays[v][:2]
+            b.compute(self.grid, o, d, bp, mask)
+            bb = b if sampler == "mid" else ac.apply(b, n_mean, n_min, n_cap, 64)
+            used["b"] = bb
+            out = rend.render(o, d, bb) if sampler != "cf" else hb.render(o, d, bb)
+            if rec is not None:
+                rec.apply(self.grid, o, d, bp, tau, out, b)
+            return out
+
+        def evals(v):
+            bb = used["b"]
+            e = int(bb.offsets[-1].item())
+            if sampler == "cf":
+                e += cfg["n_fine"] * int((bb.n > 0).sum().item())
+            return e + (int(rec.bounds.offsets[-1].item()) if rec is not None else 0)
+        r = self.run(cfg["name"], render_view, evals)
+        r["params"] = {k: v for k, v in cfg.items() if k != "name"}
+        return r
+
+    def diagnostics(self, kept, kept_h):
+        """Per view, from the default bounds of every ray and the 64 + 32 comparator's depth as
+        the surface t* (rays with its weight sum above 0.5): mean count, histogram of n (share at
+        n_max), share of BOUNDED rays whose far phase ran to t_end, t_f - t* and t* - t_n in
+        voxels, and the share of BOUNDED rays with t* outside [t_n, t_f] (Tab. 1's failures)."""
+        import torch
+        vs = self.wl.grid.voxel_size
+        g = self.wl.grid
+        lo = torch.tensor(g.origin, dtype=torch.float64, device=self.dev)
+        hi = lo + torch.tensor([g.nx, g.ny, g.nz], dtype=torch.float64, device=self.dev) * vs
+        edges = sorted({e for e in (1, 2, 4, 8, 16, 32, self.bp.n_max - 1, self.bp.n_max) if 1 <= e <= self.bp.n_max})
+        out = []
+        for v in range(N_VIEWS_TIMED):
+            k, kh = kept[v], kept_h[v]
+            o = self.rays[v][0].double()
+            d = self.rays[v][1].double()
+            inv = 1.0 / d
+            ta, tb = (lo - o) * inv, (hi - o) * inv
+            t_end = torch.clamp(torch.nan_to_num(torch.maximum(ta, tb), nan=float("inf")).amin(1), max=self.bp.t_far)
+            st = k["status"]
+            bnd = st == 1
+            nb = max(int(bnd.sum().item()), 1)
+            nn = k["n"][bnd]
+            hist, prev = {}, 0
+            for e in edges:
+                hist[f"{prev + 1}-{e}" if e > prev + 1 else f"{e}"] = round(
+                    float(((nn > prev) & (nn <= e)).sum().item()) / nb, 4)
+                prev = e
+            tn, tf = k["t_n"].double(), k["t_f"].double()
+            far_end = bnd & (tf >= t_end - 1e-4)
+            hit = bnd & (kh["wsum"] > 0.5)
+            ts = kh["depth"].double()
+            nh = max(int(hit.sum().item()), 1)
+            dfar = ((tf - ts) / vs)[hit]
+            dnear = ((ts - tn) / vs)[hit]
+            fail = hit & ((ts < tn) | (ts > tf))
+
+            def q(x, p_):
+                return round(float(torch.quantile(x.float(), p_).item()), 2) if x.numel() else None
+            out.append({"view": v, "samples_per_ray": round(float(k["n"].float().mean().item()), 2),
+                        "bounded": round(nb / len(st), 4),
+                        "fallback": round(float((st == 2).float().mean().item()), 4),
+                        "n_hist_bounded": hist, "far_ran_to_t_end": round(float(far_end.sum().item()) / nb, 4),
+                        "t_f_minus_tstar_vox": {"p50": q(dfar, 0.5), "p90": q(dfar, 0.9)},
+                        "tstar_minus_t_n_vox": {"p10": q(dnear, 0.1), "p50": q(dnear, 0.5)},
+                        "tab1_failed": round(float(fail.sum().item()) / nh, 4),
+                        "wsum_below_0p95": round(float((bnd & (k["wsum"] < 0.95)).sum().item()) / nb, 4)})
+        return out
+
+    def run_all(self, hier_renderer, sweep_on):
+        import torch
+        from paper_2311_17878_gb300 import tsdfs as T
+        t = self.tsdf_default()
+        hier, kept_h = self.hier(hier_renderer)
+        diag = self.diagnostics(t["_kept"], kept_h)
+        sweep = []
+        if sweep_on:
+            pools = {"bounds": T.Bounds(self.n, device=self.dev), "ac": T.AdaptiveCounts(self.n, device=self.dev),
+                     "rec": T.Recovery(self.mlp, self.n, self.bp.n_fallback, device=self.dev),
+                     "rend": self.rend, "rend_cap": self.rend.max_samples}
+            for cfg in SWEEP:
+                sweep.append(self.operating_point(cfg, pools))
+                torch.cuda.synchronize()
+            del pools
+        dd = self.dense
+        hit = dd["wsum"] > 0.5
+        geom = {"depth_mae_m": float(np.mean(np.abs(t["_depth"][hit] - dd["depth"][hit]))) if hit.any() else None}
+        r = self.refs
+        bnd = (r["status"] == 1) & hit
+        failed = bnd & ((dd["depth"] < r["t_n"]) | (dd["depth"] > r["t_f"]))
+        err = np.abs(t["_rgb"] - dd["rgb"]).max(1)
+        p_or = psnr(r["tsdf_rgb"], dd["rgb"])
+        for c in [t] + hier + sweep:
+            for k_ in [k_ for k_ in c if k_.startswith("_")]:
+                del c[k_]
+        t["name"] = "default"
+        return {"pixels": int(self.cuts[-1]), "views": N_VIEWS_TIMED,
+                "reference": f"oracle FP64 dense {DENSE_SAMPLES} midpoints over [t0, t_end], {r['source']}",
+                "psnr_tsdf_gpu": t["psnr"], "psnr_tsdf_oracle": p_or,
+                "meets_oracle_minus_0p1dB": bool(t["psnr"] >= p_or - 0.1),
+                "psnr_hier96_gpu": hier[0]["psnr"], "tsdf_ge_hier96": bool(t["psnr"] >= hier[0]["psnr"]),
+                "tsdf": t, "hier": hier, "sweep": sweep, "per_view": diag,
+                "tab1_failed_frac_oracle_bounds": float(failed.sum() / max(bnd.sum(), 1)),
+                "geometry_tsdf_gpu": geom, "colour_err_p99": float(np.percentile(err, 99)),
+                "colour_err_max": float(err.max()), "oracle_s": r["seconds"]}
 
 
 def run_cpu_baseline(wl, grid, rays, bp, spec, seconds=10.0, chunk=2048):
@@ -867,33 +1032,66 @@ def run_cpu_baseline(wl, grid, rays, bp, spec, seconds=10.0, chunk=2048):
 
 
 def oracle_references(wl, grid, rays, bp, spec, tau=None):
-    """The rest of the cpu_baseline leg: the oracle's outputs on the quality pixels of view 0,
-    which the quality fields compare the GPU renders against -- its dense FP64 reference over
-    [t0, t_end], its fp32 Alg. 1 bounds on the same grid and its TSDF-bounded render (with its
-    own recovery pass of Sec. 4.5 when tau is set)."""
+    """The rest of the cpu_baseline leg: the oracle's outputs on the quality pixels (seeded,
+    spread over every timed view), which the quality leg scores the GPU renders against --
+    the dense FP64 reference over [t0, t_end] (stored by oracle/make_quality_reference.py for
+    the room views and checked here on a few pixels; rendered in the run otherwise), the
+    oracle's fp32 Alg. 1 bounds on the same grid and its TSDF-bounded render (with its own
+    recovery pass of Sec. 4.5 when tau is set)."""
     import torch
     from oracle import cgrid
     from oracle import render as orr
+    from paper_2311_17878_gb300 import synth
     t_q = time.perf_counter()
-    idx = quality_pixels(rays[0][2].shape[0])
-    on, dn = rays[0][2][idx], rays[0][3][idx]
-    t0, te, ok = cgrid.clip_rays(wl.grid, on, dn, bp.t_near, bp.t_far, "f64")
+    n_rays = rays[0][2].shape[0]
     net = orr.Net(spec)
-    dd = orr.dense_reference(net, on, dn, t0, te, n=DENSE_SAMPLES)
-    ob = cgrid.ray_bounds(wl.grid, grid.V.cpu().numpy(), on, dn, bp, "f32")
-    tn, tf, cnt = ob["t_n"].astype(np.float64), ob["t_f"].astype(np.float64), ob["n"]
-    again = None
-    if tau is not None:
-        t0f, tef, _ = cgrid.clip_rays(wl.grid, on, dn, bp.t_near, bp.t_far, "f32")
-        ro, again = orr.render_recovered(net, on, dn, tn, tf, cnt, ob["status"], t0f.astype(np.float64),
-                                         tef.astype(np.float64), tau, bp.n_fallback)
-        ort = ro["rgb"].numpy()
-    else:
-        with torch.no_grad():
-            ort = orr.render_bounded(net, on, dn, tn, tf, cnt)["rgb"].numpy()
-    dense = {k: dd[k].numpy() for k in ("rgb", "depth", "wsum", "normal")}
-    return {"dense_rgb": dense["rgb"], "dense": dense, "tsdf_rgb": ort, "t_n": tn, "t_f": tf, "n": cnt,
-            "status": ob["status"], "again": again, "seconds": time.perf_counter() - t_q}
+    dense, source = None, None
+    if WORKLOAD == WORKLOADS["view"] and os.path.exists(DENSE_REF):
+        from oracle import make_quality_reference as mqr
+        z = np.load(DENSE_REF)
+        sets = synth.quality_pixels(n_rays, N_VIEWS_TIMED, QUALITY_PIXELS)
+        same = (str(z["networks_sha256"]) == mqr.network_digest(spec) and int(z["dense_samples"]) == DENSE_SAMPLES
+                and np.array_equal(z["pixel"], np.concatenate(sets)))
+        if same:
+            # a live check of the stored values on the first pixels of view 0
+            _, live = mqr.dense_for_view(0, spec, wl.grid, bp, pixels=8)
+            diff = max(float(np.abs(live[k] - z[k][:8]).max()) for k in ("rgb", "depth", "wsum"))
+            if diff < 1e-7:
+                dense = {k: z[k] for k in ("rgb", "depth", "wsum", "normal")}
+                source = f"stored by oracle/make_quality_reference.py, 8 pixels re-rendered here (max diff {diff:.1e})"
+    if dense is None:
+        sets = synth.quality_pixels(n_rays, N_VIEWS_TIMED, QUALITY_PIXELS_LIVE)
+        parts = []
+        for v in range(N_VIEWS_TIMED):
+            on, dn = rays[v][2][sets[v]], rays[v][3][sets[v]]
+            t0, te, _ = cgrid.clip_rays(wl.grid, on, dn, bp.t_near, bp.t_far, "f64")
+            dd = orr.dense_reference(net, on, dn, t0, te, n=DENSE_SAMPLES)
+            parts.append({k: dd[k].numpy() for k in ("rgb", "depth", "wsum", "normal")})
+        dense = {k: np.concatenate([p_[k] for p_ in parts]) for k in parts[0]}
+        source = "rendered in this run"
+    V = grid.V.view(torch.int16).cpu().numpy().view(np.uint16) if grid.V.dtype == torch.float16 else grid.V.cpu().numpy()
+    tn, tf, cnt, st, ort, again = [], [], [], [], [], []
+    for v in range(N_VIEWS_TIMED):
+        on, dn = rays[v][2][sets[v]], rays[v][3][sets[v]]
+        ob = cgrid.ray_bounds(wl.grid, V, on, dn, bp, "f32")
+        tn_v, tf_v = ob["t_n"].astype(np.float64), ob["t_f"].astype(np.float64)
+        if tau is not None:
+            t0f, tef, _ = cgrid.clip_rays(wl.grid, on, dn, bp.t_near, bp.t_far, "f32")
+            ro, ag = orr.render_recovered(net, on, dn, tn_v, tf_v, ob["n"], ob["status"], t0f.astype(np.float64),
+                                          tef.astype(np.float64), tau, bp.n_fallback)
+            ort.append(ro["rgb"].numpy())
+            again.append(ag)
+        else:
+            with torch.no_grad():
+                ort.append(orr.render_bounded(net, on, dn, tn_v, tf_v, ob["n"])["rgb"].numpy())
+        tn.append(tn_v)
+        tf.append(tf_v)
+        cnt.append(ob["n"])
+        st.append(ob["status"])
+    return {"pixels": sets, "dense": dense, "source": source, "tsdf_rgb": np.concatenate(ort),
+            "t_n": np.concatenate(tn), "t_f": np.concatenate(tf), "n": np.concatenate(cnt),
+            "status": np.concatenate(st), "again": np.concatenate(again) if again else None,
+            "seconds": time.perf_counter() - t_q}
 
 
 # ----------------------------------------------------------------------------

@@ -508,6 +508,17 @@ def sub_sample(n_total, n, seed=SEED_RAYS):
     return np.sort(rng.choice(n_total, size=min(n, n_total), replace=False))
 
 
+QUALITY_SEED = 31
+
+
+def quality_pixels(n_rays, n_views, total=4096, seed=QUALITY_SEED):
+    """Seeded pixel subsets for scoring image quality: `total` pixels spread over
+    `n_views` views (the first total % n_views views take one more), a sorted
+    subset of each view's n_rays rays, seed + v for view v."""
+    base, extra = divmod(int(total), int(n_views))
+    return [sub_sample(n_rays, base + (1 if v < extra else 0), seed=seed + v) for v in range(n_views)]
+
+
 def random_tsdf(shape_zyx, seed, frac_neg=0.3):
     """Random normalised TSDF values in [-1, 1] with a share of exact -1 (unseen) voxels."""
     rng = np.random.default_rng(seed)
