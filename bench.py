@@ -30,7 +30,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-HIER_LADDER = ((32, 16), (16, 8), (8, 4), (4, 2))
+HIER_LADDER = ((32, 16), (24, 12), (16, 8), (12, 6), (8, 4), (6, 3), (4, 2))
 METRIC = "rays/s at PSNR≥oracle−0.1dB, TSDF-bounded vs 96-sample hierarchical, 1 GB300"
 UNIT = "rays/s"
 WORKLOADS = {
@@ -51,7 +51,11 @@ MLP_TC_TRAFFIC = {"sha256": "ba0400f966c61f635448f92c6329d13ccd2215e34715a1c36e3
 MARCH_TRAFFIC = {"sha256": "b0949ace8b80982bc36c712a3e070b510fd14704b852a0badbb755be355d62a2", "bytes_per_launch": 9985254,
                  "profile": "profiles/k_ray_bounds_room_view_traffic.md"}
 ALGO_FLOP_PER_SAMPLE = 2.25e6   # SDF fwd + minimal reverse-mode grad + colour, 8x256 / 4x256 networks
-EXEC_FLOP_PER_SAMPLE = 4.75e6   # what the tensor-core kernel issues: value + 3 tangent rows, padded colour rows
+# what the tensor-core kernels issue per sample (value + 3 tangent rows through the SDF layers):
+# serial, 64-sample tiles: M = 128 colour MMAs with 64 live rows; pipelined, 32-sample tiles:
+# 4 rows per sample through both networks (M = 128 colour MMAs with 32 live rows), the SDF MMAs
+# twice with split operands
+EXEC_FLOP_PER_SAMPLE = {"serial": 4.75e6, "pipelined": 5.93e6, "pipelined-split": 9.63e6}
 N_VIEWS_TIMED = 10   # views cycled by the timed steps (4 for the panorama workload)
 QUALITY_PIXELS = 4096          # seeded pixels spread over every timed view (synth.quality_pixels)
 QUALITY_PIXELS_LIVE = 1024     # when the dense reference is rendered during the run (panorama workload)
@@ -88,7 +92,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["f16", "bf16", "f32"], default="f16")
+    ap.add_argument("--precision", choices=["f16", "bf16", "bf16x2", "f32"], default="f16",
+                    help="network operands: f16, bf16, bf16x2 (SDF activations split in two bf16 parts), f32 (SIMT)")
+    ap.add_argument("--net-kernel", choices=["auto", "serial", "pipelined"], default="auto",
+                    help="tensor-core network kernel; auto: the library's autotuner picks on view 0")
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-sweep", dest="sweep", action="store_false", default=True,
                     help="skip the operating-point sweep of the quality leg (D_s, M, neighbourhood, spacing, "
@@ -211,7 +218,7 @@ def source_hash(files) -> str:
     return h.hexdigest()
 
 
-MLP_TC_SOURCES = ("mlp_tc.cu", "common.cuh")
+MLP_TC_SOURCES = ("mlp_tc.cu", "tc_common.cuh", "common.cuh")
 MARCH_SOURCES = ("bounds.cu", "march.cuh", "common.cuh")
 
 
@@ -368,7 +375,7 @@ def run_ours(args, ws, rank, local):
     dev = f"cuda:{local}"
     spec = synth.scene_mlp("room")
     prec = args.precision
-    PREC = {"f16": T.TSDFS_PREC_F16, "bf16": T.TSDFS_PREC_BF16, "f32": T.TSDFS_PREC_F32}
+    PREC = {"f16": T.TSDFS_PREC_F16, "bf16": T.TSDFS_PREC_BF16, "bf16x2": T.TSDFS_PREC_BF16X2, "f32": T.TSDFS_PREC_F32}
     mlp = T.Mlp(spec, PREC[prec], device=dev)
     mlp_depth = mlp if prec != "f32" else T.Mlp(spec, T.TSDFS_PREC_F16, device=dev)
     if args.workload == "large":
@@ -402,6 +409,17 @@ def run_ours(args, ws, rank, local):
     # the march's launch shape, picked by the library's autotuner on the first view's rays
     tuned = bounds.autotune(grid, rays[0][0], rays[0][1], bp, mask, reps=3)
     rend = T.Renderer(mlp, n, max_samples, device=dev)
+    # the network kernel: fixed, or picked by the library's autotuner on view 0's rays
+    net_kernel = None
+    if prec != "f32":
+        if args.net_kernel == "auto":
+            bounds.compute(grid, rays[0][0], rays[0][1], bp, mask)
+            kk, ms_s, ms_p = rend.autotune(rays[0][0], rays[0][1], bounds, reps=3)
+            net_kernel = {"kernel": {1: "serial", 2: "pipelined"}[kk], "autotuned_ms": {"serial": ms_s, "pipelined": ms_p}}
+        else:
+            kk = {"serial": T.TSDFS_NETKERNEL_SERIAL, "pipelined": T.TSDFS_NETKERNEL_PIPELINED}[args.net_kernel]
+            T.tsdfs_set_network_kernel(PREC[prec], kk)
+            net_kernel = {"kernel": args.net_kernel, "autotuned_ms": None}
     rec = T.Recovery(mlp, n, bp.n_fallback, device=dev) if args.recovery_tau is not None else None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
@@ -472,7 +490,8 @@ def run_ours(args, ws, rank, local):
             step(k)
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    mlp_name = "mlp_simt" if prec == "f32" else "mlp_tc"
+    mlp_name = "mlp_simt" if prec == "f32" else (
+        "mlp_pipe" if T.tsdfs_network_kernel(PREC[prec]) == T.TSDFS_NETKERNEL_PIPELINED else "mlp_tc")
     import ctypes as C
     ms_k, n_k = C.c_double(0), C.c_int64(0)
     T.lib().tsdfs_profile_read(mlp_name.encode(), C.byref(ms_k), C.byref(n_k))
@@ -495,7 +514,10 @@ def run_ours(args, ws, rank, local):
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_burst, "unit": "TFLOP/s",
                 "frac": achieved / bf16_burst, "traffic": captured_traffic(MLP_TC_TRAFFIC, MLP_TC_SOURCES, args, prec),
                 "peak_kind": f"bf16 dense burst ({peak_src}); fp16 dense has the same nominal rate",
-                "kernel": "mlp_tc", "executed_tflops": achieved * EXEC_FLOP_PER_SAMPLE / ALGO_FLOP_PER_SAMPLE}
+                "kernel": mlp_name,
+                "executed_tflops": achieved * EXEC_FLOP_PER_SAMPLE[
+                    "serial" if mlp_name == "mlp_tc" else ("pipelined-split" if prec == "bf16x2" else "pipelined")]
+                / ALGO_FLOP_PER_SAMPLE}
     else:
         fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
@@ -522,6 +544,7 @@ def run_ours(args, ws, rank, local):
     hier_r = None if lean else T.HierRenderer(mlp, n, device=dev)
     quality = QualityLeg(refs, args, wl, grid, mask, bounds, rend, rec, mlp, rays, bp, n, dev, flush).run_all(
         hier_r, args.sweep) if (want_q and hier_r is not None) else None
+    oracle_best_gate(refs, quality)
     comparator = None
     if quality is not None:
         comparator = {"impl": "hier n_c + n_f (same GPU, same network engine)",
@@ -548,6 +571,7 @@ def run_ours(args, ws, rank, local):
                    "ray_subset": args.rays or None,
                    "cuda_graph": bool(graphs), "train_pitch_deg": synth.TRAIN_PITCH_DEG,
                    "march_launch": {"block": tuned[0], "blocks_per_sm": tuned[1], "autotuned_ms": tuned[2]},
+                   "network_kernel": net_kernel,
                    "recovery_tau": args.recovery_tau,
                    "networks": "SDF 8x256 PE6 skip4 + colour 4x256 PE4", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}, rays independent", "wall_s": t_wall},
@@ -616,6 +640,8 @@ def equal_psnr_comparison(q):
             best = {"name": c["name"], "rays_s": c["rays_s"], "psnr": c["psnr"],
                     "samples_per_ray": c["samples_per_ray"], "hier": bh["name"], "hier_rays_s": bh["rays_s"],
                     "hier_psnr": bh["psnr"], "tsdf_over_hier": r}
+    if best is not None and q.get("best_operating_point_gate"):
+        best["gate"] = q["best_operating_point_gate"]
     out["best_operating_point"] = best
     return out
 
@@ -916,6 +942,8 @@ class QualityLeg:
             return e + (int(rec.bounds.offsets[-1].item()) if rec is not None else 0)
         r = self.run(cfg["name"], render_view, evals)
         r["params"] = {k: v for k, v in cfg.items() if k != "name"}
+        r["_bp"] = bp
+        r["_cfg"] = cfg
         return r
 
     def diagnostics(self, kept, kept_h):
@@ -982,6 +1010,13 @@ class QualityLeg:
                 sweep.append(self.operating_point(cfg, pools))
                 torch.cuda.synchronize()
             del pools
+        # the best operating point of the sweep, whose PSNR gate the cpu_baseline leg computes
+        q_tmp = {"hier": hier, "tsdf": t, "sweep": sweep}
+        bo = (equal_psnr_comparison(q_tmp) or {}).get("best_operating_point")
+        best_cfg = None
+        if bo is not None and bo["name"] != "default":
+            c = next(c for c in sweep if c["name"] == bo["name"])
+            best_cfg = (c["name"], c["psnr"], c["_cfg"], c["_bp"])
         dd = self.dense
         hit = dd["wsum"] > 0.5
         geom = {"depth_mae_m": float(np.mean(np.abs(t["_depth"][hit] - dd["depth"][hit]))) if hit.any() else None}
@@ -999,6 +1034,7 @@ class QualityLeg:
                 "psnr_tsdf_gpu": t["psnr"], "psnr_tsdf_oracle": p_or,
                 "meets_oracle_minus_0p1dB": bool(t["psnr"] >= p_or - 0.1),
                 "psnr_hier96_gpu": hier[0]["psnr"], "tsdf_ge_hier96": bool(t["psnr"] >= hier[0]["psnr"]),
+                "best_operating_point_gate": None, "_best_cfg": best_cfg,
                 "tsdf": t, "hier": hier, "sweep": sweep, "per_view": diag,
                 "tab1_failed_frac_oracle_bounds": float(failed.sum() / max(bnd.sum(), 1)),
                 "geometry_tsdf_gpu": geom, "colour_err_p99": float(np.percentile(err, 99)),
@@ -1088,10 +1124,49 @@ def oracle_references(wl, grid, rays, bp, spec, tau=None):
         tf.append(tf_v)
         cnt.append(ob["n"])
         st.append(ob["status"])
-    return {"pixels": sets, "dense": dense, "source": source, "tsdf_rgb": np.concatenate(ort),
+    def tsdf_for(cfg, bp_cfg):
+        """The oracle's TSDF render of a midpoint operating point of the sweep (Alg. 1 with its
+        parameters, counts from its spacing, its recovery pass when it has one) on the quality
+        pixels."""
+        out = []
+        for v in range(N_VIEWS_TIMED):
+            on, dn = rays[v][2][sets[v]], rays[v][3][sets[v]]
+            ob = cgrid.ray_bounds(wl.grid, V, on, dn, bp_cfg, "f32")
+            tn_v, tf_v = ob["t_n"].astype(np.float64), ob["t_f"].astype(np.float64)
+            cnt_v = ob["n"]
+            with torch.no_grad():
+                if cfg.get("tau") is not None:
+                    t0f, tef, _ = cgrid.clip_rays(wl.grid, on, dn, bp_cfg.t_near, bp_cfg.t_far, "f32")
+                    r, _ = orr.render_recovered(net, on, dn, tn_v, tf_v, cnt_v, ob["status"], t0f.astype(np.float64),
+                                                tef.astype(np.float64), cfg["tau"], bp_cfg.n_fallback)
+                else:
+                    r = orr.render_bounded(net, on, dn, tn_v, tf_v, cnt_v)
+            out.append(r["rgb"].numpy())
+        return np.concatenate(out)
+
+    return {"pixels": sets, "dense": dense, "source": source, "tsdf_rgb": np.concatenate(ort), "tsdf_for": tsdf_for,
             "t_n": np.concatenate(tn), "t_f": np.concatenate(tf), "n": np.concatenate(cnt),
             "status": np.concatenate(st), "again": np.concatenate(again) if again else None,
             "seconds": time.perf_counter() - t_q}
+
+
+def oracle_best_gate(refs, quality):
+    """The rest of the cpu_baseline leg: the metric's PSNR gate for the best operating point
+    of the quality leg's sweep -- the oracle's render of that operating point (Alg. 1 with
+    its parameters, counts from its spacing, its recovery pass when it has one) on the
+    quality pixels against the GPU's.  Counts relative to the batch mean are not gated (the
+    mean is over each view's full ray set, which the oracle does not march)."""
+    if quality is None:
+        return
+    best = quality.pop("_best_cfg", None)
+    if best is None:
+        return
+    name, p_gpu, cfg, bp = best
+    gate = {"name": name, "psnr_gpu": p_gpu, "psnr_oracle": None, "meets_oracle_minus_0p1dB": None}
+    if cfg.get("sampler", "mid") == "mid":
+        p_o = psnr(refs["tsdf_for"](cfg, bp), refs["dense"]["rgb"])
+        gate.update(psnr_oracle=p_o, meets_oracle_minus_0p1dB=bool(p_gpu >= p_o - 0.1))
+    quality["best_operating_point_gate"] = gate
 
 
 # ----------------------------------------------------------------------------

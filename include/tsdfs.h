@@ -111,6 +111,11 @@ typedef struct {
 #define TSDFS_PREC_F32 0  /* FP32 SIMT networks                                  */
 #define TSDFS_PREC_BF16 1 /* BF16 tcgen05 networks, FP32 accumulate (packed required) */
 #define TSDFS_PREC_F16 2  /* FP16 operands on the same tcgen05 path (packed required)  */
+#define TSDFS_PREC_BF16X2 3 /* BF16 tcgen05 networks with every SDF layer's operand split
+                             * into two BF16 parts, hi = bf16(x) and lo = bf16(x - hi),
+                             * two MMAs per K step into the FP32 accumulator (about 16
+                             * significant bits per activation); colour layers in plain
+                             * BF16; packed BF16 weights required; pipelined kernel only */
 typedef struct {
     int32_t arch;
     int32_t precision;
@@ -232,8 +237,8 @@ int tsdf_ray_bounds_noalloc(const tsdfs_grid* grid, const uint32_t* inside_mask,
  * eik (nullable): per-ray sum over samples of (|grad f| - 1)^2, written only
  * for BOUNDED rays (0 otherwise).  normal may be NULL.
  * max_samples bounds offsets[n_rays]; workspace >= tsdfs_render_workspace_size.
- * precision TSDFS_PREC_BF16 / TSDFS_PREC_F16 needs mlp->packed from
- * tsdfs_pack_mlp (packed for that precision).                               */
+ * precision TSDFS_PREC_BF16 / TSDFS_PREC_F16 / TSDFS_PREC_BF16X2 needs
+ * mlp->packed from tsdfs_pack_mlp (packed for that precision).              */
 size_t tsdfs_render_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays, int64_t max_samples);
 int render_rays(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n, const float* t_f,
                 const int32_t* offsets, const uint8_t* status, int64_t n_rays, int64_t max_samples, float* rgb,
@@ -304,6 +309,53 @@ int tsdfs_autotune_bounds(const tsdfs_grid* grid, const uint32_t* inside_mask, c
 int tsdfs_set_bounds_launch_shape(int32_t block, int32_t blocks_per_sm);
 int tsdfs_bounds_launch_shape(int32_t* block, int32_t* blocks_per_sm);
 
+/* ---- which tensor-core kernel evaluates the networks (Eq. 1's MLP samples) ----
+ * Both kernels compute the same per-sample quantities (SDF value and gradient,
+ * colour) for render_rays and the full-evaluation passes of the samplers:
+ *   TSDFS_NETKERNEL_SERIAL     64-sample tiles (four rows per sample fill both
+ *                              TMEM accumulators); a layer's epilogue and the
+ *                              next layer's MMAs run one after the other;
+ *   TSDFS_NETKERNEL_PIPELINED  32-sample tiles, consecutive layers in alternate
+ *                              halves of TMEM, so the next layer's MMAs run on
+ *                              each 64-column block of its operand as soon as the
+ *                              epilogue has written it.
+ * The choice is process-wide, per precision (TSDFS_PREC_BF16, _F16; BF16X2 runs
+ * on the pipelined kernel only and rejects SERIAL); it takes effect at the next
+ * launch.  Returns 0 or TSDFS_E_INVALID.  tsdfs_network_kernel returns the
+ * current choice for a precision, or TSDFS_E_INVALID.                       */
+/* ---- test-only limits of the failure paths (no paper counterpart) ----
+ * For tests of the device-side failure reporting without a GPU fault:
+ * spin_limit (0: the default, about 6.7e7) bounds the polls of every mbarrier
+ * wait of the tensor-core network kernels before the wait gives up;
+ * withhold_chunk >= 0 makes their weight producers stop before that weight
+ * chunk of each CTA's first tile, so the MMA issuer's wait for it runs out
+ * (-1: never); march_step_cap > 0 bounds the voxel steps of a ray walk in
+ * tsdf_ray_bounds (0: nx + ny + nz + 8, more than any walk takes).  A wait that
+ * runs out sets TSDFS_DEV_TIMEOUT (the kernel drains its copies and MMAs, frees
+ * TMEM and returns; compositing writes zeros while the status word holds it);
+ * a walk cut short sets TSDFS_DEV_MARCH_CAP and ends as if it had left the
+ * grid (FALLBACK over [t0, t_end] in the near phase, t_f = t_end in the far
+ * phase).  Process-wide, read at each launch; 0 / -1 / 0 restores normal
+ * operation.  Returns 0 or TSDFS_E_INVALID.                                 */
+int tsdfs_set_test_limits(uint32_t spin_limit, int32_t march_step_cap, int32_t withhold_chunk);
+
+#define TSDFS_NETKERNEL_SERIAL 1
+#define TSDFS_NETKERNEL_PIPELINED 2
+int tsdfs_set_network_kernel(int32_t precision, int32_t kernel);
+int tsdfs_network_kernel(int32_t precision);
+/* Set-up call: times render_rays (arguments as there, eik not written) with each
+ * network kernel the precision has, reps calls each after one untimed call,
+ * with CUDA events on `stream` (synchronises it), keeps the faster for
+ * mlp->precision (tsdfs_set_network_kernel) and returns it (> 0), or a negative
+ * code (the previous choice is then kept).  ms_out (nullable, host, 2 floats)
+ * receives the mean time per call of the serial and the pipelined kernel (-1
+ * for a kernel the precision does not have).  The outputs hold the last call's
+ * render.                                                                   */
+int tsdfs_autotune_network(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
+                           const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
+                           int64_t max_samples, float* rgb, float* depth, float* wsum, float* normal, void* ws,
+                           size_t ws_bytes, int32_t reps, float* ms_out, tsdfs_stream_t stream);
+
 /* ---- adaptive sample counts relative to the mean interval (Sec. 3.4) -------
  * Samples sit at equal spacing inside [t_n, t_f], so a ray's count is
  * proportional to its interval's length; the supplementary ray study scales it
@@ -371,6 +423,28 @@ int render_rays_backward(const tsdfs_mlp* mlp, const float* ray_o, const float* 
  * tcgen05 path reads -- bf16, or fp16 when mlp->precision is TSDFS_PREC_F16 --
  * rounded to nearest even, into `packed` (device, tsdfs_packed_size bytes,
  * 16-byte aligned).  Repeat after every parameter update.                    */
+/* ---- FP64 finite-difference harness of render_rays_backward (test use) ----
+ * The bounded render of render_rays (same inputs: rays, [t_n, t_f], offsets,
+ * status; midpoint samples; both networks with the SDF gradient; the network's
+ * opacity; Eq. 1 / Eq. 2) evaluated in FP64 on the GPU with FP64 parameters
+ * sdf_w64 / rgb_w64 (device, the packed (W, b) layout of tsdfs_sdf_param_count /
+ * tsdfs_rgb_param_count doubles; mlp supplies the architecture, constants and
+ * opacity, its own parameter pointers are not read), reduced to
+ *   *loss = sum_r g_rgb[r] . rgb[r] + g_depth[r] depth[r] + g_eik[r] eik[r]
+ * (g_depth, g_eik nullable; eik as in render_rays: BOUNDED rays only), the
+ * functional whose parameter gradient render_rays_backward returns for output
+ * gradients g_rgb, g_depth, g_eik.  Central differences of *loss over single
+ * parameters check that gradient.  The one use of FP64 arithmetic on the GPU;
+ * it synchronises `stream` once to read the sample total.  loss is a device
+ * double; ws >= tsdfs_loss_f64_workspace_size(n_rays, max_samples) (about 20 KB
+ * per sample).  Returns 0 or a negative TSDFS_E_* code.                     */
+size_t tsdfs_loss_f64_workspace_size(int64_t n_rays, int64_t max_samples);
+int tsdfs_loss_f64(const tsdfs_mlp* mlp, const double* sdf_w64, const double* rgb_w64, const float* ray_o,
+                   const float* ray_d, const float* t_n, const float* t_f, const int32_t* offsets,
+                   const uint8_t* status, int64_t n_rays, int64_t max_samples, const float* g_rgb,
+                   const float* g_depth, const float* g_eik, double* loss, void* ws, size_t ws_bytes,
+                   tsdfs_stream_t stream);
+
 size_t tsdfs_packed_size(int32_t arch);
 int tsdfs_pack_mlp(const tsdfs_mlp* mlp, void* packed, tsdfs_stream_t stream);
 

@@ -22,7 +22,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libtsdfs.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["abi.cu", "integrate.cu", "bounds.cu", "mlp_simt.cu", "composite.cu", "mlp_tc.cu", "backward.cu"]
+SOURCES = ["abi.cu", "integrate.cu", "bounds.cu", "mlp_simt.cu", "composite.cu", "mlp_tc.cu", "mlp_pipe.cu", "backward.cu", "fd64.cu"]
 EXACT = {"integrate.cu", "bounds.cu"}
 
 

@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -91,6 +92,17 @@ int symbol_address(SymbolCache& cache, const void* symbol, void** out, const cha
     return TSDFS_OK;
 }
 
+// test-only limits of the failure paths (tsdfs_set_test_limits)
+static std::atomic<uint32_t> g_test_spin{0};
+static std::atomic<int> g_test_march{0};
+static std::atomic<int> g_test_withhold{-1};
+uint32_t test_spin_limit(uint32_t dflt) {
+    const uint32_t v = g_test_spin.load();
+    return v ? v : dflt;
+}
+int test_march_cap() { return g_test_march.load(); }
+int test_withhold_chunk() { return g_test_withhold.load(); }
+
 // one status word per device context
 static __device__ uint32_t g_status_word;
 static SymbolCache g_status_cache;
@@ -176,13 +188,25 @@ int mlp_tc_available(int arch);
 int launch_mlp_full_tc(const tsdfs_mlp* mlp, const SampleSource& src, SampleRec* rec, int64_t max_samples,
                        cudaStream_t st);
 int launch_mlp_value_tc(const tsdfs_mlp* mlp, const SampleSource& src, float* f_out, cudaStream_t st);
+int launch_mlp_pipe(const tsdfs_mlp* mlp, const SampleSource& src, SampleRec* rec, int64_t max_samples,
+                    cudaStream_t st);
+
+// network kernel per precision (tsdfs_set_network_kernel), index = TSDFS_PREC_*
+static int g_netkernel[4] = {0, TSDFS_NETKERNEL_SERIAL, TSDFS_NETKERNEL_SERIAL, TSDFS_NETKERNEL_PIPELINED};
+static std::mutex g_netkernel_mu;
+
+static int netkernel_of(int precision) {
+    std::lock_guard<std::mutex> lk(g_netkernel_mu);
+    return g_netkernel[precision];
+}
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 static int mlp_check(const tsdfs_mlp* m) {
     if (!m) return fail(TSDFS_E_INVALID, "mlp is NULL");
     if (m->arch != TSDFS_ARCH_TINY && m->arch != TSDFS_ARCH_ROOM) return fail(TSDFS_E_INVALID, "unknown arch %d", m->arch);
-    if (m->precision != TSDFS_PREC_F32 && m->precision != TSDFS_PREC_BF16 && m->precision != TSDFS_PREC_F16)
+    if (m->precision != TSDFS_PREC_F32 && m->precision != TSDFS_PREC_BF16 && m->precision != TSDFS_PREC_F16 &&
+        m->precision != TSDFS_PREC_BF16X2)
         return fail(TSDFS_E_INVALID, "unknown precision %d", m->precision);
     if (!m->sdf_w || !m->rgb_w) return fail(TSDFS_E_INVALID, "sdf_w and rgb_w must be non-NULL");
     if (!(m->scale > 0.0f) || !(m->beta > 0.0f) || !(m->inv_s > 0.0f) || !(m->alpha_eps >= 0.0f))
@@ -212,6 +236,10 @@ static NetParams net_params(const tsdfs_mlp* m) {
 static int run_full_mlp(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64_t max_samples,
                         cudaStream_t st) {
     if (m->precision != TSDFS_PREC_F32) {
+        if (netkernel_of(m->precision) == TSDFS_NETKERNEL_PIPELINED) {
+            ProfScope ps("mlp_pipe", st);
+            return launch_mlp_pipe(m, src, rec, max_samples, st);
+        }
         ProfScope ps("mlp_tc", st);
         return launch_mlp_full_tc(m, src, rec, max_samples, st);
     }
@@ -226,6 +254,33 @@ static int run_full_mlp(const tsdfs_mlp* m, const SampleSource& src, SampleRec* 
 using namespace tsdfs;
 
 extern "C" const char* tsdfs_last_error(void) { return g_msg; }
+
+extern "C" int tsdfs_set_test_limits(uint32_t spin_limit, int32_t march_step_cap, int32_t withhold_chunk) {
+    if (march_step_cap < 0) return fail(TSDFS_E_INVALID, "tsdfs_set_test_limits: march_step_cap must be >= 0");
+    if (withhold_chunk < -1) return fail(TSDFS_E_INVALID, "tsdfs_set_test_limits: withhold_chunk must be >= -1");
+    g_test_spin.store(spin_limit);
+    g_test_march.store(march_step_cap);
+    g_test_withhold.store(withhold_chunk);
+    return TSDFS_OK;
+}
+
+extern "C" int tsdfs_set_network_kernel(int32_t precision, int32_t kernel) {
+    if (precision != TSDFS_PREC_BF16 && precision != TSDFS_PREC_F16 && precision != TSDFS_PREC_BF16X2)
+        return fail(TSDFS_E_INVALID, "tsdfs_set_network_kernel: precision %d has no tensor-core kernel", precision);
+    if (kernel != TSDFS_NETKERNEL_SERIAL && kernel != TSDFS_NETKERNEL_PIPELINED)
+        return fail(TSDFS_E_INVALID, "tsdfs_set_network_kernel: unknown kernel %d", kernel);
+    if (precision == TSDFS_PREC_BF16X2 && kernel != TSDFS_NETKERNEL_PIPELINED)
+        return fail(TSDFS_E_INVALID, "tsdfs_set_network_kernel: BF16X2 runs on the pipelined kernel only");
+    std::lock_guard<std::mutex> lk(g_netkernel_mu);
+    g_netkernel[precision] = kernel;
+    return TSDFS_OK;
+}
+
+extern "C" int tsdfs_network_kernel(int32_t precision) {
+    if (precision != TSDFS_PREC_BF16 && precision != TSDFS_PREC_F16 && precision != TSDFS_PREC_BF16X2)
+        return fail(TSDFS_E_INVALID, "tsdfs_network_kernel: precision %d has no tensor-core kernel", precision);
+    return netkernel_of(precision);
+}
 
 extern "C" int tsdfs_profile(int32_t enable) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -339,6 +394,57 @@ extern "C" int render_rays(const tsdfs_mlp* mlp, const float* ray_o, const float
     ProfScope ps("composite", st);
     return launch_composite(rec, offsets, 0, status, n_rays, offsets + n_rays, max_samples, opacity_of(mlp),
                             rgb, depth, wsum, normal, eik, st);
+}
+
+extern "C" int tsdfs_autotune_network(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
+                                      const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
+                                      int64_t max_samples, float* rgb, float* depth, float* wsum, float* normal,
+                                      void* ws, size_t ws_bytes, int32_t reps, float* ms_out,
+                                      tsdfs_stream_t stream) {
+    int rc = mlp_check(mlp);
+    if (rc) return rc;
+    if (mlp->precision == TSDFS_PREC_F32) return fail(TSDFS_E_INVALID, "tsdfs_autotune_network: FP32 has one kernel");
+    if (reps < 1) return fail(TSDFS_E_INVALID, "tsdfs_autotune_network: reps must be >= 1");
+    const int cands[2] = {TSDFS_NETKERNEL_SERIAL, TSDFS_NETKERNEL_PIPELINED};
+    float best_ms = 0.0f;
+    int best = TSDFS_NETKERNEL_PIPELINED;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    rc = cuda_check(cudaEventCreate(&e0), "autotune_network event");
+    if (!rc) rc = cuda_check(cudaEventCreate(&e1), "autotune_network event");
+    const int old = netkernel_of(mlp->precision);
+    for (int c = 0; c < 2 && !rc; ++c) {
+        float ms = -1.0f;
+        if (cands[c] == TSDFS_NETKERNEL_SERIAL && mlp->precision == TSDFS_PREC_BF16X2) {
+            if (ms_out) ms_out[c] = ms;
+            continue;
+        }
+        {
+            std::lock_guard<std::mutex> lk(g_netkernel_mu);
+            g_netkernel[mlp->precision] = cands[c];
+        }
+        rc = render_rays(mlp, ray_o, ray_d, t_n, t_f, offsets, status, n_rays, max_samples, rgb, depth, wsum, normal,
+                         nullptr, ws, ws_bytes, stream);
+        if (!rc) rc = cuda_check(cudaEventRecord(e0, st), "autotune_network record");
+        for (int r = 0; r < reps && !rc; ++r)
+            rc = render_rays(mlp, ray_o, ray_d, t_n, t_f, offsets, status, n_rays, max_samples, rgb, depth, wsum,
+                             normal, nullptr, ws, ws_bytes, stream);
+        if (!rc) rc = cuda_check(cudaEventRecord(e1, st), "autotune_network record");
+        if (!rc) rc = cuda_check(cudaEventSynchronize(e1), "autotune_network sync");
+        if (!rc) rc = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "autotune_network elapsed");
+        if (rc) break;
+        ms /= (float)reps;
+        if (ms_out) ms_out[c] = ms;
+        if (best_ms == 0.0f || ms < best_ms) {
+            best_ms = ms;
+            best = cands[c];
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_netkernel_mu);
+    g_netkernel[mlp->precision] = rc ? old : best;
+    return rc ? rc : best;
 }
 
 // ---- hierarchical comparator ------------------------------------------------

@@ -25,6 +25,7 @@ constexpr int kScanChunk = kScanBlock * kScanItems;
 struct BoundsDev {
     float d_s, t_near, t_far, step;
     int nb_radius, m_confirm, n_max, n_fallback;
+    int max_steps;   // voxel steps a walk may take (0: nx + ny + nz + 8, more than any walk needs)
 };
 
 __device__ __forceinline__ float trilinear(const GridDev& g, const float p[3]) {
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(kBoundsMaxBlock) k_ray_bounds(GridDev g, const
     const float kInf = __int_as_float(0x7f800000);
     const float kNaN = __int_as_float(0x7fffffff);
     const float ds_norm = __fdiv_rn(p.d_s, g.trunc);
-    const int max_steps = g.n[0] + g.n[1] + g.n[2] + 8;
+    const int max_steps = p.max_steps > 0 ? p.max_steps : g.n[0] + g.n[1] + g.n[2] + 8;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
         float o[3], d[3];
 #pragma unroll
@@ -371,7 +372,8 @@ extern "C" int tsdf_ray_bounds(const tsdfs_grid* g, const uint32_t* mask, const 
     if (n_rays > 0) {
         GridDev gd{g->tsdf, g->dtype == TSDFS_F16, {g->nx, g->ny, g->nz}, {g->origin[0], g->origin[1], g->origin[2]},
                    g->voxel_size, g->trunc};
-        BoundsDev bd{p->d_s, p->t_near, p->t_far, p->step, p->nb_radius, p->m_confirm, p->n_max, p->n_fallback};
+        BoundsDev bd{p->d_s, p->t_near, p->t_far, p->step, p->nb_radius, p->m_confirm, p->n_max, p->n_fallback,
+                     test_march_cap()};
         const MarchShape sh = march_shape();
         ProfScope ps("ray_bounds", st);
         k_ray_bounds<<<march_grid(n_rays, sh), sh.block, 0, st>>>(gd, mask, ray_o, ray_d, n_rays, bd, t_n, t_f,
@@ -404,7 +406,8 @@ extern "C" int tsdf_recovery_bounds(const tsdfs_grid* g, const float* ray_o, con
     if (n_rays > 0) {
         GridDev gd{g->tsdf, g->dtype == TSDFS_F16, {g->nx, g->ny, g->nz}, {g->origin[0], g->origin[1], g->origin[2]},
                    g->voxel_size, g->trunc};
-        BoundsDev bd{p->d_s, p->t_near, p->t_far, p->step, p->nb_radius, p->m_confirm, p->n_max, p->n_fallback};
+        BoundsDev bd{p->d_s, p->t_near, p->t_far, p->step, p->nb_radius, p->m_confirm, p->n_max, p->n_fallback,
+                     test_march_cap()};
         const MarchShape sh = march_shape();
         ProfScope ps("recovery_bounds", st);
         k_recovery_bounds<<<march_grid(n_rays, sh), sh.block, 0, st>>>(

@@ -28,6 +28,14 @@ struct SymbolCache {
     unsigned long long ctx[kDevices] = {};
 };
 int symbol_address(SymbolCache& cache, const void* symbol, void** out, const char* what);
+// test-only limits (tsdfs_set_test_limits): polls of a bounded mbarrier wait before it
+// gives up (default kMaxSpin of the tensor-core kernels) and voxel steps of a ray walk
+// (0: the grid's own bound nx + ny + nz + 8)
+uint32_t test_spin_limit(uint32_t dflt);
+int test_march_cap();
+// test-only: the tensor-core kernels' producers stop before this weight chunk of each CTA's
+// first tile (-1: never), so the MMA warp's wait for it runs out
+int test_withhold_chunk();
 
 // exclusive scan of n counts into offsets[0..n]; `sums` needs scan_chunks(n) + 1 ints (bounds.cu)
 int64_t scan_chunks(int64_t n);

@@ -21,8 +21,11 @@ __global__ void __launch_bounds__(kCompBlock) k_composite(const SampleRec* __res
                                                           const int32_t* total_dev, int64_t capacity, Opacity op,
                                                           float* __restrict__ rgb, float* __restrict__ depth,
                                                           float* __restrict__ wsum_out, float* __restrict__ normal,
-                                                          float* __restrict__ eik_out) {
-    const bool overflow = total_dev && (int64_t)__ldg(total_dev) > capacity;
+                                                          float* __restrict__ eik_out, const uint32_t* dev_status) {
+    // outputs are zero when the samples overflowed the workspace, and while the device
+    // status word holds a timeout of a network kernel (its records may be incomplete)
+    const bool overflow = (total_dev && (int64_t)__ldg(total_dev) > capacity) ||
+                          (dev_status && (*(const volatile uint32_t*)dev_status & TSDFS_DEV_TIMEOUT));
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
         int64_t b, e;
         if (offsets) {
@@ -284,7 +287,8 @@ int launch_composite(const SampleRec* rec, const int32_t* offsets, int per_ray, 
                      float* wsum, float* normal, float* eik, cudaStream_t st) {
     if (n_rays == 0) return TSDFS_OK;
     k_composite<<<grid_1d(n_rays, kCompBlock), kCompBlock, 0, st>>>(rec, offsets, per_ray, status, n_rays, total_dev,
-                                                                    capacity, op, rgb, depth, wsum, normal, eik);
+                                                                    capacity, op, rgb, depth, wsum, normal, eik,
+                                                                    device_status_word());
     return cuda_check(cudaGetLastError(), "composite launch");
 }
 

@@ -27,7 +27,8 @@ TSDFS_OK, TSDFS_E_INVALID, TSDFS_E_CUDA, TSDFS_E_WORKSPACE, TSDFS_E_UNSUPPORTED,
 TSDFS_F32, TSDFS_F16 = 0, 1
 TSDFS_MISS, TSDFS_BOUNDED, TSDFS_FALLBACK = 0, 1, 2
 TSDFS_ARCH_TINY, TSDFS_ARCH_ROOM = 0, 1
-TSDFS_PREC_F32, TSDFS_PREC_BF16, TSDFS_PREC_F16 = 0, 1, 2
+TSDFS_PREC_F32, TSDFS_PREC_BF16, TSDFS_PREC_F16, TSDFS_PREC_BF16X2 = 0, 1, 2, 3
+TSDFS_NETKERNEL_SERIAL, TSDFS_NETKERNEL_PIPELINED = 1, 2
 TSDFS_OPACITY_NEUS, TSDFS_OPACITY_VOLSDF = 0, 1
 TSDFS_DEV_SAMPLES_OVERFLOW, TSDFS_DEV_MARCH_CAP, TSDFS_DEV_TIMEOUT, TSDFS_DEV_NONFINITE = 1, 2, 4, 8
 
@@ -39,6 +40,8 @@ EXPORTS = ["tsdfs_last_error", "tsdfs_sync_status", "tsdfs_grid_init", "tsdf_int
            "tsdf_recovery_bounds", "tsdf_recovery_merge", "tsdfs_check_mlp", "tsdfs_adaptive_counts_workspace_size",
            "tsdf_adaptive_counts", "tsdfs_hier_bounded_workspace_size", "render_rays_hier_bounded",
            "tsdfs_autotune_bounds", "tsdfs_set_bounds_launch_shape", "tsdfs_bounds_launch_shape",
+           "tsdfs_set_network_kernel", "tsdfs_network_kernel", "tsdfs_set_test_limits",
+           "tsdfs_loss_f64_workspace_size", "tsdfs_loss_f64", "tsdfs_autotune_network",
            "tsdfs_raycast_workspace_size", "tsdf_integrate_raycast", "tsdfs_profile", "tsdfs_profile_read"]
 
 
@@ -75,7 +78,8 @@ def lib():
             L.tsdfs_last_error.restype = C.c_char_p
             for name in ["tsdfs_bounds_workspace_size", "tsdfs_render_workspace_size", "tsdfs_hier_workspace_size",
                          "tsdfs_backward_workspace_size", "tsdfs_packed_size", "tsdfs_adaptive_counts_workspace_size",
-                         "tsdfs_hier_bounded_workspace_size", "tsdfs_raycast_workspace_size"]:
+                         "tsdfs_hier_bounded_workspace_size", "tsdfs_raycast_workspace_size",
+                         "tsdfs_loss_f64_workspace_size"]:
                 getattr(L, name).restype = C.c_size_t
             for name in ["tsdfs_inside_mask_words", "tsdfs_sdf_param_count", "tsdfs_rgb_param_count"]:
                 getattr(L, name).restype = C.c_int64
@@ -258,6 +262,36 @@ def tsdfs_autotune_bounds(grid: "Grid", inside_mask, ray_o, ray_d, p, t_n, t_f, 
 
 def tsdfs_set_bounds_launch_shape(block=0, blocks_per_sm=0):
     _check(lib().tsdfs_set_bounds_launch_shape(C.c_int32(block), C.c_int32(blocks_per_sm)))
+
+
+def tsdfs_set_network_kernel(precision, kernel):
+    """Process-wide choice of the tensor-core network kernel for a 16-bit precision."""
+    _check(lib().tsdfs_set_network_kernel(C.c_int32(precision), C.c_int32(kernel)))
+
+
+def tsdfs_loss_f64_workspace_size(n_rays, max_samples) -> int:
+    return int(lib().tsdfs_loss_f64_workspace_size(C.c_int64(n_rays), C.c_int64(max_samples)))
+
+
+def tsdfs_loss_f64(mlp: "Mlp", sdf_w64, rgb_w64, ray_o, ray_d, t_n, t_f, offsets, status, max_samples, g_rgb, g_depth,
+                   g_eik, loss, workspace):
+    """FP64 functional of the bounded render (the finite-difference harness); `loss` is a
+    one-element float64 device tensor."""
+    n = ray_o.shape[0]
+    _check(lib().tsdfs_loss_f64(C.byref(mlp.c), _p(sdf_w64), _p(rgb_w64), _p(ray_o), _p(ray_d), _p(t_n), _p(t_f),
+                                _p(offsets), _p(status), C.c_int64(n), C.c_int64(max_samples), _p(g_rgb), _p(g_depth),
+                                _p(g_eik), _p(loss), _p(workspace), C.c_size_t(workspace.numel()), _stream()))
+
+
+def tsdfs_set_test_limits(spin_limit=0, march_step_cap=0, withhold_chunk=-1):
+    """Test-only limits of the failure paths (0, 0, -1: normal operation)."""
+    _check(lib().tsdfs_set_test_limits(C.c_uint32(spin_limit), C.c_int32(march_step_cap), C.c_int32(withhold_chunk)))
+
+
+def tsdfs_network_kernel(precision) -> int:
+    rc = int(lib().tsdfs_network_kernel(C.c_int32(precision)))
+    _check(min(rc, 0))
+    return rc
 
 
 def tsdfs_bounds_launch_shape():
@@ -496,6 +530,19 @@ class Renderer:
         render_rays(self.mlp, rays_o, rays_d, b.t_n, b.t_f, b.offsets, b.status, self.max_samples, o.rgb, o.depth,
                     o.wsum, o.normal, o.eik, self.workspace)
         return o
+
+    def autotune(self, rays_o, rays_d, b: Bounds, reps=3):
+        """Pick the faster network kernel for this precision on these rays
+        (tsdfs_autotune_network); returns (kernel, ms serial, ms pipelined)."""
+        o = self.out
+        ms = (C.c_float * 2)(-1.0, -1.0)
+        rc = int(lib().tsdfs_autotune_network(C.byref(self.mlp.c), _p(rays_o), _p(rays_d), _p(b.t_n), _p(b.t_f),
+                                              _p(b.offsets), _p(b.status), C.c_int64(rays_o.shape[0]),
+                                              C.c_int64(self.max_samples), _p(o.rgb), _p(o.depth), _p(o.wsum),
+                                              _p(o.normal), _p(self.workspace), C.c_size_t(self.workspace.numel()),
+                                              C.c_int32(reps), ms, _stream()))
+        _check(min(rc, 0))
+        return rc, float(ms[0]), float(ms[1])
 
 
 class Recovery:

@@ -139,6 +139,21 @@ def test_adaptive_counts_and_bounded_hier_arguments_fail_on_host(L):
     assert hb(8, 0, 0) == T.TSDFS_OK
 
 
+def test_network_kernel_choice(L):
+    """Per-precision choice of the network kernel: both kernels for BF16 / FP16, the
+    pipelined one only for BF16X2, nothing for FP32."""
+    assert L.tsdfs_network_kernel(3) == 2
+    assert L.tsdfs_set_network_kernel(3, 1) < 0
+    assert L.tsdfs_set_network_kernel(0, 1) < 0 and L.tsdfs_network_kernel(0) < 0
+    assert L.tsdfs_set_network_kernel(2, 7) < 0
+    for prec in (1, 2):
+        old = L.tsdfs_network_kernel(prec)
+        assert old in (1, 2)
+        assert L.tsdfs_set_network_kernel(prec, 2) == 0 and L.tsdfs_network_kernel(prec) == 2
+        assert L.tsdfs_set_network_kernel(prec, 1) == 0 and L.tsdfs_network_kernel(prec) == 1
+        assert L.tsdfs_set_network_kernel(prec, old) == 0
+
+
 def test_bounds_launch_shape_arguments(L):
     for b, sm in [(16, 8), (96 + 1, 8), (512, 8), (128, 0), (128, 2000)]:
         assert L.tsdfs_set_bounds_launch_shape(C.c_int32(b), C.c_int32(sm)) == T.TSDFS_E_INVALID

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def coefficients():
-    src = open(os.path.join(ROOT, "paper_2311_17878_gb300", "csrc", "mlp_tc.cu")).read()
+    src = open(os.path.join(ROOT, "paper_2311_17878_gb300", "csrc", "tc_common.cuh")).read()
     body = src[src.index("float log1p_unit(float u)"):]
     body = body[:body.index("return p * u;")]
     return [float(v) for v in re.findall(r"(-?\d+\.\d+(?:e-?\d+)?)f", body)]

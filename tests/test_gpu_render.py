@@ -211,13 +211,14 @@ def test_render_f16_operands_match_oracle(scene):
 
 
 @pytest.mark.parametrize("scene", ["tiny", "room"])
+@pytest.mark.xfail(reason="plain BF16 operands keep 8 significant bits (unit roundoff 2^-8 against FP16's "
+                          "2^-11); the rounding of the SDF network's activations reaches the bars on the worst "
+                          "rays: an FP64 emulation with every operand rounded to BF16 gives room colour p99 "
+                          "7.0e-3, max 1.3e-2, depth p99 2.5e-3, max 5.8e-3; TSDFS_PREC_BF16X2 meets the bars",
+                   strict=False)
 def test_render_bf16_operands_match_oracle(scene):
-    """tcgen05 path with bf16 operands.  bf16 keeps 8 significant bits (unit
-    roundoff 2^-8) against fp16's 11 (2^-11), so the bar that fp16 operands meet
-    (2e-3) scales by 8 for bf16: 99% of the rays within 1.6e-2 colour / depth.
-    The largest error over 4096 rays is a tail value that moves with any change
-    of rounding order (a flipped bf16 rounding near the surface is amplified by
-    the logistic density), so it gets twice that."""
+    """tcgen05 path with plain bf16 operands, at the stated 16-bit bars (colour 2e-3
+    absolute, depth 2e-3 relative, every ray)."""
     o, d, b = _scene_case(scene)
     spec = synth.scene_mlp(scene)
     got = gpu_render(spec, o, d, b, precision=T.TSDFS_PREC_BF16)
@@ -226,9 +227,7 @@ def test_render_bf16_operands_match_oracle(scene):
     ref, _ = oracle_render(spec, o, d, b)
     er, ed = _errors(got, ref)
     print(f"{scene} bf16: rgb p99 {np.percentile(er, 99):.2e} max {er.max():.2e}; depth p99 {np.percentile(ed, 99):.2e} max {ed.max():.2e}")
-    bf16_factor = 2.0 ** -8 / 2.0 ** -11
-    assert np.percentile(er, 99) <= bf16_factor * RGB_ABS and np.percentile(ed, 99) <= bf16_factor * DEPTH_REL_BF16
-    assert er.max() <= 2 * bf16_factor * RGB_ABS and ed.max() <= 2 * bf16_factor * DEPTH_REL_BF16
+    compare(got, ref, depth_rel=DEPTH_REL_BF16)
 
 
 @pytest.mark.parametrize("n_coarse,n_fine", [(64, 32), (24, 9)])
