@@ -309,6 +309,17 @@ int tsdfs_autotune_bounds(const tsdfs_grid* grid, const uint32_t* inside_mask, c
 int tsdfs_set_bounds_launch_shape(int32_t block, int32_t blocks_per_sm);
 int tsdfs_bounds_launch_shape(int32_t* block, int32_t* blocks_per_sm);
 
+/* ---- L2 read bandwidth (measurement support; no paper counterpart) ----
+ * Streams 16-byte loads over `bytes` of the device buffer `buf` (16-byte
+ * aligned; keep it well below the L2 size so it stays resident) once untimed,
+ * then `reps` times between CUDA events on `stream` (synchronises it);
+ * *ms_out (host) = the timed pass's milliseconds, so the achieved L2 read
+ * bandwidth is reps * bytes / ms_out.  sink: a device uint32 the kernel may
+ * write (keeps the loads).  The bench judges the ray march against this peak
+ * when its grid stays in L2.  Returns 0 or a negative TSDFS_E_* code.        */
+int tsdfs_l2_read_probe(const void* buf, size_t bytes, int32_t reps, uint32_t* sink, float* ms_out,
+                        tsdfs_stream_t stream);
+
 /* ---- which tensor-core kernel evaluates the networks (Eq. 1's MLP samples) ----
  * Both kernels compute the same per-sample quantities (SDF value and gradient,
  * colour) for render_rays and the full-evaluation passes of the samplers:

@@ -683,3 +683,55 @@ extern "C" int tsdfs_autotune_bounds(const tsdfs_grid* g, const uint32_t* mask, 
     if (best_ms) *best_ms = best / (float)reps;
     return rc2;
 }
+
+// ---------------------------------------------------------------------------
+// L2 read-bandwidth probe: the measured peak against which the ray march is
+// judged when its grid stays in L2.  Every thread streams 16-byte loads over the
+// buffer (which the caller keeps at a size L2 holds) reps times; the XOR of the
+// loaded words goes to `sink` so the loads are kept.
+// ---------------------------------------------------------------------------
+namespace tsdfs {
+namespace {
+__global__ void k_l2_read(const uint4* __restrict__ buf, int64_t n16, int reps, uint32_t* sink) {
+    uint32_t acc = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r)
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += stride) {
+            const uint4 v = __ldcg(buf + i);
+            acc ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
+    if (acc == 0x9e3779b9u) *sink = acc;   // practically never taken; keeps the loads live
+}
+}  // namespace
+}  // namespace tsdfs
+
+extern "C" int tsdfs_l2_read_probe(const void* buf, size_t bytes, int32_t reps, uint32_t* sink, float* ms_out,
+                                   tsdfs_stream_t stream) {
+    using namespace tsdfs;
+    if (!buf || !sink || !ms_out || bytes < 16 || reps < 1 || (reinterpret_cast<uintptr_t>(buf) & 15u) != 0)
+        return fail(TSDFS_E_INVALID, "tsdfs_l2_read_probe: buf (16-byte aligned), sink, ms_out, bytes >= 16, reps >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t n16 = (int64_t)(bytes / 16);
+    const uint4* b = static_cast<const uint4*>(buf);
+    // one pass to bring the buffer into L2, then the timed passes
+    k_l2_read<<<sms * 4, 512, 0, st>>>(b, n16, 1, sink);
+    int rc = cuda_check(cudaGetLastError(), "l2 probe launch");
+    if (rc) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    rc = cuda_check(cudaEventCreate(&e0), "l2 probe event");
+    if (!rc) rc = cuda_check(cudaEventCreate(&e1), "l2 probe event");
+    if (!rc) rc = cuda_check(cudaEventRecord(e0, st), "l2 probe record");
+    if (!rc) {
+        k_l2_read<<<sms * 4, 512, 0, st>>>(b, n16, reps, sink);
+        rc = cuda_check(cudaGetLastError(), "l2 probe launch");
+    }
+    if (!rc) rc = cuda_check(cudaEventRecord(e1, st), "l2 probe record");
+    if (!rc) rc = cuda_check(cudaEventSynchronize(e1), "l2 probe sync");
+    if (!rc) rc = cuda_check(cudaEventElapsedTime(ms_out, e0, e1), "l2 probe elapsed");
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return rc;
+}

@@ -45,6 +45,7 @@ constexpr int kPMaxBlocks = 5;        // 64-column operand blocks of the widest 
 constexpr uint32_t kPABytes = 64 * 1024;        // 128 rows x 256 16-bit columns
 constexpr uint32_t kPXMax = 128 * 64 * 2;       // the colour input beyond column 256 (<= 64 columns)
 constexpr uint32_t kPBarBytes = 256;
+constexpr int kPBatch = 4;            // 8-column groups an epilogue thread loads and computes together
 
 template <int MODE> struct PipeMode {
     static constexpr bool kF16 = MODE == TSDFS_PREC_F16;
@@ -140,12 +141,16 @@ __device__ __forceinline__ void tmem_wait_ld8(float (&d)[8]) {
                  :
                  : "memory");
 }
-// the low part of a split: x - bf16(x), rounded to bf16 (paired with pack2<false>(x))
-__device__ __forceinline__ uint32_t pack2_lo(float a, float b) {
-    const float ha = __bfloat162float(__float2bfloat16_rn(a));
-    const float hb = __bfloat162float(__float2bfloat16_rn(b));
-    __nv_bfloat162 h = __floats2bfloat162_rn(a - ha, b - hb);
-    return *reinterpret_cast<uint32_t*>(&h);
+__device__ __forceinline__ void tmem_wait_ld4(float (&d)[4]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3]) : : "memory");
+}
+// a split pair: hi = bf16(x), lo = bf16(x - hi), packed two columns at a time
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 template <int ARCH, int MODE>
@@ -336,6 +341,8 @@ __global__ void __launch_bounds__(PipeMode<MODE>::kThreads, 1) k_mlp_pipe(PipePa
         const uint32_t lq = (uint32_t)(32 * q) << 16, lq16 = (uint32_t)(32 * q + 16) << 16;
         const float half_beta = 0.5f * p.beta, inv_beta = 1.0f / p.beta;
         constexpr float kInvSqrt2 = 0.70710678118654752f;
+        const SoftplusH2 spk = softplus_h2_consts(half_beta, inv_beta);
+        const __half2 inv_sqrt2_h2 = __float2half2_rn(kInvSqrt2);
         const int et = threadIdx.x;
         uint32_t acc_uses[2] = {0, 0}, epi_ph = 0, lc = 0;
         bool ok = true;
@@ -358,11 +365,16 @@ __global__ void __launch_bounds__(PipeMode<MODE>::kThreads, 1) k_mlp_pipe(PipePa
         // a value / d-dx / d-dy / d-dz quadruple of 8-column groups: hi (and lo) operand parts
         auto store4 = [&](uint32_t ra_hi, uint32_t ra_lo, int c, const float (&v)[8], bool split) {
             const uint32_t co = (uint32_t)(c >> 3) * 128u;
-            stmatrix4(ra_hi + co, pack2<F16>(v[0], v[1]), pack2<F16>(v[2], v[3]), pack2<F16>(v[4], v[5]),
-                      pack2<F16>(v[6], v[7]));
-            if (split)
-                stmatrix4(ra_lo + co, pack2_lo(v[0], v[1]), pack2_lo(v[2], v[3]), pack2_lo(v[4], v[5]),
-                          pack2_lo(v[6], v[7]));
+            if (split) {
+                uint32_t hi[4], lo[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) split2(v[2 * j], v[2 * j + 1], hi[j], lo[j]);
+                stmatrix4(ra_hi + co, hi[0], hi[1], hi[2], hi[3]);
+                stmatrix4(ra_lo + co, lo[0], lo[1], lo[2], lo[3]);
+            } else {
+                stmatrix4(ra_hi + co, pack2<F16>(v[0], v[1]), pack2<F16>(v[2], v[3]), pack2<F16>(v[4], v[5]),
+                          pack2<F16>(v[6], v[7]));
+            }
         };
         // the tile's sample table: x~, direction, t, delta, then sin / cos of the encodings
         auto build_table = [&](int64_t tile) -> bool {
@@ -462,18 +474,45 @@ __global__ void __launch_bounds__(PipeMode<MODE>::kThreads, 1) k_mlp_pipe(PipePa
                     const float* sx = s_x + s * 8;
                     const float* sp = s_pe + s * A::kPeSdf * 6;
                     float part = 0.0f;   // dot product of the value row with the extra column's weights
-                    const int ng = Kn / 8;
-                    for (int b = 0; b * 8 < ng; ++b) {
-                        for (int g = 8 * b + ((pt - 8 * b) % kPParts + kPParts) % kPParts; g < 8 * b + 8 && g < ng;
-                             g += kPParts) {
-                            const int c = 8 * g;
-                            float d[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-                            if (c < ly.Np) {
-                                tmem_ld16x256_x1(th + lq + c, d);
-                                tmem_ld16x256_x1(th + lq16 + c, d + 4);
-                                tmem_wait_ld8(d);
+                    const int ng = Kn / 8, nblk = (ng + 7) / 8;
+                    const int n_full = ly.N / 8;   // groups wholly inside the layer's outputs
+                    // one group: value, d/dx, d/dy, d/dz of sample s at columns c + fc, c + fc + 1
+                    auto group = [&](int c, const float (&d)[8]) {
+                        float v[8];
+                        if (c + 8 <= ly.N) {
+                            const float2 bb = *reinterpret_cast<const float2*>(bias + c + fc);
+                            if constexpr (F16) {
+                                // FP16 operands: softplus, slope and tangent products in half2 (the
+                                // results are FP16 operands of the next layer either way)
+                                __half2 h, sg;
+                                softplus_slope_h2(d[0] + bb.x, d[1] + bb.y, spk, h, sg);
+                                if (dot) {
+                                    const float2 hf = __half22float2(h);
+                                    part = fmaf(hf.x, s_w255[c + fc], fmaf(hf.y, s_w255[c + fc + 1], part));
+                                }
+                                if (skip_next) {
+                                    sg = __hmul2(sg, inv_sqrt2_h2);
+                                    h = __hmul2(h, inv_sqrt2_h2);
+                                }
+                                const uint32_t co = (uint32_t)(c >> 3) * 128u;
+                                stmatrix4(ra_hi + co, h2u(h), h2u(__hmul2(sg, __floats2half2_rn(d[2], d[3]))),
+                                          h2u(__hmul2(sg, __floats2half2_rn(d[4], d[5]))),
+                                          h2u(__hmul2(sg, __floats2half2_rn(d[6], d[7]))));
+                                return;
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 2; ++e) {
+                                    float h, sg;
+                                    softplus_slope_tanh(d[e] + (e ? bb.y : bb.x), half_beta, inv_beta, h, sg);
+                                    if (dot) part = fmaf(h, s_w255[c + fc + e], part);
+                                    sg *= sc;
+                                    v[e] = h * sc;
+                                    v[2 + e] = sg * d[2 + e];
+                                    v[4 + e] = sg * d[4 + e];
+                                    v[6 + e] = sg * d[6 + e];
+                                }
                             }
-                            float v[8];
+                        } else {
 #pragma unroll
                             for (int e = 0; e < 2; ++e) {
                                 const int col = c + fc + e;
@@ -511,10 +550,39 @@ __global__ void __launch_bounds__(PipeMode<MODE>::kThreads, 1) k_mlp_pipe(PipePa
                                     v[6 + e] = ax == 2 ? der * sc : 0.0f;
                                 }
                             }
-                            store4(ra_hi, ra_lo, c, v, kSplit);
                         }
-                        block_done(b);
+                        store4(ra_hi, ra_lo, c, v, kSplit);
+                    };
+                    (void)n_full;
+                    // this part's groups g = pt, pt + 3, ... in batches of kPBatch: the batch's TMEM
+                    // loads are issued together and waited for once, then its groups are computed as
+                    // independent chains; each block is signalled once this part has no more groups in it
+                    int next_blk = 0;
+                    for (int g0 = pt; g0 < ng; g0 += kPBatch * kPParts) {
+                        float buf[kPBatch][8];
+#pragma unroll
+                        for (int i = 0; i < kPBatch; ++i) {
+                            const int c = 8 * (g0 + i * kPParts);
+                            if (c < 8 * ng && c < ly.Np) {
+                                tmem_ld16x256_x1(th + lq + c, buf[i]);
+                                tmem_ld16x256_x1(th + lq16 + c, buf[i] + 4);
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) buf[i][j] = 0.0f;
+                            }
+                        }
+#pragma unroll
+                        for (int i = 0; i < kPBatch; ++i) tmem_wait_ld8(buf[i]);
+#pragma unroll
+                        for (int i = 0; i < kPBatch; ++i) {
+                            const int g = g0 + i * kPParts;
+                            if (g < ng) group(8 * g, buf[i]);
+                        }
+                        const int gl = g0 + kPBatch * kPParts;
+                        const int b_next = gl < ng ? gl / 8 : nblk;
+                        for (; next_blk < b_next; ++next_blk) block_done(next_blk);
                     }
+                    for (; next_blk < nblk; ++next_blk) block_done(next_blk);
                     if (dot) {
                         part += __shfl_xor_sync(0xffffffffu, part, 1);
                         part += __shfl_xor_sync(0xffffffffu, part, 2);
@@ -572,21 +640,29 @@ __global__ void __launch_bounds__(PipeMode<MODE>::kThreads, 1) k_mlp_pipe(PipePa
                     const uint32_t rv_x = smem_u32(X) + a_off(32 * q + (lane & 7), 0, TA::kPitchX > 0 ? TA::kPitchX : 8);
                     for (int b = 0; b * 8 < ncg; ++b) {
                         const int g0 = b * 8 < kD / 8 ? kD / 8 : b * 8;
-                        for (int cg = g0 + ((pt - g0) % kPParts + kPParts) % kPParts; cg < 8 * b + 8 && cg < ncg;
-                             cg += kPParts) {
+                        const int gf = g0 + ((pt - g0) % kPParts + kPParts) % kPParts;
+                        float d[3][4];
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            const int cg = gf + i * kPParts;
                             const int oc = 8 * (cg - kD / 8);   // first output column of the group
-                            float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-                            if (oc < TA::kOutMma) {
-                                tmem_ld16x256_x1(th + lq + oc, d);
-                                tmem_wait_ld();
-                            }
+                            if (cg < 8 * b + 8 && cg < ncg && oc < TA::kOutMma) tmem_ld16x256_x1(th + lq + oc, d[i]);
+                            else d[i][0] = d[i][1] = d[i][2] = d[i][3] = 0.0f;
+                        }
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) tmem_wait_ld4(d[i]);
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            const int cg = gf + i * kPParts;
+                            if (cg >= 8 * b + 8 || cg >= ncg) continue;
+                            const int oc = 8 * (cg - kD / 8);
                             float o[2];
 #pragma unroll
                             for (int e = 0; e < 2; ++e) {
                                 const int col = oc + fc + e;
                                 float val = 0.0f;
                                 if (col == 0) val = s_out[s * 8 + 7];
-                                else if (col < TA::kOutMma && col < ly.N) val = d[e] + bias[col];
+                                else if (col < TA::kOutMma && col < ly.N) val = d[i][e] + bias[col];
                                 else if (col < ly.N)
                                     val = s_f255[s] + s_f255[kPTile + s] + s_f255[2 * kPTile + s] + bias[col];
                                 o[e] = val;
@@ -605,19 +681,27 @@ __global__ void __launch_bounds__(PipeMode<MODE>::kThreads, 1) k_mlp_pipe(PipePa
                     const uint32_t rv = smem_u32(A_hi) + a_off(32 * q + (lane & 7), 0, Kn);
                     const int ng = Kn / 8;
                     for (int b = 0; b * 8 < ng; ++b) {
-                        for (int g = 8 * b + ((pt - 8 * b) % kPParts + kPParts) % kPParts; g < 8 * b + 8 && g < ng;
-                             g += kPParts) {
+                        // this part's (at most three) groups of the block: loads together, one wait
+                        const int gf = 8 * b + ((pt - 8 * b) % kPParts + kPParts) % kPParts;
+                        float d[3][4];
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            const int c = 8 * (gf + i * kPParts);
+                            if (c < 8 * (8 * b + 8) && c < 8 * ng && c < ly.Np) tmem_ld16x256_x1(th + lq + c, d[i]);
+                            else d[i][0] = d[i][1] = d[i][2] = d[i][3] = 0.0f;
+                        }
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) tmem_wait_ld4(d[i]);
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            const int g = gf + i * kPParts;
+                            if (g >= 8 * b + 8 || g >= ng) continue;
                             const int c = 8 * g;
-                            float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-                            if (c < ly.Np) {
-                                tmem_ld16x256_x1(th + lq + c, d);
-                                tmem_wait_ld();
-                            }
                             float o[2];
 #pragma unroll
                             for (int e = 0; e < 2; ++e) {
                                 const int col = c + fc + e;
-                                o[e] = col < ly.N ? fmaxf(d[e] + bias[col], 0.0f) : 0.0f;
+                                o[e] = col < ly.N ? fmaxf(d[i][e] + bias[col], 0.0f) : 0.0f;
                             }
                             stmatrix1(rv + (uint32_t)(c >> 3) * 128u, pack2<F16>(o[0], o[1]));
                         }

@@ -41,7 +41,7 @@ EXPORTS = ["tsdfs_last_error", "tsdfs_sync_status", "tsdfs_grid_init", "tsdf_int
            "tsdf_adaptive_counts", "tsdfs_hier_bounded_workspace_size", "render_rays_hier_bounded",
            "tsdfs_autotune_bounds", "tsdfs_set_bounds_launch_shape", "tsdfs_bounds_launch_shape",
            "tsdfs_set_network_kernel", "tsdfs_network_kernel", "tsdfs_set_test_limits",
-           "tsdfs_loss_f64_workspace_size", "tsdfs_loss_f64", "tsdfs_autotune_network",
+           "tsdfs_loss_f64_workspace_size", "tsdfs_loss_f64", "tsdfs_autotune_network", "tsdfs_l2_read_probe",
            "tsdfs_raycast_workspace_size", "tsdf_integrate_raycast", "tsdfs_profile", "tsdfs_profile_read"]
 
 
@@ -281,6 +281,16 @@ def tsdfs_loss_f64(mlp: "Mlp", sdf_w64, rgb_w64, ray_o, ray_d, t_n, t_f, offsets
     _check(lib().tsdfs_loss_f64(C.byref(mlp.c), _p(sdf_w64), _p(rgb_w64), _p(ray_o), _p(ray_d), _p(t_n), _p(t_f),
                                 _p(offsets), _p(status), C.c_int64(n), C.c_int64(max_samples), _p(g_rgb), _p(g_depth),
                                 _p(g_eik), _p(loss), _p(workspace), C.c_size_t(workspace.numel()), _stream()))
+
+
+def tsdfs_l2_read_probe(buf, reps=20):
+    """Milliseconds of `reps` streaming reads of the device tensor `buf` (kept in L2);
+    returns the achieved read bandwidth in GB/s."""
+    sink = torch.zeros(1, dtype=torch.int32, device=buf.device)
+    ms = C.c_float(0.0)
+    nbytes = buf.numel() * buf.element_size()
+    _check(lib().tsdfs_l2_read_probe(_p(buf), C.c_size_t(nbytes), C.c_int32(reps), _p(sink), C.byref(ms), _stream()))
+    return reps * nbytes / (ms.value / 1e3) / 1e9
 
 
 def tsdfs_set_test_limits(spin_limit=0, march_step_cap=0, withhold_chunk=-1):
