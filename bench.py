@@ -42,13 +42,13 @@ WORKLOADS = {
 }
 WORKLOAD = WORKLOADS["view"]
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of k_mlp_tc per launch, the mean
-# over the 10 timed launches of `bench.py --steps 10 --warmup 3 --only-main` (room views 0-9,
+# over the 10 timed launches of `bench.py --only-main --no-graph --steps 10 --warmup 3` (room views 0-9,
 # network-fused grid, fp16 operands) in one ncu capture; reported only for that
 # configuration and while the kernel sources hash to the ones it was captured on
-MLP_TC_TRAFFIC = {"sha256": "ba0400f966c61f635448f92c6329d13ccd2215e34715a1c36e3c19373196f2c8", "bytes_per_launch": 257857075,
+MLP_TC_TRAFFIC = {"sha256": "5c9043b2f7abb29d29ca08f66732164be1cad39ce2a166e79c29e97af14a4eb3", "bytes_per_launch": 257188688,
                   "profile": "profiles/k_mlp_tc_room_view_traffic.md"}
 # the same for k_ray_bounds (the march of Alg. 1) on the same ten timed views
-MARCH_TRAFFIC = {"sha256": "b0949ace8b80982bc36c712a3e070b510fd14704b852a0badbb755be355d62a2", "bytes_per_launch": 9985254,
+MARCH_TRAFFIC = {"sha256": "c4307e3a56049f67dc00d5274645fbd858f05161b8c533815f880fbb3a07392b", "bytes_per_launch": 9989350,
                  "profile": "profiles/k_ray_bounds_room_view_traffic.md"}
 ALGO_FLOP_PER_SAMPLE = 2.25e6   # SDF fwd + minimal reverse-mode grad + colour, 8x256 / 4x256 networks
 # what the tensor-core kernels issue per sample (value + 3 tangent rows through the SDF layers):
@@ -227,7 +227,7 @@ def captured_traffic(t, files, args, prec):
     configuration or the kernel has changed since."""
     same_run = (args.workload == "view" and args.grid_source == "network" and args.fusion == "projective"
                 and prec == "f16" and args.steps % N_VIEWS_TIMED == 0 and not args.rays
-                and args.recovery_tau is None and not args.graph)
+                and args.recovery_tau is None)
     if not same_run or t["bytes_per_launch"] is None or t["sha256"] != source_hash(files):
         return None
     return t["bytes_per_launch"]
@@ -516,7 +516,8 @@ def run_ours(args, ws, rank, local):
     achieved = ALGO_FLOP_PER_SAMPLE * samples_timed / (ms_k.value / 1e3) / 1e12 if ms_k.value > 0 else 0.0
     if prec != "f32":
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_burst, "unit": "TFLOP/s",
-                "frac": achieved / bf16_burst, "traffic": captured_traffic(MLP_TC_TRAFFIC, MLP_TC_SOURCES, args, prec),
+                "frac": achieved / bf16_burst,
+                "traffic": captured_traffic(MLP_TC_TRAFFIC, MLP_TC_SOURCES, args, prec) if mlp_name == "mlp_tc" else None,
                 "peak_kind": f"bf16 dense burst ({peak_src}); fp16 dense has the same nominal rate",
                 "kernel": mlp_name,
                 "executed_tflops": achieved * EXEC_FLOP_PER_SAMPLE[

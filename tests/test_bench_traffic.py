@@ -29,7 +29,9 @@ def test_traffic_null_for_other_configurations():
     t = {"sha256": bench.source_hash(bench.MARCH_SOURCES), "bytes_per_launch": 7}
     for kw, prec in [({"workload": "panorama"}, "f16"), ({"grid_source": "analytic"}, "f16"), ({}, "bf16"),
                      ({"steps": 3}, "f16"), ({"rays": 65536}, "f16"), ({"recovery_tau": 0.95}, "f16"),
-                     ({"fusion": "raycast"}, "f16"), ({"graph": True}, "f16")]:
+                     ({"fusion": "raycast"}, "f16")]:
         assert bench.captured_traffic(t, bench.MARCH_SOURCES, args(**kw), prec) is None, kw
     assert bench.captured_traffic(t, bench.MARCH_SOURCES, args(), "f16") == 7
+    # graph replay launches the same kernels as the eager steps the capture timed
+    assert bench.captured_traffic(t, bench.MARCH_SOURCES, args(graph=True), "f16") == 7
 
