@@ -558,8 +558,16 @@ def run_ours(args, ws, rank, local):
     elif hier_r is not None:
         comparator = time_hier_only(hier_r, grid, rays, bp, n, flush)
     del hier_r
-    train = run_train(spec, wl, grid, mask, dev, n_rays=65536 if args.workload == "large" else 8192) \
-        if (rank == 0 and not lean) else None
+    train = None
+    if rank == 0 and not lean:
+        from paper_2311_17878_gb300 import tsdfs as T
+        large = args.workload == "large"
+        train = run_train(spec, wl, grid, mask, dev, n_rays=65536 if large else 8192, peak_bf16=bf16_burst)
+        if not large:
+            # the FP32 SIMT backward on the same step, and the layer-major one at 65 536 rays
+            train["simt_backward"] = run_train(spec, wl, grid, mask, dev, n_rays=8192, iters=2,
+                                               kind=T.TSDFS_BACKWARD_SIMT)
+            train["rays_65536"] = run_train(spec, wl, grid, mask, dev, n_rays=65536, iters=3, peak_bf16=bf16_burst)
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -711,13 +719,28 @@ def march_roofline(spec, o, d, t_f, status, bp, ms_per_launch, hbm, peak_src, l2
     return out
 
 
-def run_train(spec, wl, grid, mask, dev, n_rays=8192, iters=5):
-    """One training step of the networks (FP32): 8192 random rays of the training
+def backward_gemm_flops(spec):
+    """Algorithmic FLOPs per sample of the layer-major backward's GEMMs: the forward
+    recomputation P = X W^T (value + 3 tangent rows per sample in the SDF network), the
+    weight gradients G^T X (as many FLOPs) and the input adjoints G W (all layers but
+    the SDF network's first)."""
+    sdf = 4 * sum(2 * W.shape[0] * W.shape[1] for W, _ in spec.sdf)
+    rgb = sum(2 * W.shape[0] * W.shape[1] for W, _ in spec.rgb)
+    fwd = sdf + rgb
+    first = 4 * 2 * spec.sdf[0][0].size
+    return {"forward": fwd, "weight_grad": fwd, "input_adjoint": fwd - first}
+
+
+def run_train(spec, wl, grid, mask, dev, n_rays=8192, iters=5, kind=None, peak_bf16=None):
+    """One training step of the networks (FP32): n_rays random rays of the training
     views, bounds, render through the autograd op, L1 colour + 0.1 eikonal on the
-    bounded samples, backward (render_rays_backward)."""
+    bounded samples, backward (render_rays_backward with the given implementation)."""
     import torch
     from paper_2311_17878_gb300 import synth
     from paper_2311_17878_gb300 import tsdfs as T
+    kind = T.TSDFS_BACKWARD_GEMM if kind is None else kind
+    old_kind = T.tsdfs_backward_kernel()
+    T.tsdfs_set_backward_kernel(kind)
     mlp = T.Mlp(spec, T.TSDFS_PREC_F32, device=dev)
     o, d, vi, px, py = synth.random_rays_from_views(wl.views, n_rays)
     o, d = torch.tensor(o, device=dev), torch.tensor(d, device=dev)
@@ -737,27 +760,53 @@ def run_train(spec, wl, grid, mask, dev, n_rays=8192, iters=5):
         loss.backward()
         return loss
 
-    for _ in range(2):
-        step()
-    torch.cuda.synchronize()
-    import ctypes as C
-    T.lib().tsdfs_profile(1)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(iters):
-        loss = step()
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / iters
-    split = {}
-    for name in ("mlp_simt", "composite", "backward", "ray_bounds"):
-        t, c = C.c_double(0), C.c_int64(0)
-        T.lib().tsdfs_profile_read(name.encode(), C.byref(t), C.byref(c))
-        split[name + "_ms"] = t.value / iters
-    T.lib().tsdfs_profile(0)
-    return {"rays": n_rays, "ms_per_step": ms, "rays_per_s": n_rays / (ms / 1e3),
-            "samples": int(b.offsets[-1].item()), "loss": float(loss.item()), "kernel_ms": split,
-            "what": "bounds + render (fp32) + L1 + 0.1 eikonal + backward through both networks"}
+    try:
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        import ctypes as C
+        T.lib().tsdfs_profile(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(iters):
+            loss = step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / iters
+        split = {}
+        for name in ("mlp_simt", "composite", "backward", "backward_forward", "backward_composite",
+                     "backward_network", "ray_bounds"):
+            t, c = C.c_double(0), C.c_int64(0)
+            T.lib().tsdfs_profile_read(name.encode(), C.byref(t), C.byref(c))
+            if c.value:
+                split[name + "_ms"] = t.value / iters
+        T.lib().tsdfs_profile(0)
+    finally:
+        T.tsdfs_set_backward_kernel(old_kind)
+    samples = int(b.offsets[-1].item())
+    out = {"rays": n_rays, "ms_per_step": ms, "rays_per_s": n_rays / (ms / 1e3), "samples": samples,
+           "loss": float(loss.item()), "kernel_ms": split,
+           "backward": "layer-major GEMMs (cuBLAS BF16x9-emulated FP32 on the tensor cores)"
+           if kind == T.TSDFS_BACKWARD_GEMM else "FP32 SIMT, tiles of 8 samples",
+           "what": "bounds + render (fp32) + L1 + 0.1 eikonal + backward through both networks"}
+    if kind == T.TSDFS_BACKWARD_GEMM and "backward_ms" in split:
+        f = backward_gemm_flops(spec)
+        chunk = T.tsdfs_backward_chunk_samples(mlp, ms_cap)
+        passes = 1 if samples <= chunk else 2   # more than one chunk recomputes the forward
+        flops = samples * (f["forward"] * passes + f["weight_grad"] + f["input_adjoint"])
+        t_net = split.get("backward_forward_ms", 0.0) + split.get("backward_network_ms", 0.0)
+        ach = flops / (t_net / 1e3) / 1e12 if t_net > 0 else None
+        peak = peak_bf16 / 9.0 if peak_bf16 else None
+        out["roofline"] = {"bound": "tensor", "achieved": ach, "unit": "TFLOP/s",
+                           "peak": peak, "frac": (ach / peak) if (ach and peak) else None,
+                           "flops_per_sample": f, "chunk_samples": chunk, "forward_passes": passes,
+                           "workspace_bytes": T.tsdfs_backward_workspace_size(mlp, n_rays, ms_cap),
+                           "what": "GEMM FLOPs (forward recomputation, weight gradients, input adjoints) over the "
+                                   "time of the backward's forward and network phases (element-wise kernels and "
+                                   "bias GEMVs included)",
+                           "peak_kind": "measured bf16 dense peak / 9 (each FP32 operand as three BF16 parts, nine "
+                                        "products per FP32 product)"}
+    return out
 
 
 def run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev, flush):

@@ -417,12 +417,41 @@ int render_rays_hier_bounded(const tsdfs_mlp* mlp, const float* ray_o, const flo
  * packed fp32 parameters, ACCUMULATED (+=) into d_sdf_w / d_rgb_w (layout of
  * sdf_w / rgb_w; the caller zeroes them).  This includes the second-order
  * terms through grad f (opacity, colour-network normal, eikonal).  d_rgb:
- * [n_rays][3]; d_depth, d_eik: [n_rays] or NULL (zero).  Activations are
- * recomputed per tile of samples, never stored per batch: the workspace is
- * the per-sample records plus a fixed per-SM scratch (activations of one tile
- * and a private gradient copy per block), independent of the batch beyond
- * max_samples.  FP32 networks only (mlp->precision is ignored).
- * workspace >= tsdfs_backward_workspace_size.                                */
+ * [n_rays][3]; d_depth, d_eik: [n_rays] or NULL (zero).  FP32 parameters and
+ * arithmetic (mlp->precision is ignored).  Two implementations, chosen
+ * process-wide by tsdfs_set_backward_kernel:
+ *  - TSDFS_BACKWARD_GEMM (default): layer-major.  Each layer of both networks
+ *    is a GEMM over a chunk of samples (4 rows per sample for the SDF
+ *    network: the value and its three x-derivative rows) on the tensor cores,
+ *    FP32 operands emulated by three BF16 parts (cuBLAS BF16x9, FP32
+ *    accumulation); the element-wise steps are the library's kernels.  The
+ *    call reads the sample total offsets[n_rays] from the device first (one
+ *    synchronisation of `stream`).  The workspace holds the per-sample records
+ *    and the activations of one chunk (tsdfs_set_backward_chunk; by default as
+ *    many samples as fit 16 GiB, at most max_samples); a batch larger than one
+ *    chunk recomputes each chunk's activations once more.  The first call on
+ *    a device creates the library's cuBLAS handle (cuBLAS allocates its own
+ *    state then); the GEMMs' workspace is taken from `workspace`.
+ *  - TSDFS_BACKWARD_SIMT: FP32 SIMT; activations recomputed per tile of 8
+ *    samples; the workspace is the per-sample records plus a per-SM scratch
+ *    and a private gradient copy per block.  Fully asynchronous.
+ * workspace >= tsdfs_backward_workspace_size, which sizes it for the current
+ * choice of implementation and chunk.                                       */
+#define TSDFS_BACKWARD_SIMT 1
+#define TSDFS_BACKWARD_GEMM 2
+/* Choose the implementation of render_rays_backward (process-wide).  Returns 0
+ * or TSDFS_E_INVALID.  tsdfs_backward_kernel returns the current choice.     */
+int tsdfs_set_backward_kernel(int32_t kind);
+int32_t tsdfs_backward_kernel(void);
+/* Samples per chunk of the layer-major backward (0: as many as fit 16 GiB of
+ * activations).  Smaller chunks need less workspace and recompute the
+ * forward once more.  Returns 0 or TSDFS_E_INVALID (negative, or 2^29
+ * samples or more).                                                         */
+int tsdfs_set_backward_chunk(int64_t samples);
+/* Samples per chunk the layer-major backward uses for this network and
+ * max_samples (>= 1) under the current chunk setting; a batch of more samples
+ * runs in several chunks.  Returns the count or TSDFS_E_INVALID.            */
+int64_t tsdfs_backward_chunk_samples(const tsdfs_mlp* mlp, int64_t max_samples);
 size_t tsdfs_backward_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays, int64_t max_samples);
 int render_rays_backward(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
                          const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,

@@ -22,7 +22,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libtsdfs.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["abi.cu", "integrate.cu", "bounds.cu", "mlp_simt.cu", "composite.cu", "mlp_tc.cu", "mlp_pipe.cu", "backward.cu", "fd64.cu"]
+SOURCES = ["abi.cu", "integrate.cu", "bounds.cu", "mlp_simt.cu", "composite.cu", "mlp_tc.cu", "mlp_pipe.cu", "backward.cu", "backward_gemm.cu", "fd64.cu"]
 EXACT = {"integrate.cu", "bounds.cu"}
 
 
@@ -68,7 +68,7 @@ def build(force=False, verbose=False, extra=()) -> str:
                 print(err, file=sys.stderr)
     if force or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcuda", "-lcublas"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -46,6 +46,7 @@ using CtxGetIdFn = int (*)(void*, unsigned long long*);
 std::once_flag g_ctx_fn_once;
 CtxGetCurrentFn g_ctx_get_current = nullptr;
 CtxGetIdFn g_ctx_get_id = nullptr;
+}  // namespace
 
 // id of the current context of the calling thread; 0 when there is none yet or the
 // driver lacks the query (the cache then keys on the device alone)
@@ -69,7 +70,6 @@ unsigned long long current_context_id() {
     if (g_ctx_get_id(ctx, &id) != 0) return 0;
     return id;
 }
-}  // namespace
 
 int symbol_address(SymbolCache& cache, const void* symbol, void** out, const char* what) {
     int dev = 0;

@@ -1,17 +1,23 @@
 // Backward of render_rays: parameter gradients of
 //   L = sum_r d_rgb_r . rgb_r + d_depth_r depth_r + d_eik_r eik_r.
 //
-// 1. the forward network kernel recomputes the per-sample records;
+// Two paths share the first two steps:
+// 1. a forward network pass recomputes the per-sample records;
 // 2. k_comp_bwd (one thread per ray) differentiates the compositing of Eq. 1,
 //    Eq. 2 and the NeuS opacity, and adds the eikonal term: per-sample adjoints
-//    of f, grad f and the colour;
+//    of f, grad f and the colour.
+// The layer-major path (backward_gemm.cu, the default) then runs each layer of
+// both networks as GEMMs over a chunk of samples on the tensor cores.  The SIMT
+// path of this file:
 // 3. k_mlp_bwd (FP32 SIMT, tiles of kTB samples) recomputes both networks with
 //    their forward-mode tangent rows into a per-block scratch, then
 //    back-propagates values and tangents (the slope sigma(beta z) of a hidden
 //    layer is differentiated too: d slope / dz = beta sigma (1 - sigma)), and
 //    accumulates parameter gradients into a private copy per block;
 // 4. k_reduce_grads adds the private copies into the caller's gradients.
-#include "common.cuh"
+#include <atomic>
+
+#include "backward.cuh"
 
 namespace tsdfs {
 
@@ -26,12 +32,6 @@ constexpr int kTB = 8;                // samples per tile
 constexpr int kRows = 4 * kTB;        // SDF rows (value + 3 tangents per sample)
 constexpr int kLD = 292;              // row stride of the shared buffers (>= 289 + pad)
 constexpr int kKC = 16;
-
-// per-sample adjoints produced by the compositing backward
-struct __align__(16) SampleAdj {
-    float gf, ggx, ggy, ggz;
-    float gr, gg, gb, pad;
-};
 
 __device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + expf(-x)); }
 
@@ -552,14 +552,52 @@ BwdWs bwd_layout(void* base, int arch, int64_t max_samples, int blocks) {
     return w;
 }
 
+std::atomic<int> g_bwd_kind{TSDFS_BACKWARD_GEMM};
+std::atomic<int64_t> g_bwd_chunk{0};
+
 }  // namespace
+
+int launch_comp_bwd(const SampleRec* rec, const int32_t* offsets, const uint8_t* status, const float* ray_d,
+                    int64_t n_rays, const tsdfs_mlp* mlp, const float* d_rgb, const float* d_depth,
+                    const float* d_eik, SampleAdj* adj, cudaStream_t st) {
+    k_comp_bwd<<<grid_1d(n_rays, 128), 128, 0, st>>>(rec, offsets, status, ray_d, n_rays,
+                                                     Opacity{mlp->opacity, mlp->inv_s, mlp->alpha_eps}, d_rgb, d_depth,
+                                                     d_eik, adj);
+    return cuda_check(cudaGetLastError(), "backward composite launch");
+}
+
+int64_t backward_chunk_setting() { return g_bwd_chunk.load(); }
+
 }  // namespace tsdfs
 
 using namespace tsdfs;
 
+extern "C" int tsdfs_set_backward_kernel(int32_t kind) {
+    if (kind != TSDFS_BACKWARD_SIMT && kind != TSDFS_BACKWARD_GEMM) return fail(TSDFS_E_INVALID, "unknown backward kind %d", kind);
+    g_bwd_kind.store(kind);
+    return TSDFS_OK;
+}
+
+extern "C" int32_t tsdfs_backward_kernel(void) { return g_bwd_kind.load(); }
+
+extern "C" int tsdfs_set_backward_chunk(int64_t samples) {
+    if (samples < 0 || samples > (int64_t)INT32_MAX / 4) return fail(TSDFS_E_INVALID, "backward chunk %lld out of range",
+                                                                    (long long)samples);
+    g_bwd_chunk.store(samples);
+    return TSDFS_OK;
+}
+
+extern "C" int64_t tsdfs_backward_chunk_samples(const tsdfs_mlp* mlp, int64_t max_samples) {
+    if (!mlp || max_samples < 1) return fail(TSDFS_E_INVALID, "mlp is NULL or max_samples < 1");
+    if (mlp->arch != TSDFS_ARCH_TINY && mlp->arch != TSDFS_ARCH_ROOM) return fail(TSDFS_E_INVALID, "unknown arch %d", mlp->arch);
+    return gemm_backward_chunk(mlp, max_samples);
+}
+
 extern "C" size_t tsdfs_backward_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays, int64_t max_samples) {
     (void)n_rays;
     if (!mlp || max_samples < 0) return 0;
+    if (mlp->arch != TSDFS_ARCH_TINY && mlp->arch != TSDFS_ARCH_ROOM) return 0;
+    if (g_bwd_kind.load() == TSDFS_BACKWARD_GEMM) return gemm_backward_workspace(mlp, max_samples);
     return bwd_layout(nullptr, mlp->arch, max_samples, bwd_blocks()).bytes + 256;
 }
 
@@ -578,6 +616,11 @@ extern "C" int render_rays_backward(const tsdfs_mlp* mlp, const float* ray_o, co
     if (!ray_o || !ray_d || !t_n || !t_f || !offsets || !status || !d_rgb || !d_sdf_w || !d_rgb_w)
         return fail(TSDFS_E_INVALID, "ray, bound, d_rgb and gradient pointers must be non-NULL");
     if (max_samples > (int64_t)INT32_MAX) return fail(TSDFS_E_INVALID, "max_samples must fit int32 offsets");
+    if (g_bwd_kind.load() == TSDFS_BACKWARD_GEMM) {
+        if (max_samples == 0) return TSDFS_OK;
+        return gemm_backward(mlp, ray_o, ray_d, t_n, t_f, offsets, status, n_rays, max_samples, d_rgb, d_depth, d_eik,
+                             d_sdf_w, d_rgb_w, ws, ws_bytes, (cudaStream_t)stream);
+    }
     const int blocks = bwd_blocks();
     BwdWs w = bwd_layout(ws, mlp->arch, max_samples, blocks);
     if (!ws || ws_bytes < w.bytes) return fail(TSDFS_E_WORKSPACE, "backward workspace too small");
@@ -604,9 +647,7 @@ extern "C" int render_rays_backward(const tsdfs_mlp* mlp, const float* ray_o, co
     int rc = mlp->arch == TSDFS_ARCH_TINY ? launch_mlp_full_simt<TSDFS_ARCH_TINY>(np, src, w.rec, max_samples, st)
                                           : launch_mlp_full_simt<TSDFS_ARCH_ROOM>(np, src, w.rec, max_samples, st);
     if (rc) return rc;
-    k_comp_bwd<<<grid_1d(n_rays, 128), 128, 0, st>>>(w.rec, offsets, status, ray_d, n_rays, Opacity{mlp->opacity, mlp->inv_s, mlp->alpha_eps},
-                                                     d_rgb, d_depth, d_eik, w.adj);
-    rc = cuda_check(cudaGetLastError(), "backward composite launch");
+    rc = launch_comp_bwd(w.rec, offsets, status, ray_d, n_rays, mlp, d_rgb, d_depth, d_eik, w.adj, st);
     if (rc) return rc;
     const int64_t gf = mlp->arch == TSDFS_ARCH_TINY ? sdf_param_count<TSDFS_ARCH_TINY>() + rgb_param_count<TSDFS_ARCH_TINY>()
                                                     : sdf_param_count<TSDFS_ARCH_ROOM>() + rgb_param_count<TSDFS_ARCH_ROOM>();

@@ -29,6 +29,7 @@ TSDFS_MISS, TSDFS_BOUNDED, TSDFS_FALLBACK = 0, 1, 2
 TSDFS_ARCH_TINY, TSDFS_ARCH_ROOM = 0, 1
 TSDFS_PREC_F32, TSDFS_PREC_BF16, TSDFS_PREC_F16, TSDFS_PREC_BF16X2 = 0, 1, 2, 3
 TSDFS_NETKERNEL_SERIAL, TSDFS_NETKERNEL_PIPELINED = 1, 2
+TSDFS_BACKWARD_SIMT, TSDFS_BACKWARD_GEMM = 1, 2
 TSDFS_OPACITY_NEUS, TSDFS_OPACITY_VOLSDF = 0, 1
 TSDFS_DEV_SAMPLES_OVERFLOW, TSDFS_DEV_MARCH_CAP, TSDFS_DEV_TIMEOUT, TSDFS_DEV_NONFINITE = 1, 2, 4, 8
 
@@ -42,7 +43,9 @@ EXPORTS = ["tsdfs_last_error", "tsdfs_sync_status", "tsdfs_grid_init", "tsdf_int
            "tsdfs_autotune_bounds", "tsdfs_set_bounds_launch_shape", "tsdfs_bounds_launch_shape",
            "tsdfs_set_network_kernel", "tsdfs_network_kernel", "tsdfs_set_test_limits",
            "tsdfs_loss_f64_workspace_size", "tsdfs_loss_f64", "tsdfs_autotune_network", "tsdfs_l2_read_probe",
-           "tsdfs_raycast_workspace_size", "tsdf_integrate_raycast", "tsdfs_profile", "tsdfs_profile_read"]
+           "tsdfs_raycast_workspace_size", "tsdf_integrate_raycast", "tsdfs_profile", "tsdfs_profile_read",
+           "tsdfs_set_backward_kernel", "tsdfs_backward_kernel", "tsdfs_set_backward_chunk",
+           "tsdfs_backward_chunk_samples"]
 
 
 class TsdfsError(RuntimeError):
@@ -81,7 +84,8 @@ def lib():
                          "tsdfs_hier_bounded_workspace_size", "tsdfs_raycast_workspace_size",
                          "tsdfs_loss_f64_workspace_size"]:
                 getattr(L, name).restype = C.c_size_t
-            for name in ["tsdfs_inside_mask_words", "tsdfs_sdf_param_count", "tsdfs_rgb_param_count"]:
+            for name in ["tsdfs_inside_mask_words", "tsdfs_sdf_param_count", "tsdfs_rgb_param_count",
+                         "tsdfs_backward_chunk_samples"]:
                 getattr(L, name).restype = C.c_int64
             L.tsdfs_bounds_workspace_size.argtypes = [C.c_int64]
             L.tsdfs_render_workspace_size.argtypes = [C.c_void_p, C.c_int64, C.c_int64]
@@ -267,6 +271,26 @@ def tsdfs_set_bounds_launch_shape(block=0, blocks_per_sm=0):
 def tsdfs_set_network_kernel(precision, kernel):
     """Process-wide choice of the tensor-core network kernel for a 16-bit precision."""
     _check(lib().tsdfs_set_network_kernel(C.c_int32(precision), C.c_int32(kernel)))
+
+
+def tsdfs_set_backward_kernel(kind):
+    """Process-wide choice of render_rays_backward's implementation (TSDFS_BACKWARD_*)."""
+    _check(lib().tsdfs_set_backward_kernel(C.c_int32(kind)))
+
+
+def tsdfs_backward_kernel() -> int:
+    return int(lib().tsdfs_backward_kernel())
+
+
+def tsdfs_set_backward_chunk(samples=0):
+    """Samples per chunk of the layer-major backward (0: the default, 16 GiB of activations)."""
+    _check(lib().tsdfs_set_backward_chunk(C.c_int64(samples)))
+
+
+def tsdfs_backward_chunk_samples(mlp: "Mlp", max_samples) -> int:
+    rc = int(lib().tsdfs_backward_chunk_samples(C.byref(mlp.c), C.c_int64(max_samples)))
+    _check(min(rc, 0))
+    return rc
 
 
 def tsdfs_loss_f64_workspace_size(n_rays, max_samples) -> int:

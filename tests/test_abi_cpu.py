@@ -154,6 +154,35 @@ def test_network_kernel_choice(L):
         assert L.tsdfs_set_network_kernel(prec, old) == 0
 
 
+def test_backward_kernel_choice_and_workspace(L):
+    """The layer-major backward is the default; the workspace follows the choice and the
+    chunk (records of every sample plus the activations of one chunk)."""
+    assert L.tsdfs_backward_kernel() == T.TSDFS_BACKWARD_GEMM
+    assert L.tsdfs_set_backward_kernel(0) < 0 and L.tsdfs_set_backward_kernel(3) < 0
+    assert L.tsdfs_set_backward_chunk(C.c_int64(-1)) < 0 and L.tsdfs_set_backward_chunk(C.c_int64(1 << 29)) < 0
+    mlp = T.Mlp(synth.room_mlp(), device="cpu")
+    size = lambda ms: T.tsdfs_backward_workspace_size(mlp, 1000, ms)
+    try:
+        big = size(200000)
+        assert T.tsdfs_backward_chunk_samples(mlp, 200000) > 150000
+        assert L.tsdfs_set_backward_chunk(C.c_int64(1000)) == 0
+        assert T.tsdfs_backward_chunk_samples(mlp, 200000) == 1000
+        assert T.tsdfs_backward_chunk_samples(mlp, 10) == 10
+        small = size(200000)
+        assert small < big
+        # room: 4 SDF rows of every layer's padded input and output, the colour rows and
+        # two work buffers make about 79 KB per sample of a chunk; records 80 B per sample
+        per_sample = (small - size(1) - 199999 * 80) / 999
+        assert 75e3 < per_sample < 85e3, per_sample
+        assert size(500) < small
+        assert L.tsdfs_set_backward_kernel(T.TSDFS_BACKWARD_SIMT) == 0
+        assert L.tsdfs_backward_kernel() == T.TSDFS_BACKWARD_SIMT
+        assert size(200000) != small
+    finally:
+        L.tsdfs_set_backward_chunk(C.c_int64(0))
+        L.tsdfs_set_backward_kernel(T.TSDFS_BACKWARD_GEMM)
+
+
 def test_bounds_launch_shape_arguments(L):
     for b, sm in [(16, 8), (96 + 1, 8), (512, 8), (128, 0), (128, 2000)]:
         assert L.tsdfs_set_bounds_launch_shape(C.c_int32(b), C.c_int32(sm)) == T.TSDFS_E_INVALID

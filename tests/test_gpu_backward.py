@@ -60,31 +60,132 @@ def oracle_grads(spec, o, d, b, d_rgb, d_depth, d_eik):
     return sdf, rgb
 
 
-@pytest.mark.parametrize("scene,n_rays", [("tiny", 96), ("room", 48)])
-def test_backward_matches_oracle_gradient(scene, n_rays):
-    o, d, b = case(scene, n_rays, seed=41)
-    spec = synth.scene_mlp(scene)
-    rng = np.random.default_rng(7)
-    d_rgb = rng.normal(0, 1, (n_rays, 3)).astype(np.float32)
-    d_depth = rng.normal(0, 1, n_rays).astype(np.float32)
-    d_eik = np.full(n_rays, 0.1, np.float32)
+@pytest.fixture
+def restore_backward():
+    old = T.tsdfs_backward_kernel()
+    yield
+    T.tsdfs_set_backward_kernel(old)
+    T.tsdfs_set_backward_chunk(0)
+
+
+def gpu_grads(spec, o, d, b, d_rgb, d_depth, d_eik, kind=T.TSDFS_BACKWARD_GEMM, chunk=0, max_samples=None,
+              calls=1):
+    """Parameter gradients from render_rays_backward with the given implementation and
+    chunk; `calls` calls accumulate into the same buffers."""
+    T.tsdfs_set_backward_kernel(kind)
+    T.tsdfs_set_backward_chunk(chunk)
+    n_rays = len(o)
     mlp = T.Mlp(spec)
     offsets = np.concatenate([[0], np.cumsum(b["n"])]).astype(np.int32)
     total = int(offsets[-1])
+    ms = total if max_samples is None else max_samples
     d_sdf = torch.zeros_like(mlp.sdf_w)
     d_rw = torch.zeros_like(mlp.rgb_w)
-    ws = torch.empty(T.tsdfs_backward_workspace_size(mlp, n_rays, total), dtype=torch.uint8, device="cuda")
-    T.render_rays_backward(mlp, dev(o), dev(d), dev(b["t_n"].astype(np.float32)), dev(b["t_f"].astype(np.float32)),
-                           dev(offsets), dev(b["status"]), total, dev(d_rgb), dev(d_depth), dev(d_eik), d_sdf, d_rw, ws)
+    ws = torch.empty(max(T.tsdfs_backward_workspace_size(mlp, n_rays, ms), 1), dtype=torch.uint8, device="cuda")
+    for _ in range(calls):
+        T.render_rays_backward(mlp, dev(o), dev(d), dev(b["t_n"].astype(np.float32)), dev(b["t_f"].astype(np.float32)),
+                               dev(offsets), dev(b["status"]), ms, dev(d_rgb), dev(d_depth), dev(d_eik), d_sdf, d_rw, ws)
     torch.cuda.synchronize()
+    return d_sdf.cpu().numpy(), d_rw.cpu().numpy()
+
+
+def seeded_adjoints(n_rays, seed=7):
+    rng = np.random.default_rng(seed)
+    d_rgb = rng.normal(0, 1, (n_rays, 3)).astype(np.float32)
+    d_depth = rng.normal(0, 1, n_rays).astype(np.float32)
+    d_eik = np.full(n_rays, 0.1, np.float32)
+    return d_rgb, d_depth, d_eik
+
+
+def rel_err(got, ref):
+    return np.abs(got - ref).max() / np.abs(ref).max()
+
+
+@pytest.mark.parametrize("kind", [T.TSDFS_BACKWARD_GEMM, T.TSDFS_BACKWARD_SIMT], ids=["gemm", "simt"])
+@pytest.mark.parametrize("scene,n_rays", [("tiny", 96), ("room", 48)])
+def test_backward_matches_oracle_gradient(scene, n_rays, kind, restore_backward):
+    o, d, b = case(scene, n_rays, seed=41)
+    spec = synth.scene_mlp(scene)
+    d_rgb, d_depth, d_eik = seeded_adjoints(n_rays)
+    got_sdf, got_rgb = gpu_grads(spec, o, d, b, d_rgb, d_depth, d_eik, kind=kind)
     rc, bits = T.tsdfs_sync_status()
     assert rc == 0, bits
     ref_sdf, ref_rgb = oracle_grads(spec, o, d, b, d_rgb, d_depth, d_eik)
-    for got, ref, name in [(d_sdf.cpu().numpy(), ref_sdf, "sdf"), (d_rw.cpu().numpy(), ref_rgb, "rgb")]:
-        scale = np.abs(ref).max()
-        err = np.abs(got - ref).max() / scale
-        print(f"{scene} d{name}: max |err| / max |grad| = {err:.2e} (max |grad| {scale:.3e})")
+    for got, ref, name in [(got_sdf, ref_sdf, "sdf"), (got_rgb, ref_rgb, "rgb")]:
+        err = rel_err(got, ref)
+        print(f"{scene} kind {kind} d{name}: max |err| / max |grad| = {err:.2e} (max |grad| {np.abs(ref).max():.3e})")
         assert err < 2e-3, name
+
+
+@pytest.mark.parametrize("scene,n_rays", [("tiny", 96), ("room", 48)])
+def test_layer_major_matches_simt_backward(scene, n_rays, restore_backward):
+    """The two FP32 implementations differ by rounding order and the BF16x9 emulation
+    of the GEMM operands: far inside the oracle bar, layer by layer."""
+    o, d, b = case(scene, n_rays, seed=43)
+    spec = synth.scene_mlp(scene)
+    adj = seeded_adjoints(n_rays, 8)
+    g = gpu_grads(spec, o, d, b, *adj, kind=T.TSDFS_BACKWARD_GEMM)
+    s = gpu_grads(spec, o, d, b, *adj, kind=T.TSDFS_BACKWARD_SIMT)
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == 0, bits
+    for net, (a, r), layers in [("sdf", (g[0], s[0]), spec.sdf), ("rgb", (g[1], s[1]), spec.rgb)]:
+        off = 0
+        for l, (W, bv) in enumerate(layers):
+            k = W.size + bv.size
+            err = rel_err(a[off:off + k], r[off:off + k]) if np.abs(r[off:off + k]).max() > 0 else 0.0
+            print(f"{scene} {net} layer {l}: {err:.2e}")
+            assert err < 2e-4, (net, l)
+            off += k
+
+
+@pytest.mark.parametrize("scene,n_rays,chunk", [("tiny", 96, 37), ("room", 48, 71)])
+def test_chunked_backward_matches_one_chunk(scene, n_rays, chunk, restore_backward):
+    """Chunks smaller than the batch (a ragged last chunk; the forward recomputed in pass 2)
+    give the single-chunk gradients up to the order of the sums."""
+    o, d, b = case(scene, n_rays, seed=44)
+    total = int(b["n"].sum())
+    assert total > 3 * chunk and total % chunk != 0
+    spec = synth.scene_mlp(scene)
+    adj = seeded_adjoints(n_rays, 9)
+    one = gpu_grads(spec, o, d, b, *adj)
+    many = gpu_grads(spec, o, d, b, *adj, chunk=chunk)
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == 0, bits
+    for a, r in zip(many, one):
+        assert rel_err(a, r) < 1e-4
+
+
+def test_gradients_accumulate(restore_backward):
+    o, d, b = case("tiny", 64, seed=45)
+    spec = synth.scene_mlp("tiny")
+    adj = seeded_adjoints(64, 10)
+    one = gpu_grads(spec, o, d, b, *adj)
+    two = gpu_grads(spec, o, d, b, *adj, calls=2)
+    assert np.array_equal(two[0], 2 * one[0]) and np.array_equal(two[1], 2 * one[1])
+
+
+def test_sample_overflow_sets_status_and_leaves_gradients(restore_backward):
+    o, d, b = case("tiny", 64, seed=46)
+    spec = synth.scene_mlp("tiny")
+    total = int(b["n"].sum())
+    got = gpu_grads(spec, o, d, b, *seeded_adjoints(64), max_samples=total - 1)
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == T.TSDFS_E_DEVICE and bits & T.TSDFS_DEV_SAMPLES_OVERFLOW
+    assert not got[0].any() and not got[1].any()
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == 0, bits
+
+
+@pytest.mark.parametrize("kind", [T.TSDFS_BACKWARD_GEMM, T.TSDFS_BACKWARD_SIMT], ids=["gemm", "simt"])
+def test_rays_without_samples_give_zero_gradients(kind, restore_backward):
+    o, d, b = case("tiny", 32, seed=47)
+    b = dict(b)
+    b["n"] = np.zeros_like(b["n"])
+    b["status"] = np.zeros_like(b["status"])
+    got = gpu_grads(synth.scene_mlp("tiny"), o, d, b, *seeded_adjoints(32), kind=kind, max_samples=16)
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == 0, bits
+    assert not got[0].any() and not got[1].any()
 
 
 def _bounds_of(o, b):
