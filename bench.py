@@ -774,8 +774,8 @@ def run_train(spec, wl, grid, mask, dev, n_rays=8192, iters=5, kind=None, peak_b
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / iters
         split = {}
-        for name in ("mlp_simt", "composite", "backward", "backward_forward", "backward_composite",
-                     "backward_network", "ray_bounds"):
+        for name in ("mlp_simt", "composite", "train_forward", "train_forward_network", "train_forward_composite",
+                     "backward", "backward_forward", "backward_composite", "backward_network", "ray_bounds"):
             t, c = C.c_double(0), C.c_int64(0)
             T.lib().tsdfs_profile_read(name.encode(), C.byref(t), C.byref(c))
             if c.value:
@@ -784,26 +784,30 @@ def run_train(spec, wl, grid, mask, dev, n_rays=8192, iters=5, kind=None, peak_b
     finally:
         T.tsdfs_set_backward_kernel(old_kind)
     samples = int(b.offsets[-1].item())
+    gemm = kind == T.TSDFS_BACKWARD_GEMM
     out = {"rays": n_rays, "ms_per_step": ms, "rays_per_s": n_rays / (ms / 1e3), "samples": samples,
            "loss": float(loss.item()), "kernel_ms": split,
-           "backward": "layer-major GEMMs (cuBLAS BF16x9-emulated FP32 on the tensor cores)"
-           if kind == T.TSDFS_BACKWARD_GEMM else "FP32 SIMT, tiles of 8 samples",
+           "backward": "render_rays_train (layer-major FP32 forward that keeps its activations) + "
+                       "render_rays_backward_kept: GEMMs in cuBLAS BF16x9-emulated FP32 on the tensor cores"
+           if gemm else "render_rays (FP32 SIMT) + render_rays_backward (FP32 SIMT, tiles of 8 samples)",
            "what": "bounds + render (fp32) + L1 + 0.1 eikonal + backward through both networks"}
-    if kind == T.TSDFS_BACKWARD_GEMM and "backward_ms" in split:
+    if gemm and "backward_network_ms" in split:
         f = backward_gemm_flops(spec)
         chunk = T.tsdfs_backward_chunk_samples(mlp, ms_cap)
-        passes = 1 if samples <= chunk else 2   # more than one chunk recomputes the forward
-        flops = samples * (f["forward"] * passes + f["weight_grad"] + f["input_adjoint"])
-        t_net = split.get("backward_forward_ms", 0.0) + split.get("backward_network_ms", 0.0)
+        n_chunks = -(-samples // chunk)
+        passes = n_chunks   # the training forward, then every chunk but the last recomputed
+        flops = samples * f["weight_grad"] + samples * f["input_adjoint"] + \
+            min(samples, chunk * (n_chunks - 1)) * f["forward"] + samples * f["forward"]
+        t_net = split.get("train_forward_network_ms", 0.0) + split.get("backward_network_ms", 0.0)
         ach = flops / (t_net / 1e3) / 1e12 if t_net > 0 else None
         peak = peak_bf16 / 9.0 if peak_bf16 else None
         out["roofline"] = {"bound": "tensor", "achieved": ach, "unit": "TFLOP/s",
                            "peak": peak, "frac": (ach / peak) if (ach and peak) else None,
-                           "flops_per_sample": f, "chunk_samples": chunk, "forward_passes": passes,
+                           "flops_per_sample": f, "chunk_samples": chunk, "chunks": passes,
                            "workspace_bytes": T.tsdfs_backward_workspace_size(mlp, n_rays, ms_cap),
-                           "what": "GEMM FLOPs (forward recomputation, weight gradients, input adjoints) over the "
-                                   "time of the backward's forward and network phases (element-wise kernels and "
-                                   "bias GEMVs included)",
+                           "what": "GEMM FLOPs (the training forward, chunks other than the last recomputed, "
+                                   "weight gradients, input adjoints) over the time of the forward's and the "
+                                   "backward's network phases (element-wise kernels and bias GEMVs included)",
                            "peak_kind": "measured bf16 dense peak / 9 (each FP32 operand as three BF16 parts, nine "
                                         "products per FP32 product)"}
     return out

@@ -424,9 +424,11 @@ int render_rays_hier_bounded(const tsdfs_mlp* mlp, const float* ray_o, const flo
  *    is a GEMM over a chunk of samples (4 rows per sample for the SDF
  *    network: the value and its three x-derivative rows) on the tensor cores,
  *    FP32 operands emulated by three BF16 parts (cuBLAS BF16x9, FP32
- *    accumulation); the element-wise steps are the library's kernels.  The
- *    call reads the sample total offsets[n_rays] from the device first (one
- *    synchronisation of `stream`).  The workspace holds the per-sample records
+ *    accumulation, the emulation's handling of infinite and NaN operands
+ *    off: non-finite parameters set TSDFS_DEV_NONFINITE instead); the
+ *    element-wise steps are the library's kernels.  The call reads the sample
+ *    total offsets[n_rays] from the device first (one synchronisation of
+ *    `stream`).  The workspace holds the per-sample records
  *    and the activations of one chunk (tsdfs_set_backward_chunk; by default as
  *    many samples as fit 16 GiB, at most max_samples); a batch larger than one
  *    chunk recomputes each chunk's activations once more.  The first call on
@@ -457,6 +459,32 @@ int render_rays_backward(const tsdfs_mlp* mlp, const float* ray_o, const float* 
                          const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
                          int64_t max_samples, const float* d_rgb, const float* d_depth, const float* d_eik,
                          float* d_sdf_w, float* d_rgb_w, void* workspace, size_t ws_bytes, tsdfs_stream_t stream);
+
+/* ---- training step: a forward that keeps what the backward needs -----------
+ * render_rays_train: render_rays with FP32 networks evaluated by the
+ * layer-major path of render_rays_backward (every layer a GEMM over a chunk of
+ * samples, FP32 operands emulated by BF16 parts on the tensor cores); same
+ * outputs as render_rays.  It leaves the per-sample records and the last
+ * chunk's activations (all of them when the batch fits one chunk) in
+ * `workspace`.  render_rays_backward_kept, called next with the same mlp
+ * parameters, rays, bounds, max_samples and workspace (none of them changed in
+ * between), returns the gradients of render_rays_backward without
+ * recomputing what was kept.  Both read the sample total offsets[n_rays] from
+ * the device (one synchronisation of `stream`).  workspace >=
+ * tsdfs_train_workspace_size: the layer-major backward's workspace, whatever
+ * tsdfs_set_backward_kernel chose.  mlp->precision is ignored (FP32).  The
+ * paper trains its networks (Sec. 4.2) but prescribes no such split; it is
+ * the training step of this library's render path.                           */
+size_t tsdfs_train_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays, int64_t max_samples);
+int render_rays_train(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
+                      const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
+                      int64_t max_samples, float* rgb, float* depth, float* wsum, float* normal, float* eik,
+                      void* workspace, size_t ws_bytes, tsdfs_stream_t stream);
+int render_rays_backward_kept(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
+                              const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
+                              int64_t max_samples, const float* d_rgb, const float* d_depth, const float* d_eik,
+                              float* d_sdf_w, float* d_rgb_w, void* workspace, size_t ws_bytes,
+                              tsdfs_stream_t stream);
 
 /* ---- BF16 tensor-core parameter layout --------------------------------------
  * tsdfs_pack_mlp converts sdf_w / rgb_w to the 16-bit K-major tiles the

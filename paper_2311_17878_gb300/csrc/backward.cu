@@ -601,10 +601,10 @@ extern "C" size_t tsdfs_backward_workspace_size(const tsdfs_mlp* mlp, int64_t n_
     return bwd_layout(nullptr, mlp->arch, max_samples, bwd_blocks()).bytes + 256;
 }
 
-extern "C" int render_rays_backward(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
-                                    const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
-                                    int64_t max_samples, const float* d_rgb, const float* d_depth, const float* d_eik,
-                                    float* d_sdf_w, float* d_rgb_w, void* ws, size_t ws_bytes, tsdfs_stream_t stream) {
+// checks shared by the backward entry points and the training forward
+static int check_mlp_and_rays(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
+                              const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
+                              int64_t max_samples) {
     if (!mlp) return fail(TSDFS_E_INVALID, "mlp is NULL");
     if (mlp->arch != TSDFS_ARCH_TINY && mlp->arch != TSDFS_ARCH_ROOM) return fail(TSDFS_E_INVALID, "unknown arch %d", mlp->arch);
     if (!mlp->sdf_w || !mlp->rgb_w) return fail(TSDFS_E_INVALID, "sdf_w and rgb_w must be non-NULL");
@@ -612,14 +612,63 @@ extern "C" int render_rays_backward(const tsdfs_mlp* mlp, const float* ray_o, co
     if (mlp->opacity != TSDFS_OPACITY_NEUS && mlp->opacity != TSDFS_OPACITY_VOLSDF)
         return fail(TSDFS_E_INVALID, "unknown opacity %d", mlp->opacity);
     if (n_rays < 0 || max_samples < 0) return fail(TSDFS_E_INVALID, "n_rays and max_samples must be >= 0");
-    if (n_rays == 0) return TSDFS_OK;
-    if (!ray_o || !ray_d || !t_n || !t_f || !offsets || !status || !d_rgb || !d_sdf_w || !d_rgb_w)
-        return fail(TSDFS_E_INVALID, "ray, bound, d_rgb and gradient pointers must be non-NULL");
+    if (n_rays > 0 && (!ray_o || !ray_d || !t_n || !t_f || !offsets || !status))
+        return fail(TSDFS_E_INVALID, "ray and bound pointers must be non-NULL");
     if (max_samples > (int64_t)INT32_MAX) return fail(TSDFS_E_INVALID, "max_samples must fit int32 offsets");
+    return TSDFS_OK;
+}
+
+extern "C" size_t tsdfs_train_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays, int64_t max_samples) {
+    (void)n_rays;
+    if (!mlp || max_samples < 0) return 0;
+    if (mlp->arch != TSDFS_ARCH_TINY && mlp->arch != TSDFS_ARCH_ROOM) return 0;
+    return gemm_backward_workspace(mlp, max_samples);
+}
+
+extern "C" int render_rays_train(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
+                                 const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
+                                 int64_t max_samples, float* rgb, float* depth, float* wsum, float* normal, float* eik,
+                                 void* ws, size_t ws_bytes, tsdfs_stream_t stream) {
+    int rc = check_mlp_and_rays(mlp, ray_o, ray_d, t_n, t_f, offsets, status, n_rays, max_samples);
+    if (rc) return rc;
+    if (n_rays == 0) return TSDFS_OK;
+    if (!rgb || !depth || !wsum) return fail(TSDFS_E_INVALID, "rgb, depth and wsum must be non-NULL (normal, eik may be NULL)");
+    if (!ws || ws_bytes < tsdfs_train_workspace_size(mlp, n_rays, max_samples))
+        return fail(TSDFS_E_WORKSPACE, "training workspace too small");
+    return gemm_train_forward(mlp, ray_o, ray_d, t_n, t_f, offsets, status, n_rays, max_samples, rgb, depth, wsum,
+                              normal, eik, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" int render_rays_backward_kept(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d,
+                                         const float* t_n, const float* t_f, const int32_t* offsets,
+                                         const uint8_t* status, int64_t n_rays, int64_t max_samples,
+                                         const float* d_rgb, const float* d_depth, const float* d_eik,
+                                         float* d_sdf_w, float* d_rgb_w, void* ws, size_t ws_bytes,
+                                         tsdfs_stream_t stream) {
+    int rc = check_mlp_and_rays(mlp, ray_o, ray_d, t_n, t_f, offsets, status, n_rays, max_samples);
+    if (rc) return rc;
+    if (n_rays == 0 || max_samples == 0) return TSDFS_OK;
+    if (!d_rgb || !d_sdf_w || !d_rgb_w) return fail(TSDFS_E_INVALID, "d_rgb and gradient pointers must be non-NULL");
+    if (!ws || ws_bytes < tsdfs_train_workspace_size(mlp, n_rays, max_samples))
+        return fail(TSDFS_E_WORKSPACE, "training workspace too small");
+    return gemm_backward(mlp, ray_o, ray_d, t_n, t_f, offsets, status, n_rays, max_samples, d_rgb, d_depth, d_eik,
+                         d_sdf_w, d_rgb_w, ws, ws_bytes, (cudaStream_t)stream, true);
+}
+
+extern "C" int render_rays_backward(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
+                                    const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
+                                    int64_t max_samples, const float* d_rgb, const float* d_depth, const float* d_eik,
+                                    float* d_sdf_w, float* d_rgb_w, void* ws, size_t ws_bytes, tsdfs_stream_t stream) {
+    int rc = check_mlp_and_rays(mlp, ray_o, ray_d, t_n, t_f, offsets, status, n_rays, max_samples);
+    if (rc) return rc;
+    if (n_rays == 0) return TSDFS_OK;
+    if (!d_rgb || !d_sdf_w || !d_rgb_w) return fail(TSDFS_E_INVALID, "d_rgb and gradient pointers must be non-NULL");
     if (g_bwd_kind.load() == TSDFS_BACKWARD_GEMM) {
         if (max_samples == 0) return TSDFS_OK;
+        if (!ws || ws_bytes < gemm_backward_workspace(mlp, max_samples))
+            return fail(TSDFS_E_WORKSPACE, "backward workspace too small");
         return gemm_backward(mlp, ray_o, ray_d, t_n, t_f, offsets, status, n_rays, max_samples, d_rgb, d_depth, d_eik,
-                             d_sdf_w, d_rgb_w, ws, ws_bytes, (cudaStream_t)stream);
+                             d_sdf_w, d_rgb_w, ws, ws_bytes, (cudaStream_t)stream, false);
     }
     const int blocks = bwd_blocks();
     BwdWs w = bwd_layout(ws, mlp->arch, max_samples, blocks);
@@ -644,8 +693,8 @@ extern "C" int render_rays_backward(const tsdfs_mlp* mlp, const float* ray_o, co
     src.total_dev = offsets + n_rays;
     src.capacity = max_samples;
     if (max_samples == 0) return TSDFS_OK;
-    int rc = mlp->arch == TSDFS_ARCH_TINY ? launch_mlp_full_simt<TSDFS_ARCH_TINY>(np, src, w.rec, max_samples, st)
-                                          : launch_mlp_full_simt<TSDFS_ARCH_ROOM>(np, src, w.rec, max_samples, st);
+    rc = mlp->arch == TSDFS_ARCH_TINY ? launch_mlp_full_simt<TSDFS_ARCH_TINY>(np, src, w.rec, max_samples, st)
+                                      : launch_mlp_full_simt<TSDFS_ARCH_ROOM>(np, src, w.rec, max_samples, st);
     if (rc) return rc;
     rc = launch_comp_bwd(w.rec, offsets, status, ray_d, n_rays, mlp, d_rgb, d_depth, d_eik, w.adj, st);
     if (rc) return rc;

@@ -28,9 +28,15 @@ int64_t backward_chunk_setting();
 // the layer-major path (backward_gemm.cu); arguments checked by render_rays_backward
 size_t gemm_backward_workspace(const tsdfs_mlp* mlp, int64_t max_samples);
 int64_t gemm_backward_chunk(const tsdfs_mlp* mlp, int64_t max_samples);
+// kept: from the records and activations a gemm_train_forward call left in ws
 int gemm_backward(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n, const float* t_f,
                   const int32_t* offsets, const uint8_t* status, int64_t n_rays, int64_t max_samples,
                   const float* d_rgb, const float* d_depth, const float* d_eik, float* d_sdf_w, float* d_rgb_w,
-                  void* ws, size_t ws_bytes, cudaStream_t st);
+                  void* ws, size_t ws_bytes, cudaStream_t st, bool kept);
+// render_rays through the layer-major forward, keeping records and activations in ws
+int gemm_train_forward(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
+                       const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
+                       int64_t max_samples, float* rgb, float* depth, float* wsum, float* normal, float* eik, void* ws,
+                       size_t ws_bytes, cudaStream_t st);
 
 }  // namespace tsdfs

@@ -18,11 +18,13 @@
 //
 // The GEMMs run in cuBLAS with FP32 operands emulated on the BF16 tensor cores
 // (each operand split into three BF16 parts, FP32 accumulation:
-// CUBLAS_COMPUTE_32F_EMULATED_16BFX9).  Every matrix is row-major with its row
-// length padded to a multiple of 4 floats (16 bytes), zero in the padding; the
-// weights are copied once per call into that padded layout, and the gradients
-// accumulate in a padded scratch that is added into the caller's packed
-// gradients at the end.
+// CUBLAS_COMPUTE_32F_EMULATED_16BFX9), without the emulation's handling of
+// infinite and NaN operands: the parameters are checked for non-finite values
+// (TSDFS_DEV_NONFINITE) instead.  Every matrix is row-major with both of its
+// widths padded to a multiple of 4 floats (16 bytes), zero in the padding, which
+// keeps every GEMM on the tensor-core kernels; the weights are copied once per
+// call into that padded layout, and the gradients accumulate in a padded scratch
+// that is added into the caller's packed gradients at the end.
 //
 // The sample total sizes the GEMMs, so the call reads it from the device first
 // (one synchronisation of the stream).  When all samples fit one chunk, the
@@ -37,6 +39,12 @@
 #include "backward.cuh"
 
 namespace tsdfs {
+int launch_composite(const SampleRec* rec, const int32_t* offsets, int per_ray, const uint8_t* status, int64_t n_rays,
+                     const int32_t* total_dev, int64_t capacity, Opacity op, float* rgb, float* depth,
+                     float* wsum, float* normal, float* eik, cudaStream_t st);
+}  // namespace tsdfs
+
+namespace tsdfs {
 namespace {
 
 constexpr int64_t kDefaultChunkBytes = 16ll << 30;  // activations of one chunk
@@ -46,14 +54,14 @@ constexpr float kSkipScale = 0.70710678118654752f;  // 1 / sqrt(2) at the skip c
 
 __host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
 
-// padded layout of one architecture: weights W [out][pad4(in)] then b [pad4(out)] per
-// layer, the SDF layers first; activation rows padded to pad4(width)
+// padded layout of one architecture: weights W [pad4(out)][pad4(in)] then b [pad4(out)]
+// per layer, the SDF layers first; activation rows padded to pad4(width)
 template <int ARCH>
 struct GLayout {
     using A = Arch<ARCH>;
     static constexpr int LS = A::kSdfLayers, LC = A::kRgbLayers;
     __host__ __device__ static constexpr int64_t layer_floats(Layer ly) {
-        return (int64_t)ly.out * pad4(ly.in) + pad4(ly.out);
+        return (int64_t)pad4(ly.out) * pad4(ly.in) + pad4(ly.out);
     }
     __host__ __device__ static constexpr int64_t sdf_off(int l) {
         int64_t o = 0;
@@ -120,11 +128,11 @@ __global__ void k_pad_weights(const float* __restrict__ sdf_w, const float* __re
         const float* src = sdf ? sdf_w + sdf_layer_offset<ARCH>(l) : rgb_w + rgb_layer_offset<ARCH>(l);
         const int kp = pad4(ly.in);
         float v = 0.0f;
-        if (e < (int64_t)ly.out * kp) {
+        if (e < (int64_t)pad4(ly.out) * kp) {
             const int n = (int)(e / kp), k = (int)(e % kp);
-            if (k < ly.in) v = src[(int64_t)n * ly.in + k];
+            if (n < ly.out && k < ly.in) v = src[(int64_t)n * ly.in + k];
         } else {
-            const int n = (int)(e - (int64_t)ly.out * kp);
+            const int n = (int)(e - (int64_t)pad4(ly.out) * kp);
             if (n < ly.out) v = src[(int64_t)ly.out * ly.in + n];
         }
         wp[i] = v;
@@ -149,7 +157,7 @@ __global__ void k_add_grads(const float* __restrict__ dwp, float* __restrict__ d
         const int kp = pad4(ly.in);
         float v;
         if (e < (int64_t)ly.out * ly.in) v = dwp[po + (e / ly.in) * kp + e % ly.in];
-        else v = dwp[po + (int64_t)ly.out * kp + (e - (int64_t)ly.out * ly.in)];
+        else v = dwp[po + (int64_t)pad4(ly.out) * kp + (e - (int64_t)ly.out * ly.in)];
         if (sdf) d_sdf[j] += v;
         else d_rgb[j] += v;
     }
@@ -161,6 +169,17 @@ __global__ void k_fill(float* __restrict__ p, int64_t n, float v) {
 
 __global__ void k_flag_overflow(const int32_t* __restrict__ total, int64_t capacity, uint32_t* status) {
     if (threadIdx.x == 0 && blockIdx.x == 0 && (int64_t)*total > capacity) set_status(status, TSDFS_DEV_SAMPLES_OVERFLOW);
+}
+
+// TSDFS_DEV_NONFINITE when a parameter is infinite or NaN (the GEMMs assume finite operands)
+__global__ void k_check_params(const float* __restrict__ sdf_w, int64_t n_sdf, const float* __restrict__ rgb_w,
+                               int64_t n_rgb, uint32_t* status) {
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_sdf + n_rgb; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = i < n_sdf ? sdf_w[i] : rgb_w[i - n_sdf];
+        bad = bad || !isfinite(v);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_status(status, TSDFS_DEV_NONFINITE);
 }
 
 // ---- forward element-wise steps -------------------------------------------------
@@ -331,16 +350,17 @@ __global__ void k_grgb_bwd(const float* __restrict__ P, int ldp, const float* __
             const float y = 1.0f / (1.0f + expf(-(P[s * ldp + ch] + __ldg(bias + ch))));
             G[s * ldg + ch] = gy[ch] * y * (1.0f - y);
         }
+        for (int ch = 3; ch < ldg; ++ch) G[s * ldg + ch] = 0.0f;
     }
 }
 
-// through a hidden colour layer's ReLU: G = D where P + b > 0
+// through a hidden colour layer's ReLU: G = D where P + b > 0 (zero padding)
 __global__ void k_grelu_bwd(const float* __restrict__ D, int ldd, const float* __restrict__ P, int ldp,
                             const float* __restrict__ bias, int N, int64_t n, float* __restrict__ G, int ldg) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * N; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = e / N;
-        const int j = (int)(e % N);
-        G[s * ldg + j] = P[s * ldp + j] + __ldg(bias + j) > 0.0f ? D[s * ldd + j] : 0.0f;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * ldg; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = e / ldg;
+        const int j = (int)(e % ldg);
+        G[s * ldg + j] = j < N && P[s * ldp + j] + __ldg(bias + j) > 0.0f ? D[s * ldd + j] : 0.0f;
     }
 }
 
@@ -353,11 +373,13 @@ __global__ void k_gsdf_out_bwd(const float* __restrict__ D, int ldd, const Sampl
                                float* __restrict__ G, int ldg) {
     using A = Arch<ARCH>;
     constexpr int kDir = A::kDirEnc, fo = 3 + kDir + 3, No = A::sdf(A::kSdfLayers - 1).out;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * No; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = e / No;
-        const int j = (int)(e % No);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * ldg; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = e / ldg;
+        const int j = (int)(e % ldg);
         float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (j == 0) {
+        if (j >= No) {
+            // padding
+        } else if (j == 0) {
             const SampleAdj& Ad = adj[c0 + s];
             const SampleRec& R = rec[c0 + s];
             v[0] = Ad.gf * scale;
@@ -382,9 +404,14 @@ __global__ void k_gsdf_out_bwd(const float* __restrict__ D, int ldd, const Sampl
 __global__ void k_gsp_bwd(const float* __restrict__ D, int ldd, const float* __restrict__ P, int ldp,
                           const float* __restrict__ bias, int N, float sc, float beta, int64_t n,
                           float* __restrict__ G, int ldg) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * N; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = e / N;
-        const int j = (int)(e % N);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * ldg; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = e / ldg;
+        const int j = (int)(e % ldg);
+        if (j >= N) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) G[(4 * s + c) * ldg + j] = 0.0f;
+            continue;
+        }
         const float z = P[4 * s * ldp + j] + __ldg(bias + j);
         const float bz = beta * z;
         const float sg = bz > 20.0f ? 1.0f : 1.0f / (1.0f + expf(-bz));
@@ -428,6 +455,8 @@ int blas_handle(cublasHandle_t* out) {
     rc = blas_check(cublasCreate(&h), "create");
     if (rc) return rc;
     rc = blas_check(cublasSetPointerMode(h, CUBLAS_POINTER_MODE_HOST), "pointer mode");
+    if (!rc) rc = blas_check(cublasSetEmulationSpecialValuesSupport(h, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE),
+                             "emulation special values");
     if (rc) return rc;
     g_blas.h[dev] = h;
     g_blas.ctx[dev] = id ? id : current_context_id();
@@ -536,6 +565,19 @@ GemmWs<ARCH> gemm_layout(void* base, int64_t max_samples) {
 
 // ---- the two passes over one chunk ---------------------------------------------------
 
+// what one call of the layer-major path does: the backward from scratch (records and
+// activations recomputed), the forward of a training step that keeps them in the
+// workspace, or the backward from what that forward kept
+enum class Pass { kBackward, kForwardKeep, kBackwardKept };
+
+struct RenderOut {
+    float* rgb;
+    float* depth;
+    float* wsum;
+    float* normal;
+    float* eik;
+};
+
 template <int ARCH>
 int chunk_forward(cublasHandle_t h, const GemmWs<ARCH>& w, const NetParams& np, const SampleSource& src, int64_t c0,
                   int64_t n, cudaStream_t st) {
@@ -549,9 +591,9 @@ int chunk_forward(cublasHandle_t h, const GemmWs<ARCH>& w, const NetParams& np, 
     for (int l = 0; l < L::LS; ++l) {
         const Layer ly = A::sdf(l);
         const float* W = w.wp + L::sdf_off(l);
-        rc = mm_fwd(h, 4 * n, pad4(ly.in), ly.out, w.X[l], pad4(ly.in), W, pad4(ly.in), w.P[l], pad4(ly.out));
+        rc = mm_fwd(h, 4 * n, pad4(ly.in), pad4(ly.out), w.X[l], pad4(ly.in), W, pad4(ly.in), w.P[l], pad4(ly.out));
         if (rc) return rc;
-        const float* b = W + (int64_t)ly.out * pad4(ly.in);
+        const float* b = W + (int64_t)pad4(ly.out) * pad4(ly.in);
         if (l + 1 < L::LS) {
             const int ldn = pad4(A::sdf(l + 1).in);
             const bool skip = l + 1 == A::kSkip;
@@ -568,9 +610,9 @@ int chunk_forward(cublasHandle_t h, const GemmWs<ARCH>& w, const NetParams& np, 
     for (int l = 0; l < L::LC; ++l) {
         const Layer ly = A::rgb(l);
         const float* W = w.wp + L::rgb_off(l);
-        rc = mm_fwd(h, n, pad4(ly.in), ly.out, w.Xc[l], pad4(ly.in), W, pad4(ly.in), w.Pc[l], pad4(ly.out));
+        rc = mm_fwd(h, n, pad4(ly.in), pad4(ly.out), w.Xc[l], pad4(ly.in), W, pad4(ly.in), w.Pc[l], pad4(ly.out));
         if (rc) return rc;
-        const float* b = W + (int64_t)ly.out * pad4(ly.in);
+        const float* b = W + (int64_t)pad4(ly.out) * pad4(ly.in);
         if (l + 1 < L::LC) {
             const int ldn = pad4(A::rgb(l + 1).in);
             k_grelu_fwd<<<grid_1d(n * ldn, kEw), kEw, 0, st>>>(w.Pc[l], pad4(ly.out), b, ly.out, n, w.Xc[l + 1], ldn);
@@ -591,7 +633,7 @@ int chunk_backward(cublasHandle_t h, const GemmWs<ARCH>& w, const NetParams& np,
     int rc;
     {
         const Layer ly = A::rgb(L::LC - 1);
-        const float* b = w.wp + L::rgb_off(L::LC - 1) + (int64_t)ly.out * pad4(ly.in);
+        const float* b = w.wp + L::rgb_off(L::LC - 1) + (int64_t)pad4(ly.out) * pad4(ly.in);
         k_grgb_bwd<<<grid_1d(n, kEw), kEw, 0, st>>>(w.Pc[L::LC - 1], pad4(ly.out), b, w.adj, n, c0, w.G, pad4(ly.out));
         rc = cuda_check(cudaGetLastError(), "backward colour output launch");
         if (rc) return rc;
@@ -601,23 +643,23 @@ int chunk_backward(cublasHandle_t h, const GemmWs<ARCH>& w, const NetParams& np,
         const int kp = pad4(ly.in), ldg = pad4(ly.out);
         const float* W = w.wp + L::rgb_off(l);
         float* dW = w.dwp + L::rgb_off(l);
-        rc = mm_dw(h, n, ly.out, kp, w.G, ldg, w.Xc[l], kp, dW, kp);
-        if (!rc) rc = mv_db(h, n, ly.out, w.G, ldg, 1, w.ones, dW + (int64_t)ly.out * kp);
-        if (!rc) rc = mm_dx(h, n, ly.out, kp, w.G, ldg, W, kp, w.D, kp);
+        rc = mm_dw(h, n, ldg, kp, w.G, ldg, w.Xc[l], kp, dW, kp);
+        if (!rc) rc = mv_db(h, n, ly.out, w.G, ldg, 1, w.ones, dW + (int64_t)ldg * kp);
+        if (!rc) rc = mm_dx(h, n, ldg, kp, w.G, ldg, W, kp, w.D, kp);
         if (rc) return rc;
         if (l == 0) break;
         const Layer lp = A::rgb(l - 1);
-        const float* bp = w.wp + L::rgb_off(l - 1) + (int64_t)lp.out * pad4(lp.in);
-        k_grelu_bwd<<<grid_1d(n * lp.out, kEw), kEw, 0, st>>>(w.D, kp, w.Pc[l - 1], pad4(lp.out), bp, lp.out, n, w.G,
-                                                             pad4(lp.out));
+        const float* bp = w.wp + L::rgb_off(l - 1) + (int64_t)pad4(lp.out) * pad4(lp.in);
+        k_grelu_bwd<<<grid_1d(n * pad4(lp.out), kEw), kEw, 0, st>>>(w.D, kp, w.Pc[l - 1], pad4(lp.out), bp, lp.out, n,
+                                                                   w.G, pad4(lp.out));
         rc = cuda_check(cudaGetLastError(), "backward ReLU launch");
         if (rc) return rc;
     }
     // w.D = adjoint of the colour input rows; the SDF output rows' adjoint
     {
         constexpr Layer lo = A::sdf(L::LS - 1);
-        k_gsdf_out_bwd<ARCH><<<grid_1d(n * lo.out, kEw), kEw, 0, st>>>(w.D, pad4(A::rgb(0).in), w.adj, w.rec, n, c0,
-                                                                        np.scale, w.G, pad4(lo.out));
+        k_gsdf_out_bwd<ARCH><<<grid_1d(n * pad4(lo.out), kEw), kEw, 0, st>>>(w.D, pad4(A::rgb(0).in), w.adj, w.rec, n,
+                                                                              c0, np.scale, w.G, pad4(lo.out));
         rc = cuda_check(cudaGetLastError(), "backward SDF output launch");
         if (rc) return rc;
     }
@@ -626,15 +668,15 @@ int chunk_backward(cublasHandle_t h, const GemmWs<ARCH>& w, const NetParams& np,
         const int kp = pad4(ly.in), ldg = pad4(ly.out);
         const float* W = w.wp + L::sdf_off(l);
         float* dW = w.dwp + L::sdf_off(l);
-        rc = mm_dw(h, 4 * n, ly.out, kp, w.G, ldg, w.X[l], kp, dW, kp);
-        if (!rc) rc = mv_db(h, n, ly.out, w.G, ldg, 4, w.ones, dW + (int64_t)ly.out * kp);
+        rc = mm_dw(h, 4 * n, ldg, kp, w.G, ldg, w.X[l], kp, dW, kp);
+        if (!rc) rc = mv_db(h, n, ly.out, w.G, ldg, 4, w.ones, dW + (int64_t)ldg * kp);
         if (rc) return rc;
         if (l == 0) break;
-        rc = mm_dx(h, 4 * n, ly.out, kp, w.G, ldg, W, kp, w.D, kp);
+        rc = mm_dx(h, 4 * n, ldg, kp, w.G, ldg, W, kp, w.D, kp);
         if (rc) return rc;
         const Layer lp = A::sdf(l - 1);
-        const float* bp = w.wp + L::sdf_off(l - 1) + (int64_t)lp.out * pad4(lp.in);
-        k_gsp_bwd<<<grid_1d(n * lp.out, kEw), kEw, 0, st>>>(w.D, kp, w.P[l - 1], pad4(lp.out), bp, lp.out,
+        const float* bp = w.wp + L::sdf_off(l - 1) + (int64_t)pad4(lp.out) * pad4(lp.in);
+        k_gsp_bwd<<<grid_1d(n * pad4(lp.out), kEw), kEw, 0, st>>>(w.D, kp, w.P[l - 1], pad4(lp.out), bp, lp.out,
                                                            l == A::kSkip ? kSkipScale : 1.0f, np.beta, n, w.G,
                                                            pad4(lp.out));
         rc = cuda_check(cudaGetLastError(), "backward softplus launch");
@@ -644,26 +686,34 @@ int chunk_backward(cublasHandle_t h, const GemmWs<ARCH>& w, const NetParams& np,
 }
 
 template <int ARCH>
-int run(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n, const float* t_f,
+int run(Pass pass, const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n, const float* t_f,
         const int32_t* offsets, const uint8_t* status, int64_t n_rays, int64_t max_samples, const float* d_rgb,
-        const float* d_depth, const float* d_eik, float* d_sdf_w, float* d_rgb_w, void* ws, size_t ws_bytes,
-        cudaStream_t st) {
+        const float* d_depth, const float* d_eik, float* d_sdf_w, float* d_rgb_w, const RenderOut& out, void* ws,
+        size_t ws_bytes, cudaStream_t st) {
     using L = GLayout<ARCH>;
     GemmWs<ARCH> w = gemm_layout<ARCH>(ws, max_samples);
-    if (!ws || ws_bytes < w.bytes) return fail(TSDFS_E_WORKSPACE, "backward workspace too small");
-    ProfScope ps("backward", st);
+    if (!ws || ws_bytes < w.bytes) return fail(TSDFS_E_WORKSPACE, "layer-major workspace too small");
+    const bool forward = pass == Pass::kForwardKeep;
+    ProfScope ps(forward ? "train_forward" : "backward", st);
     // the sample total sizes the GEMMs
     int32_t total32 = 0;
     int rc = cuda_check(cudaMemcpyAsync(&total32, offsets + n_rays, sizeof(int32_t), cudaMemcpyDeviceToHost, st),
-                        "backward total read");
-    if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "backward total sync");
+                        "layer-major total read");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "layer-major total sync");
     if (rc) return rc;
     const int64_t total = total32;
-    if (total > max_samples) {
-        k_flag_overflow<<<1, 32, 0, st>>>(offsets + n_rays, max_samples, device_status_word());
-        return cuda_check(cudaGetLastError(), "backward overflow flag");
+    const Opacity op{mlp->opacity, mlp->inv_s, mlp->alpha_eps};
+    if (total > max_samples || total <= 0) {
+        if (total > max_samples) {
+            k_flag_overflow<<<1, 32, 0, st>>>(offsets + n_rays, max_samples, device_status_word());
+            rc = cuda_check(cudaGetLastError(), "layer-major overflow flag");
+            if (rc) return rc;
+        }
+        // no network work; the forward still writes its outputs (zero for an overflow, as render_rays)
+        if (!forward) return TSDFS_OK;
+        return launch_composite(w.rec, offsets, 0, status, n_rays, offsets + n_rays, max_samples, op, out.rgb,
+                                out.depth, out.wsum, out.normal, out.eik, st);
     }
-    if (total <= 0) return TSDFS_OK;
     NetParams np;
     np.sdf_w = mlp->sdf_w;
     np.rgb_w = mlp->rgb_w;
@@ -689,30 +739,41 @@ int run(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const floa
     rc = blas_check(cublasSetStream(h, st), "set stream");
     if (!rc) rc = blas_check(cublasSetWorkspace(h, w.blas, kBlasWorkspace), "set workspace");
     if (rc) return rc;
+    k_check_params<<<grid_1d(sdf_param_count<ARCH>() + rgb_param_count<ARCH>(), kEw), kEw, 0, st>>>(
+        mlp->sdf_w, sdf_param_count<ARCH>(), mlp->rgb_w, rgb_param_count<ARCH>(), device_status_word());
     k_pad_weights<ARCH><<<grid_1d(L::total(), kEw), kEw, 0, st>>>(mlp->sdf_w, mlp->rgb_w, w.wp);
-    k_fill<<<grid_1d(w.chunk, kEw), kEw, 0, st>>>(w.ones, w.chunk, 1.0f);
-    rc = cuda_check(cudaGetLastError(), "backward weight copy launch");
-    if (!rc) rc = cuda_check(cudaMemsetAsync(w.dwp, 0, (size_t)L::total() * 4, st), "backward gradient clear");
+    rc = cuda_check(cudaGetLastError(), "layer-major weight copy launch");
     if (rc) return rc;
     const int64_t C = w.chunk;
-    const bool one_chunk = total <= C;
-    {
-        ProfScope pf("backward_forward", st);
+    const int64_t last_c0 = (total - 1) / C * C;   // first sample of the last chunk
+    // pass 1: the records of every sample, chunk by chunk; the last chunk's activations stay
+    if (pass != Pass::kBackwardKept) {
+        ProfScope pf(forward ? "train_forward_network" : "backward_forward", st);
         for (int64_t c0 = 0; c0 < total; c0 += C) {
             rc = chunk_forward<ARCH>(h, w, np, src, c0, total - c0 < C ? total - c0 : C, st);
             if (rc) return rc;
         }
     }
+    if (forward) {
+        ProfScope pc("train_forward_composite", st);
+        return launch_composite(w.rec, offsets, 0, status, n_rays, offsets + n_rays, max_samples, op, out.rgb,
+                                out.depth, out.wsum, out.normal, out.eik, st);
+    }
+    k_fill<<<grid_1d(w.chunk, kEw), kEw, 0, st>>>(w.ones, w.chunk, 1.0f);
+    rc = cuda_check(cudaGetLastError(), "backward fill launch");
+    if (!rc) rc = cuda_check(cudaMemsetAsync(w.dwp, 0, (size_t)L::total() * 4, st), "backward gradient clear");
+    if (rc) return rc;
     {
         ProfScope pc("backward_composite", st);
         rc = launch_comp_bwd(w.rec, offsets, status, ray_d, n_rays, mlp, d_rgb, d_depth, d_eik, w.adj, st);
         if (rc) return rc;
     }
     {
+        // the last chunk first, from the activations pass 1 left; the others recomputed
         ProfScope pn("backward_network", st);
-        for (int64_t c0 = 0; c0 < total; c0 += C) {
+        for (int64_t c0 = last_c0; c0 >= 0; c0 -= C) {
             const int64_t n = total - c0 < C ? total - c0 : C;
-            if (!one_chunk) {
+            if (c0 != last_c0) {
                 rc = chunk_forward<ARCH>(h, w, np, src, c0, n, st);
                 if (rc) return rc;
             }
@@ -740,12 +801,26 @@ int64_t gemm_backward_chunk(const tsdfs_mlp* mlp, int64_t max_samples) {
 int gemm_backward(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n, const float* t_f,
                   const int32_t* offsets, const uint8_t* status, int64_t n_rays, int64_t max_samples,
                   const float* d_rgb, const float* d_depth, const float* d_eik, float* d_sdf_w, float* d_rgb_w,
-                  void* ws, size_t ws_bytes, cudaStream_t st) {
+                  void* ws, size_t ws_bytes, cudaStream_t st, bool kept) {
+    const Pass pass = kept ? Pass::kBackwardKept : Pass::kBackward;
+    const RenderOut none{};
     if (mlp->arch == TSDFS_ARCH_TINY)
-        return run<TSDFS_ARCH_TINY>(mlp, ray_o, ray_d, t_n, t_f, offsets, status, n_rays, max_samples, d_rgb, d_depth,
-                                    d_eik, d_sdf_w, d_rgb_w, ws, ws_bytes, st);
-    return run<TSDFS_ARCH_ROOM>(mlp, ray_o, ray_d, t_n, t_f, offsets, status, n_rays, max_samples, d_rgb, d_depth, d_eik,
-                                d_sdf_w, d_rgb_w, ws, ws_bytes, st);
+        return run<TSDFS_ARCH_TINY>(pass, mlp, ray_o, ray_d, t_n, t_f, offsets, status, n_rays, max_samples, d_rgb,
+                                    d_depth, d_eik, d_sdf_w, d_rgb_w, none, ws, ws_bytes, st);
+    return run<TSDFS_ARCH_ROOM>(pass, mlp, ray_o, ray_d, t_n, t_f, offsets, status, n_rays, max_samples, d_rgb,
+                                d_depth, d_eik, d_sdf_w, d_rgb_w, none, ws, ws_bytes, st);
+}
+
+int gemm_train_forward(const tsdfs_mlp* mlp, const float* ray_o, const float* ray_d, const float* t_n,
+                       const float* t_f, const int32_t* offsets, const uint8_t* status, int64_t n_rays,
+                       int64_t max_samples, float* rgb, float* depth, float* wsum, float* normal, float* eik, void* ws,
+                       size_t ws_bytes, cudaStream_t st) {
+    const RenderOut out{rgb, depth, wsum, normal, eik};
+    if (mlp->arch == TSDFS_ARCH_TINY)
+        return run<TSDFS_ARCH_TINY>(Pass::kForwardKeep, mlp, ray_o, ray_d, t_n, t_f, offsets, status, n_rays,
+                                    max_samples, nullptr, nullptr, nullptr, nullptr, nullptr, out, ws, ws_bytes, st);
+    return run<TSDFS_ARCH_ROOM>(Pass::kForwardKeep, mlp, ray_o, ray_d, t_n, t_f, offsets, status, n_rays, max_samples,
+                                nullptr, nullptr, nullptr, nullptr, nullptr, out, ws, ws_bytes, st);
 }
 
 }  // namespace tsdfs

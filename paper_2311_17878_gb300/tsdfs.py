@@ -45,7 +45,8 @@ EXPORTS = ["tsdfs_last_error", "tsdfs_sync_status", "tsdfs_grid_init", "tsdf_int
            "tsdfs_loss_f64_workspace_size", "tsdfs_loss_f64", "tsdfs_autotune_network", "tsdfs_l2_read_probe",
            "tsdfs_raycast_workspace_size", "tsdf_integrate_raycast", "tsdfs_profile", "tsdfs_profile_read",
            "tsdfs_set_backward_kernel", "tsdfs_backward_kernel", "tsdfs_set_backward_chunk",
-           "tsdfs_backward_chunk_samples"]
+           "tsdfs_backward_chunk_samples", "tsdfs_train_workspace_size", "render_rays_train",
+           "render_rays_backward_kept"]
 
 
 class TsdfsError(RuntimeError):
@@ -80,12 +81,13 @@ def lib():
             L = C.CDLL(LIB_PATH)
             L.tsdfs_last_error.restype = C.c_char_p
             for name in ["tsdfs_bounds_workspace_size", "tsdfs_render_workspace_size", "tsdfs_hier_workspace_size",
-                         "tsdfs_backward_workspace_size", "tsdfs_packed_size", "tsdfs_adaptive_counts_workspace_size",
+                         "tsdfs_backward_workspace_size", "tsdfs_train_workspace_size", "tsdfs_packed_size", "tsdfs_adaptive_counts_workspace_size",
                          "tsdfs_hier_bounded_workspace_size", "tsdfs_raycast_workspace_size",
                          "tsdfs_loss_f64_workspace_size"]:
                 getattr(L, name).restype = C.c_size_t
             for name in ["tsdfs_inside_mask_words", "tsdfs_sdf_param_count", "tsdfs_rgb_param_count",
-                         "tsdfs_backward_chunk_samples"]:
+                         "tsdfs_backward_chunk_samples", "tsdfs_train_workspace_size", "render_rays_train",
+           "render_rays_backward_kept"]:
                 getattr(L, name).restype = C.c_int64
             L.tsdfs_bounds_workspace_size.argtypes = [C.c_int64]
             L.tsdfs_render_workspace_size.argtypes = [C.c_void_p, C.c_int64, C.c_int64]
@@ -94,6 +96,7 @@ def lib():
             L.tsdfs_raycast_workspace_size.argtypes = [C.c_void_p]
             L.tsdfs_hier_bounded_workspace_size.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_int64]
             L.tsdfs_backward_workspace_size.argtypes = [C.c_void_p, C.c_int64, C.c_int64]
+            L.tsdfs_train_workspace_size.argtypes = [C.c_void_p, C.c_int64, C.c_int64]
             L.tsdfs_packed_size.argtypes = [C.c_int32]
             L.tsdfs_sdf_param_count.argtypes = [C.c_int32]
             L.tsdfs_rgb_param_count.argtypes = [C.c_int32]
@@ -370,6 +373,29 @@ def render_rays_backward(mlp: "Mlp", ray_o, ray_d, t_n, t_f, offsets, status, ma
                                       _p(status), C.c_int64(n), C.c_int64(max_samples), _p(d_rgb), _p(d_depth),
                                       _p(d_eik), _p(d_sdf_w), _p(d_rgb_w), _p(workspace),
                                       C.c_size_t(workspace.numel()), _stream()))
+
+
+def tsdfs_train_workspace_size(mlp: "Mlp", n_rays: int, max_samples: int) -> int:
+    return int(lib().tsdfs_train_workspace_size(C.byref(mlp.c), C.c_int64(n_rays), C.c_int64(max_samples)))
+
+
+def render_rays_train(mlp: "Mlp", ray_o, ray_d, t_n, t_f, offsets, status, max_samples, rgb, depth, wsum, normal, eik,
+                      workspace):
+    """render_rays with the layer-major FP32 networks, keeping records and activations in
+    `workspace` for render_rays_backward_kept."""
+    n = ray_o.shape[0]
+    _check(lib().render_rays_train(C.byref(mlp.c), _p(ray_o), _p(ray_d), _p(t_n), _p(t_f), _p(offsets), _p(status),
+                                   C.c_int64(n), C.c_int64(max_samples), _p(rgb), _p(depth), _p(wsum), _p(normal),
+                                   _p(eik), _p(workspace), C.c_size_t(workspace.numel()), _stream()))
+
+
+def render_rays_backward_kept(mlp: "Mlp", ray_o, ray_d, t_n, t_f, offsets, status, max_samples, d_rgb, d_depth, d_eik,
+                              d_sdf_w, d_rgb_w, workspace):
+    n = ray_o.shape[0]
+    _check(lib().render_rays_backward_kept(C.byref(mlp.c), _p(ray_o), _p(ray_d), _p(t_n), _p(t_f), _p(offsets),
+                                           _p(status), C.c_int64(n), C.c_int64(max_samples), _p(d_rgb), _p(d_depth),
+                                           _p(d_eik), _p(d_sdf_w), _p(d_rgb_w), _p(workspace),
+                                           C.c_size_t(workspace.numel()), _stream()))
 
 
 def tsdfs_packed_size(arch: int) -> int:
@@ -657,9 +683,11 @@ class RenderFunction(torch.autograd.Function):
     forward(sdf_w, rgb_w, mlp, rays_o, rays_d, bounds, max_samples) -> (rgb, depth, eik)
     renders with ``mlp``'s architecture, precision and constants over the parameter
     tensors ``sdf_w`` / ``rgb_w`` themselves (read in place; 16-bit precisions pack them
-    on every call), so an optimizer stepping those tensors changes the next render;
-    backward calls render_rays_backward (FP32 networks, activations recomputed) at the
-    same tensors and returns their gradients.
+    on every call), so an optimizer stepping those tensors changes the next render.
+    With FP32 networks and the layer-major backward (the default) the forward is
+    render_rays_train and the backward render_rays_backward_kept over the workspace the
+    forward kept; otherwise the forward is render_rays and the backward calls
+    render_rays_backward (FP32 networks, activations recomputed) at the same tensors.
     """
 
     @staticmethod
@@ -667,13 +695,20 @@ class RenderFunction(torch.autograd.Function):
         n = rays_o.shape[0]
         m = mlp.with_params(sdf_w, rgb_w)
         out = RenderOut(n, device=rays_o.device)
+        ctx.b, ctx.max_samples = b, max_samples
+        ctx.save_for_backward(rays_o, rays_d)
+        if m.precision == TSDFS_PREC_F32 and tsdfs_backward_kernel() == TSDFS_BACKWARD_GEMM:
+            ws = _bytes(tsdfs_train_workspace_size(m, n, max_samples), rays_o.device)
+            render_rays_train(m, rays_o, rays_d, b.t_n, b.t_f, b.offsets, b.status, max_samples, out.rgb, out.depth,
+                              out.wsum, out.normal, out.eik, ws)
+            ctx.mlp, ctx.kept = m, ws
+            return out.rgb, out.depth, out.eik
         ws = _bytes(tsdfs_render_workspace_size(m, n, max_samples), rays_o.device)
         render_rays(m, rays_o, rays_d, b.t_n, b.t_f, b.offsets, b.status, max_samples, out.rgb, out.depth,
                     out.wsum, out.normal, out.eik, ws)
         # the backward runs the FP32 networks over the same parameter tensors
         ctx.mlp = m if m.precision == TSDFS_PREC_F32 else Mlp(mlp.spec, TSDFS_PREC_F32, sdf_w=sdf_w, rgb_w=rgb_w)
-        ctx.b, ctx.max_samples = b, max_samples
-        ctx.save_for_backward(rays_o, rays_d)
+        ctx.kept = None
         return out.rgb, out.depth, out.eik
 
     @staticmethod
@@ -683,9 +718,15 @@ class RenderFunction(torch.autograd.Function):
         n = rays_o.shape[0]
         d_sdf = torch.zeros_like(mlp.sdf_w)
         d_rgb = torch.zeros_like(mlp.rgb_w)
-        ws = _bytes(tsdfs_backward_workspace_size(mlp, n, ms), rays_o.device)
         gr = (g_rgb if g_rgb is not None else torch.zeros((n, 3), device=rays_o.device)).contiguous().float()
         gd = None if g_depth is None else g_depth.contiguous().float()
         ge = None if g_eik is None else g_eik.contiguous().float()
-        render_rays_backward(mlp, rays_o, rays_d, b.t_n, b.t_f, b.offsets, b.status, ms, gr, gd, ge, d_sdf, d_rgb, ws)
+        if ctx.kept is not None:
+            render_rays_backward_kept(mlp, rays_o, rays_d, b.t_n, b.t_f, b.offsets, b.status, ms, gr, gd, ge, d_sdf,
+                                      d_rgb, ctx.kept)
+            ctx.kept = None
+        else:
+            ws = _bytes(tsdfs_backward_workspace_size(mlp, n, ms), rays_o.device)
+            render_rays_backward(mlp, rays_o, rays_d, b.t_n, b.t_f, b.offsets, b.status, ms, gr, gd, ge, d_sdf, d_rgb,
+                                 ws)
         return d_sdf, d_rgb, None, None, None, None, None

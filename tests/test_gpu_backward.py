@@ -212,9 +212,16 @@ def test_autograd_function_matches_direct_call(precision):
     rgb_w = (mlp.rgb_w * (1.0 + 0.01 * torch.randn(mlp.rgb_w.shape, device="cuda", generator=g))).requires_grad_(True)
     ro, rd = dev(o), dev(d)
     rgb, depth, eik = T.RenderFunction.apply(sdf_w, rgb_w, mlp, ro, rd, bb, total)
-    # the same render through a descriptor built directly on the leaves' values
+    # the same render through a descriptor built directly on the leaves' values: the
+    # training forward for FP32 networks, render_rays for 16-bit ones
     ref = T.Mlp(spec, precision, sdf_w=sdf_w.detach().clone(), rgb_w=rgb_w.detach().clone())
-    out = T.Renderer(ref, len(o), total).render(ro, rd, bb)
+    if precision == T.TSDFS_PREC_F32:
+        out = T.RenderOut(len(o))
+        wst = torch.empty(T.tsdfs_train_workspace_size(ref, len(o), total), dtype=torch.uint8, device="cuda")
+        T.render_rays_train(ref, ro, rd, bb.t_n, bb.t_f, bb.offsets, bb.status, total, out.rgb, out.depth, out.wsum,
+                            out.normal, out.eik, wst)
+    else:
+        out = T.Renderer(ref, len(o), total).render(ro, rd, bb)
     torch.cuda.synchronize()
     assert torch.equal(rgb, out.rgb) and torch.equal(depth, out.depth)
     own = T.Renderer(mlp, len(o), total).render(ro, rd, bb)
@@ -258,3 +265,88 @@ def test_optimizer_step_on_the_leaves_changes_the_render():
     assert loss1.item() < loss0.item()
     # the descriptor's own copy is untouched
     assert torch.equal(mlp.sdf_w, torch.tensor(spec.packed("sdf"), device="cuda"))
+
+
+def train_call(spec, o, d, b, adj, max_samples=None, chunk=0):
+    """render_rays_train then render_rays_backward_kept over one workspace: outputs and gradients."""
+    T.tsdfs_set_backward_chunk(chunk)
+    n = len(o)
+    mlp = T.Mlp(spec)
+    bb, total = _bounds_of(o, b)
+    ms = total if max_samples is None else max_samples
+    out = T.RenderOut(n)
+    ws = torch.empty(max(T.tsdfs_train_workspace_size(mlp, n, ms), 1), dtype=torch.uint8, device="cuda")
+    ro, rd = dev(o), dev(d)
+    T.render_rays_train(mlp, ro, rd, bb.t_n, bb.t_f, bb.offsets, bb.status, ms, out.rgb, out.depth, out.wsum,
+                        out.normal, out.eik, ws)
+    d_sdf = torch.zeros_like(mlp.sdf_w)
+    d_rw = torch.zeros_like(mlp.rgb_w)
+    T.render_rays_backward_kept(mlp, ro, rd, bb.t_n, bb.t_f, bb.offsets, bb.status, ms, *[dev(a) for a in adj], d_sdf,
+                                d_rw, ws)
+    torch.cuda.synchronize()
+    fwd = {k: getattr(out, k).cpu().numpy() for k in ("rgb", "depth", "wsum", "normal", "eik")}
+    return fwd, (d_sdf.cpu().numpy(), d_rw.cpu().numpy())
+
+
+@pytest.mark.parametrize("scene,n_rays", [("tiny", 96), ("room", 48)])
+def test_train_forward_matches_oracle_and_render(scene, n_rays, restore_backward):
+    """The layer-major FP32 forward meets the FP32 render bars against the oracle and agrees
+    with the SIMT FP32 render far inside them."""
+    from test_gpu_render import DEPTH_REL_F32, compare, gpu_render, oracle_render
+    o, d, b = case(scene, n_rays, seed=48)
+    spec = synth.scene_mlp(scene)
+    fwd, _ = train_call(spec, o, d, b, seeded_adjoints(n_rays))
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == 0, bits
+    ref, _ = oracle_render(spec, o, d, b)
+    compare(fwd, ref, depth_rel=DEPTH_REL_F32)
+    simt = gpu_render(spec, o, d, b)
+    assert np.max(np.abs(fwd["rgb"] - simt["rgb"])) < 1e-4
+    assert np.max(np.abs(fwd["eik"] - simt["eik"])) <= 1e-4 * max(1.0, np.abs(simt["eik"]).max())
+
+
+@pytest.mark.parametrize("scene,n_rays,chunk", [("tiny", 96, 0), ("room", 48, 0), ("tiny", 96, 37), ("room", 48, 71)])
+def test_kept_backward_equals_backward(scene, n_rays, chunk, restore_backward):
+    """render_rays_backward_kept after render_rays_train returns exactly the gradients of a
+    render_rays_backward call on the same inputs, in one chunk and in several."""
+    o, d, b = case(scene, n_rays, seed=49)
+    spec = synth.scene_mlp(scene)
+    adj = seeded_adjoints(n_rays, 11)
+    _, kept = train_call(spec, o, d, b, adj, chunk=chunk)
+    direct = gpu_grads(spec, o, d, b, *adj, chunk=chunk)
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == 0, bits
+    assert np.array_equal(kept[0], direct[0]) and np.array_equal(kept[1], direct[1])
+
+
+def test_train_forward_overflow_zeroes_outputs(restore_backward):
+    o, d, b = case("tiny", 64, seed=50)
+    total = int(b["n"].sum())
+    fwd, grads = train_call(synth.scene_mlp("tiny"), o, d, b, seeded_adjoints(64), max_samples=total - 1)
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == T.TSDFS_E_DEVICE and bits & T.TSDFS_DEV_SAMPLES_OVERFLOW
+    assert not fwd["rgb"].any() and not fwd["wsum"].any()
+    assert not grads[0].any() and not grads[1].any()
+
+
+def test_nonfinite_parameter_flagged(restore_backward):
+    """The layer-major GEMMs assume finite operands: a NaN or an infinity planted in the
+    parameters is reported as TSDFS_DEV_NONFINITE, and the context stays usable."""
+    o, d, b = case("tiny", 32, seed=51)
+    spec = synth.scene_mlp("tiny")
+    adj = seeded_adjoints(32, 12)
+    for bad in (float("nan"), float("inf")):
+        mlp = T.Mlp(spec)
+        mlp.sdf_w[7] = bad
+        bb, total = _bounds_of(o, b)
+        d_sdf = torch.zeros_like(mlp.sdf_w)
+        d_rw = torch.zeros_like(mlp.rgb_w)
+        ws = torch.empty(T.tsdfs_backward_workspace_size(mlp, len(o), total), dtype=torch.uint8, device="cuda")
+        T.render_rays_backward(mlp, dev(o), dev(d), bb.t_n, bb.t_f, bb.offsets, bb.status, total,
+                               *[dev(a) for a in adj], d_sdf, d_rw, ws)
+        rc, bits = T.tsdfs_sync_status()
+        assert rc == T.TSDFS_E_DEVICE and bits & T.TSDFS_DEV_NONFINITE
+    good = gpu_grads(spec, o, d, b, *adj)
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == 0, bits
+    assert np.isfinite(good[0]).all() and np.abs(good[0]).max() > 0
