@@ -118,6 +118,12 @@ def parse():
                                                                    "training legs)")
     ap.add_argument("--only-main", action="store_true", help="time the render path only (no e2e / comparator / "
                                                                   "quality / cpu / training legs): the small profiling case")
+    ap.add_argument("--train-only", action="store_true",
+                    help="one training step in an NVTX range 'timed' (autograd on the calling thread), on the grid "
+                         "fused from the analytic depth maps: the profiling case of the training step")
+    ap.add_argument("--train-rays", type=int, default=8192, help="rays of the --train-only step")
+    ap.add_argument("--train-chunk", type=int, default=0,
+                    help="samples per chunk of the layer-major backward in the --train-only step (0: default)")
     ap.add_argument("--ref-rays", type=int, default=2048, help="rays per reference-arm step")
     ap.add_argument("--ds-vox", type=float, default=1.0, help="D_s of Alg. 1 in voxels (Sec. 4.2 uses 1)")
     ap.add_argument("--m-confirm", type=int, default=None, help="M of Alg. 1 (Sec. 4.2 uses 15)")
@@ -731,7 +737,7 @@ def backward_gemm_flops(spec):
     return {"forward": fwd, "weight_grad": fwd, "input_adjoint": fwd - first}
 
 
-def run_train(spec, wl, grid, mask, dev, n_rays=8192, iters=5, kind=None, peak_bf16=None):
+def run_train(spec, wl, grid, mask, dev, n_rays=8192, iters=5, kind=None, peak_bf16=None, nvtx=False):
     """One training step of the networks (FP32): n_rays random rays of the training
     views, bounds, render through the autograd op, L1 colour + 0.1 eikonal on the
     bounded samples, backward (render_rays_backward with the given implementation)."""
@@ -764,6 +770,12 @@ def run_train(spec, wl, grid, mask, dev, n_rays=8192, iters=5, kind=None, peak_b
         for _ in range(2):
             step()
         torch.cuda.synchronize()
+        if nvtx:
+            with torch.autograd.set_multithreading_enabled(False):
+                torch.cuda.nvtx.range_push("timed")
+                step()
+                torch.cuda.nvtx.range_pop()
+            torch.cuda.synchronize()
         import ctypes as C
         T.lib().tsdfs_profile(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -811,6 +823,27 @@ def run_train(spec, wl, grid, mask, dev, n_rays=8192, iters=5, kind=None, peak_b
                            "peak_kind": "measured bf16 dense peak / 9 (each FP32 operand as three BF16 parts, nine "
                                         "products per FP32 product)"}
     return out
+
+
+def run_train_only(args):
+    """The profiling case of the training step: two warm-up steps, then one step inside an
+    NVTX range named 'timed' with autograd on the calling thread (so the backward's kernels
+    fall inside the range), on the room grid fused from the 100 analytic depth maps."""
+    import torch
+    from paper_2311_17878_gb300 import build, synth
+    from paper_2311_17878_gb300 import tsdfs as T
+    build.build()
+    dev = "cuda"
+    wl = synth.room_workload_torch(device=dev)
+    grid = T.Grid(wl.grid, device=dev).init()
+    grid.integrate(wl.views.depth.contiguous(), torch.tensor(wl.views.K, device=dev),
+                   torch.tensor(wl.views.c2w, device=dev))
+    mask = grid.inside_mask(wl.bounds.nb_radius)
+    T.tsdfs_set_backward_chunk(args.train_chunk)
+    try:
+        return run_train(synth.scene_mlp("room"), wl, grid, mask, dev, n_rays=args.train_rays, iters=1, nvtx=True)
+    finally:
+        T.tsdfs_set_backward_chunk(0)
 
 
 def run_e2e(args, grid, mask, bp, bounds, rend, rays, n, dev, flush):
@@ -1297,6 +1330,9 @@ def main():
         line = run_reference(args, ws, rank)
         if line is not None:
             print(json.dumps(line), flush=True)
+        return
+    if args.train_only:
+        print(json.dumps(run_train_only(args)), flush=True)
         return
     ws, rank, local = dist_setup()
     line = run_ours(args, ws, rank, local)
