@@ -444,8 +444,11 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                     const float sc = ly.idx + 1 == A::kSkip ? kInvSqrt2 : 1.0f;
                     const uint32_t row0 = smem_u32(A0) + a_off(32 * q + lane, 0, Kn);
                     const uint32_t row1 = smem_u32(A1) + a_off(32 * q + lane, 0, Kn);
-                    const int c_lo = part8_lo(Kn, pt, kPartsF), c_hi = part8_hi(Kn, pt, kPartsF);
-                    const int c_full = (ly.N / 16) * 16 < c_hi ? (ly.N / 16) * 16 : c_hi;
+                    // the columns below c_fa (whole 16-column blocks of hidden units) are split
+                    // among the three parts; the slower tail groups above it (hidden units
+                    // < N mixed with the skip input's encoding) go round-robin to the parts
+                    const int c_fa = (ly.N / 16) * 16 < Kn ? (ly.N / 16) * 16 : Kn;
+                    const int c_lo = part8_lo(c_fa, pt, kPartsF), c_full = part8_hi(c_fa, pt, kPartsF);
                     // 8-column groups, software-pipelined: the TMEM loads of group c + 8 are in
                     // flight while group c is computed.  buf = [value(4) | d/dx(4) | d/dy(4) | d/dz(4)],
                     // each 4 = (sample a, col 0), (a, col 1), (b, col 0), (b, col 1)
@@ -525,7 +528,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                     const float* sxb = sxa + 8 * 8;
                     const float* spa = s_pe + (16 * q + fs) * A::kPeSdf * 6;
                     const float* spb = spa + 8 * A::kPeSdf * 6;
-                    for (int c8 = c_full > c_lo ? c_full : c_lo; c8 < c_hi; c8 += 8) {
+                    for (int c8 = c_fa + 8 * pt; c8 < Kn; c8 += 8 * kPartsF) {
                         float d[16];   // [value(4) | d/dx(4) | d/dy(4) | d/dz(4)], as ld8
 #pragma unroll
                         for (int j = 0; j < 16; ++j) d[j] = 0.0f;
