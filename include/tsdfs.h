@@ -11,9 +11,13 @@
  * Conventions for every entry point:
  *  - Pointers named in a struct or argument are DEVICE pointers unless the
  *    comment says "host".  The caller owns every buffer; the library
- *    allocates and frees nothing (no cudaMalloc / cudaFree anywhere).
+ *    allocates and frees nothing itself (no cudaMalloc / cudaFree in it; the
+ *    layer-major backward's first call on a device creates a cuBLAS handle,
+ *    whose state cuBLAS allocates).
  *  - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL = the
- *    legacy default stream).  Arguments are checked on the host before any
+ *    legacy default stream); the calls that synchronise say so (the autotuners,
+ *    the layer-major backward and training forward, which read the sample
+ *    total, and the FP64 harness).  Arguments are checked on the host before any
  *    launch; a check failure returns a negative TSDFS_E_* code, enqueues
  *    nothing and records a message for tsdfs_last_error().
  *  - Kernels never trap.  Conditions that only the device can see (a sample
