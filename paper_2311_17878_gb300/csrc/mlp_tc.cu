@@ -261,27 +261,47 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                         const int kc = ci.kc_keep & 0x7fff;
                         const uint32_t b0 = slot_addr(s);
                         const uint32_t b_sbo = (uint32_t)(kc / 8) * 128u;
-                        for (int kk = 0; kk < kc / 16; ++kk) {
-                            const int k = c * kKChunk + kk * 16;
-                            const uint32_t acc = k > 0 ? 1u : 0u;
-                            const uint64_t bd = mdesc(b0 + kk * 256, 128, b_sbo);
-                            const uint64_t ad0 = mdesc(a0 + (uint32_t)(k / 8) * 128u, 128, a_sbo);
-                            if (ly.sdf) {
-                                const uint64_t ad1 = mdesc(a1 + (uint32_t)(k / 8) * 128u, 128, a_sbo);
-                                if (!last_sdf) {
-                                    mma_bf16(tmem, ad0, bd, idesc_mma<F16>(128, ly.Np), acc);
-                                    mma_bf16(tmem + 256, ad1, bd, idesc_mma<F16>(128, ly.Np), acc);
-                                } else {
-                                    const int n0 = ly.Np < 256 ? ly.Np : 256;
-                                    mma_bf16(tmem, ad0, bd, idesc_mma<F16>(128, n0), acc);
-                                    mma_bf16(tmem + 256, ad1, bd, idesc_mma<F16>(128, 16), acc);
-                                    if (ly.Np > 256) {
-                                        const uint64_t bx = mdesc(b0 + kk * 256 + (256 / 8) * b_sbo, 128, b_sbo);
-                                        mma_bf16(tmem + 256 + 16, ad0, bx, idesc_mma<F16>(128, ly.Np - 256), acc);
-                                    }
-                                }
-                            } else {
-                                mma_bf16(tmem, ad0, bd, idesc_mma<F16>(128, ly.Np), acc);
+                        const int k0 = c * kKChunk;
+                        const int nk = kc / 16;
+                        // descriptors of the chunk's first K step; each further step of 16
+                        // columns moves both operands by two 8x8 core matrices (256 bytes,
+                        // 16 in the descriptor's address field, which stays below 2^14 for
+                        // any shared-memory address), so the loop only adds
+                        uint64_t bd = mdesc(b0, 128, b_sbo);
+                        uint64_t ad0 = mdesc(a0 + (uint32_t)(k0 / 8) * 128u, 128, a_sbo);
+                        if (ly.sdf && !last_sdf) {
+                            uint64_t ad1 = mdesc(a1 + (uint32_t)(k0 / 8) * 128u, 128, a_sbo);
+                            const uint32_t id = idesc_mma<F16>(128, ly.Np);
+                            for (int kk = 0; kk < nk; ++kk) {
+                                const uint32_t acc = (k0 | kk) != 0 ? 1u : 0u;
+                                mma_bf16(tmem, ad0, bd, id, acc);
+                                mma_bf16(tmem + 256, ad1, bd, id, acc);
+                                ad0 += 16;
+                                ad1 += 16;
+                                bd += 16;
+                            }
+                        } else if (ly.sdf) {
+                            uint64_t ad1 = mdesc(a1 + (uint32_t)(k0 / 8) * 128u, 128, a_sbo);
+                            uint64_t bx = mdesc(b0 + (256 / 8) * b_sbo, 128, b_sbo);
+                            const uint32_t id0 = idesc_mma<F16>(128, ly.Np < 256 ? ly.Np : 256);
+                            const uint32_t id1 = idesc_mma<F16>(128, 16);
+                            const uint32_t idx = idesc_mma<F16>(128, ly.Np > 256 ? ly.Np - 256 : 16);
+                            for (int kk = 0; kk < nk; ++kk) {
+                                const uint32_t acc = (k0 | kk) != 0 ? 1u : 0u;
+                                mma_bf16(tmem, ad0, bd, id0, acc);
+                                mma_bf16(tmem + 256, ad1, bd, id1, acc);
+                                if (ly.Np > 256) mma_bf16(tmem + 256 + 16, ad0, bx, idx, acc);
+                                ad0 += 16;
+                                ad1 += 16;
+                                bd += 16;
+                                bx += 16;
+                            }
+                        } else {
+                            const uint32_t id = idesc_mma<F16>(128, ly.Np);
+                            for (int kk = 0; kk < nk; ++kk) {
+                                mma_bf16(tmem, ad0, bd, id, (k0 | kk) != 0 ? 1u : 0u);
+                                ad0 += 16;
+                                bd += 16;
                             }
                         }
                         // release the slot, except the A1 slot after its last colour chunk of the
