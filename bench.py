@@ -52,10 +52,11 @@ MARCH_TRAFFIC = {"sha256": "c4307e3a56049f67dc00d5274645fbd858f05161b8c533815f88
                  "profile": "profiles/k_ray_bounds_room_view_traffic.md"}
 ALGO_FLOP_PER_SAMPLE = 2.25e6   # SDF fwd + minimal reverse-mode grad + colour, 8x256 / 4x256 networks
 # what the tensor-core kernels issue per sample (value + 3 tangent rows through the SDF layers):
-# serial, 64-sample tiles: M = 128 colour MMAs with 64 live rows; pipelined, 32-sample tiles:
-# 4 rows per sample through both networks (M = 128 colour MMAs with 32 live rows), the SDF MMAs
-# twice with split operands
-EXEC_FLOP_PER_SAMPLE = {"serial": 4.75e6, "pipelined": 5.93e6, "pipelined-split": 9.63e6}
+# serial, 64-sample tiles: 4 rows per sample through SDF layers 0-6, the folded output layer's
+# value column (N = 16), M = 128 colour MMAs with 64 live rows (the folded first colour layer
+# with K = 256 + 48); pipelined, 32-sample tiles: 4 rows per sample through both networks
+# (M = 128 colour MMAs with 32 live rows), the SDF MMAs twice with split operands
+EXEC_FLOP_PER_SAMPLE = {"serial": 4.33e6, "pipelined": 5.93e6, "pipelined-split": 9.63e6}
 N_VIEWS_TIMED = 10   # views cycled by the timed steps (4 for the panorama workload)
 QUALITY_PIXELS = 4096          # seeded pixels spread over every timed view (synth.quality_pixels)
 QUALITY_PIXELS_LIVE = 1024     # when the dense reference is rendered during the run (panorama workload)

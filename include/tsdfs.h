@@ -494,7 +494,15 @@ int render_rays_backward_kept(const tsdfs_mlp* mlp, const float* ray_o, const fl
  * tsdfs_pack_mlp converts sdf_w / rgb_w to the 16-bit K-major tiles the
  * tcgen05 path reads -- bf16, or fp16 when mlp->precision is TSDFS_PREC_F16 --
  * rounded to nearest even, into `packed` (device, tsdfs_packed_size bytes,
- * 16-byte aligned).  Repeat after every parameter update.                    */
+ * 16-byte aligned).  Repeat after every parameter update.  Layout: every
+ * layer of both networks in order, each padded to 16 rows and columns and cut
+ * into 64-column chunks of 8x8 core matrices; then the serial kernel's two
+ * folded layers (the SDF output layer's value row net_0, and the first colour
+ * layer applied to [h, x~, direction encoding, unit normal] with h the last
+ * hidden SDF activation: weights [W_c,feat W_f | W_c,x | W_c,dir | W_c,n],
+ * the product summed in FP32 and then rounded), and their FP32 biases
+ * (b_f,0, and b_c + W_c,feat b_f), 16-byte aligned.  The folding is exact in
+ * real arithmetic: the features enter the colour network linearly.          */
 /* ---- FP64 finite-difference harness of render_rays_backward (test use) ----
  * The bounded render of render_rays (same inputs: rays, [t_n, t_f], offsets,
  * status; midpoint samples; both networks with the SDF gradient; the network's

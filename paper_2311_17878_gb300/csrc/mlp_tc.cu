@@ -12,7 +12,12 @@
 // the epilogue in the no-swizzle K-major core-matrix layout; weights are
 // pre-packed in the same layout (tsdfs_pack_mlp) and streamed chunk by chunk
 // (kKChunk columns of K) with 1-D bulk TMA copies through a kStages-deep ring.
-// The colour network reuses acc0 with the value rows only.
+// The colour network reuses acc0 with the value rows only.  The full kernel runs the
+// folded tables of tc_common.cuh (TcArch<ARCH, true>): the SDF output layer computes only
+// net_0 (N = 16 MMAs on both accumulators, for f and grad f), and the first colour layer
+// multiplies the last hidden SDF activation h, still in A0 as that layer's input, by the
+// folded weights W_c,feat W_f, with x~, the direction encoding and the unit normal in a
+// small block at the start of A1; the 256 feature columns are never formed.
 //
 // The full kernel (SDF value, gradient and colour): 16 warps, one persistent CTA per SM.
 // Warps 0-11 are the epilogue (warp w: TMEM lane quarter w % 4, column part w / 4 of three),
@@ -58,13 +63,15 @@ static_assert(!kA1Slots || kStages == 2, "the A1 weight slot assumes the 2-stage
 constexpr uint32_t kABytes = 64 * 1024;   // one A region (128 rows x 256 bf16)
 
 // the full kernel's own sizes on top of the layer tables
-template <int ARCH> struct TcFull : TcArch<ARCH> {
-    using TcArch<ARCH>::layer;
-    using TcArch<ARCH>::kLayers;
-    using TcArch<ARCH>::stage_bytes;
-    using TcArch<ARCH>::bias_bytes;
-    using TcArch<ARCH>::chunk_tab_bytes;
-    using TcArch<ARCH>::max_rgb_chunk_bytes;
+template <int ARCH> struct TcFull : TcArch<ARCH, true> {
+    using Base = TcArch<ARCH, true>;
+    using Base::layer;
+    using Base::kLayers;
+    using Base::kXp;
+    using Base::stage_bytes;
+    using Base::bias_bytes;
+    using Base::chunk_tab_bytes;
+    using Base::max_rgb_chunk_bytes;
     using A = Arch<ARCH>;
     // per-tile sample table of the full kernel (coordinates, direction, t, delta, encodings)
     __host__ __device__ static constexpr uint32_t table_bytes() {
@@ -74,16 +81,10 @@ template <int ARCH> struct TcFull : TcArch<ARCH> {
         return 2 * (size_t)kABytes + kStages * (size_t)stage_bytes() + bias_bytes() + kBarBytes + table_bytes() +
                chunk_tab_bytes();
     }
-    // bytes of the A1 region the colour layers' input rows spill into (A0 holds 128 rows of
-    // 256 columns; a wider colour input continues into A1), rounded up to 1 KB
-    __host__ __device__ static constexpr uint32_t a1_spill() {
-        int64_t m = 0;
-        for (int l = A::kSdfLayers; l < kLayers; ++l) {
-            const int64_t b = 256 * (int64_t)layer(l).Kp - (int64_t)kABytes;
-            m = b > m ? b : m;
-        }
-        return (uint32_t)((m + 1023) / 1024 * 1024);
-    }
+    // bytes at the start of A1 holding the folded colour input's x~ / direction / normal
+    // columns (128 rows of kXp columns; its h columns are the last SDF layer's input rows in
+    // A0), rounded up to 1 KB
+    __host__ __device__ static constexpr uint32_t a1_spill() { return (uint32_t)((128 * kXp * 2 + 1023) / 1024 * 1024); }
     // weight slots that fit in the rest of A1 while the colour layers run (at most one)
     __host__ __device__ static constexpr int a1_slots() {
         const int64_t n = ((int64_t)kABytes - a1_spill()) / max_rgb_chunk_bytes();
@@ -174,24 +175,27 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         // the tile's chunk schedule, computed once (the producers and the MMA warp read it
         // instead of re-deriving offsets and slots in their loops)
-        uint32_t off = 0;
         for (int L = 0, j = 0; L < NL; ++L)
             for (int c = 0; c < TA::chunks(L); ++c, ++j) {
                 const uint32_t sl = slot_of(L, c);
                 const bool keep = sl >= (uint32_t)kStages && j - TA::sdf_chunks() + kColSlots >= TA::rgb_chunks();
-                s_chunks[j] = ChunkInfo{off, (uint32_t)TA::chunk_bytes(L, c), (uint16_t)sl,
+                s_chunks[j] = ChunkInfo{(uint32_t)TA::packed_offset(L, c), (uint32_t)TA::chunk_bytes(L, c), (uint16_t)sl,
                                         (uint16_t)(TA::chunk_k(L, c) | (keep ? 0x8000 : 0))};
-                off += (uint32_t)TA::chunk_bytes(L, c);
             }
     }
-    // all biases of both networks, staged once
+    // all biases of both networks, staged once (the two folded layers' from the packed buffer)
     for (int i = threadIdx.x; i < TA::bias_total(); i += kThreadsF) {
         int L = 0;
         while (L + 1 < NL && TA::bias_offset(L + 1) <= i) ++L;
         const TcLayer ly = TA::layer(L);
-        const float* W = (ly.sdf ? p.sdf_w : p.rgb_w) + TA::param_offset(L);
         const int j = i - TA::bias_offset(L);
-        sbias[i] = j < ly.N ? __ldg(W + (int64_t)ly.N * ly.K + j) : 0.0f;
+        if (TA::folded(L)) {
+            const float* fb = reinterpret_cast<const float*>(p.packed + TA::fold_bias_offset());
+            sbias[i] = __ldg(fb + (L == LS ? TA::layer(LS - 1).Np : 0) + j);
+        } else {
+            const float* W = (ly.sdf ? p.sdf_w : p.rgb_w) + TA::param_offset(L);
+            sbias[i] = j < ly.N ? __ldg(W + (int64_t)ly.N * ly.K + j) : 0.0f;
+        }
     }
     if (warp == kMmaWarpF) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -268,7 +272,12 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                         // 16 in the descriptor's address field, which stays below 2^14 for
                         // any shared-memory address), so the loop only adds
                         uint64_t bd = mdesc(b0, 128, b_sbo);
+                        // the folded colour input: its h chunks are the last SDF layer's input rows
+                        // in A0 (that layer's layout), its x~ / direction / normal chunk starts A1
                         uint64_t ad0 = mdesc(a0 + (uint32_t)(k0 / 8) * 128u, 128, a_sbo);
+                        if (!ly.sdf && ly.idx == 0)
+                            ad0 = k0 < TA::kH ? mdesc(a0 + (uint32_t)(k0 / 8) * 128u, 128, (TA::kH / 8) * 128u)
+                                              : mdesc(a1 + (uint32_t)((k0 - TA::kH) / 8) * 128u, 128, (TA::kXp / 8) * 128u);
                         if (ly.sdf && !last_sdf) {
                             uint64_t ad1 = mdesc(a1 + (uint32_t)(k0 / 8) * 128u, 128, a_sbo);
                             const uint32_t id = idesc_mma<F16>(128, ly.Np);
@@ -607,17 +616,11 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                                   pack2<F16>(zv[0], zv[1]), pack2<F16>(zv[2], zv[3]));
                     }
                 } else if (ly.sdf) {
-                    // ---- output layer: f, grad f, feature -> colour input rows ----
-                    // colour row: [x~ (3), direction encoding, unit normal (3), feature, 0 pad];
-                    // output oc >= 1 (feature oc - 1) sits at colour column oc + kD
+                    // ---- SDF output layer, folded to its value column: f and grad f from column 0
+                    // of both accumulators, then the folded colour input's x~ / direction / normal
+                    // columns at the start of A1 (its h columns are this layer's input rows in A0) ----
                     constexpr int kDir = A::kDirEnc;
-                    constexpr int kFeatCol = 3 + kDir + 3;
-                    constexpr int kD = kFeatCol - 1;
-                    constexpr int kOff = (16 - kD % 16) % 16;
-                    constexpr int kPrefix = (kFeatCol + 15) / 16;  // blocks holding x~, dir, normal
-                    const int Kc = TA::layer(L + 1).Kp;
-                    float n_hat[3] = {0.0f, 0.0f, 0.0f};
-                    float venc[kDir];
+                    constexpr int kXp = TA::kXp;
                     if (pt == 0) {
                         float x0[16], x1[16];
                         tmem_ld16(tmem + lane_addr, x0);
@@ -626,6 +629,8 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                         const float gx = __shfl_sync(0xffffffffu, x0[0], val_lane + 16);
                         const float gz = __shfl_sync(0xffffffffu, x1[0], val_lane + 16);
                         const float gy = x1[0];
+                        float n_hat[3] = {0.0f, 0.0f, 0.0f};
+                        float venc[kDir];
                         f_out = p.scale * (x0[0] + bias[0]);
                         gn_out = sqrtf(gx * gx + gy * gy + gz * gz);
                         const float inv = gn_out > 0.0f ? 1.0f / gn_out : 0.0f;
@@ -637,50 +642,21 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                         rec_dl = s_x[s * 8 + 7];
 #pragma unroll
                         for (int e = 0; e < kDir; ++e) venc[e] = enc_tab(ds, s_pd + s * A::kPeDir * 6, A::kPeDir, e, 0);
-                    }
-                    auto feature_block = [&](int c0, float (&o)[16], bool prefix) {
-                        const int w0 = c0 - kD - kOff;   // 16-aligned output block behind column c0 + kOff
-                        float xa[16], xb[16];
+                        // value rows: [x~ (3), direction encoding, unit normal (3), 0 pad]; the
+                        // other rows (tangent rows, whose colour outputs are not read) zero
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) { xa[j] = 0.0f; xb[j] = 0.0f; }
-                        if (w0 >= 0) tmem_ld16(tmem + lane_addr + (w0 < 256 ? w0 : w0 + 16), xa);
-                        if (kOff != 0) tmem_ld16(tmem + lane_addr + (w0 + 16 < 256 ? w0 + 16 : w0 + 32), xb);
-                        tmem_wait_ld();
+                        for (int c0 = 0; c0 < kXp; c0 += 8) {
+                            float o[8];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int col = c0 + j;
-                            const int idx = j + kOff;
-                            const float acc = idx < 16 ? xa[idx < 16 ? idx : 0] : xb[idx >= 16 ? idx - 16 : 0];
-                            const bool feat = col >= kFeatCol && col < kFeatCol + A::kFeat;
-                            o[j] = feat ? acc + bias[feat ? col - kD : 0] : 0.0f;
-                            if (prefix) {
-                                if (col < 3) o[j] = s_x[s * 8 + (col < 3 ? col : 0)];
-                                else if (col < 3 + kDir) o[j] = venc[col - 3 < kDir ? col - 3 : 0];
-                                else if (col < kFeatCol) o[j] = n_hat[col - 3 - kDir < 3 ? col - 3 - kDir : 0];
+                            for (int j = 0; j < 8; ++j) {
+                                const int col = c0 + j;
+                                float v = 0.0f;
+                                if (col < 3) v = s_x[s * 8 + (col < 3 ? col : 0)];
+                                else if (col < 3 + kDir) v = venc[col - 3 < kDir ? col - 3 : 0];
+                                else if (col < 3 + kDir + 3) v = n_hat[col - 3 - kDir < 3 ? col - 3 - kDir : 0];
+                                o[j] = is_val ? v : 0.0f;
                             }
-                        }
-                    };
-                    // part 0 writes the prefix blocks (x~, direction, normal); every part
-                    // writes the feature blocks of its column range beyond them
-                    const int lo = part_lo(Kc, pt, kPartsF), hi = part_hi(Kc, pt, kPartsF);
-                    const int c_start = lo > 16 * kPrefix ? lo : 16 * kPrefix;
-                    if (pt == 0) {
-#pragma unroll
-                        for (int pb = 0; pb < kPrefix; ++pb) {
-                            float o[16];
-                            feature_block(16 * pb, o, true);
-                            if (is_val) {
-                                st_row8<F16>(A0, r, 16 * pb, Kc, o);
-                                st_row8<F16>(A0, r, 16 * pb + 8, Kc, o + 8);
-                            }
-                        }
-                    }
-                    for (int c0 = c_start; c0 < hi; c0 += 16) {
-                        float o[16];
-                        feature_block(c0, o, false);
-                        if (is_val) {
-                            st_row8<F16>(A0, r, c0, Kc, o);
-                            st_row8<F16>(A0, r, c0 + 8, Kc, o + 8);
+                            st_row8<F16>(A1, r, c0, kXp, o);
                         }
                     }
                 } else if (!last) {
@@ -1036,6 +1012,81 @@ __global__ void k_pack(const float* __restrict__ sdf_w, const float* __restrict_
     }
 }
 
+// ---- the serial kernel's folded layers: the SDF output layer's value row, and the first
+// colour layer on [h, x~, direction, normal] with W_c,feat W_f (FP32 sums, then rounded like
+// every packed weight) and the FP32 biases of both ----
+template <int ARCH, bool F16>
+__global__ void k_pack_fold(const float* __restrict__ sdf_w, const float* __restrict__ rgb_w, uint8_t* __restrict__ out,
+                            uint32_t* status) {
+    using TF = TcArch<ARCH, true>;
+    using A = Arch<ARCH>;
+    constexpr int LS = A::kSdfLayers;
+    constexpr Layer lo = A::sdf(LS - 1), c0 = A::rgb(0);
+    const float* Wo = sdf_w + sdf_layer_offset<ARCH>(LS - 1);   // [1 + feat][kH], then its bias
+    const float* bo = Wo + (int64_t)lo.out * lo.in;
+    const float* Wc = rgb_w + rgb_layer_offset<ARCH>(0);         // [out][kX + feat], then its bias
+    const float* bc = Wc + (int64_t)c0.out * c0.in;
+    constexpr int kFeat = A::kFeat;
+    const int64_t base = TF::packed_offset(LS - 1, 0);
+    const int64_t n_w = (TF::layer_bytes(LS - 1) + TF::layer_bytes(LS)) / 2;
+    const int64_t n_b = TF::fold_bias_count();
+    uint16_t* out16 = reinterpret_cast<uint16_t*>(out + base);
+    float* fb = reinterpret_cast<float*>(out + TF::fold_bias_offset());
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_w + n_b; e += (int64_t)gridDim.x * blockDim.x) {
+        if (e >= n_w) {
+            // biases: the value column's, then the folded colour layer's
+            const int i = (int)(e - n_w);
+            float v = 0.0f;
+            if (i < TF::layer(LS - 1).Np) {
+                v = i == 0 ? bo[0] : 0.0f;
+            } else {
+                const int n = i - TF::layer(LS - 1).Np;
+                if (n < c0.out) {
+                    float acc = bc[n];
+                    for (int j = 0; j < kFeat; ++j) acc = fmaf(Wc[(int64_t)n * c0.in + TF::kX + j], bo[1 + j], acc);
+                    v = acc;
+                }
+            }
+            if (!isfinite(v)) set_status(status, TSDFS_DEV_NONFINITE);
+            fb[i] = v;
+            continue;
+        }
+        // locate the layer and chunk holding element e of the folded weights
+        const int L = e < TF::layer_bytes(LS - 1) / 2 ? LS - 1 : LS;
+        int64_t w = L == LS - 1 ? e : e - TF::layer_bytes(LS - 1) / 2;
+        int c = 0;
+        while (c + 1 < TF::chunks(L) && w >= TF::chunk_bytes(L, c) / 2) {
+            w -= TF::chunk_bytes(L, c) / 2;
+            ++c;
+        }
+        const int kc = TF::chunk_k(L, c);
+        const int core = (int)(w / 64), within = (int)(w % 64);
+        const int n = (core / (kc / 8)) * 8 + within / 8;
+        const int k = c * kKChunk + (core % (kc / 8)) * 8 + within % 8;
+        float v = 0.0f;
+        if (L == LS - 1) {
+            if (n == 0 && k < lo.in) v = Wo[k];
+        } else if (n < c0.out) {
+            if (k < TF::kH) {
+                float acc = 0.0f;
+                for (int j = 0; j < kFeat; ++j)
+                    acc = fmaf(Wc[(int64_t)n * c0.in + TF::kX + j], Wo[(int64_t)(1 + j) * lo.in + k], acc);
+                v = acc;
+            } else if (k - TF::kH < TF::kX) {
+                v = Wc[(int64_t)n * c0.in + (k - TF::kH)];
+            }
+        }
+        if (!isfinite(v)) set_status(status, TSDFS_DEV_NONFINITE);
+        if constexpr (F16) {
+            __half h = __float2half_rn(v);
+            out16[e] = *reinterpret_cast<uint16_t*>(&h);
+        } else {
+            __nv_bfloat16 h = __float2bfloat16_rn(v);
+            out16[e] = *reinterpret_cast<uint16_t*>(&h);
+        }
+    }
+}
+
 template <int ARCH, bool F16>
 int launch_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64_t max_samples, cudaStream_t st) {
     using TA = TcFull<ARCH>;
@@ -1094,9 +1145,11 @@ int launch_mlp_value_tc(const tsdfs_mlp* m, const SampleSource& src, float* f_ou
                : launch_tc_value<TSDFS_ARCH_ROOM, false>(m, src, f_out, st);
 }
 
+// the whole packed buffer: the unfolded layers (read by every tensor-core kernel), then the
+// serial kernel's folded layers and their biases
 int64_t packed_bytes(int arch) {
-    return arch == TSDFS_ARCH_TINY ? TcArch<TSDFS_ARCH_TINY>::packed_bytes()
-                                   : (arch == TSDFS_ARCH_ROOM ? TcArch<TSDFS_ARCH_ROOM>::packed_bytes() : 0);
+    return arch == TSDFS_ARCH_TINY ? TcArch<TSDFS_ARCH_TINY, true>::packed_bytes()
+                                   : (arch == TSDFS_ARCH_ROOM ? TcArch<TSDFS_ARCH_ROOM, true>::packed_bytes() : 0);
 }
 
 }  // namespace tsdfs
@@ -1109,17 +1162,31 @@ extern "C" int tsdfs_pack_mlp(const tsdfs_mlp* m, void* packed, tsdfs_stream_t s
     if (!m || !packed || !m->sdf_w || !m->rgb_w) return fail(TSDFS_E_INVALID, "mlp, its weights and packed must be non-NULL");
     if (m->arch != TSDFS_ARCH_TINY && m->arch != TSDFS_ARCH_ROOM) return fail(TSDFS_E_INVALID, "unknown arch %d", m->arch);
     if ((reinterpret_cast<uintptr_t>(packed) & 15u) != 0) return fail(TSDFS_E_INVALID, "packed must be 16-byte aligned");
-    const int64_t n = packed_bytes(m->arch) / 2;
+    const bool tiny = m->arch == TSDFS_ARCH_TINY;
+    const int64_t plain = tiny ? TcArch<TSDFS_ARCH_TINY>::packed_bytes() : TcArch<TSDFS_ARCH_ROOM>::packed_bytes();
+    const int64_t n = plain / 2, nf = (packed_bytes(m->arch) - plain) / 2;
     cudaStream_t st = (cudaStream_t)stream;
     ProfScope ps("pack", st);
     uint16_t* out = static_cast<uint16_t*>(packed);
+    uint8_t* out8 = static_cast<uint8_t*>(packed);
+    uint32_t* dsw = device_status_word();
     const bool f16 = m->precision == TSDFS_PREC_F16;
-    if (m->arch == TSDFS_ARCH_TINY) {
-        if (f16) k_pack<TSDFS_ARCH_TINY, true><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out, device_status_word());
-        else k_pack<TSDFS_ARCH_TINY, false><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out, device_status_word());
+    if (tiny) {
+        if (f16) {
+            k_pack<TSDFS_ARCH_TINY, true><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out, dsw);
+            k_pack_fold<TSDFS_ARCH_TINY, true><<<grid_1d(nf, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out8, dsw);
+        } else {
+            k_pack<TSDFS_ARCH_TINY, false><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out, dsw);
+            k_pack_fold<TSDFS_ARCH_TINY, false><<<grid_1d(nf, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out8, dsw);
+        }
     } else {
-        if (f16) k_pack<TSDFS_ARCH_ROOM, true><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out, device_status_word());
-        else k_pack<TSDFS_ARCH_ROOM, false><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out, device_status_word());
+        if (f16) {
+            k_pack<TSDFS_ARCH_ROOM, true><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out, dsw);
+            k_pack_fold<TSDFS_ARCH_ROOM, true><<<grid_1d(nf, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out8, dsw);
+        } else {
+            k_pack<TSDFS_ARCH_ROOM, false><<<grid_1d(n, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out, dsw);
+            k_pack_fold<TSDFS_ARCH_ROOM, false><<<grid_1d(nf, 256), 256, 0, st>>>(m->sdf_w, m->rgb_w, out8, dsw);
+        }
     }
     return cuda_check(cudaGetLastError(), "tsdfs_pack_mlp launch");
 }

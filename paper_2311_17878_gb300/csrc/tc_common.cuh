@@ -29,10 +29,26 @@ __host__ __device__ constexpr int part_hi(int K, int pt, int parts) { return pt 
 __host__ __device__ constexpr int part8_lo(int K, int pt, int parts) { return ((K / 8) * pt + parts - 1) / parts * 8; }
 __host__ __device__ constexpr int part8_hi(int K, int pt, int parts) { return pt + 1 == parts ? K : part8_lo(K, pt + 1, parts); }
 
-template <int ARCH> struct TcArch {
+// Layer tables of the packed 16-bit weights.  FOLD: the serial kernel's tables, in which
+// the SDF output layer keeps only its value column net_0 and the colour network's first
+// layer reads the last hidden SDF activation h directly: the feature columns
+// feat = W_f h + b_f enter the colour network only through W_c,feat, so
+// W_c,feat feat = (W_c,feat W_f) h + W_c,feat b_f, and the folded first colour layer has the
+// inputs [h, x~, direction encoding, unit normal] with the weights
+// [W_c,feat W_f | W_c,x | W_c,dir | W_c,n] and the bias b_c + W_c,feat b_f.  Its weights and
+// the two folded layers' FP32 biases follow the unfolded layers in the packed buffer.
+template <int ARCH, bool FOLD = false> struct TcArch {
     using A = Arch<ARCH>;
+    using Plain = TcArch<ARCH, false>;
     static constexpr int kLayers = A::kSdfLayers + A::kRgbLayers;
+    static constexpr int kLS = A::kSdfLayers;
+    static constexpr int kH = A::sdf(A::kSdfLayers - 1).in;   // width of h, the last SDF layer's input
+    static constexpr int kX = 3 + A::kDirEnc + 3;               // x~, direction encoding, unit normal
+    static constexpr int kXp = pad16(kX);
+    static_assert(kH % kKChunk == 0, "the folded colour input's h part fills whole weight chunks");
     __host__ __device__ static constexpr TcLayer layer(int L) {
+        if (FOLD && L == kLS - 1) return TcLayer{kH, kH, 1, 16, true, L};
+        if (FOLD && L == kLS) return TcLayer{kH + kX, kH + kXp, A::rgb(0).out, pad16(A::rgb(0).out), false, 0};
         if (L < A::kSdfLayers) {
             const Layer l = A::sdf(L);
             return TcLayer{l.in, pad16(l.in), l.out, pad16(l.out), true, L};
@@ -40,19 +56,41 @@ template <int ARCH> struct TcArch {
         const Layer l = A::rgb(L - A::kSdfLayers);
         return TcLayer{l.in, pad16(l.in), l.out, pad16(l.out), false, L - A::kSdfLayers};
     }
+    __host__ __device__ static constexpr bool folded(int L) { return FOLD && (L == kLS - 1 || L == kLS); }
     __host__ __device__ static constexpr int chunks(int L) { return (layer(L).Kp + kKChunk - 1) / kKChunk; }
     __host__ __device__ static constexpr int chunk_k(int L, int c) {
         return layer(L).Kp - c * kKChunk < kKChunk ? layer(L).Kp - c * kKChunk : kKChunk;
     }
     __host__ __device__ static constexpr int64_t chunk_bytes(int L, int c) { return (int64_t)layer(L).Np * chunk_k(L, c) * 2; }
+    __host__ __device__ static constexpr int64_t layer_bytes(int L) {
+        int64_t b = 0;
+        for (int cc = 0; cc < chunks(L); ++cc) b += chunk_bytes(L, cc);
+        return b;
+    }
+    // offset of chunk c of layer L in the packed buffer: the unfolded layers in order, then
+    // (FOLD) the folded SDF output layer and the folded first colour layer
     __host__ __device__ static constexpr int64_t packed_offset(int L, int c) {
         int64_t off = 0;
-        for (int l = 0; l < L; ++l)
-            for (int cc = 0; cc < chunks(l); ++cc) off += chunk_bytes(l, cc);
+        if (folded(L)) {
+            off = Plain::packed_bytes();
+            if (L == kLS) off += layer_bytes(kLS - 1);
+        } else {
+            for (int l = 0; l < L; ++l) off += Plain::layer_bytes(l);
+        }
         for (int cc = 0; cc < c; ++cc) off += chunk_bytes(L, cc);
         return off;
     }
-    __host__ __device__ static constexpr int64_t packed_bytes() { return packed_offset(kLayers, 0); }
+    // FP32 biases of the two folded layers (Np each), after their weights, 16-byte aligned
+    __host__ __device__ static constexpr int64_t fold_bias_offset() {
+        return (Plain::packed_bytes() + layer_bytes(kLS - 1) + layer_bytes(kLS) + 15) / 16 * 16;
+    }
+    __host__ __device__ static constexpr int fold_bias_count() { return layer(kLS - 1).Np + layer(kLS).Np; }
+    __host__ __device__ static constexpr int64_t packed_bytes() {
+        if constexpr (FOLD) return fold_bias_offset() + (int64_t)fold_bias_count() * 4;
+        int64_t off = 0;
+        for (int l = 0; l < kLayers; ++l) off += layer_bytes(l);
+        return off;
+    }
     __host__ __device__ static constexpr int64_t param_offset(int L) {
         return L < A::kSdfLayers ? sdf_layer_offset<ARCH>(L) : rgb_layer_offset<ARCH>(L - A::kSdfLayers);
     }

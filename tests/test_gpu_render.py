@@ -163,17 +163,75 @@ def test_tiny_hier_f32_matches_oracle(n_coarse, n_fine):
 DEPTH_REL_BF16 = 2e-3
 
 
+def _pad16(x):
+    return (x + 15) // 16 * 16
+
+
+def _plain_packed_bytes(spec):
+    """Bytes of the unfolded layers: every layer's weights padded to 16 rows and columns."""
+    return sum(2 * _pad16(W.shape[0]) * _pad16(W.shape[1]) for W, _ in list(spec.sdf) + list(spec.rgb))
+
+
 def test_pack_layout_roundtrip():
-    """The packed bf16 tiles hold every weight once (rounded to nearest even)
-    and zeros in the padding: the multiset of packed values equals the weights."""
+    """The unfolded part of the packed bf16 tiles holds every weight once (rounded to
+    nearest even) and zeros in the padding: the multiset of its values equals the weights."""
     for spec in (synth.tiny_mlp(), synth.room_mlp()):
         mlp = T.Mlp(spec, T.TSDFS_PREC_BF16)
         torch.cuda.synchronize()
-        packed = mlp.packed.view(torch.bfloat16).float().cpu().numpy()
+        nb = _plain_packed_bytes(spec)
+        packed = mlp.packed[:nb].view(torch.bfloat16).float().cpu().numpy()
         w = np.concatenate([np.concatenate([W.reshape(-1) for W, _ in spec.sdf]),
                             np.concatenate([W.reshape(-1) for W, _ in spec.rgb])]).astype(np.float32)
         nz = np.sort(packed[packed != 0])
         assert np.array_equal(nz, np.sort(w[w != 0]))
+
+
+def _unpack_chunks(raw, n_rows, k_cols):
+    """Inverse of the chunked no-swizzle K-major core-matrix layout of one layer: 64-column
+    chunks (the last one narrower), within a chunk 8x8 core matrices, row blocks outermost."""
+    out = np.zeros((n_rows, k_cols), np.float64)
+    pos = 0
+    for c0 in range(0, k_cols, 64):
+        kc = min(64, k_cols - c0)
+        blk = raw[pos:pos + n_rows * kc].reshape(n_rows // 8, kc // 8, 8, 8)
+        out[:, c0:c0 + kc] = blk.transpose(0, 2, 1, 3).reshape(n_rows, kc)
+        pos += n_rows * kc
+    return out, pos
+
+
+@pytest.mark.parametrize("precision", [T.TSDFS_PREC_F16, T.TSDFS_PREC_BF16])
+def test_folded_layers_match_fp64_product(precision):
+    """The serial kernel's folded layers after the unfolded ones: the SDF output's value row,
+    and the first colour layer on [h, x~, direction, normal] whose h columns hold
+    W_c,feat W_f, against the product in FP64 rounded once (within one unit in the 16-bit
+    format's last place); the folded biases b_f,0 and b_c + W_c,feat b_f in FP32 (1e-6)."""
+    dt = torch.float16 if precision == T.TSDFS_PREC_F16 else torch.bfloat16
+    ulp = 2.0 ** -10 if precision == T.TSDFS_PREC_F16 else 2.0 ** -7
+    for spec in (synth.tiny_mlp(), synth.room_mlp()):
+        mlp = T.Mlp(spec, precision)
+        torch.cuda.synchronize()
+        nb = _plain_packed_bytes(spec)
+        raw = mlp.packed[nb:].view(dt).float().cpu().numpy().astype(np.float64)
+        Wo, bo = [np.asarray(a, np.float64) for a in spec.sdf[-1]]
+        Wc, bc = [np.asarray(a, np.float64) for a in spec.rgb[0]]
+        kh = Wo.shape[1]
+        nfeat = Wo.shape[0] - 1
+        kx = Wc.shape[1] - nfeat
+        vrow, used = _unpack_chunks(raw, 16, _pad16(kh))
+        assert np.all(np.abs(vrow[0, :kh] - Wo[0]) <= ulp * np.abs(Wo[0]) + 1e-7)
+        assert not vrow[1:].any()
+        nc = _pad16(Wc.shape[0])
+        fold, used2 = _unpack_chunks(raw[used:], nc, kh + _pad16(kx))
+        ref = np.zeros_like(fold)
+        ref[:Wc.shape[0], :kh] = Wc[:, kx:] @ Wo[1:]
+        ref[:Wc.shape[0], kh:kh + kx] = Wc[:, :kx]
+        assert np.all(np.abs(fold - ref) <= ulp * np.abs(ref) + 1e-7), np.abs(fold - ref).max()
+        fb_off = (nb + 2 * (used + used2) + 15) // 16 * 16
+        fb = mlp.packed[fb_off:fb_off + 4 * (16 + nc)].view(torch.float32).cpu().numpy().astype(np.float64)
+        ref_b = np.zeros(16 + nc)
+        ref_b[0] = bo[0]
+        ref_b[16:16 + Wc.shape[0]] = bc + Wc[:, kx:] @ bo[1:]
+        assert np.allclose(fb, ref_b, rtol=1e-6, atol=1e-7), np.abs(fb - ref_b).max()
 
 
 def _scene_case(scene):
