@@ -309,16 +309,26 @@ __global__ void __launch_bounds__(PipeMode<MODE>::kThreads, 1) k_mlp_pipe(PipePa
                         tc_fence_after();
                         const uint32_t b0 = smem_u32(stage_base + ci.slot * kStage);
                         const uint32_t b_sbo = (uint32_t)(ci.kc / 8) * 128u;
-                        for (int kk = 0; kk < ci.kc / 16; ++kk) {
-                            const int k = c * kKChunk + kk * 16;
-                            const uint64_t bd = mdesc(b0 + kk * 256, 128, b_sbo);
-                            if (k < 256) {
-                                const uint32_t ko = (uint32_t)(k / 8) * 128u;
-                                mma_bf16(d_tmem, mdesc(a_hi + ko, 128, a_sbo), bd, idesc, k > 0 ? 1u : 0u);
-                                if (two) mma_bf16(d_tmem, mdesc(a_lo + ko, 128, a_sbo), bd, idesc, 1u);
-                            } else {
-                                const uint32_t ko = (uint32_t)((k - 256) / 8) * 128u;
-                                mma_bf16(d_tmem, mdesc(a_x + ko, 128, (uint32_t)(TA::kPitchX / 8) * 128u), bd, idesc, 1u);
+                        // descriptors built once per chunk (a chunk lies wholly below or above
+                        // column 256) and advanced by 16 (256 bytes) per K step
+                        const int k0 = c * kKChunk;
+                        uint64_t bd = mdesc(b0, 128, b_sbo);
+                        if (k0 < 256) {
+                            const uint32_t ko = (uint32_t)(k0 / 8) * 128u;
+                            uint64_t ah = mdesc(a_hi + ko, 128, a_sbo), al = mdesc(a_lo + ko, 128, a_sbo);
+                            for (int kk = 0; kk < ci.kc / 16; ++kk) {
+                                mma_bf16(d_tmem, ah, bd, idesc, (k0 | kk) != 0 ? 1u : 0u);
+                                if (two) mma_bf16(d_tmem, al, bd, idesc, 1u);
+                                ah += 16;
+                                al += 16;
+                                bd += 16;
+                            }
+                        } else {
+                            uint64_t ax = mdesc(a_x + (uint32_t)((k0 - 256) / 8) * 128u, 128, (uint32_t)(TA::kPitchX / 8) * 128u);
+                            for (int kk = 0; kk < ci.kc / 16; ++kk) {
+                                mma_bf16(d_tmem, ax, bd, idesc, 1u);
+                                ax += 16;
+                                bd += 16;
                             }
                         }
                         mma_commit(bar_empty0 + 8 * ci.slot);

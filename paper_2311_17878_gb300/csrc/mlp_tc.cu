@@ -829,10 +829,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
                         const int kc = TA::chunk_k(L, c);
                         const uint32_t b0 = smem_u32(stage_base + s * kStage);
                         const uint32_t b_sbo = (uint32_t)(kc / 8) * 128u;
+                        // descriptors built once per chunk, advanced by 16 (256 bytes) per K step
+                        const int k0 = c * kKChunk;
+                        uint64_t ad = mdesc(a0 + (uint32_t)(k0 / 8) * 128u, 128, a_sbo);
+                        uint64_t bd = mdesc(b0, 128, b_sbo);
+                        const uint32_t id = idesc_mma<F16>(128, n_mma);
                         for (int kk = 0; kk < kc / 16; ++kk) {
-                            const int k = c * kKChunk + kk * 16;
-                            mma_bf16(tmem, mdesc(a0 + (uint32_t)(k / 8) * 128u, 128, a_sbo), mdesc(b0 + kk * 256, 128, b_sbo),
-                                     idesc_mma<F16>(128, n_mma), k > 0 ? 1u : 0u);
+                            mma_bf16(tmem, ad, bd, id, (k0 | kk) != 0 ? 1u : 0u);
+                            ad += 16;
+                            bd += 16;
                         }
                         mma_commit(bar_empty0 + 8 * s);
                         ++seq;
