@@ -239,23 +239,43 @@ __global__ void k_genc(const SampleAux* __restrict__ aux, int64_t n, float* __re
 __global__ void k_gsp_fwd(const float* __restrict__ P, int ldp, const float* __restrict__ bias, int No,
                           const float* __restrict__ X0, int ldx0, int E, bool skip, float sc, float beta, int64_t n,
                           float* __restrict__ Xn, int ldxn) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * ldxn; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = e / ldxn;
-        const int j = (int)(e % ldxn);
-        float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (j < No) {
-            const float z = P[4 * s * ldp + j] + __ldg(bias + j);
-            const float bz = beta * z;
-            const float sg = bz > 20.0f ? 1.0f : 1.0f / (1.0f + expf(-bz));
-            v[0] = sc * (bz > 20.0f ? z : log1pf(expf(bz)) / beta);
+    // one thread per sample and group of 4 columns (every row length is a multiple of 4, so
+    // the P, bias and Xn accesses are 16-byte vectors; P and bias hold pad4(No) columns)
+    const int q4 = ldxn / 4;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * q4; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = e / q4;
+        const int j0 = 4 * (int)(e % q4);
+        float v[4][4] = {};   // [row][column]
+        float pz[4] = {}, pt[3][4] = {}, bz4[4] = {};
+        if (j0 < No) {
+            const float4 z = *reinterpret_cast<const float4*>(P + 4 * s * ldp + j0);
+            const float4 b = __ldg(reinterpret_cast<const float4*>(bias + j0));
+            pz[0] = z.x; pz[1] = z.y; pz[2] = z.z; pz[3] = z.w;
+            bz4[0] = b.x; bz4[1] = b.y; bz4[2] = b.z; bz4[3] = b.w;
 #pragma unroll
-            for (int a = 1; a < 4; ++a) v[a] = sc * sg * P[(4 * s + a) * ldp + j];
-        } else if (skip && j < No + E) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) v[c] = sc * X0[(4 * s + c) * ldx0 + (j - No)];
+            for (int a = 0; a < 3; ++a) {
+                const float4 t = *reinterpret_cast<const float4*>(P + (4 * s + 1 + a) * ldp + j0);
+                pt[a][0] = t.x; pt[a][1] = t.y; pt[a][2] = t.z; pt[a][3] = t.w;
+            }
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) Xn[(4 * s + c) * ldxn + j] = v[c];
+        for (int i = 0; i < 4; ++i) {
+            const int j = j0 + i;
+            if (j < No) {
+                const float zz = pz[i] + bz4[i];
+                const float bz = beta * zz;
+                const float sg = bz > 20.0f ? 1.0f : 1.0f / (1.0f + expf(-bz));
+                v[0][i] = sc * (bz > 20.0f ? zz : log1pf(expf(bz)) / beta);
+#pragma unroll
+                for (int a = 1; a < 4; ++a) v[a][i] = sc * sg * pt[a - 1][i];
+            } else if (skip && j < No + E) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v[c][i] = sc * X0[(4 * s + c) * ldx0 + (j - No)];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<float4*>(Xn + (4 * s + c) * ldxn + j0) = make_float4(v[c][0], v[c][1], v[c][2], v[c][3]);
     }
 }
 
@@ -404,24 +424,41 @@ __global__ void k_gsdf_out_bwd(const float* __restrict__ D, int ldd, const Sampl
 __global__ void k_gsp_bwd(const float* __restrict__ D, int ldd, const float* __restrict__ P, int ldp,
                           const float* __restrict__ bias, int N, float sc, float beta, int64_t n,
                           float* __restrict__ G, int ldg) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * ldg; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = e / ldg;
-        const int j = (int)(e % ldg);
-        if (j >= N) {
+    // one thread per sample and group of 4 columns (16-byte vectors: every row length is a
+    // multiple of 4, and D, P and bias hold at least pad4(N) columns)
+    const int q4 = ldg / 4;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * q4; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = e / q4;
+        const int j0 = 4 * (int)(e % q4);
+        float g[4][4] = {};   // [row][column]
+        if (j0 < N) {
+            float d[4][4], p[4][4], b[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) G[(4 * s + c) * ldg + j] = 0.0f;
-            continue;
+            for (int r = 0; r < 4; ++r) {
+                const float4 dv = *reinterpret_cast<const float4*>(D + (4 * s + r) * ldd + j0);
+                const float4 pv = *reinterpret_cast<const float4*>(P + (4 * s + r) * ldp + j0);
+                d[r][0] = dv.x; d[r][1] = dv.y; d[r][2] = dv.z; d[r][3] = dv.w;
+                p[r][0] = pv.x; p[r][1] = pv.y; p[r][2] = pv.z; p[r][3] = pv.w;
+            }
+            const float4 bv = __ldg(reinterpret_cast<const float4*>(bias + j0));
+            b[0] = bv.x; b[1] = bv.y; b[2] = bv.z; b[3] = bv.w;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (j0 + i >= N) continue;
+                const float bz = beta * (p[0][i] + b[i]);
+                const float sg = bz > 20.0f ? 1.0f : 1.0f / (1.0f + expf(-bz));
+                const float dsg = bz > 20.0f ? 0.0f : beta * sg * (1.0f - sg);
+                float second = 0.0f;
+#pragma unroll
+                for (int a = 1; a < 4; ++a) second += d[a][i] * p[a][i];
+                g[0][i] = sc * (sg * d[0][i] + dsg * second);
+#pragma unroll
+                for (int a = 1; a < 4; ++a) g[a][i] = sc * sg * d[a][i];
+            }
         }
-        const float z = P[4 * s * ldp + j] + __ldg(bias + j);
-        const float bz = beta * z;
-        const float sg = bz > 20.0f ? 1.0f : 1.0f / (1.0f + expf(-bz));
-        const float dsg = bz > 20.0f ? 0.0f : beta * sg * (1.0f - sg);
-        float second = 0.0f;
 #pragma unroll
-        for (int a = 1; a < 4; ++a) second += D[(4 * s + a) * ldd + j] * P[(4 * s + a) * ldp + j];
-        G[4 * s * ldg + j] = sc * (sg * D[4 * s * ldd + j] + dsg * second);
-#pragma unroll
-        for (int a = 1; a < 4; ++a) G[(4 * s + a) * ldg + j] = sc * sg * D[(4 * s + a) * ldd + j];
+        for (int r = 0; r < 4; ++r)
+            *reinterpret_cast<float4*>(G + (4 * s + r) * ldg + j0) = make_float4(g[r][0], g[r][1], g[r][2], g[r][3]);
     }
 }
 
@@ -597,7 +634,7 @@ int chunk_forward(cublasHandle_t h, const GemmWs<ARCH>& w, const NetParams& np, 
         if (l + 1 < L::LS) {
             const int ldn = pad4(A::sdf(l + 1).in);
             const bool skip = l + 1 == A::kSkip;
-            k_gsp_fwd<<<grid_1d(n * ldn, kEw), kEw, 0, st>>>(w.P[l], pad4(ly.out), b, ly.out, w.X[0], pad4(E), E, skip,
+            k_gsp_fwd<<<grid_1d(n * ldn / 4, kEw), kEw, 0, st>>>(w.P[l], pad4(ly.out), b, ly.out, w.X[0], pad4(E), E, skip,
                                                              skip ? kSkipScale : 1.0f, np.beta, n, w.X[l + 1], ldn);
         } else {
             const int ldc = pad4(A::rgb(0).in);
@@ -676,7 +713,7 @@ int chunk_backward(cublasHandle_t h, const GemmWs<ARCH>& w, const NetParams& np,
         if (rc) return rc;
         const Layer lp = A::sdf(l - 1);
         const float* bp = w.wp + L::sdf_off(l - 1) + (int64_t)pad4(lp.out) * pad4(lp.in);
-        k_gsp_bwd<<<grid_1d(n * pad4(lp.out), kEw), kEw, 0, st>>>(w.D, kp, w.P[l - 1], pad4(lp.out), bp, lp.out,
+        k_gsp_bwd<<<grid_1d(n * pad4(lp.out) / 4, kEw), kEw, 0, st>>>(w.D, kp, w.P[l - 1], pad4(lp.out), bp, lp.out,
                                                            l == A::kSkip ? kSkipScale : 1.0f, np.beta, n, w.G,
                                                            pad4(lp.out));
         rc = cuda_check(cudaGetLastError(), "backward softplus launch");
