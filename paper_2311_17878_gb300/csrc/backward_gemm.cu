@@ -339,10 +339,21 @@ __global__ void k_gsdf_out(const float* __restrict__ P, int ldp, const float* __
 // next colour layer input: ReLU(P + b), zero padding
 __global__ void k_grelu_fwd(const float* __restrict__ P, int ldp, const float* __restrict__ bias, int N, int64_t n,
                             float* __restrict__ Xn, int ldxn) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * ldxn; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = e / ldxn;
-        const int j = (int)(e % ldxn);
-        Xn[s * ldxn + j] = j < N ? fmaxf(P[s * ldp + j] + __ldg(bias + j), 0.0f) : 0.0f;
+    // 4 columns per thread as 16-byte vectors (P and bias hold pad4(N) columns, ldxn too)
+    const int q4 = ldxn / 4;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * q4; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = e / q4;
+        const int j0 = 4 * (int)(e % q4);
+        float4 o = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (j0 < N) {
+            const float4 pv = *reinterpret_cast<const float4*>(P + s * ldp + j0);
+            const float4 bv = __ldg(reinterpret_cast<const float4*>(bias + j0));
+            o.x = fmaxf(pv.x + bv.x, 0.0f);
+            o.y = j0 + 1 < N ? fmaxf(pv.y + bv.y, 0.0f) : 0.0f;
+            o.z = j0 + 2 < N ? fmaxf(pv.z + bv.z, 0.0f) : 0.0f;
+            o.w = j0 + 3 < N ? fmaxf(pv.w + bv.w, 0.0f) : 0.0f;
+        }
+        *reinterpret_cast<float4*>(Xn + s * ldxn + j0) = o;
     }
 }
 
@@ -377,10 +388,22 @@ __global__ void k_grgb_bwd(const float* __restrict__ P, int ldp, const float* __
 // through a hidden colour layer's ReLU: G = D where P + b > 0 (zero padding)
 __global__ void k_grelu_bwd(const float* __restrict__ D, int ldd, const float* __restrict__ P, int ldp,
                             const float* __restrict__ bias, int N, int64_t n, float* __restrict__ G, int ldg) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * ldg; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = e / ldg;
-        const int j = (int)(e % ldg);
-        G[s * ldg + j] = j < N && P[s * ldp + j] + __ldg(bias + j) > 0.0f ? D[s * ldd + j] : 0.0f;
+    // 4 columns per thread as 16-byte vectors (D, P and bias hold at least pad4(N) columns)
+    const int q4 = ldg / 4;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * q4; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = e / q4;
+        const int j0 = 4 * (int)(e % q4);
+        float4 o = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (j0 < N) {
+            const float4 dv = *reinterpret_cast<const float4*>(D + s * ldd + j0);
+            const float4 pv = *reinterpret_cast<const float4*>(P + s * ldp + j0);
+            const float4 bv = __ldg(reinterpret_cast<const float4*>(bias + j0));
+            o.x = pv.x + bv.x > 0.0f ? dv.x : 0.0f;
+            o.y = j0 + 1 < N && pv.y + bv.y > 0.0f ? dv.y : 0.0f;
+            o.z = j0 + 2 < N && pv.z + bv.z > 0.0f ? dv.z : 0.0f;
+            o.w = j0 + 3 < N && pv.w + bv.w > 0.0f ? dv.w : 0.0f;
+        }
+        *reinterpret_cast<float4*>(G + s * ldg + j0) = o;
     }
 }
 
@@ -652,7 +675,7 @@ int chunk_forward(cublasHandle_t h, const GemmWs<ARCH>& w, const NetParams& np, 
         const float* b = W + (int64_t)pad4(ly.out) * pad4(ly.in);
         if (l + 1 < L::LC) {
             const int ldn = pad4(A::rgb(l + 1).in);
-            k_grelu_fwd<<<grid_1d(n * ldn, kEw), kEw, 0, st>>>(w.Pc[l], pad4(ly.out), b, ly.out, n, w.Xc[l + 1], ldn);
+            k_grelu_fwd<<<grid_1d(n * ldn / 4, kEw), kEw, 0, st>>>(w.Pc[l], pad4(ly.out), b, ly.out, n, w.Xc[l + 1], ldn);
         } else {
             k_grgb_out<<<grid_1d(n, kEw), kEw, 0, st>>>(w.Pc[l], pad4(ly.out), b, n, c0, w.rec);
         }
@@ -687,7 +710,7 @@ int chunk_backward(cublasHandle_t h, const GemmWs<ARCH>& w, const NetParams& np,
         if (l == 0) break;
         const Layer lp = A::rgb(l - 1);
         const float* bp = w.wp + L::rgb_off(l - 1) + (int64_t)pad4(lp.out) * pad4(lp.in);
-        k_grelu_bwd<<<grid_1d(n * pad4(lp.out), kEw), kEw, 0, st>>>(w.D, kp, w.Pc[l - 1], pad4(lp.out), bp, lp.out, n,
+        k_grelu_bwd<<<grid_1d(n * pad4(lp.out) / 4, kEw), kEw, 0, st>>>(w.D, kp, w.Pc[l - 1], pad4(lp.out), bp, lp.out, n,
                                                                    w.G, pad4(lp.out));
         rc = cuda_check(cudaGetLastError(), "backward ReLU launch");
         if (rc) return rc;
