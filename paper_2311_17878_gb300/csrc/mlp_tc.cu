@@ -77,9 +77,11 @@ template <int ARCH> struct TcFull : TcArch<ARCH, true> {
     __host__ __device__ static constexpr uint32_t table_bytes() {
         return (uint32_t)(kTileS * (8 + 6 * (A::kPeSdf + A::kPeDir)) * 4);
     }
+    // the MMA warp's per-chunk records (descriptors precomputed once per CTA): 32 bytes a chunk
+    __host__ __device__ static constexpr uint32_t mma_tab_bytes() { return (uint32_t)Base::total_chunks() * 32u; }
     __host__ __device__ static constexpr size_t full_smem_bytes() {
         return 2 * (size_t)kABytes + kStages * (size_t)stage_bytes() + bias_bytes() + kBarBytes + table_bytes() +
-               chunk_tab_bytes();
+               chunk_tab_bytes() + mma_tab_bytes();
     }
     // bytes at the start of A1 holding the folded colour input's x~ / direction / normal
     // columns (128 rows of kXp columns; its h columns are the last SDF layer's input rows in
@@ -100,6 +102,25 @@ struct ChunkInfo {
     uint16_t slot, kc_keep;   // kc_keep: K columns | 0x8000 when the slot is kept
 };
 static_assert(sizeof(ChunkInfo) == 12, "chunk table entry");
+
+// the MMA warp's record of one weight chunk, written once per CTA: the shared-memory
+// descriptors of the chunk's first K step (weights, and the operand rows of both
+// accumulators), the instruction descriptor, and the flags below; the issue loop then only
+// waits, adds and issues
+struct MmaRec {
+    uint64_t bd, ad0, ad1;
+    uint32_t id, flags;
+};
+static_assert(sizeof(MmaRec) == 32, "MMA record");
+constexpr uint32_t kRecNk = 7u;              // bits 0-2: K steps of 16 columns
+constexpr uint32_t kRecTwo = 1u << 3;        // both accumulators (SDF layers)
+constexpr uint32_t kRecKeep = 1u << 4;       // the slot stays with the MMA warp (no release)
+constexpr uint32_t kRecFirst = 1u << 5;      // first chunk of its layer: wait for the operand
+constexpr uint32_t kRecLast = 1u << 6;       // last chunk of its layer: signal the accumulator
+constexpr uint32_t kRecRelA1 = 1u << 7;      // after the SDF MMAs: release the A1 slots
+constexpr int kRecSlotShift = 8;             // bits 8-9: weight slot
+constexpr uint32_t kRecPar = 1u << 10;       // parity of the slot's use within the tile
+constexpr uint32_t kRecFlip = 1u << 11;      // the slot's uses per tile are odd
 
 struct TcParams {
     const uint8_t* packed;
@@ -152,6 +173,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
     float* s_pe = s_x + kTileS * 8;
     float* s_pd = s_pe + kTileS * A::kPeSdf * 6;
     ChunkInfo* s_chunks = reinterpret_cast<ChunkInfo*>(reinterpret_cast<uint8_t*>(s_x) + TA::table_bytes());
+    MmaRec* s_mma = reinterpret_cast<MmaRec*>(reinterpret_cast<uint8_t*>(s_chunks) + TA::chunk_tab_bytes());
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const int64_t total = sample_total(p.src);
@@ -182,6 +204,41 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                 s_chunks[j] = ChunkInfo{(uint32_t)TA::packed_offset(L, c), (uint32_t)TA::chunk_bytes(L, c), (uint16_t)sl,
                                         (uint16_t)(TA::chunk_k(L, c) | (keep ? 0x8000 : 0))};
             }
+        // the MMA warp's records: the same descriptors its loop computed per chunk before
+        {
+            static_assert(TA::layer(LS - 1).Np <= 256, "the SDF output layer fits one MMA per accumulator");
+            int uses[kSlots];
+            for (int i = 0; i < kSlots; ++i) uses[i] = 0;
+            const uint32_t a0 = smem_u32(A0), a1 = smem_u32(A1);
+            for (int L = 0, j = 0; L < NL; ++L) {
+                const TcLayer ly = TA::layer(L);
+                const uint32_t a_sbo = (uint32_t)(ly.Kp / 8) * 128u;
+                for (int c = 0; c < TA::chunks(L); ++c, ++j) {
+                    const ChunkInfo ci = s_chunks[j];
+                    const uint32_t sl = ci.slot;
+                    const int kc = ci.kc_keep & 0x7fff;
+                    const int k0 = c * kKChunk;
+                    MmaRec r;
+                    r.bd = mdesc(slot_addr(sl), 128, (uint32_t)(kc / 8) * 128u);
+                    r.ad0 = mdesc(a0 + (uint32_t)(k0 / 8) * 128u, 128, a_sbo);
+                    // the folded colour input: its h chunks are the last SDF layer's input rows in
+                    // A0 (that layer's layout), its x~ / direction / normal chunk starts A1
+                    if (!ly.sdf && ly.idx == 0)
+                        r.ad0 = k0 < TA::kH ? mdesc(a0 + (uint32_t)(k0 / 8) * 128u, 128, (TA::kH / 8) * 128u)
+                                            : mdesc(a1 + (uint32_t)((k0 - TA::kH) / 8) * 128u, 128, (TA::kXp / 8) * 128u);
+                    r.ad1 = mdesc(a1 + (uint32_t)(k0 / 8) * 128u, 128, a_sbo);
+                    r.id = idesc_mma<F16>(128, ly.Np);
+                    r.flags = (uint32_t)(kc / 16) | (ly.sdf ? kRecTwo : 0u) | ((ci.kc_keep & 0x8000) ? kRecKeep : 0u) |
+                              (c == 0 ? kRecFirst : 0u) | (c + 1 == TA::chunks(L) ? kRecLast : 0u) |
+                              (c + 1 == TA::chunks(L) && L == LS - 1 ? kRecRelA1 : 0u) | (sl << kRecSlotShift) |
+                              ((uses[sl] & 1) ? kRecPar : 0u);
+                    ++uses[sl];
+                    s_mma[j] = r;
+                }
+            }
+            for (int j = 0; j < TA::total_chunks(); ++j)
+                if (uses[s_chunks[j].slot] & 1) s_mma[j].flags |= kRecFlip;
+        }
     }
     // all biases of both networks, staged once (the two folded layers' from the packed buffer)
     for (int i = threadIdx.x; i < TA::bias_total(); i += kThreadsF) {
@@ -237,92 +294,60 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
             }
         }
     } else if (warp == kMmaWarpF) {
-        // ---------------------------------------------------------- MMA issuer
+        // ---------------------------------------------------------- MMA issuer: one record
+        // per chunk (descriptors built once per CTA); the next record is read while the
+        // current chunk's MMAs are issued
         if (lane == 0) {
-            uint32_t uses[kSlots];
-#pragma unroll
-            for (int i = 0; i < kSlots; ++i) uses[i] = 0;
-            uint32_t lc = 0;
+            uint32_t lc = 0, tpar = 0;
             bool ok = true;
-            for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-                int j = 0;   // chunk of the tile's schedule
-                for (int L = 0; L < NL && ok; ++L, ++lc) {
-                    const TcLayer ly = TA::layer(L);
-                    if (!mbar_wait(bar_a, lc & 1u, abort_flag, p.spin)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t a_sbo = (uint32_t)(ly.Kp / 8) * 128u;
-                    const uint32_t a0 = smem_u32(A0), a1 = smem_u32(A1);
-                    const bool last_sdf = ly.sdf && ly.idx == LS - 1;
-                    for (int c = 0; c < TA::chunks(L); ++c, ++j) {
-                        const ChunkInfo ci = s_chunks[j];
-                        const uint32_t s = ci.slot;
-                        uint32_t ph = 0;
-#pragma unroll
-                        for (int i = 0; i < kSlots; ++i)
-                            if ((uint32_t)i == s) ph = uses[i]++ & 1u;
-                        if (!mbar_wait(bar_full0 + 8 * s, ph, abort_flag, p.spin)) { ok = false; break; }
+            for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, tpar ^= 1u) {
+                MmaRec cr = s_mma[0];
+                for (int j = 0; j < TA::total_chunks(); ++j) {
+                    const uint32_t f = cr.flags;
+                    if (f & kRecFirst) {
+                        if (!mbar_wait(bar_a, lc & 1u, abort_flag, p.spin)) { ok = false; break; }
                         tc_fence_after();
-                        const int kc = ci.kc_keep & 0x7fff;
-                        const uint32_t b0 = slot_addr(s);
-                        const uint32_t b_sbo = (uint32_t)(kc / 8) * 128u;
-                        const int k0 = c * kKChunk;
-                        const int nk = kc / 16;
-                        // descriptors of the chunk's first K step; each further step of 16
-                        // columns moves both operands by two 8x8 core matrices (256 bytes,
-                        // 16 in the descriptor's address field, which stays below 2^14 for
-                        // any shared-memory address), so the loop only adds
-                        uint64_t bd = mdesc(b0, 128, b_sbo);
-                        // the folded colour input: its h chunks are the last SDF layer's input rows
-                        // in A0 (that layer's layout), its x~ / direction / normal chunk starts A1
-                        uint64_t ad0 = mdesc(a0 + (uint32_t)(k0 / 8) * 128u, 128, a_sbo);
-                        if (!ly.sdf && ly.idx == 0)
-                            ad0 = k0 < TA::kH ? mdesc(a0 + (uint32_t)(k0 / 8) * 128u, 128, (TA::kH / 8) * 128u)
-                                              : mdesc(a1 + (uint32_t)((k0 - TA::kH) / 8) * 128u, 128, (TA::kXp / 8) * 128u);
-                        if (ly.sdf && !last_sdf) {
-                            uint64_t ad1 = mdesc(a1 + (uint32_t)(k0 / 8) * 128u, 128, a_sbo);
-                            const uint32_t id = idesc_mma<F16>(128, ly.Np);
-                            for (int kk = 0; kk < nk; ++kk) {
-                                const uint32_t acc = (k0 | kk) != 0 ? 1u : 0u;
-                                mma_bf16(tmem, ad0, bd, id, acc);
-                                mma_bf16(tmem + 256, ad1, bd, id, acc);
-                                ad0 += 16;
-                                ad1 += 16;
-                                bd += 16;
-                            }
-                        } else if (ly.sdf) {
-                            uint64_t ad1 = mdesc(a1 + (uint32_t)(k0 / 8) * 128u, 128, a_sbo);
-                            uint64_t bx = mdesc(b0 + (256 / 8) * b_sbo, 128, b_sbo);
-                            const uint32_t id0 = idesc_mma<F16>(128, ly.Np < 256 ? ly.Np : 256);
-                            const uint32_t id1 = idesc_mma<F16>(128, 16);
-                            const uint32_t idx = idesc_mma<F16>(128, ly.Np > 256 ? ly.Np - 256 : 16);
-                            for (int kk = 0; kk < nk; ++kk) {
-                                const uint32_t acc = (k0 | kk) != 0 ? 1u : 0u;
-                                mma_bf16(tmem, ad0, bd, id0, acc);
-                                mma_bf16(tmem + 256, ad1, bd, id1, acc);
-                                if (ly.Np > 256) mma_bf16(tmem + 256 + 16, ad0, bx, idx, acc);
-                                ad0 += 16;
-                                ad1 += 16;
-                                bd += 16;
-                                bx += 16;
-                            }
-                        } else {
-                            const uint32_t id = idesc_mma<F16>(128, ly.Np);
-                            for (int kk = 0; kk < nk; ++kk) {
-                                mma_bf16(tmem, ad0, bd, id, (k0 | kk) != 0 ? 1u : 0u);
-                                ad0 += 16;
-                                bd += 16;
-                            }
+                    }
+                    const uint32_t s = (f >> kRecSlotShift) & 3u;
+                    const uint32_t ph = ((f & kRecPar) ? 1u : 0u) ^ ((f & kRecFlip) ? tpar : 0u);
+                    if (!mbar_wait(bar_full0 + 8 * s, ph, abort_flag, p.spin)) { ok = false; break; }
+                    tc_fence_after();
+                    const MmaRec nx = s_mma[j + 1 < TA::total_chunks() ? j + 1 : 0];
+                    const int nk = (int)(f & kRecNk);
+                    uint64_t ad0 = cr.ad0, bd = cr.bd;
+                    uint32_t acc = (f & kRecFirst) ? 0u : 1u;
+                    // each K step of 16 columns moves both operands by two 8x8 core matrices
+                    // (256 bytes, 16 in the descriptor's address field, which stays below 2^14
+                    // for any shared-memory address), so the loop only adds
+                    if (f & kRecTwo) {
+                        uint64_t ad1 = cr.ad1;
+                        for (int kk = 0; kk < nk; ++kk) {
+                            mma_bf16(tmem, ad0, bd, cr.id, acc);
+                            mma_bf16(tmem + 256, ad1, bd, cr.id, acc);
+                            acc = 1u;
+                            ad0 += 16;
+                            ad1 += 16;
+                            bd += 16;
                         }
-                        // release the slot, except the A1 slot after its last colour chunk of the
-                        // tile: the next tile's SDF layers own A1 until their MMAs are done
-                        if (!(ci.kc_keep & 0x8000)) mma_commit(bar_empty0 + 8 * s);
+                    } else {
+                        for (int kk = 0; kk < nk; ++kk) {
+                            mma_bf16(tmem, ad0, bd, cr.id, acc);
+                            acc = 1u;
+                            ad0 += 16;
+                            bd += 16;
+                        }
                     }
-                    if (!ok) break;
-                    mma_commit(bar_acc);
-                    if (L == LS - 1) {
+                    // release the slot, except the A1 slot after its last colour chunk of the
+                    // tile: the next tile's SDF layers own A1 until their MMAs are done
+                    if (!(f & kRecKeep)) mma_commit(bar_empty0 + 8 * s);
+                    if (f & kRecLast) {
+                        mma_commit(bar_acc);
+                        ++lc;
                         // the SDF MMAs are the last readers of A1 in this tile: release its slots
-                        for (int i = kStages; i < kColSlots; ++i) mma_commit(bar_empty0 + 8 * i);
+                        if (f & kRecRelA1)
+                            for (int i = kStages; i < kColSlots; ++i) mma_commit(bar_empty0 + 8 * i);
                     }
+                    cr = nx;
                 }
             }
             if (!ok) {
