@@ -122,6 +122,15 @@ constexpr int kRecSlotShift = 8;             // bits 8-9: weight slot
 constexpr uint32_t kRecPar = 1u << 10;       // parity of the slot's use within the tile
 constexpr uint32_t kRecFlip = 1u << 11;      // the slot's uses per tile are odd
 
+// the value kernel's record of one weight chunk (written once per CTA): packed offset and size
+// for its producers; for the MMA warp the descriptors of the chunk's first K step, the
+// weights' as if in ring stage 0 (a stage further on adds its offset to the address field)
+struct ValRec {
+    uint64_t bd0, ad;
+    uint32_t id, flags, off, bytes;
+};
+static_assert(sizeof(ValRec) == 32, "value-kernel record");
+
 struct TcParams {
     const uint8_t* packed;
     const float* sdf_w;
@@ -295,9 +304,11 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
         }
     } else if (warp == kMmaWarpF) {
         // ---------------------------------------------------------- MMA issuer: one record
-        // per chunk (descriptors built once per CTA); the next record is read while the
-        // current chunk's MMAs are issued
-        if (lane == 0) {
+        // per chunk (descriptors built once per CTA), the next record read while the current
+        // chunk's MMAs are issued; the whole warp runs the loop (converged: the descriptors
+        // stay warp-uniform) and one elected lane issues the MMAs and commits
+        {
+            const uint32_t el = elect_one();
             uint32_t lc = 0, tpar = 0;
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, tpar ^= 1u) {
@@ -305,12 +316,12 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                 for (int j = 0; j < TA::total_chunks(); ++j) {
                     const uint32_t f = cr.flags;
                     if (f & kRecFirst) {
-                        if (!mbar_wait(bar_a, lc & 1u, abort_flag, p.spin)) { ok = false; break; }
+                        if (!__all_sync(0xffffffffu, mbar_wait(bar_a, lc & 1u, abort_flag, p.spin))) { ok = false; break; }
                         tc_fence_after();
                     }
                     const uint32_t s = (f >> kRecSlotShift) & 3u;
                     const uint32_t ph = ((f & kRecPar) ? 1u : 0u) ^ ((f & kRecFlip) ? tpar : 0u);
-                    if (!mbar_wait(bar_full0 + 8 * s, ph, abort_flag, p.spin)) { ok = false; break; }
+                    if (!__all_sync(0xffffffffu, mbar_wait(bar_full0 + 8 * s, ph, abort_flag, p.spin))) { ok = false; break; }
                     tc_fence_after();
                     const MmaRec nx = s_mma[j + 1 < TA::total_chunks() ? j + 1 : 0];
                     const int nk = (int)(f & kRecNk);
@@ -322,8 +333,8 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                     if (f & kRecTwo) {
                         uint64_t ad1 = cr.ad1;
                         for (int kk = 0; kk < nk; ++kk) {
-                            mma_bf16(tmem, ad0, bd, cr.id, acc);
-                            mma_bf16(tmem + 256, ad1, bd, cr.id, acc);
+                            mma_el(el, tmem, ad0, bd, cr.id, acc);
+                            mma_el(el, tmem + 256, ad1, bd, cr.id, acc);
                             acc = 1u;
                             ad0 += 16;
                             ad1 += 16;
@@ -331,7 +342,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                         }
                     } else {
                         for (int kk = 0; kk < nk; ++kk) {
-                            mma_bf16(tmem, ad0, bd, cr.id, acc);
+                            mma_el(el, tmem, ad0, bd, cr.id, acc);
                             acc = 1u;
                             ad0 += 16;
                             bd += 16;
@@ -339,18 +350,18 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                     }
                     // release the slot, except the A1 slot after its last colour chunk of the
                     // tile: the next tile's SDF layers own A1 until their MMAs are done
-                    if (!(f & kRecKeep)) mma_commit(bar_empty0 + 8 * s);
+                    if (!(f & kRecKeep)) commit_el(el, bar_empty0 + 8 * s);
                     if (f & kRecLast) {
-                        mma_commit(bar_acc);
+                        commit_el(el, bar_acc);
                         ++lc;
                         // the SDF MMAs are the last readers of A1 in this tile: release its slots
                         if (f & kRecRelA1)
-                            for (int i = kStages; i < kColSlots; ++i) mma_commit(bar_empty0 + 8 * i);
+                            for (int i = kStages; i < kColSlots; ++i) commit_el(el, bar_empty0 + 8 * i);
                     }
                     cr = nx;
                 }
             }
-            if (!ok) {
+            if (!ok && el) {
                 // wait for every MMA issued so far before TMEM is released
                 mma_commit(bar_drain);
                 for (uint32_t it = 0; it < kMaxSpin && !mbar_try(bar_drain, 0); ++it) {
@@ -772,6 +783,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
     const uint32_t bar_full0 = smem_u32(bars + 0), bar_empty0 = smem_u32(bars + kStages);
     const uint32_t bar_acc = smem_u32(bars + 2 * kStages), bar_a = smem_u32(bars + 2 * kStages + 1);
     const uint32_t bar_drain = smem_u32(bars + 2 * kStages + 2);
+    ValRec* s_rec = reinterpret_cast<ValRec*>(reinterpret_cast<uint8_t*>(bars) + kBarBytes);
+    constexpr int kChunksV = TA::sdf_chunks();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t total = sample_total(p.src);
     if (total > p.src.capacity) {
@@ -790,6 +803,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
         mbar_init(bar_drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // per-chunk records (offsets and descriptors computed here once instead of per chunk
+        // and tile in the producers' and the MMA warp's loops)
+        uint32_t off = 0;
+        for (int L = 0, j = 0; L < LS; ++L) {
+            const TcLayer ly = TA::layer(L);
+            const uint32_t a_sbo = (uint32_t)(ly.Kp / 8) * 128u;
+            const int n_mma = L == LS - 1 ? 16 : ly.Np;
+            for (int c = 0; c < TA::chunks(L); ++c, ++j) {
+                const int kc = TA::chunk_k(L, c);
+                const int k0 = c * kKChunk;
+                ValRec r;
+                r.bd0 = mdesc(smem_u32(stage_base), 128, (uint32_t)(kc / 8) * 128u);
+                r.ad = mdesc(smem_u32(A0) + (uint32_t)(k0 / 8) * 128u, 128, a_sbo);
+                r.id = idesc_mma<F16>(128, n_mma);
+                r.flags = (uint32_t)(kc / 16) | (c == 0 ? kRecFirst : 0u) | (c + 1 == TA::chunks(L) ? kRecLast : 0u);
+                r.off = off;
+                r.bytes = (uint32_t)TA::chunk_bytes(L, c);
+                off += r.bytes;
+                s_rec[j] = r;
+            }
+        }
     }
     for (int i = threadIdx.x; i < TA::bias_offset(LS); i += kThreads) {
         int L = 0;
@@ -814,20 +848,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
             uint32_t seq = 0, issued = 0;
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-                uint32_t off = 0;   // packed offset of chunk (L, c), kept running
-                for (int L = 0; L < LS && ok; ++L) {
-                    for (int c = 0; c < TA::chunks(L); ++c, ++seq) {
-                        const uint32_t bytes = (uint32_t)TA::chunk_bytes(L, c);
-                        const uint32_t at = off;
-                        off += bytes;
-                        if (seq % kStages != own) continue;
-                        if (tile == blockIdx.x && (int)seq == p.withhold) { ok = false; break; }
-                        const uint32_t ph = (seq / kStages) & 1u;
-                        if (!mbar_wait(bar_empty0 + 8 * own, ph ^ 1u, abort_flag, p.spin)) { ok = false; break; }
-                        mbar_expect_tx(bar_full0 + 8 * own, bytes);
-                        bulk_g2s(smem_u32(stage_base + own * kStage), p.packed + at, bytes, bar_full0 + 8 * own);
-                        ++issued;
-                    }
+                for (int j = 0; j < kChunksV; ++j, ++seq) {
+                    if (seq % kStages != own) continue;
+                    if (tile == blockIdx.x && (int)seq == p.withhold) { ok = false; break; }
+                    const ValRec& r = s_rec[j];
+                    const uint32_t ph = (seq / kStages) & 1u;
+                    if (!mbar_wait(bar_empty0 + 8 * own, ph ^ 1u, abort_flag, p.spin)) { ok = false; break; }
+                    mbar_expect_tx(bar_full0 + 8 * own, r.bytes);
+                    bulk_g2s(smem_u32(stage_base + own * kStage), p.packed + r.off, r.bytes, bar_full0 + 8 * own);
+                    ++issued;
                 }
             }
             if (!ok && issued > 0) {
@@ -836,42 +865,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
             }
         }
     } else if (warp == kMmaWarp) {
-        if (lane == 0) {
+        // the whole warp runs the issue loop (converged: the descriptors stay warp-uniform),
+        // one elected lane issues the MMAs and commits
+        {
+            const uint32_t el = elect_one();
             uint32_t seq = 0, lc = 0;
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-                for (int L = 0; L < LS && ok; ++L, ++lc) {
-                    const TcLayer ly = TA::layer(L);
-                    if (!mbar_wait(bar_a, lc & 1u, abort_flag, p.spin)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t a_sbo = (uint32_t)(ly.Kp / 8) * 128u;
-                    const uint32_t a0 = smem_u32(A0);
-                    const int n_mma = L == LS - 1 ? 16 : ly.Np;
-                    for (int c = 0; c < TA::chunks(L); ++c) {
-                        const uint32_t s = seq % kStages, ph = (seq / kStages) & 1u;
-                        if (!mbar_wait(bar_full0 + 8 * s, ph, abort_flag, p.spin)) { ok = false; break; }
+                ValRec cr = s_rec[0];
+                for (int j = 0; j < kChunksV; ++j, ++seq) {
+                    const uint32_t f = cr.flags;
+                    if (f & kRecFirst) {
+                        if (!__all_sync(0xffffffffu, mbar_wait(bar_a, lc & 1u, abort_flag, p.spin))) { ok = false; break; }
                         tc_fence_after();
-                        const int kc = TA::chunk_k(L, c);
-                        const uint32_t b0 = smem_u32(stage_base + s * kStage);
-                        const uint32_t b_sbo = (uint32_t)(kc / 8) * 128u;
-                        // descriptors built once per chunk, advanced by 16 (256 bytes) per K step
-                        const int k0 = c * kKChunk;
-                        uint64_t ad = mdesc(a0 + (uint32_t)(k0 / 8) * 128u, 128, a_sbo);
-                        uint64_t bd = mdesc(b0, 128, b_sbo);
-                        const uint32_t id = idesc_mma<F16>(128, n_mma);
-                        for (int kk = 0; kk < kc / 16; ++kk) {
-                            mma_bf16(tmem, ad, bd, id, (k0 | kk) != 0 ? 1u : 0u);
-                            ad += 16;
-                            bd += 16;
-                        }
-                        mma_commit(bar_empty0 + 8 * s);
-                        ++seq;
                     }
-                    if (!ok) break;
-                    mma_commit(bar_acc);
+                    const uint32_t s = seq % kStages, ph = (seq / kStages) & 1u;
+                    if (!__all_sync(0xffffffffu, mbar_wait(bar_full0 + 8 * s, ph, abort_flag, p.spin))) { ok = false; break; }
+                    tc_fence_after();
+                    const ValRec nx = s_rec[j + 1 < kChunksV ? j + 1 : 0];
+                    // descriptors of the chunk's first K step (the weights' moved to stage s:
+                    // kStage / 16 in the address field, which stays below 2^14), advanced by 16
+                    // (256 bytes) per K step
+                    uint64_t ad = cr.ad, bd = cr.bd0 + (uint64_t)(s * (kStage >> 4));
+                    uint32_t acc = (f & kRecFirst) ? 0u : 1u;
+                    for (int kk = 0; kk < (int)(f & kRecNk); ++kk) {
+                        mma_el(el, tmem, ad, bd, cr.id, acc);
+                        acc = 1u;
+                        ad += 16;
+                        bd += 16;
+                    }
+                    commit_el(el, bar_empty0 + 8 * s);
+                    if (f & kRecLast) {
+                        commit_el(el, bar_acc);
+                        ++lc;
+                    }
+                    cr = nx;
                 }
             }
-            if (!ok) {
+            if (!ok && el) {
                 mma_commit(bar_drain);
                 for (uint32_t it = 0; it < kMaxSpin && !mbar_try(bar_drain, 0); ++it) {
                 }
@@ -975,7 +1006,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_value(TcParams p, float*
 template <int ARCH, bool F16>
 int launch_tc_value(const tsdfs_mlp* m, const SampleSource& src, float* f_out, cudaStream_t st) {
     using TA = TcArch<ARCH>;
-    const size_t smem = 2 * kABytes + kStages * (size_t)TA::stage_bytes() + TA::bias_bytes() + kBarBytes;
+    const size_t smem = 2 * kABytes + kStages * (size_t)TA::stage_bytes() + TA::bias_bytes() + kBarBytes +
+                        (size_t)TA::sdf_chunks() * sizeof(ValRec);
     static bool attr[2] = {false, false};
     if (!attr[ARCH]) {
         int rc = cuda_check(cudaFuncSetAttribute(k_mlp_tc_value<ARCH, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
