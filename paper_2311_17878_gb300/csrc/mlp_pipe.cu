@@ -276,8 +276,11 @@ __global__ void __launch_bounds__(PipeMode<MODE>::kThreads, 1) k_mlp_pipe(PipePa
             }
         }
     } else if (warp == kPMmaWarp) {
-        // ---------------------------------------------------------------- MMA issuer
-        if (lane == 0) {
+        // ---------------------------------------------------------------- MMA issuer: the
+        // whole warp runs the loop (converged: the descriptors stay warp-uniform), one elected
+        // lane issues the MMAs and commits
+        {
+            const uint32_t el = elect_one();
             uint32_t full_uses[kStages], blk_uses[kPMaxBlocks];
 #pragma unroll
             for (int i = 0; i < kStages; ++i) full_uses[i] = 0;
@@ -299,13 +302,13 @@ __global__ void __launch_bounds__(PipeMode<MODE>::kThreads, 1) k_mlp_pipe(PipePa
 #pragma unroll
                         for (int i = 0; i < kPMaxBlocks; ++i)
                             if (i == c) bph = blk_uses[i]++ & 1u;
-                        if (!mbar_wait(bar_blk0 + 8 * c, bph, abort_flag, p.spin)) { ok = false; break; }
+                        if (!__all_sync(0xffffffffu, mbar_wait(bar_blk0 + 8 * c, bph, abort_flag, p.spin))) { ok = false; break; }
                         const PChunk ci = s_chunks[j];
                         uint32_t fph = 0;
 #pragma unroll
                         for (int i = 0; i < kStages; ++i)
                             if ((uint32_t)i == ci.slot) fph = full_uses[i]++ & 1u;
-                        if (!mbar_wait(bar_full0 + 8 * ci.slot, fph, abort_flag, p.spin)) { ok = false; break; }
+                        if (!__all_sync(0xffffffffu, mbar_wait(bar_full0 + 8 * ci.slot, fph, abort_flag, p.spin))) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t b0 = smem_u32(stage_base + ci.slot * kStage);
                         const uint32_t b_sbo = (uint32_t)(ci.kc / 8) * 128u;
@@ -317,8 +320,8 @@ __global__ void __launch_bounds__(PipeMode<MODE>::kThreads, 1) k_mlp_pipe(PipePa
                             const uint32_t ko = (uint32_t)(k0 / 8) * 128u;
                             uint64_t ah = mdesc(a_hi + ko, 128, a_sbo), al = mdesc(a_lo + ko, 128, a_sbo);
                             for (int kk = 0; kk < ci.kc / 16; ++kk) {
-                                mma_bf16(d_tmem, ah, bd, idesc, (k0 | kk) != 0 ? 1u : 0u);
-                                if (two) mma_bf16(d_tmem, al, bd, idesc, 1u);
+                                mma_el(el, d_tmem, ah, bd, idesc, (k0 | kk) != 0 ? 1u : 0u);
+                                if (two) mma_el(el, d_tmem, al, bd, idesc, 1u);
                                 ah += 16;
                                 al += 16;
                                 bd += 16;
@@ -326,18 +329,18 @@ __global__ void __launch_bounds__(PipeMode<MODE>::kThreads, 1) k_mlp_pipe(PipePa
                         } else {
                             uint64_t ax = mdesc(a_x + (uint32_t)((k0 - 256) / 8) * 128u, 128, (uint32_t)(TA::kPitchX / 8) * 128u);
                             for (int kk = 0; kk < ci.kc / 16; ++kk) {
-                                mma_bf16(d_tmem, ax, bd, idesc, 1u);
+                                mma_el(el, d_tmem, ax, bd, idesc, 1u);
                                 ax += 16;
                                 bd += 16;
                             }
                         }
-                        mma_commit(bar_empty0 + 8 * ci.slot);
+                        commit_el(el, bar_empty0 + 8 * ci.slot);
                     }
                     if (!ok) break;
-                    mma_commit(bar_accf0 + 8 * (lc & 1u));
+                    commit_el(el, bar_accf0 + 8 * (lc & 1u));
                 }
             }
-            if (!ok) {
+            if (!ok && el) {
                 mma_commit(bar_drain);
                 for (uint32_t it = 0; it < kMaxSpin && !mbar_try(bar_drain, 0); ++it) {
                 }
