@@ -21,7 +21,8 @@
 //
 // The full kernel (SDF value, gradient and colour): 16 warps, one persistent CTA per SM.
 // Warps 0-11 are the epilogue (warp w: TMEM lane quarter w % 4, column part w / 4 of three),
-// warp 12 lane 0 issues the MMAs (warp 12 also allocates / frees TMEM), warps 13-15 lane 0
+// warp 12 issues the MMAs from precomputed per-chunk records, converged, through one elected
+// lane (warp 12 also allocates / frees TMEM), warps 13-15 lane 0
 // stream weight chunks, one per slot (two ring stages, and a slot in the free part of A1 while
 // the colour layers run): bulk copies issued by one thread towards different mbarriers do not
 // overlap (measured), so each slot has a thread of its own.  The value kernel (the
