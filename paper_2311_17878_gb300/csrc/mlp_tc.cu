@@ -71,19 +71,30 @@ template <int ARCH> struct TcFull : TcArch<ARCH, true> {
     using Base::kXp;
     using Base::stage_bytes;
     using Base::bias_bytes;
-    using Base::chunk_tab_bytes;
     using Base::max_rgb_chunk_bytes;
+    using Base::kH;
     using A = Arch<ARCH>;
     // per-tile sample table of the full kernel (coordinates, direction, t, delta, encodings)
     __host__ __device__ static constexpr uint32_t table_bytes() {
         return (uint32_t)(kTileS * (8 + 6 * (A::kPeSdf + A::kPeDir)) * 4);
     }
+    // tiles run in pairs: the SDF layers of both tiles, then the colour layers once for both
+    __host__ __device__ static constexpr int pair_chunks() { return 2 * Base::sdf_chunks() + Base::rgb_chunks(); }
+    __host__ __device__ static constexpr uint32_t pair_chunk_tab_bytes() {
+        return (uint32_t)((pair_chunks() * 12 + 15) / 16 * 16);
+    }
     // the MMA warp's per-chunk records (descriptors precomputed once per CTA): 32 bytes a chunk
-    __host__ __device__ static constexpr uint32_t mma_tab_bytes() { return (uint32_t)Base::total_chunks() * 32u; }
+    __host__ __device__ static constexpr uint32_t mma_tab_bytes() { return (uint32_t)pair_chunks() * 32u; }
     __host__ __device__ static constexpr size_t full_smem_bytes() {
         return 2 * (size_t)kABytes + kStages * (size_t)stage_bytes() + bias_bytes() + kBarBytes + table_bytes() +
-               chunk_tab_bytes() + mma_tab_bytes();
+               pair_chunk_tab_bytes() + mma_tab_bytes();
     }
+    // one 8-row core-matrix group of the last SDF layer's input rows (h) and of the folded colour
+    // input's extra columns; a pair's first tile parks its value rows (two groups per TMEM lane
+    // quarter of each) in global memory while the second tile's SDF layers run
+    __host__ __device__ static constexpr uint32_t h_grp() { return (uint32_t)(kH / 8) * 128u; }
+    __host__ __device__ static constexpr uint32_t x_grp() { return (uint32_t)(kXp / 8) * 128u; }
+    __host__ __device__ static constexpr uint32_t stash_bytes() { return 4u * 2u * (h_grp() + x_grp()); }
     // bytes at the start of A1 holding the folded colour input's x~ / direction / normal
     // columns (128 rows of kXp columns; its h columns are the last SDF layer's input rows in
     // A0), rounded up to 1 KB
@@ -121,7 +132,16 @@ constexpr uint32_t kRecLast = 1u << 6;       // last chunk of its layer: signal 
 constexpr uint32_t kRecRelA1 = 1u << 7;      // after the SDF MMAs: release the A1 slots
 constexpr int kRecSlotShift = 8;             // bits 8-9: weight slot
 constexpr uint32_t kRecPar = 1u << 10;       // parity of the slot's use within the tile
-constexpr uint32_t kRecFlip = 1u << 11;      // the slot's uses per tile are odd
+constexpr uint32_t kRecFlip = 1u << 11;      // the slot's uses per pair of tiles are odd
+constexpr uint32_t kRecRestore = 1u << 12;   // first colour chunk: the pair's first tile is back in place
+
+// most CTAs of one launch of the full kernel, and the global parking space of each: the first
+// tile of a pair keeps its last SDF layer's input value rows and its folded colour input
+// extras there while the second tile's SDF layers use the operand regions (the room networks
+// need the most: 4 x 2 x (4096 + 768) bytes)
+constexpr int kPairCtas = 256;
+constexpr uint32_t kStashMax = 4u * 2u * (4096u + 768u);
+__device__ __align__(128) uint8_t g_pair_stash[(size_t)kPairCtas * kStashMax];
 
 // the value kernel's record of one weight chunk (written once per CTA): packed offset and size
 // for its producers; for the MMA warp the descriptors of the chunk's first K step, the
@@ -158,12 +178,15 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
     uint8_t* stage_base = smem + 2 * kABytes;
     float* sbias = reinterpret_cast<float*>(stage_base + kStages * kStage);
     uint64_t* bars = reinterpret_cast<uint64_t*>(stage_base + kStages * kStage + TA::bias_bytes());
-    // bars: full[kSlots], empty[kSlots], acc_ready, a_ready, drain, table
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kSlots + 4);
+    // bars: full[kSlots], empty[kSlots], acc_ready, a_ready, drain, table, restored (the pair's
+    // first tile back in the operand regions)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kSlots + 5);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const uint32_t bar_full0 = smem_u32(bars + 0), bar_empty0 = smem_u32(bars + kSlots);
     const uint32_t bar_acc = smem_u32(bars + 2 * kSlots), bar_a = smem_u32(bars + 2 * kSlots + 1);
     const uint32_t bar_drain = smem_u32(bars + 2 * kSlots + 2), bar_tab = smem_u32(bars + 2 * kSlots + 3);
+    const uint32_t bar_rest = smem_u32(bars + 2 * kSlots + 4);
+    static_assert(TA::stash_bytes() <= kStashMax, "pair stash size");
     // weight slot of chunk c of layer L: SDF chunks alternate over the ring stages, colour
     // chunks cycle over the ring stages and the free part of A1; and the slot's shared address
     constexpr int kColSlots = kA1Slots ? kStages + TA::a1_slots() : kStages;
@@ -183,7 +206,8 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
     float* s_pe = s_x + kTileS * 8;
     float* s_pd = s_pe + kTileS * A::kPeSdf * 6;
     ChunkInfo* s_chunks = reinterpret_cast<ChunkInfo*>(reinterpret_cast<uint8_t*>(s_x) + TA::table_bytes());
-    MmaRec* s_mma = reinterpret_cast<MmaRec*>(reinterpret_cast<uint8_t*>(s_chunks) + TA::chunk_tab_bytes());
+    MmaRec* s_mma = reinterpret_cast<MmaRec*>(reinterpret_cast<uint8_t*>(s_chunks) + TA::pair_chunk_tab_bytes());
+    constexpr int kPC = TA::pair_chunks();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const int64_t total = sample_total(p.src);
@@ -192,7 +216,10 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
         return;
     }
     const int64_t n_tiles = (total + kTileS - 1) / kTileS;
-    if ((int64_t)blockIdx.x >= n_tiles) return;
+    // pair k: tiles 2k and 2k + 1 (the second past n_tiles when the count is odd: its samples
+    // are all invalid, its table zero and its records not written)
+    const int64_t n_pairs = (n_tiles + 1) / 2;
+    if ((int64_t)blockIdx.x >= n_pairs) return;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kSlots; ++i) {
@@ -203,30 +230,30 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
         mbar_init(bar_a, kEpiArrivals);
         mbar_init(bar_drain, 1);
         mbar_init(bar_tab, kEpiArrivals);
+        mbar_init(bar_rest, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        // the tile's chunk schedule, computed once (the producers and the MMA warp read it
-        // instead of re-deriving offsets and slots in their loops)
-        for (int L = 0, j = 0; L < NL; ++L)
-            for (int c = 0; c < TA::chunks(L); ++c, ++j) {
-                const uint32_t sl = slot_of(L, c);
-                const bool keep = sl >= (uint32_t)kStages && j - TA::sdf_chunks() + kColSlots >= TA::rgb_chunks();
-                s_chunks[j] = ChunkInfo{(uint32_t)TA::packed_offset(L, c), (uint32_t)TA::chunk_bytes(L, c), (uint16_t)sl,
-                                        (uint16_t)(TA::chunk_k(L, c) | (keep ? 0x8000 : 0))};
-            }
-        // the MMA warp's records: the same descriptors its loop computed per chunk before
+        // the pair's chunk schedule (the first tile's SDF layers, the second's, then the colour
+        // layers once), computed once: SDF chunks alternate over the ring stages, colour chunks
+        // cycle over the ring stages and the free part of A1 (the producers and the MMA warp
+        // read it instead of re-deriving offsets and slots in their loops)
+        static_assert(TA::layer(LS - 1).Np <= 256, "the SDF output layer fits one MMA per accumulator");
         {
-            static_assert(TA::layer(LS - 1).Np <= 256, "the SDF output layer fits one MMA per accumulator");
             int uses[kSlots];
             for (int i = 0; i < kSlots; ++i) uses[i] = 0;
             const uint32_t a0 = smem_u32(A0), a1 = smem_u32(A1);
-            for (int L = 0, j = 0; L < NL; ++L) {
+            int j = 0, sdf_j = 0, col_j = 0;
+            for (int u = 0; u < 2 * LS + (NL - LS); ++u) {
+                const int L = u < 2 * LS ? u % LS : u - LS;
                 const TcLayer ly = TA::layer(L);
                 const uint32_t a_sbo = (uint32_t)(ly.Kp / 8) * 128u;
                 for (int c = 0; c < TA::chunks(L); ++c, ++j) {
-                    const ChunkInfo ci = s_chunks[j];
-                    const uint32_t sl = ci.slot;
-                    const int kc = ci.kc_keep & 0x7fff;
+                    const uint32_t sl = L < LS ? (uint32_t)(sdf_j++ % kStages) : (uint32_t)(col_j % kColSlots);
+                    const bool keep = L >= LS && sl >= (uint32_t)kStages && col_j + kColSlots >= TA::rgb_chunks();
+                    if (L >= LS) ++col_j;
+                    const int kc = TA::chunk_k(L, c);
+                    s_chunks[j] = ChunkInfo{(uint32_t)TA::packed_offset(L, c), (uint32_t)TA::chunk_bytes(L, c), (uint16_t)sl,
+                                            (uint16_t)(kc | (keep ? 0x8000 : 0))};
                     const int k0 = c * kKChunk;
                     MmaRec r;
                     r.bd = mdesc(slot_addr(sl), 128, (uint32_t)(kc / 8) * 128u);
@@ -238,16 +265,18 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                                             : mdesc(a1 + (uint32_t)((k0 - TA::kH) / 8) * 128u, 128, (TA::kXp / 8) * 128u);
                     r.ad1 = mdesc(a1 + (uint32_t)(k0 / 8) * 128u, 128, a_sbo);
                     r.id = idesc_mma<F16>(128, ly.Np);
-                    r.flags = (uint32_t)(kc / 16) | (ly.sdf ? kRecTwo : 0u) | ((ci.kc_keep & 0x8000) ? kRecKeep : 0u) |
+                    // the A1 slots are released after the second tile's SDF MMAs (the last to read A1)
+                    r.flags = (uint32_t)(kc / 16) | (ly.sdf ? kRecTwo : 0u) | (keep ? kRecKeep : 0u) |
                               (c == 0 ? kRecFirst : 0u) | (c + 1 == TA::chunks(L) ? kRecLast : 0u) |
-                              (c + 1 == TA::chunks(L) && L == LS - 1 ? kRecRelA1 : 0u) | (sl << kRecSlotShift) |
+                              (c + 1 == TA::chunks(L) && u == 2 * LS - 1 ? kRecRelA1 : 0u) |
+                              (c == 0 && u == 2 * LS ? kRecRestore : 0u) | (sl << kRecSlotShift) |
                               ((uses[sl] & 1) ? kRecPar : 0u);
                     ++uses[sl];
                     s_mma[j] = r;
                 }
             }
-            for (int j = 0; j < TA::total_chunks(); ++j)
-                if (uses[s_chunks[j].slot] & 1) s_mma[j].flags |= kRecFlip;
+            for (int jj = 0; jj < kPC; ++jj)
+                if (uses[s_chunks[jj].slot] & 1) s_mma[jj].flags |= kRecFlip;
         }
     }
     // all biases of both networks, staged once (the two folded layers' from the packed buffer)
@@ -280,17 +309,17 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
         if (lane == 0 && warp - kMmaWarpF - 1 < kColSlots) {
             const uint32_t own = (uint32_t)(warp - kMmaWarpF - 1);
             // ring stages: use u waits for the release of use u - 1; the A1 slot: use u waits
-            // for release u (release 0 of a tile is the end of the SDF MMAs, which read A1)
+            // for release u (release 0 of a pair is the end of its SDF MMAs, which read A1)
             const uint32_t first = own < (uint32_t)kStages ? 1u : 0u;
             uint32_t issued = 0;
             bool ok = true;
             const uint32_t dst = slot_addr(own);
-            for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-                for (int j = 0; j < TA::total_chunks(); ++j) {
+            for (int64_t pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
+                for (int j = 0; j < kPC; ++j) {
                     const ChunkInfo ci = s_chunks[j];
                     if (ci.slot != own) continue;
-                    // test-only: stop before the withheld chunk of the first tile
-                    if (tile == blockIdx.x && j == p.withhold) { ok = false; break; }
+                    // test-only: stop before the withheld chunk of the first pair
+                    if (pr == blockIdx.x && j == p.withhold) { ok = false; break; }
                     if (!mbar_wait(bar_empty0 + 8 * own, (issued & 1u) ^ first, abort_flag, p.spin)) { ok = false; break; }
                     mbar_expect_tx(bar_full0 + 8 * own, ci.bytes);
                     bulk_g2s(dst, p.packed + ci.off, ci.bytes, bar_full0 + 8 * own);
@@ -312,19 +341,26 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
             const uint32_t el = elect_one();
             uint32_t lc = 0, tpar = 0;
             bool ok = true;
-            for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, tpar ^= 1u) {
+            for (int64_t pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x, tpar ^= 1u) {
                 MmaRec cr = s_mma[0];
-                for (int j = 0; j < TA::total_chunks(); ++j) {
+                for (int j = 0; j < kPC; ++j) {
                     const uint32_t f = cr.flags;
                     if (f & kRecFirst) {
                         if (!__all_sync(0xffffffffu, mbar_wait(bar_a, lc & 1u, abort_flag, p.spin))) { ok = false; break; }
+                        // the colour layers' first input rows also hold the pair's first tile, back
+                        // from its parking space
+                        if ((f & kRecRestore) &&
+                            !__all_sync(0xffffffffu, mbar_wait(bar_rest, tpar, abort_flag, p.spin))) {
+                            ok = false;
+                            break;
+                        }
                         tc_fence_after();
                     }
                     const uint32_t s = (f >> kRecSlotShift) & 3u;
                     const uint32_t ph = ((f & kRecPar) ? 1u : 0u) ^ ((f & kRecFlip) ? tpar : 0u);
                     if (!__all_sync(0xffffffffu, mbar_wait(bar_full0 + 8 * s, ph, abort_flag, p.spin))) { ok = false; break; }
                     tc_fence_after();
-                    const MmaRec nx = s_mma[j + 1 < TA::total_chunks() ? j + 1 : 0];
+                    const MmaRec nx = s_mma[j + 1 < kPC ? j + 1 : 0];
                     const int nk = (int)(f & kRecNk);
                     uint64_t ad0 = cr.ad0, bd = cr.bd;
                     uint32_t acc = (f & kRecFirst) ? 0u : 1u;
@@ -398,7 +434,29 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
             __syncwarp();
             if (!kWarpArrive || lane == 0) mbar_arrive(bar);
         };
-        auto build_table = [&](int64_t tile) -> bool {
+        // one epilogue thread parks the pair's first tile (its last SDF layer's input value rows
+        // in A0 and its folded colour input extras in A1, two 8-row groups per lane quarter each)
+        // in global memory with bulk copies, and brings it back into the tangent-row groups of
+        // the same regions once the second tile's SDF MMAs are done
+        const bool stasher = et == 4 * 32;
+        uint8_t* stash = g_pair_stash + (size_t)blockIdx.x * kStashMax;
+        auto build_table = [&](int64_t tile, bool between) -> bool {
+                if (between) {
+                    // every warp is past the first tile's SDF output layer (the last reader of
+                    // its table and the writer of its extras): park the first tile
+                    fence_proxy_async();
+                    epi_arrive(bar_tab);
+                    if (!__all_sync(0xffffffffu, mbar_wait(bar_tab, tab_ph & 1u, abort_flag, p.spin))) return false;
+                    ++tab_ph;
+                    if (stasher) {
+                        for (int qq = 0; qq < 4; ++qq) {
+                            bulk_s2g(stash + qq * 2u * TA::h_grp(), smem_u32(A0) + 4u * qq * TA::h_grp(), 2u * TA::h_grp());
+                            bulk_s2g(stash + 8u * TA::h_grp() + qq * 2u * TA::x_grp(), smem_u32(A1) + 4u * qq * TA::x_grp(),
+                                     2u * TA::x_grp());
+                        }
+                        bulk_commit();
+                    }
+                }
                 if (et < kTileS) {
                     const int64_t g = tile * kTileS + et;
                     float t = 0.0f, dl = 0.0f, xs[3] = {0.0f, 0.0f, 0.0f}, ds[3] = {0.0f, 0.0f, 0.0f};
@@ -454,211 +512,231 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                         }
                     }
                 }
+                // the parked rows must have been read before the second tile's layer-0 input
+                // overwrites them
+                if (between && stasher) bulk_wait_read();
                 epi_arrive(bar_tab);
                 if (!__all_sync(0xffffffffu, mbar_wait(bar_tab, tab_ph & 1u, abort_flag, p.spin))) return false;
                 ++tab_ph;
             return true;
         };
-        ok = build_table(blockIdx.x);
-        for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-            // (the sample table of this tile was built before the loop or during the last one)
-            // ---- layer-0 input: encoding rows, stored as 16x256b-ordered stmatrix fragments ----
-            {
-                constexpr int Kp0 = TA::layer(0).Kp;
-                const int sa = 16 * q + fs, sb = sa + 8;
-                const float* xa = s_x + sa * 8;
-                const float* xb = s_x + sb * 8;
-                const float* pa = s_pe + sa * A::kPeSdf * 6;
-                const float* pb = s_pe + sb * A::kPeSdf * 6;
-                const uint32_t row0 = smem_u32(A0) + a_off(32 * q + lane, 0, Kp0);
-                const uint32_t row1 = smem_u32(A1) + a_off(32 * q + lane, 0, Kp0);
-                for (int c8 = part_lo(Kp0, pt, kPartsF); c8 < part_hi(Kp0, pt, kPartsF); c8 += 8) {
-                    float v[4][4];   // [component][(sample a, col 0), (a, 1), (b, 0), (b, 1)]
-#pragma unroll
-                    for (int cp = 0; cp < 4; ++cp)
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int j = c8 + fc + (e & 1);
-                            v[cp][e] = j < A::kEnc ? enc_tab((e & 2) ? xb : xa, (e & 2) ? pb : pa, A::kPeSdf, j, cp) : 0.0f;
-                        }
-                    const uint32_t co = (uint32_t)(c8 >> 3) * 128u;
-                    stmatrix4(row0 + co, pack2<F16>(v[0][0], v[0][1]), pack2<F16>(v[0][2], v[0][3]),
-                              pack2<F16>(v[1][0], v[1][1]), pack2<F16>(v[1][2], v[1][3]));
-                    stmatrix4(row1 + co, pack2<F16>(v[2][0], v[2][1]), pack2<F16>(v[2][2], v[2][3]),
-                              pack2<F16>(v[3][0], v[3][1]), pack2<F16>(v[3][2], v[3][3]));
+        ok = build_table(2 * (int64_t)blockIdx.x, false);
+        for (int64_t pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
+            // ---- the SDF layers of the pair's two tiles ----
+            for (int pass = 0; pass < 2 && ok; ++pass) {
+                const int64_t tile = 2 * pr + pass;
+                if (pass == 1 && !build_table(tile, true)) {
+                    ok = false;
+                    break;
                 }
-            }
-            fence_proxy_async();
-            epi_arrive(bar_a);
-            float f_out = 0.0f, dd_out = 0.0f, gn_out = 0.0f, nrm[3] = {0.0f, 0.0f, 0.0f};
-            float rec_t = 0.0f, rec_dl = 0.0f;   // this row's sample t and delta, for the record
-            int boff = 0;                        // this layer's first bias (running, not re-derived)
-            for (int L = 0; L < NL; ++L, ++lc) {
-                const TcLayer ly = TA::layer(L);
-                const bool w_ok = mbar_wait(bar_acc, lc & 1u, abort_flag, p.spin);
-                if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
-                tc_fence_after();
-                const float* bias = sbias + boff;
-                boff += ly.Np;
-                const bool last = L == NL - 1;
-                if (ly.sdf && ly.idx < LS - 1) {
-                    // ---- hidden SDF layer -> next layer's input (skip concat when due) ----
-                    // thread: samples fs, fs + 8 of quarter q; columns c0 + 8g + fc + {0, 1};
-                    // stmatrix rows: lane i addresses A row 32q + i (value rows, then d/dx
-                    // rows in A0; d/dy, then d/dz in A1), matching the fragment order
-                    const int Kn = TA::layer(L + 1).Kp;
-                    const float sc = ly.idx + 1 == A::kSkip ? kInvSqrt2 : 1.0f;
-                    const uint32_t row0 = smem_u32(A0) + a_off(32 * q + lane, 0, Kn);
-                    const uint32_t row1 = smem_u32(A1) + a_off(32 * q + lane, 0, Kn);
-                    // the columns below c_fa (whole 16-column blocks of hidden units) are split
-                    // among the three parts; the slower tail groups above it (hidden units
-                    // < N mixed with the skip input's encoding) go round-robin to the parts
-                    const int c_fa = (ly.N / 16) * 16 < Kn ? (ly.N / 16) * 16 : Kn;
-                    const int c_lo = part8_lo(c_fa, pt, kPartsF), c_full = part8_hi(c_fa, pt, kPartsF);
-                    // 8-column groups, software-pipelined: the TMEM loads of group c + 8 are in
-                    // flight while group c is computed.  buf = [value(4) | d/dx(4) | d/dy(4) | d/dz(4)],
-                    // each 4 = (sample a, col 0), (a, col 1), (b, col 0), (b, col 1)
-                    auto ld8 = [&](int c, float (&d)[16]) {
-                        tmem_ld16x256_x1(t_v + c, d);
-                        tmem_ld16x256_x1(t_x + c, d + 4);
-                        tmem_ld16x256_x1(t_y + c, d + 8);
-                        tmem_ld16x256_x1(t_z + c, d + 12);
-                    };
-                    auto group = [&](int c, const float (&d)[16], auto skip_tag) {
-                        constexpr bool kSkipIn = decltype(skip_tag)::value;
-                        const float2 b = *reinterpret_cast<const float2*>(bias + c + fc);
-                        if constexpr (F16) {
-                            // pairs (sample a, columns c, c+1) and (sample b, columns c, c+1)
-                            __half2 hv2[2], xv2[2], yv2[2], zv2[2];
-#pragma unroll
-                            for (int pr = 0; pr < 2; ++pr) {
-                                __half2 h, sg;
-                                softplus_slope_h2(d[2 * pr] + b.x, d[2 * pr + 1] + b.y, spk, h, sg);
-                                if constexpr (kSkipIn) {
-                                    sg = __hmul2(sg, inv_sqrt2_h2);
-                                    h = __hmul2(h, inv_sqrt2_h2);
+                // (the sample table of this tile was built before the loop, during the last
+                // pair's colour layers, or just now)
+                // ---- layer-0 input: encoding rows, stored as 16x256b-ordered stmatrix fragments ----
+                {
+                    constexpr int Kp0 = TA::layer(0).Kp;
+                    const int sa = 16 * q + fs, sb = sa + 8;
+                    const float* xa = s_x + sa * 8;
+                    const float* xb = s_x + sb * 8;
+                    const float* pa = s_pe + sa * A::kPeSdf * 6;
+                    const float* pb = s_pe + sb * A::kPeSdf * 6;
+                    const uint32_t row0 = smem_u32(A0) + a_off(32 * q + lane, 0, Kp0);
+                    const uint32_t row1 = smem_u32(A1) + a_off(32 * q + lane, 0, Kp0);
+                    for (int c8 = part_lo(Kp0, pt, kPartsF); c8 < part_hi(Kp0, pt, kPartsF); c8 += 8) {
+                        float v[4][4];   // [component][(sample a, col 0), (a, 1), (b, 0), (b, 1)]
+    #pragma unroll
+                        for (int cp = 0; cp < 4; ++cp)
+    #pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int j = c8 + fc + (e & 1);
+                                v[cp][e] = j < A::kEnc ? enc_tab((e & 2) ? xb : xa, (e & 2) ? pb : pa, A::kPeSdf, j, cp) : 0.0f;
+                            }
+                        const uint32_t co = (uint32_t)(c8 >> 3) * 128u;
+                        stmatrix4(row0 + co, pack2<F16>(v[0][0], v[0][1]), pack2<F16>(v[0][2], v[0][3]),
+                                  pack2<F16>(v[1][0], v[1][1]), pack2<F16>(v[1][2], v[1][3]));
+                        stmatrix4(row1 + co, pack2<F16>(v[2][0], v[2][1]), pack2<F16>(v[2][2], v[2][3]),
+                                  pack2<F16>(v[3][0], v[3][1]), pack2<F16>(v[3][2], v[3][3]));
+                    }
+                }
+                fence_proxy_async();
+                epi_arrive(bar_a);
+                int boff = 0;   // this layer's first bias (running, not re-derived)
+                for (int L = 0; L < LS; ++L, ++lc) {
+                    const TcLayer ly = TA::layer(L);
+                    const bool w_ok = mbar_wait(bar_acc, lc & 1u, abort_flag, p.spin);
+                    if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
+                    tc_fence_after();
+                    const float* bias = sbias + boff;
+                    boff += ly.Np;
+                    if (pass == 1 && L == LS - 1 && stasher) {
+                        // the second tile's SDF MMAs are done: bring the first tile back into
+                        // the tangent-row groups of A0 and of A1's extras block
+                        bulk_wait();
+                        mbar_expect_tx(bar_rest, TA::stash_bytes());
+                        for (int qq = 0; qq < 4; ++qq) {
+                            bulk_g2s(smem_u32(A0) + (4u * qq + 2u) * TA::h_grp(), stash + qq * 2u * TA::h_grp(), 2u * TA::h_grp(),
+                                     bar_rest);
+                            bulk_g2s(smem_u32(A1) + (4u * qq + 2u) * TA::x_grp(), stash + 8u * TA::h_grp() + qq * 2u * TA::x_grp(),
+                                     2u * TA::x_grp(), bar_rest);
+                        }
+                    }
+                    if (ly.sdf && ly.idx < LS - 1) {
+                        // ---- hidden SDF layer -> next layer's input (skip concat when due) ----
+                        // thread: samples fs, fs + 8 of quarter q; columns c0 + 8g + fc + {0, 1};
+                        // stmatrix rows: lane i addresses A row 32q + i (value rows, then d/dx
+                        // rows in A0; d/dy, then d/dz in A1), matching the fragment order
+                        const int Kn = TA::layer(L + 1).Kp;
+                        const float sc = ly.idx + 1 == A::kSkip ? kInvSqrt2 : 1.0f;
+                        const uint32_t row0 = smem_u32(A0) + a_off(32 * q + lane, 0, Kn);
+                        const uint32_t row1 = smem_u32(A1) + a_off(32 * q + lane, 0, Kn);
+                        // the columns below c_fa (whole 16-column blocks of hidden units) are split
+                        // among the three parts; the slower tail groups above it (hidden units
+                        // < N mixed with the skip input's encoding) go round-robin to the parts
+                        const int c_fa = (ly.N / 16) * 16 < Kn ? (ly.N / 16) * 16 : Kn;
+                        const int c_lo = part8_lo(c_fa, pt, kPartsF), c_full = part8_hi(c_fa, pt, kPartsF);
+                        // 8-column groups, software-pipelined: the TMEM loads of group c + 8 are in
+                        // flight while group c is computed.  buf = [value(4) | d/dx(4) | d/dy(4) | d/dz(4)],
+                        // each 4 = (sample a, col 0), (a, col 1), (b, col 0), (b, col 1)
+                        auto ld8 = [&](int c, float (&d)[16]) {
+                            tmem_ld16x256_x1(t_v + c, d);
+                            tmem_ld16x256_x1(t_x + c, d + 4);
+                            tmem_ld16x256_x1(t_y + c, d + 8);
+                            tmem_ld16x256_x1(t_z + c, d + 12);
+                        };
+                        auto group = [&](int c, const float (&d)[16], auto skip_tag) {
+                            constexpr bool kSkipIn = decltype(skip_tag)::value;
+                            const float2 b = *reinterpret_cast<const float2*>(bias + c + fc);
+                            if constexpr (F16) {
+                                // pairs (sample a, columns c, c+1) and (sample b, columns c, c+1)
+                                __half2 hv2[2], xv2[2], yv2[2], zv2[2];
+    #pragma unroll
+                                for (int pr = 0; pr < 2; ++pr) {
+                                    __half2 h, sg;
+                                    softplus_slope_h2(d[2 * pr] + b.x, d[2 * pr + 1] + b.y, spk, h, sg);
+                                    if constexpr (kSkipIn) {
+                                        sg = __hmul2(sg, inv_sqrt2_h2);
+                                        h = __hmul2(h, inv_sqrt2_h2);
+                                    }
+                                    hv2[pr] = h;
+                                    xv2[pr] = __hmul2(sg, __floats2half2_rn(d[4 + 2 * pr], d[5 + 2 * pr]));
+                                    yv2[pr] = __hmul2(sg, __floats2half2_rn(d[8 + 2 * pr], d[9 + 2 * pr]));
+                                    zv2[pr] = __hmul2(sg, __floats2half2_rn(d[12 + 2 * pr], d[13 + 2 * pr]));
                                 }
-                                hv2[pr] = h;
-                                xv2[pr] = __hmul2(sg, __floats2half2_rn(d[4 + 2 * pr], d[5 + 2 * pr]));
-                                yv2[pr] = __hmul2(sg, __floats2half2_rn(d[8 + 2 * pr], d[9 + 2 * pr]));
-                                zv2[pr] = __hmul2(sg, __floats2half2_rn(d[12 + 2 * pr], d[13 + 2 * pr]));
+                                const uint32_t co = (uint32_t)(c >> 3) * 128u;
+                                stmatrix4(row0 + co, h2u(hv2[0]), h2u(hv2[1]), h2u(xv2[0]), h2u(xv2[1]));
+                                stmatrix4(row1 + co, h2u(yv2[0]), h2u(yv2[1]), h2u(zv2[0]), h2u(zv2[1]));
+                                return;
+                            }
+                            float hv[4], xv[4], yv[4], zv[4];
+    #pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                float h, sg;
+                                softplus_slope_tanh(d[e] + ((e & 1) ? b.y : b.x), half_beta, inv_beta, h, sg);
+                                if constexpr (kSkipIn) {
+                                    sg *= kInvSqrt2;
+                                    h *= kInvSqrt2;
+                                }
+                                hv[e] = h;
+                                xv[e] = sg * d[4 + e];
+                                yv[e] = sg * d[8 + e];
+                                zv[e] = sg * d[12 + e];
                             }
                             const uint32_t co = (uint32_t)(c >> 3) * 128u;
-                            stmatrix4(row0 + co, h2u(hv2[0]), h2u(hv2[1]), h2u(xv2[0]), h2u(xv2[1]));
-                            stmatrix4(row1 + co, h2u(yv2[0]), h2u(yv2[1]), h2u(zv2[0]), h2u(zv2[1]));
-                            return;
-                        }
-                        float hv[4], xv[4], yv[4], zv[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            float h, sg;
-                            softplus_slope_tanh(d[e] + ((e & 1) ? b.y : b.x), half_beta, inv_beta, h, sg);
-                            if constexpr (kSkipIn) {
-                                sg *= kInvSqrt2;
-                                h *= kInvSqrt2;
+                            stmatrix4(row0 + co, pack2<F16>(hv[0], hv[1]), pack2<F16>(hv[2], hv[3]),
+                                      pack2<F16>(xv[0], xv[1]), pack2<F16>(xv[2], xv[3]));
+                            stmatrix4(row1 + co, pack2<F16>(yv[0], yv[1]), pack2<F16>(yv[2], yv[3]),
+                                      pack2<F16>(zv[0], zv[1]), pack2<F16>(zv[2], zv[3]));
+                        };
+                        auto body = [&](auto skip_tag) {
+                            if (c_full <= c_lo) return;
+                            const int ng = (c_full - c_lo) / 8;   // groups of this part below c_full
+                            float bufA[16], bufB[16];
+                            ld8(c_lo, bufA);
+                            tmem_wait_ld16(bufA);
+                            int gi = 0;
+                            for (; gi + 1 < ng; gi += 2) {
+                                const int c0 = c_lo + 8 * gi;
+                                ld8(c0 + 8, bufB);
+                                group(c0, bufA, skip_tag);
+                                tmem_wait_ld16(bufB);
+                                const bool more = gi + 2 < ng;
+                                if (more) ld8(c0 + 16, bufA);
+                                group(c0 + 8, bufB, skip_tag);
+                                if (more) tmem_wait_ld16(bufA);
                             }
-                            hv[e] = h;
-                            xv[e] = sg * d[4 + e];
-                            yv[e] = sg * d[8 + e];
-                            zv[e] = sg * d[12 + e];
-                        }
-                        const uint32_t co = (uint32_t)(c >> 3) * 128u;
-                        stmatrix4(row0 + co, pack2<F16>(hv[0], hv[1]), pack2<F16>(hv[2], hv[3]),
-                                  pack2<F16>(xv[0], xv[1]), pack2<F16>(xv[2], xv[3]));
-                        stmatrix4(row1 + co, pack2<F16>(yv[0], yv[1]), pack2<F16>(yv[2], yv[3]),
-                                  pack2<F16>(zv[0], zv[1]), pack2<F16>(zv[2], zv[3]));
-                    };
-                    auto body = [&](auto skip_tag) {
-                        if (c_full <= c_lo) return;
-                        const int ng = (c_full - c_lo) / 8;   // groups of this part below c_full
-                        float bufA[16], bufB[16];
-                        ld8(c_lo, bufA);
-                        tmem_wait_ld16(bufA);
-                        int gi = 0;
-                        for (; gi + 1 < ng; gi += 2) {
-                            const int c0 = c_lo + 8 * gi;
-                            ld8(c0 + 8, bufB);
-                            group(c0, bufA, skip_tag);
-                            tmem_wait_ld16(bufB);
-                            const bool more = gi + 2 < ng;
-                            if (more) ld8(c0 + 16, bufA);
-                            group(c0 + 8, bufB, skip_tag);
-                            if (more) tmem_wait_ld16(bufA);
-                        }
-                        if (gi < ng) group(c_lo + 8 * gi, bufA, skip_tag);   // an odd count: the last group
-                    };
-                    if (sc != 1.0f) body(std::integral_constant<bool, true>{});
-                    else body(std::integral_constant<bool, false>{});
-                    // tail: hidden units < N, then gamma(x~) / sqrt(2) (the skip input), then zeros
-                    const float* sxa = s_x + (16 * q + fs) * 8;
-                    const float* sxb = sxa + 8 * 8;
-                    const float* spa = s_pe + (16 * q + fs) * A::kPeSdf * 6;
-                    const float* spb = spa + 8 * A::kPeSdf * 6;
-                    for (int c8 = c_fa + 8 * pt; c8 < Kn; c8 += 8 * kPartsF) {
-                        float d[16];   // [value(4) | d/dx(4) | d/dy(4) | d/dz(4)], as ld8
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) d[j] = 0.0f;
-                        if (c8 < ly.Np) {
-                            ld8(c8, d);
-                            tmem_wait_ld16(d);
-                        }
-                        float hv[4], xv[4], yv[4], zv[4];
-#pragma unroll
-                        for (int cc = 0; cc < 2; ++cc) {
-                            const int col = c8 + fc + cc;
-                            if (col < ly.N) {
-#pragma unroll
-                                for (int e = cc; e < 4; e += 2) {
-                                    float h, sg;
-                                    softplus_slope_tanh(d[e] + bias[col], half_beta, inv_beta, h, sg);
-                                    sg *= sc;
-                                    hv[e] = h * sc;
-                                    xv[e] = sg * d[4 + e];
-                                    yv[e] = sg * d[8 + e];
-                                    zv[e] = sg * d[12 + e];
-                                }
-                            } else {
-                                // encoding entry en of both samples: decoded once per column
-                                const int en = col - ly.N;
-                                const int qq = en - 3, oct = qq / 6, part = (qq % 6) / 3, b = en < 3 ? en : qq % 3;
-                                const bool coord = en < 3, in = en < A::kEnc && (coord || oct < A::kPeSdf);
-                                const float f = coord ? 1.0f : (float)(1 << (oct > 0 ? oct : 0)) * sc;
-                                const int ti = ((coord ? 0 : oct) * 3 + b) * 2;
-#pragma unroll
-                                for (int e = cc; e < 4; e += 2) {
-                                    const float* sx = (e & 2) ? sxb : sxa;
-                                    const float* sp = (e & 2) ? spb : spa;
-                                    float val = 0.0f, der = 0.0f;
-                                    if (in) {
-                                        if (coord) {
-                                            val = sx[b] * sc;
-                                            der = sc;
-                                        } else {
-                                            const float sn = sp[ti], cs = sp[ti + 1];
-                                            val = (part == 0 ? sn : cs) * sc;
-                                            der = part == 0 ? f * cs : -f * sn;
-                                        }
+                            if (gi < ng) group(c_lo + 8 * gi, bufA, skip_tag);   // an odd count: the last group
+                        };
+                        if (sc != 1.0f) body(std::integral_constant<bool, true>{});
+                        else body(std::integral_constant<bool, false>{});
+                        // tail: hidden units < N, then gamma(x~) / sqrt(2) (the skip input), then zeros
+                        const float* sxa = s_x + (16 * q + fs) * 8;
+                        const float* sxb = sxa + 8 * 8;
+                        const float* spa = s_pe + (16 * q + fs) * A::kPeSdf * 6;
+                        const float* spb = spa + 8 * A::kPeSdf * 6;
+                        for (int c8 = c_fa + 8 * pt; c8 < Kn; c8 += 8 * kPartsF) {
+                            float d[16];   // [value(4) | d/dx(4) | d/dy(4) | d/dz(4)], as ld8
+    #pragma unroll
+                            for (int j = 0; j < 16; ++j) d[j] = 0.0f;
+                            if (c8 < ly.Np) {
+                                ld8(c8, d);
+                                tmem_wait_ld16(d);
+                            }
+                            float hv[4], xv[4], yv[4], zv[4];
+    #pragma unroll
+                            for (int cc = 0; cc < 2; ++cc) {
+                                const int col = c8 + fc + cc;
+                                if (col < ly.N) {
+    #pragma unroll
+                                    for (int e = cc; e < 4; e += 2) {
+                                        float h, sg;
+                                        softplus_slope_tanh(d[e] + bias[col], half_beta, inv_beta, h, sg);
+                                        sg *= sc;
+                                        hv[e] = h * sc;
+                                        xv[e] = sg * d[4 + e];
+                                        yv[e] = sg * d[8 + e];
+                                        zv[e] = sg * d[12 + e];
                                     }
-                                    hv[e] = val;
-                                    xv[e] = b == 0 ? der : 0.0f;
-                                    yv[e] = b == 1 ? der : 0.0f;
-                                    zv[e] = b == 2 ? der : 0.0f;
+                                } else {
+                                    // encoding entry en of both samples: decoded once per column
+                                    const int en = col - ly.N;
+                                    const int qq = en - 3, oct = qq / 6, part = (qq % 6) / 3, b = en < 3 ? en : qq % 3;
+                                    const bool coord = en < 3, in = en < A::kEnc && (coord || oct < A::kPeSdf);
+                                    const float f = coord ? 1.0f : (float)(1 << (oct > 0 ? oct : 0)) * sc;
+                                    const int ti = ((coord ? 0 : oct) * 3 + b) * 2;
+    #pragma unroll
+                                    for (int e = cc; e < 4; e += 2) {
+                                        const float* sx = (e & 2) ? sxb : sxa;
+                                        const float* sp = (e & 2) ? spb : spa;
+                                        float val = 0.0f, der = 0.0f;
+                                        if (in) {
+                                            if (coord) {
+                                                val = sx[b] * sc;
+                                                der = sc;
+                                            } else {
+                                                const float sn = sp[ti], cs = sp[ti + 1];
+                                                val = (part == 0 ? sn : cs) * sc;
+                                                der = part == 0 ? f * cs : -f * sn;
+                                            }
+                                        }
+                                        hv[e] = val;
+                                        xv[e] = b == 0 ? der : 0.0f;
+                                        yv[e] = b == 1 ? der : 0.0f;
+                                        zv[e] = b == 2 ? der : 0.0f;
+                                    }
                                 }
                             }
+                            const uint32_t co = (uint32_t)(c8 >> 3) * 128u;
+                            stmatrix4(row0 + co, pack2<F16>(hv[0], hv[1]), pack2<F16>(hv[2], hv[3]),
+                                      pack2<F16>(xv[0], xv[1]), pack2<F16>(xv[2], xv[3]));
+                            stmatrix4(row1 + co, pack2<F16>(yv[0], yv[1]), pack2<F16>(yv[2], yv[3]),
+                                      pack2<F16>(zv[0], zv[1]), pack2<F16>(zv[2], zv[3]));
                         }
-                        const uint32_t co = (uint32_t)(c8 >> 3) * 128u;
-                        stmatrix4(row0 + co, pack2<F16>(hv[0], hv[1]), pack2<F16>(hv[2], hv[3]),
-                                  pack2<F16>(xv[0], xv[1]), pack2<F16>(xv[2], xv[3]));
-                        stmatrix4(row1 + co, pack2<F16>(yv[0], yv[1]), pack2<F16>(yv[2], yv[3]),
-                                  pack2<F16>(zv[0], zv[1]), pack2<F16>(zv[2], zv[3]));
-                    }
-                } else if (ly.sdf) {
-                    // ---- SDF output layer, folded to its value column: f and grad f from column 0
-                    // of both accumulators, then the folded colour input's x~ / direction / normal
-                    // columns at the start of A1 (its h columns are this layer's input rows in A0) ----
-                    constexpr int kDir = A::kDirEnc;
-                    constexpr int kXp = TA::kXp;
-                    if (pt == 0) {
+                    } else if (pt == 0) {
+                        // ---- SDF output layer, folded to its value column: f and grad f from column 0
+                        // of both accumulators; the record's SDF part now, its colour later; the folded
+                        // colour input's x~ / direction / normal columns in the value rows at the
+                        // start of A1 (its h columns are this layer's input rows in A0) ----
+                        constexpr int kDir = A::kDirEnc;
+                        constexpr int kXp = TA::kXp;
                         float x0[16], x1[16];
                         tmem_ld16(tmem + lane_addr, x0);
                         tmem_ld16(tmem + 256 + lane_addr, x1);
@@ -666,77 +744,105 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                         const float gx = __shfl_sync(0xffffffffu, x0[0], val_lane + 16);
                         const float gz = __shfl_sync(0xffffffffu, x1[0], val_lane + 16);
                         const float gy = x1[0];
-                        float n_hat[3] = {0.0f, 0.0f, 0.0f};
-                        float venc[kDir];
-                        f_out = p.scale * (x0[0] + bias[0]);
-                        gn_out = sqrtf(gx * gx + gy * gy + gz * gz);
-                        const float inv = gn_out > 0.0f ? 1.0f / gn_out : 0.0f;
-                        n_hat[0] = gx * inv; n_hat[1] = gy * inv; n_hat[2] = gz * inv;
-                        nrm[0] = n_hat[0]; nrm[1] = n_hat[1]; nrm[2] = n_hat[2];
-                        const float* ds = s_x + s * 8 + 3;
-                        dd_out = gx * ds[0] + gy * ds[1] + gz * ds[2];
-                        rec_t = s_x[s * 8 + 6];
-                        rec_dl = s_x[s * 8 + 7];
-#pragma unroll
-                        for (int e = 0; e < kDir; ++e) venc[e] = enc_tab(ds, s_pd + s * A::kPeDir * 6, A::kPeDir, e, 0);
-                        // value rows: [x~ (3), direction encoding, unit normal (3), 0 pad]; the
-                        // other rows (tangent rows, whose colour outputs are not read) zero
-#pragma unroll
-                        for (int c0 = 0; c0 < kXp; c0 += 8) {
-                            float o[8];
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const int col = c0 + j;
-                                float v = 0.0f;
-                                if (col < 3) v = s_x[s * 8 + (col < 3 ? col : 0)];
-                                else if (col < 3 + kDir) v = venc[col - 3 < kDir ? col - 3 : 0];
-                                else if (col < 3 + kDir + 3) v = n_hat[col - 3 - kDir < 3 ? col - 3 - kDir : 0];
-                                o[j] = is_val ? v : 0.0f;
+                        if (is_val) {
+                            float n_hat[3];
+                            float venc[kDir];
+                            const float f_v = p.scale * (x0[0] + bias[0]);
+                            const float gn = sqrtf(gx * gx + gy * gy + gz * gz);
+                            const float inv = gn > 0.0f ? 1.0f / gn : 0.0f;
+                            n_hat[0] = gx * inv; n_hat[1] = gy * inv; n_hat[2] = gz * inv;
+                            const float* ds = s_x + s * 8 + 3;
+                            const int64_t g = tile * kTileS + s;
+                            if (g < total) {
+                                float4* R4 = reinterpret_cast<float4*>(p.rec + g);
+                                R4[0] = make_float4(f_v, gx * ds[0] + gy * ds[1] + gz * ds[2], s_x[s * 8 + 6], s_x[s * 8 + 7]);
+                                R4[2] = make_float4(n_hat[0], n_hat[1], n_hat[2], 0.0f);
+                                reinterpret_cast<float*>(R4 + 1)[3] = gn;
                             }
-                            st_row8<F16>(A1, r, c0, kXp, o);
+#pragma unroll
+                            for (int e = 0; e < kDir; ++e) venc[e] = enc_tab(ds, s_pd + s * A::kPeDir * 6, A::kPeDir, e, 0);
+                            // value rows: [x~ (3), direction encoding, unit normal (3), 0 pad]; the
+                            // tangent-row groups are the other tile's (parked, or brought back)
+#pragma unroll
+                            for (int c0 = 0; c0 < kXp; c0 += 8) {
+                                float o[8];
+#pragma unroll
+                                for (int jj = 0; jj < 8; ++jj) {
+                                    const int col = c0 + jj;
+                                    float v = 0.0f;
+                                    if (col < 3) v = s_x[s * 8 + (col < 3 ? col : 0)];
+                                    else if (col < 3 + kDir) v = venc[col - 3 < kDir ? col - 3 : 0];
+                                    else if (col < 3 + kDir + 3) v = n_hat[col - 3 - kDir < 3 ? col - 3 - kDir : 0];
+                                    o[jj] = v;
+                                }
+                                st_row8<F16>(A1, r, c0, kXp, o);
+                            }
                         }
                     }
-                } else if (!last) {
-                    // ---- hidden colour layer (ReLU), value rows only: a 16x256b fragment at
-                    // lane 32q holds value rows only (samples 16q + fs and 16q + 8 + fs) ----
+                    tc_fence_before();
+                    // the first tile's SDF output layer feeds no MMA: the second tile's layer 0 is next
+                    if (L < LS - 1 || pass == 1) {
+                        fence_proxy_async();
+                        epi_arrive(bar_a);
+                    }
+                }
+            }
+            if (!ok) break;
+            // ---- the colour layers once for both tiles: rows 32q..32q+15 of each lane quarter
+            // hold the second tile's samples, rows 32q+16..32q+31 the first's ----
+            int boff = TA::bias_offset(LS);
+            for (int L = LS; L < NL; ++L, ++lc) {
+                const TcLayer ly = TA::layer(L);
+                const bool w_ok = mbar_wait(bar_acc, lc & 1u, abort_flag, p.spin);
+                if (!__all_sync(0xffffffffu, w_ok)) { ok = false; break; }
+                tc_fence_after();
+                const float* bias = sbias + boff;
+                boff += ly.Np;
+                const bool last = L == NL - 1;
+                if (!last) {
+                    // ---- hidden colour layer (ReLU), all 128 rows: 16x256b fragments at lanes
+                    // 32q (samples 16q + fs, 16q + 8 + fs of the second tile) and 32q + 16 (the
+                    // same of the first) ----
                     const int Kn = TA::layer(L + 1).Kp;
                     const uint32_t row0 = smem_u32(A0) + a_off(32 * q + (lane & 15), 0, Kn);
+                    const uint32_t row1 = smem_u32(A0) + a_off(32 * q + 16 + (lane & 15), 0, Kn);
                     for (int c0 = part_lo(Kn, pt, kPartsF); c0 < part_hi(Kn, pt, kPartsF); c0 += 16) {
-                        float v[8];
+                        float v[8], w[8];
                         if (c0 < ly.Np) {
                             tmem_ld16x256_x2(t_v + c0, v);
+                            tmem_ld16x256_x2(t_x + c0, w);
                             tmem_wait_ld();
                         } else {
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) v[e] = 0.0f;
+                            for (int e = 0; e < 8; ++e) v[e] = w[e] = 0.0f;
                         }
 #pragma unroll
                         for (int g8 = 0; g8 < 2; ++g8) {
-                            float o[4];
+                            float o[4], o1[4];
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 const int col = c0 + 8 * g8 + fc + (e & 1);
-                                o[e] = col < ly.N ? fmaxf(v[4 * g8 + e] + bias[col], 0.0f) : 0.0f;
+                                const float bc = col < ly.N ? bias[col] : 0.0f;
+                                o[e] = col < ly.N ? fmaxf(v[4 * g8 + e] + bc, 0.0f) : 0.0f;
+                                o1[e] = col < ly.N ? fmaxf(w[4 * g8 + e] + bc, 0.0f) : 0.0f;
                             }
-                            stmatrix2(row0 + (uint32_t)((c0 + 8 * g8) >> 3) * 128u, pack2<F16>(o[0], o[1]),
-                                      pack2<F16>(o[2], o[3]));
+                            const uint32_t co = (uint32_t)((c0 + 8 * g8) >> 3) * 128u;
+                            stmatrix2(row0 + co, pack2<F16>(o[0], o[1]), pack2<F16>(o[2], o[3]));
+                            stmatrix2(row1 + co, pack2<F16>(o1[0], o1[1]), pack2<F16>(o1[2], o1[3]));
                         }
                     }
                 } else if (pt == 0) {
-                    // ---- colour output (sigmoid) -> record ----
+                    // ---- colour output (sigmoid) -> the records' colour: lane i of quarter q is
+                    // sample 16q + i of the second tile (i < 16) or 16q + i - 16 of the first ----
                     float x0[16];
                     tmem_ld16(tmem + lane_addr, x0);
                     tmem_wait_ld();
-                    const int64_t g = tile * kTileS + s;
-                    if (is_val && g < total) {
-                        const float t = rec_t, dl = rec_dl;
-                        float4* R4 = reinterpret_cast<float4*>(p.rec + g);
-                        const float cr = __fdividef(1.0f, 1.0f + __expf(-(x0[0] + bias[0])));
-                        const float cg = __fdividef(1.0f, 1.0f + __expf(-(x0[1] + bias[1])));
-                        const float cb = __fdividef(1.0f, 1.0f + __expf(-(x0[2] + bias[2])));
-                        R4[0] = make_float4(f_out, dd_out, t, dl);
-                        R4[1] = make_float4(cr, cg, cb, gn_out);
-                        R4[2] = make_float4(nrm[0], nrm[1], nrm[2], 0.0f);
+                    const int64_t g = (2 * pr + (lane < 16 ? 1 : 0)) * kTileS + 16 * q + (lane & 15);
+                    if (g < total) {
+                        float* R = reinterpret_cast<float*>(p.rec + g);
+                        R[4] = __fdividef(1.0f, 1.0f + __expf(-(x0[0] + bias[0])));
+                        R[5] = __fdividef(1.0f, 1.0f + __expf(-(x0[1] + bias[1])));
+                        R[6] = __fdividef(1.0f, 1.0f + __expf(-(x0[2] + bias[2])));
                     }
                 }
                 tc_fence_before();
@@ -744,16 +850,17 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                     fence_proxy_async();
                     epi_arrive(bar_a);
                 }
-                // the next tile's table, while the colour layers' MMAs run: every warp
-                // has left the SDF output layer (the last reader of this tile's table)
+                // the next pair's first table, while the colour layers' MMAs run: every warp
+                // has left the second tile's SDF output layer (the last reader of its table)
                 // once colour layer 0's accumulator is complete
-                if (L == LS && tile + gridDim.x < n_tiles && !build_table(tile + gridDim.x)) {
+                if (L == LS && pr + gridDim.x < n_pairs && !build_table(2 * (pr + gridDim.x), false)) {
                     ok = false;
                     break;
                 }
             }
         }
         if (!ok) set_status(p.status, TSDFS_DEV_TIMEOUT);
+        if (stasher) bulk_wait();
     }
     tc_fence_before();
     __syncthreads();
@@ -1178,8 +1285,10 @@ int launch_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t tiles = (max_samples + kTileS - 1) / kTileS;
-    const unsigned blocks = (unsigned)(tiles < sms ? (tiles < 1 ? 1 : tiles) : sms);
+    const int64_t pairs = ((max_samples + kTileS - 1) / kTileS + 1) / 2;
+    int64_t blocks = pairs < sms ? pairs : sms;
+    if (blocks > kPairCtas) blocks = kPairCtas;
+    if (blocks < 1) blocks = 1;
     k_mlp_tc<ARCH, F16><<<(unsigned)blocks, kThreadsF, smem, st>>>(p);
     return cuda_check(cudaGetLastError(), "mlp_tc launch");
 }
