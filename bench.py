@@ -45,18 +45,19 @@ WORKLOAD = WORKLOADS["view"]
 # over the 10 timed launches of `bench.py --only-main --no-graph --steps 10 --warmup 3` (room views 0-9,
 # network-fused grid, fp16 operands) in one ncu capture; reported only for that
 # configuration and while the kernel sources hash to the ones it was captured on
-MLP_TC_TRAFFIC = {"sha256": "adf57877f79074d1788d2a28338610e4a1290b935768150cd54f8a61b2abaad9", "bytes_per_launch": 255608986,
+MLP_TC_TRAFFIC = {"sha256": "32324dd3d33174774e67c98856819a48977256e2d4d8011860be0a1fde76bb43", "bytes_per_launch": 263092864,
                   "profile": "profiles/k_mlp_tc_room_view_traffic.md"}
 # the same for k_ray_bounds (the march of Alg. 1) on the same ten timed views
 MARCH_TRAFFIC = {"sha256": "c4307e3a56049f67dc00d5274645fbd858f05161b8c533815f880fbb3a07392b", "bytes_per_launch": 9989350,
                  "profile": "profiles/k_ray_bounds_room_view_traffic.md"}
 ALGO_FLOP_PER_SAMPLE = 2.25e6   # SDF fwd + minimal reverse-mode grad + colour, 8x256 / 4x256 networks
 # what the tensor-core kernels issue per sample (value + 3 tangent rows through the SDF layers):
-# serial, 64-sample tiles: 4 rows per sample through SDF layers 0-6, the folded output layer's
-# value column (N = 16), M = 128 colour MMAs with 64 live rows (the folded first colour layer
-# with K = 256 + 48); pipelined, 32-sample tiles: 4 rows per sample through both networks
-# (M = 128 colour MMAs with 32 live rows), the SDF MMAs twice with split operands
-EXEC_FLOP_PER_SAMPLE = {"serial": 4.33e6, "pipelined": 5.93e6, "pipelined-split": 9.63e6}
+# serial, 64-sample tiles in pairs: 4 rows per sample through SDF layers 0-6 and the folded
+# output layer's value column (N = 16), one row per sample through the colour layers (M = 128
+# over both tiles of a pair; the folded first colour layer with K = 256 + 48); pipelined,
+# 32-sample tiles: 4 rows per sample through both networks (M = 128 colour MMAs with 32 live
+# rows), the SDF MMAs twice with split operands
+EXEC_FLOP_PER_SAMPLE = {"serial": 3.77e6, "pipelined": 5.93e6, "pipelined-split": 9.63e6}
 N_VIEWS_TIMED = 10   # views cycled by the timed steps (4 for the panorama workload)
 QUALITY_PIXELS = 4096          # seeded pixels spread over every timed view (synth.quality_pixels)
 QUALITY_PIXELS_LIVE = 1024     # when the dense reference is rendered during the run (panorama workload)

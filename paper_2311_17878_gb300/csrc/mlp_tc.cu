@@ -12,7 +12,13 @@
 // the epilogue in the no-swizzle K-major core-matrix layout; weights are
 // pre-packed in the same layout (tsdfs_pack_mlp) and streamed chunk by chunk
 // (kKChunk columns of K) with 1-D bulk TMA copies through a kStages-deep ring.
-// The colour network reuses acc0 with the value rows only.  The full kernel runs the
+// The full kernel runs tiles in pairs: the SDF layers of the first tile, then of the second,
+// then the colour layers once for both on acc0 (M = 128 rows, all live): the second tile's
+// samples in the value-row positions, the first tile's in the d/dx-row positions, which hold
+// nothing the colour layers need.  Between the two SDF passes one epilogue thread parks the
+// first tile's last SDF input value rows (h, in A0) and its folded colour input extras (in A1)
+// in global memory with bulk copies, and brings them back into the d/dx-row groups once the
+// second tile's SDF MMAs are done.  The full kernel runs the
 // folded tables of tc_common.cuh (TcArch<ARCH, true>): the SDF output layer computes only
 // net_0 (N = 16 MMAs on both accumulators, for f and grad f), and the first colour layer
 // multiplies the last hidden SDF activation h, still in A0 as that layer's input, by the
