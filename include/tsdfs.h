@@ -13,12 +13,10 @@
  *    comment says "host".  The caller owns every buffer; the library
  *    allocates and frees nothing itself (no cudaMalloc / cudaFree in it; the
  *    layer-major backward's first call on a device creates a cuBLAS handle,
- *    whose state cuBLAS allocates).  Its fixed device-side scratch is static
- *    module memory: the offsets scan's partial sums of the no-allocation bounds
- *    call and the tensor-core network kernel's parking space for the first
- *    tile of each pair (256 CTAs x 38 KB, about 10 MB); concurrent calls on
- *    different streams of one device must therefore not run the tensor-core
- *    network kernel at the same time.
+ *    whose state cuBLAS allocates).  The render workspaces (render_rays,
+ *    render_rays_hier, render_rays_hier_bounded) include about 10 MB for the
+ *    tensor-core network kernel, which parks the first tile of each pair of
+ *    64-sample tiles there (256 CTAs x 38 KB).
  *  - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL = the
  *    legacy default stream); the calls that synchronise say so (the autotuners,
  *    the layer-major backward and training forward, which read the sample

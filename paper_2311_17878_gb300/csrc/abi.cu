@@ -186,7 +186,8 @@ int launch_bounded_fine(const float* fcoarse, const int32_t* offsets, const floa
 int grid_check(const tsdfs_grid* g);
 int mlp_tc_available(int arch);
 int launch_mlp_full_tc(const tsdfs_mlp* mlp, const SampleSource& src, SampleRec* rec, int64_t max_samples,
-                       cudaStream_t st);
+                       uint8_t* stash, cudaStream_t st);
+size_t mlp_tc_stash_bytes();
 int launch_mlp_value_tc(const tsdfs_mlp* mlp, const SampleSource& src, float* f_out, cudaStream_t st);
 int launch_mlp_pipe(const tsdfs_mlp* mlp, const SampleSource& src, SampleRec* rec, int64_t max_samples,
                     cudaStream_t st);
@@ -233,15 +234,17 @@ static NetParams net_params(const tsdfs_mlp* m) {
     return np;
 }
 
+// the network evaluation of every render path; `stash`: the serial tensor-core kernel's parking
+// space in the caller's workspace (mlp_tc_stash_bytes(), 256-byte aligned)
 static int run_full_mlp(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64_t max_samples,
-                        cudaStream_t st) {
+                        uint8_t* stash, cudaStream_t st) {
     if (m->precision != TSDFS_PREC_F32) {
         if (netkernel_of(m->precision) == TSDFS_NETKERNEL_PIPELINED) {
             ProfScope ps("mlp_pipe", st);
             return launch_mlp_pipe(m, src, rec, max_samples, st);
         }
         ProfScope ps("mlp_tc", st);
-        return launch_mlp_full_tc(m, src, rec, max_samples, st);
+        return launch_mlp_full_tc(m, src, rec, max_samples, stash, st);
     }
     ProfScope ps("mlp_simt", st);
     const NetParams np = net_params(m);
@@ -333,12 +336,14 @@ extern "C" int64_t tsdfs_rgb_param_count(int32_t arch) {
                                    : (arch == TSDFS_ARCH_ROOM ? rgb_param_count<TSDFS_ARCH_ROOM>() : -1);
 }
 
-// render workspace: the per-sample records, then the ray index of every sample
+// render workspace: the per-sample records, then the ray index of every sample, then the
+// tensor-core network kernel's parking space
 extern "C" size_t tsdfs_render_workspace_size(const tsdfs_mlp* mlp, int64_t n_rays, int64_t max_samples) {
     (void)mlp;
     (void)n_rays;
     if (max_samples < 0) return 0;
-    return align256((size_t)max_samples * sizeof(SampleRec)) + align256((size_t)max_samples * sizeof(int32_t)) + 256;
+    return align256((size_t)max_samples * sizeof(SampleRec)) + align256((size_t)max_samples * sizeof(int32_t)) +
+           align256(mlp_tc_stash_bytes()) + 256;
 }
 
 namespace tsdfs {
@@ -370,6 +375,8 @@ extern "C" int render_rays(const tsdfs_mlp* mlp, const float* ray_o, const float
     SampleRec* rec = reinterpret_cast<SampleRec*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
     int32_t* sample_ray = reinterpret_cast<int32_t*>(reinterpret_cast<uintptr_t>(rec) +
                                                      align256((size_t)max_samples * sizeof(SampleRec)));
+    uint8_t* stash = reinterpret_cast<uint8_t*>(reinterpret_cast<uintptr_t>(sample_ray) +
+                                                align256((size_t)max_samples * sizeof(int32_t)));
     SampleSource src{};
     src.mode = kUniform;
     src.ray_o = ray_o;
@@ -388,7 +395,7 @@ extern "C" int render_rays(const tsdfs_mlp* mlp, const float* ray_o, const float
             if (rc) return rc;
             src.sample_ray = sample_ray;
         }
-        rc = run_full_mlp(mlp, src, rec, max_samples, st);
+        rc = run_full_mlp(mlp, src, rec, max_samples, stash, st);
         if (rc) return rc;
     }
     ProfScope ps("composite", st);
@@ -452,6 +459,7 @@ struct HierWs {
     float *t0, *te, *tc, *dc, *fc, *tf, *df;
     uint8_t* status;
     SampleRec* rec;
+    uint8_t* stash;
     size_t bytes;
 };
 
@@ -465,6 +473,7 @@ static HierWs hier_layout(void* base, int64_t n, int n_c = 64, int n_f = 32) {
     };
     const size_t n_h = (size_t)(n_c + n_f);
     w.rec = reinterpret_cast<SampleRec*>(take((size_t)n * n_h * sizeof(SampleRec)));
+    w.stash = reinterpret_cast<uint8_t*>(take(mlp_tc_stash_bytes()));
     w.t0 = reinterpret_cast<float*>(take((size_t)n * 4));
     w.te = reinterpret_cast<float*>(take((size_t)n * 4));
     w.tc = reinterpret_cast<float*>(take((size_t)n * n_c * 4));
@@ -539,7 +548,7 @@ extern "C" int render_rays_hier(const tsdfs_mlp* mlp, const tsdfs_grid* grid, co
     fs.per_ray = n_h;
     fs.total_host = n_rays * n_h;
     fs.capacity = n_rays * n_h;
-    rc = run_full_mlp(mlp, fs, w.rec, n_rays * n_h, st);
+    rc = run_full_mlp(mlp, fs, w.rec, n_rays * n_h, w.stash, st);
     if (rc) return rc;
     ProfScope ps("composite", st);
     return launch_composite(w.rec, nullptr, n_h, w.status, n_rays, nullptr, n_rays * n_h, opacity_of(mlp),
@@ -559,6 +568,7 @@ struct BoundedHierWs {
     int32_t *ray_c, *n2, *off2, *sums, *ray2;
     float *fc, *t2, *d2;
     SampleRec* rec;
+    uint8_t* stash;
     size_t bytes;
 };
 
@@ -571,6 +581,7 @@ static BoundedHierWs bounded_hier_layout(void* base, int64_t n, int64_t max_coar
         return q;
     };
     w.rec = reinterpret_cast<SampleRec*>(take((size_t)cap2 * sizeof(SampleRec)));
+    w.stash = reinterpret_cast<uint8_t*>(take(mlp_tc_stash_bytes()));
     w.ray_c = reinterpret_cast<int32_t*>(take((size_t)max_coarse * 4));
     w.fc = reinterpret_cast<float*>(take((size_t)max_coarse * 4));
     w.n2 = reinterpret_cast<int32_t*>(take((size_t)n * 4));
@@ -661,7 +672,7 @@ extern "C" int render_rays_hier_bounded(const tsdfs_mlp* mlp, const float* ray_o
     fs.total_dev = w.off2 + n_rays;
     fs.capacity = cap2;
     if (cap2 > 0) {
-        rc = run_full_mlp(mlp, fs, w.rec, cap2, st);
+        rc = run_full_mlp(mlp, fs, w.rec, cap2, w.stash, st);
         if (rc) return rc;
     }
     ProfScope ps("composite", st);

@@ -141,13 +141,12 @@ constexpr uint32_t kRecPar = 1u << 10;       // parity of the slot's use within 
 constexpr uint32_t kRecFlip = 1u << 11;      // the slot's uses per pair of tiles are odd
 constexpr uint32_t kRecRestore = 1u << 12;   // first colour chunk: the pair's first tile is back in place
 
-// most CTAs of one launch of the full kernel, and the global parking space of each: the first
-// tile of a pair keeps its last SDF layer's input value rows and its folded colour input
-// extras there while the second tile's SDF layers use the operand regions (the room networks
-// need the most: 4 x 2 x (4096 + 768) bytes)
+// most CTAs of one launch of the full kernel, and the parking space of each in the caller's
+// workspace: the first tile of a pair keeps its last SDF layer's input value rows and its
+// folded colour input extras there while the second tile's SDF layers use the operand
+// regions (the room networks need the most: 4 x 2 x (4096 + 768) bytes)
 constexpr int kPairCtas = 256;
 constexpr uint32_t kStashMax = 4u * 2u * (4096u + 768u);
-__device__ __align__(128) uint8_t g_pair_stash[(size_t)kPairCtas * kStashMax];
 
 // the value kernel's record of one weight chunk (written once per CTA): packed offset and size
 // for its producers; for the MMA warp the descriptors of the chunk's first K step, the
@@ -166,6 +165,7 @@ struct TcParams {
     float inv_scale, scale, beta;
     SampleSource src;
     SampleRec* rec;
+    uint8_t* stash;  // the full kernel's parking space: kStashMax bytes per CTA, 16-byte aligned
     uint32_t* status;
     uint32_t spin;   // polls of a bounded wait before it gives up
     int withhold;    // test-only: weight chunk of the first tile whose copy is never issued (-1: none)
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
         // in global memory with bulk copies, and brings it back into the tangent-row groups of
         // the same regions once the second tile's SDF MMAs are done
         const bool stasher = et == 4 * 32;
-        uint8_t* stash = g_pair_stash + (size_t)blockIdx.x * kStashMax;
+        uint8_t* stash = p.stash + (size_t)blockIdx.x * kStashMax;
         auto build_table = [&](int64_t tile, bool between) -> bool {
                 if (between) {
                     // every warp is past the first tile's SDF output layer (the last reader of
@@ -1264,7 +1264,8 @@ __global__ void k_pack_fold(const float* __restrict__ sdf_w, const float* __rest
 }
 
 template <int ARCH, bool F16>
-int launch_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64_t max_samples, cudaStream_t st) {
+int launch_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64_t max_samples, uint8_t* stash,
+              cudaStream_t st) {
     using TA = TcFull<ARCH>;
     constexpr size_t smem = TA::full_smem_bytes();
     static_assert(smem <= 232448, "k_mlp_tc shared memory exceeds 227 KB");
@@ -1285,6 +1286,7 @@ int launch_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64
     p.beta = m->beta;
     p.src = src;
     p.rec = rec;
+    p.stash = stash;
     p.status = device_status_word();
     p.spin = test_spin_limit(kMaxSpin);
     p.withhold = test_withhold_chunk();
@@ -1303,15 +1305,19 @@ int launch_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64
 
 int mlp_tc_available(int arch) { return arch == TSDFS_ARCH_TINY || arch == TSDFS_ARCH_ROOM; }
 
+size_t mlp_tc_stash_bytes() { return (size_t)kPairCtas * kStashMax; }
+
 int launch_mlp_full_tc(const tsdfs_mlp* m, const SampleSource& src, SampleRec* rec, int64_t max_samples,
-                       cudaStream_t st) {
+                       uint8_t* stash, cudaStream_t st) {
     if ((reinterpret_cast<uintptr_t>(m->packed) & 15u) != 0) return fail(TSDFS_E_INVALID, "packed weights must be 16-byte aligned");
+    if (!stash || (reinterpret_cast<uintptr_t>(stash) & 15u) != 0)
+        return fail(TSDFS_E_INVALID, "the network kernel's parking space must be 16-byte aligned workspace");
     const bool f16 = m->precision == TSDFS_PREC_F16;
     if (m->arch == TSDFS_ARCH_TINY)
-        return f16 ? launch_tc<TSDFS_ARCH_TINY, true>(m, src, rec, max_samples, st)
-                   : launch_tc<TSDFS_ARCH_TINY, false>(m, src, rec, max_samples, st);
-    return f16 ? launch_tc<TSDFS_ARCH_ROOM, true>(m, src, rec, max_samples, st)
-               : launch_tc<TSDFS_ARCH_ROOM, false>(m, src, rec, max_samples, st);
+        return f16 ? launch_tc<TSDFS_ARCH_TINY, true>(m, src, rec, max_samples, stash, st)
+                   : launch_tc<TSDFS_ARCH_TINY, false>(m, src, rec, max_samples, stash, st);
+    return f16 ? launch_tc<TSDFS_ARCH_ROOM, true>(m, src, rec, max_samples, stash, st)
+               : launch_tc<TSDFS_ARCH_ROOM, false>(m, src, rec, max_samples, stash, st);
 }
 
 int launch_mlp_value_tc(const tsdfs_mlp* m, const SampleSource& src, float* f_out, cudaStream_t st) {
