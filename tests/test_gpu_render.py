@@ -253,6 +253,48 @@ def _errors(got, ref):
     return er, ed
 
 
+def test_render_f16_tile_pairs_several_per_cta_odd_count():
+    """The tensor-core kernel runs 64-sample tiles in pairs (the colour layers once for both,
+    the first tile parked in the render workspace between the SDF passes).  609 tiles: 305
+    pairs, so the CTAs take two or three pairs each and the last pair has one tile; sampled
+    rays from the whole range (its first and last live rays among them) against the oracle
+    within the 16-bit bars."""
+    wl = synth.room_workload(with_views=False)
+    V = synth.analytic_tsdf_torch(wl.scene, wl.grid, device="cuda").cpu().numpy()
+    o, d = synth.room_heldout_rays(1)
+    idx = synth.sub_sample(len(o), 1400, seed=31)
+    o, d = o[idx], d[idx]
+    b = dict(cgrid.ray_bounds(wl.grid, V, o, d, wl.bounds, "f32"))
+    live = np.flatnonzero(b["status"] != 0)
+    target = 64 * 608 + 13          # 609 tiles of 64 samples, the last one ragged
+    rng = np.random.default_rng(7)
+    n = np.zeros(len(o), np.int64)
+    n[live] = rng.integers(1, 65, len(live))
+    # bring the total to the target one sample at a time over the live rays, within [1, 96]
+    diff = target - int(n.sum())
+    step = 1 if diff > 0 else -1
+    i = 0
+    while diff != 0:
+        r = live[i % len(live)]
+        if 1 <= n[r] + step <= 96:
+            n[r] += step
+            diff -= step
+        i += 1
+    assert int(n.sum()) == target
+    b["n"] = n.astype(np.int32)
+    spec = synth.scene_mlp("room")
+    got = gpu_render(spec, o, d, b, precision=T.TSDFS_PREC_F16)
+    rc, bits = T.tsdfs_sync_status()
+    assert rc == 0, bits
+    sel = np.unique(np.concatenate([live[:8], live[-8:], live[synth.sub_sample(len(live), 160, seed=32)]]))
+    bs = {k: v[sel] for k, v in b.items()}
+    ref, _ = oracle_render(spec, o[sel], d[sel], bs)
+    got_s = {k: v[sel] for k, v in got.items()}
+    er, ed = _errors(got_s, ref)
+    print(f"pairs f16: rgb p99 {np.percentile(er, 99):.2e} max {er.max():.2e}; depth max {ed.max() if len(ed) else 0:.2e}")
+    compare(got_s, ref, depth_rel=DEPTH_REL_BF16)
+
+
 @pytest.mark.parametrize("scene", ["tiny", "room"])
 def test_render_f16_operands_match_oracle(scene):
     """tcgen05 path with fp16 operands, fp32 accumulation: within the stated
