@@ -193,15 +193,10 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
     const uint32_t bar_drain = smem_u32(bars + 2 * kSlots + 2), bar_tab = smem_u32(bars + 2 * kSlots + 3);
     const uint32_t bar_rest = smem_u32(bars + 2 * kSlots + 4);
     static_assert(TA::stash_bytes() <= kStashMax, "pair stash size");
-    // weight slot of chunk c of layer L: SDF chunks alternate over the ring stages, colour
-    // chunks cycle over the ring stages and the free part of A1; and the slot's shared address
+    // weight slots: the ring stages, and during the colour layers the free part of A1; a slot's
+    // shared address
     constexpr int kColSlots = kA1Slots ? kStages + TA::a1_slots() : kStages;
     static_assert(kColSlots <= kSlots, "weight slot count");
-    auto slot_of = [&](int L, int c) -> uint32_t {
-        const int j = TA::chunk_index(L, c);
-        if (L < LS) return (uint32_t)(j % kStages);
-        return (uint32_t)((j - TA::sdf_chunks()) % kColSlots);
-    };
     auto slot_addr = [&](uint32_t sl) -> uint32_t {
         return sl < (uint32_t)kStages ? smem_u32(stage_base + sl * kStage)
                                       : smem_u32(A1) + TA::a1_spill() + (sl - kStages) * (uint32_t)TA::max_rgb_chunk_bytes();
