@@ -801,36 +801,39 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                 boff += ly.Np;
                 const bool last = L == NL - 1;
                 if (!last) {
-                    // ---- hidden colour layer (ReLU), all 128 rows: 16x256b fragments at lanes
-                    // 32q (samples 16q + fs, 16q + 8 + fs of the second tile) and 32q + 16 (the
-                    // same of the first) ----
+                    // ---- hidden colour layer (ReLU), all 128 rows, one row per thread (TMEM lane
+                    // 32q + lane is operand row 32q + lane): 16 columns a load, the biases read
+                    // once per 16 columns for the whole warp ----
                     const int Kn = TA::layer(L + 1).Kp;
-                    const uint32_t row0 = smem_u32(A0) + a_off(32 * q + (lane & 15), 0, Kn);
-                    const uint32_t row1 = smem_u32(A0) + a_off(32 * q + 16 + (lane & 15), 0, Kn);
+                    const int r_own = 32 * q + lane;
                     for (int c0 = part_lo(Kn, pt, kPartsF); c0 < part_hi(Kn, pt, kPartsF); c0 += 16) {
-                        float v[8], w[8];
+                        float v[16];
                         if (c0 < ly.Np) {
-                            tmem_ld16x256_x2(t_v + c0, v);
-                            tmem_ld16x256_x2(t_x + c0, w);
-                            tmem_wait_ld();
+                            tmem_ld16(tmem + lane_addr + c0, v);
+                            tmem_wait_ld16(v);
                         } else {
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) v[e] = w[e] = 0.0f;
+                            for (int e = 0; e < 16; ++e) v[e] = 0.0f;
                         }
+                        if (c0 + 16 <= ly.N) {
+                            const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
 #pragma unroll
-                        for (int g8 = 0; g8 < 2; ++g8) {
-                            float o[4], o1[4];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int col = c0 + 8 * g8 + fc + (e & 1);
-                                const float bc = col < ly.N ? bias[col] : 0.0f;
-                                o[e] = col < ly.N ? fmaxf(v[4 * g8 + e] + bc, 0.0f) : 0.0f;
-                                o1[e] = col < ly.N ? fmaxf(w[4 * g8 + e] + bc, 0.0f) : 0.0f;
+                            for (int j = 0; j < 4; ++j) {
+                                const float4 b = b4[j];
+                                v[4 * j] = fmaxf(v[4 * j] + b.x, 0.0f);
+                                v[4 * j + 1] = fmaxf(v[4 * j + 1] + b.y, 0.0f);
+                                v[4 * j + 2] = fmaxf(v[4 * j + 2] + b.z, 0.0f);
+                                v[4 * j + 3] = fmaxf(v[4 * j + 3] + b.w, 0.0f);
                             }
-                            const uint32_t co = (uint32_t)((c0 + 8 * g8) >> 3) * 128u;
-                            stmatrix2(row0 + co, pack2<F16>(o[0], o[1]), pack2<F16>(o[2], o[3]));
-                            stmatrix2(row1 + co, pack2<F16>(o1[0], o1[1]), pack2<F16>(o1[2], o1[3]));
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) {
+                                const int col = c0 + e;
+                                v[e] = col < ly.N ? fmaxf(v[e] + bias[col], 0.0f) : 0.0f;
+                            }
                         }
+                        st_row8<F16>(A0, r_own, c0, Kn, v);
+                        st_row8<F16>(A0, r_own, c0 + 8, Kn, v + 8);
                     }
                 } else if (pt == 0) {
                     // ---- colour output (sigmoid) -> the records' colour: lane i of quarter q is
