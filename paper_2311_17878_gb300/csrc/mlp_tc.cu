@@ -424,6 +424,38 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
         constexpr float kInvSqrt2 = 0.70710678118654752f;
         const SoftplusH2 spk = softplus_h2_consts(half_beta, inv_beta);
         const __half2 inv_sqrt2_h2 = __float2half2_rn(kInvSqrt2);
+        // eight encoding columns, entries EN0 .. EN0 + 7 of the SDF input encoding (zero past
+        // its end) times scl, one row per thread: A row r is sample s's value row (lanes 0-15)
+        // or its d/dx row (lanes 16-31) in A0, its d/dy or d/dz row in A1; EN0 is a
+        // compile-time constant, so each column's decode folds away
+        auto enc_rows8 = [&](auto en0_tag, int c8, int Kp, float scl) {
+            constexpr int EN0 = decltype(en0_tag)::value;
+            const float* sx = s_x + s * 8;
+            const float* sp = s_pe + s * A::kPeSdf * 6;
+            float v0[8], v1[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int en = EN0 + k;
+                float val = 0.0f, der = 0.0f;
+                int b = -1;
+                if (en < 3) {
+                    b = en;
+                    val = sx[en] * scl;
+                    der = scl;
+                } else if (en < A::kEnc) {
+                    const int qq = en - 3, oct = qq / 6, part = (qq % 6) / 3;
+                    b = qq % 3;
+                    const float sn = sp[(oct * 3 + b) * 2], cs = sp[(oct * 3 + b) * 2 + 1];
+                    const float f = (float)(1 << oct) * scl;
+                    val = (part == 0 ? sn : cs) * scl;
+                    der = part == 0 ? f * cs : -f * sn;
+                }
+                v0[k] = is_val ? val : (b == 0 ? der : 0.0f);
+                v1[k] = is_val ? (b == 1 ? der : 0.0f) : (b == 2 ? der : 0.0f);
+            }
+            st_row8<F16>(A0, r, c8, Kp, v0);
+            st_row8<F16>(A1, r, c8, Kp, v1);
+        };
         uint32_t lc = 0, tab_ph = 0;
         bool ok = true;
         // per-tile sample table (coordinates, direction, t, delta, sin / cos of the encodings):
@@ -532,31 +564,14 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                 }
                 // (the sample table of this tile was built before the loop, during the last
                 // pair's colour layers, or just now)
-                // ---- layer-0 input: encoding rows, stored as 16x256b-ordered stmatrix fragments ----
+                // ---- layer-0 input: the encoding rows, one row per thread ----
                 {
                     constexpr int Kp0 = TA::layer(0).Kp;
-                    const int sa = 16 * q + fs, sb = sa + 8;
-                    const float* xa = s_x + sa * 8;
-                    const float* xb = s_x + sb * 8;
-                    const float* pa = s_pe + sa * A::kPeSdf * 6;
-                    const float* pb = s_pe + sb * A::kPeSdf * 6;
-                    const uint32_t row0 = smem_u32(A0) + a_off(32 * q + lane, 0, Kp0);
-                    const uint32_t row1 = smem_u32(A1) + a_off(32 * q + lane, 0, Kp0);
-                    for (int c8 = part_lo(Kp0, pt, kPartsF); c8 < part_hi(Kp0, pt, kPartsF); c8 += 8) {
-                        float v[4][4];   // [component][(sample a, col 0), (a, 1), (b, 0), (b, 1)]
-    #pragma unroll
-                        for (int cp = 0; cp < 4; ++cp)
-    #pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int j = c8 + fc + (e & 1);
-                                v[cp][e] = j < A::kEnc ? enc_tab((e & 2) ? xb : xa, (e & 2) ? pb : pa, A::kPeSdf, j, cp) : 0.0f;
-                            }
-                        const uint32_t co = (uint32_t)(c8 >> 3) * 128u;
-                        stmatrix4(row0 + co, pack2<F16>(v[0][0], v[0][1]), pack2<F16>(v[0][2], v[0][3]),
-                                  pack2<F16>(v[1][0], v[1][1]), pack2<F16>(v[1][2], v[1][3]));
-                        stmatrix4(row1 + co, pack2<F16>(v[2][0], v[2][1]), pack2<F16>(v[2][2], v[2][3]),
-                                  pack2<F16>(v[3][0], v[3][1]), pack2<F16>(v[3][2], v[3][3]));
-                    }
+                    const int c_lo = part_lo(Kp0, pt, kPartsF), c_hi = part_hi(Kp0, pt, kPartsF);
+                    static_for<0, Kp0 / 8>([&](auto g) {
+                        constexpr int c8 = 8 * decltype(g)::value;
+                        if (c8 >= c_lo && c8 < c_hi) enc_rows8(std::integral_constant<int, c8>{}, c8, Kp0, 1.0f);
+                    });
                 }
                 fence_proxy_async();
                 epi_arrive(bar_a);
@@ -673,7 +688,8 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                         const float* sxb = sxa + 8 * 8;
                         const float* spa = s_pe + (16 * q + fs) * A::kPeSdf * 6;
                         const float* spb = spa + 8 * A::kPeSdf * 6;
-                        for (int c8 = c_fa + 8 * pt; c8 < Kn; c8 += 8 * kPartsF) {
+                        const int c_tl = Kn < ly.Np ? Kn : ly.Np;   // beyond: encoding columns only
+                        for (int c8 = c_fa + 8 * pt; c8 < c_tl; c8 += 8 * kPartsF) {
                             float d[16];   // [value(4) | d/dx(4) | d/dy(4) | d/dz(4)], as ld8
     #pragma unroll
                             for (int j = 0; j < 16; ++j) d[j] = 0.0f;
@@ -730,6 +746,20 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                                       pack2<F16>(xv[0], xv[1]), pack2<F16>(xv[2], xv[3]));
                             stmatrix4(row1 + co, pack2<F16>(yv[0], yv[1]), pack2<F16>(yv[2], yv[3]),
                                       pack2<F16>(zv[0], zv[1]), pack2<F16>(zv[2], zv[3]));
+                        }
+                        // the skip input's 8-column groups past the hidden units' padded width:
+                        // gamma(x~) / sqrt(2) only, one row per thread, the same round robin
+                        if constexpr (A::kSkip > 0) {
+                            if (ly.idx + 1 == A::kSkip) {
+                                constexpr int kNs = TA::layer(A::kSkip - 1).N, kNps = TA::layer(A::kSkip - 1).Np;
+                                constexpr int kKs = TA::layer(A::kSkip).Kp;
+                                constexpr int kFa = (kNs / 16) * 16;
+                                static_for<kNps / 8, kKs / 8>([&](auto g) {
+                                    constexpr int c8 = 8 * decltype(g)::value;
+                                    if (((c8 - kFa) / 8) % kPartsF == pt)
+                                        enc_rows8(std::integral_constant<int, c8 - kNs>{}, c8, kKs, kInvSqrt2);
+                                });
+                            }
                         }
                     } else if (pt == 0) {
                         // ---- SDF output layer, folded to its value column: f and grad f from column 0

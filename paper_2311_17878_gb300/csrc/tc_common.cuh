@@ -2,6 +2,8 @@
 // 16-bit weights and the PTX helpers (mbarriers, 1-D bulk copies, tcgen05 MMA /
 // TMEM loads, stmatrix, operand layout, activations).  Device code only.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace tsdfs {
@@ -356,6 +358,15 @@ __device__ __forceinline__ void softplus_slope_h2(float z0, float z1, const Soft
     h = __hadd2(__hmax2(z, k.zero), __hfma2(p, k.neg_inv_beta, k.ln2_inv_beta));
 }
 __device__ __forceinline__ uint32_t h2u(__half2 v) { return *reinterpret_cast<uint32_t*>(&v); }
+
+// f(std::integral_constant<int, I>{}) for I = B .. E - 1, expanded at compile time
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
 
 // positional encoding entry j of coordinate vector xt, and its derivative along axis a
 __device__ __forceinline__ float enc_val(const float* xt, int j, int pe, int a, bool deriv) {
