@@ -846,24 +846,26 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_mlp_tc(TcParams p) {
                             for (int e = 0; e < 16; ++e) v[e] = 0.0f;
                         }
                         if (c0 + 16 <= ly.N) {
+                            // bias in FP32, then round to 16 bits and clamp both halves at once
                             const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
+                            uint32_t w[8];
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
                                 const float4 b = b4[j];
-                                v[4 * j] = fmaxf(v[4 * j] + b.x, 0.0f);
-                                v[4 * j + 1] = fmaxf(v[4 * j + 1] + b.y, 0.0f);
-                                v[4 * j + 2] = fmaxf(v[4 * j + 2] + b.z, 0.0f);
-                                v[4 * j + 3] = fmaxf(v[4 * j + 3] + b.w, 0.0f);
+                                w[2 * j] = relu2<F16>(pack2<F16>(v[4 * j] + b.x, v[4 * j + 1] + b.y));
+                                w[2 * j + 1] = relu2<F16>(pack2<F16>(v[4 * j + 2] + b.z, v[4 * j + 3] + b.w));
                             }
+                            *reinterpret_cast<uint4*>(A0 + a_off(r_own, c0, Kn)) = make_uint4(w[0], w[1], w[2], w[3]);
+                            *reinterpret_cast<uint4*>(A0 + a_off(r_own, c0 + 8, Kn)) = make_uint4(w[4], w[5], w[6], w[7]);
                         } else {
 #pragma unroll
                             for (int e = 0; e < 16; ++e) {
                                 const int col = c0 + e;
                                 v[e] = col < ly.N ? fmaxf(v[e] + bias[col], 0.0f) : 0.0f;
                             }
+                            st_row8<F16>(A0, r_own, c0, Kn, v);
+                            st_row8<F16>(A0, r_own, c0 + 8, Kn, v + 8);
                         }
-                        st_row8<F16>(A0, r_own, c0, Kn, v);
-                        st_row8<F16>(A0, r_own, c0 + 8, Kn, v + 8);
                     }
                 } else if (pt == 0) {
                     // ---- colour output (sigmoid) -> the records' colour: lane i of quarter q is

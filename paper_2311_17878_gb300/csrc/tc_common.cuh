@@ -285,6 +285,18 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
         return *reinterpret_cast<uint32_t*>(&h);
     }
 }
+// max(x, 0) on both 16-bit halves of a packed pair; rounding is monotonic and keeps 0, so
+// clamping after the rounding gives the value clamping before it would
+template <bool F16>
+__device__ __forceinline__ uint32_t relu2(uint32_t x) {
+    if constexpr (F16) {
+        __half2 h = __hmax2(*reinterpret_cast<__half2*>(&x), __float2half2_rn(0.0f));
+        return *reinterpret_cast<uint32_t*>(&h);
+    } else {
+        __nv_bfloat162 h = __hmax2(*reinterpret_cast<__nv_bfloat162*>(&x), __float2bfloat162_rn(0.0f));
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+}
 // store 8 consecutive columns (k0 multiple of 8) of row r
 template <bool F16>
 __device__ __forceinline__ void st_row8(uint8_t* base, int r, int k0, int Kp, const float* v) {
